@@ -1,0 +1,243 @@
+/*
+ * rb.h -- C ABI of the GB300 relative-binning (RB) likelihood library (librb).
+ *
+ * The library evaluates, for thousands of sampler walkers at once, the
+ * relative-binning approximation of the Gaussian gravitational-wave
+ * log-likelihood of arXiv:2404.11397 (Jim for binary neutron stars):
+ *
+ *   log L(theta) = sum_d [ <d_d|h_d(theta)> - <h_d(theta)|h_d(theta)>/2 ]      (Eq. 2, constant -<d|d>/2 dropped)
+ *   <a|b> = 4 Re int a(f) b*(f) / S_n(f) df                                    (Eq. 3, as a sum on the grid f_k = k/T)
+ *   r(f) = h(f; theta) / h(f; theta_ref) ~ r0(b) + r1(b) (f - f_m(b)) in bin b  (Eqs. 4-5, Sec. II.C)
+ *   <d|h> ~ Re sum_b [A0 r0* + A1 r1*],  <h|h> ~ sum_b [B0 |r0|^2 + 2 B1 Re(r0 r1*)]
+ *
+ * with TaylorF2 + tidal waveforms (Sec. II.B) projected onto 1-3 detectors.
+ * All compute runs in the library's own CUDA kernels for sm_103a; there is
+ * no CPU fallback.
+ *
+ * Conventions shared by all entry points
+ * --------------------------------------
+ * Parameter vector theta (13 doubles, this order; Table III of the paper):
+ *   0 Mc [Msun, detector-frame chirp mass]   1 q = m2/m1 in (0,1]
+ *   2 chi1  3 chi2 (aligned spins)            4 Lambda1  5 Lambda2
+ *   6 d_L [Mpc]  7 t_c [s, relative to the event]  8 phi_c  9 iota
+ *   10 psi  11 ra  12 dec  [rad]
+ * Gradients are with respect to these 13 entries (iota and dec, not cos iota
+ * or sin dec; that chain rule is the caller's).
+ * Unphysical walkers (q outside (0,1], Mc <= 0, d_L <= 0, any NaN/Inf) get
+ * log L = -inf and a zero gradient; no error is raised for them.
+ *
+ * Ownership: the caller owns every theta/output buffer; an rb_event_t owns
+ * its device memory until rb_event_free.  Batch calls are asynchronous and
+ * stream-ordered: outputs are valid once the given stream has been
+ * synchronised.  A NULL stream means the legacy default stream.
+ *
+ * Errors: every entry point returns an int status (RB_OK = 0 or a negative
+ * RB_E* code, RB_PENDING for a poll that is not done).  rb_last_error()
+ * returns a thread-local description of the most recent failure on the
+ * calling thread.  No C++ exception crosses the ABI.
+ */
+#ifndef RB_H_
+#define RB_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RB_API __attribute__((visibility("default")))
+#else
+#define RB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define RB_OK 0
+#define RB_PENDING 1        /* rb_poll: request not finished yet */
+#define RB_EINVAL (-1)      /* bad argument or descriptor */
+#define RB_ENOMEM (-2)      /* device or host allocation failed */
+#define RB_ECUDA (-3)       /* a CUDA call failed (detail in rb_last_error) */
+#define RB_ETIMEDOUT (-4)   /* rb_poll: timeout elapsed */
+#define RB_EBUSY (-5)       /* rb_submit: admission refused (queue full) */
+#define RB_ENOTFOUND (-6)   /* unknown ticket */
+#define RB_ECLOSED (-7)     /* server shut down */
+
+/* ---- evaluation modes ---------------------------------------------------- */
+#define RB_MIXED 0          /* phase in float-float (FP32 pairs), trig/ratio/contraction FP32, sums FP64 */
+#define RB_FP64 1           /* everything in native FP64 (comparison path) */
+#define RB_MIXED_F64PHASE 2 /* phase accumulated in native FP64, rest as RB_MIXED */
+
+#define RB_NPAR 13
+#define RB_MAX_DET 3
+
+typedef struct rb_event_s* rb_event_t;
+typedef struct rb_server_s* rb_server_t;
+
+/* One detector.  Site geometry: latitude and longitude [rad], elevation above
+ * the WGS-84 ellipsoid [m], x- and y-arm azimuths [rad, clockwise from North];
+ * arms have zero tilt.  data: complex128 strain on the grid, [n_freq][2]
+ * (re, im).  psd: one-sided S_n(f) on the grid, [n_freq].  Both are host
+ * pointers unless rb_event_desc.data_on_device is 1. */
+typedef struct {
+  double lat, lon, elev_m, xarm_az, yarm_az;
+  const double* data;
+  const double* psd;
+} rb_detector_desc;
+
+/* One event.  The grid is f_k = k / T for k = ceil(f_low T) .. floor(f_high T)
+ * (both ends included), n_freq points, delta f = 1/T.  n_bins in [1, n_freq-1].
+ * gmst: Greenwich sidereal angle of the event [rad].  theta_ref: fiducial
+ * parameters of the relative-binning scheme (Sec. II.C, "Reference
+ * parameters"). */
+typedef struct {
+  int32_t n_det;
+  int32_t n_bins;
+  rb_detector_desc det[RB_MAX_DET];
+  double T, f_low, f_high, gmst;
+  int32_t data_on_device;
+  int32_t reserved;
+  void* cuda_stream; /* cudaStream_t used for the build; NULL = default stream */
+  double theta_ref[RB_NPAR];
+} rb_event_desc;
+
+typedef struct {
+  int32_t n_det, n_bins;
+  int64_t kmin, n_freq;
+  double T, gmst;
+  double base_logl;       /* log L_RB(theta_ref) = sum_d Re sum_b A0 - B0/2 (FP64) */
+  size_t device_bytes;    /* device memory held by the event */
+} rb_event_info;
+
+/* Build an event: grid, bin edges, fiducial waveform h0 on the full grid,
+ * summary data A0, A1, B0, B1 per (detector, bin) in FP64, and the
+ * device-resident edge and bin tables used by the batch calls.
+ *
+ * Bin placement (Sec. II.C; Zackay et al. 2018): B+1 edges equally spaced in
+ * the PN phase bound 2 pi sum_g sgn(g) (f/f*_g)^g, g in {-5/3,-2/3,1,5/3,7/3},
+ * inverted by linear interpolation on the grid, snapped to the nearest grid
+ * point, then made strictly increasing.  Bin b holds grid points
+ * edges[b] <= k < edges[b+1]; the last bin also holds edges[B].
+ * Summary data: A0 = 4 df sum_b d conj(h0) / S, A1 = same times (f - f_m(b)),
+ * B0 = 4 df sum_b |h0|^2 / S, B1 = same times (f - f_m(b)), f_m = edge midpoint.
+ *
+ * The inputs are copied; the caller may free them after return (the call
+ * synchronises desc->cuda_stream).  Errors: RB_EINVAL (n_det not in 1..3,
+ * n_bins out of range, T or band invalid, NULL pointers, unphysical
+ * theta_ref), RB_ENOMEM, RB_ECUDA. */
+RB_API int rb_build_summary(const rb_event_desc* desc, rb_event_t* out);
+
+/* Release an event's device memory.  The caller must make sure no batch call
+ * using the event is still in flight.  NULL is accepted. */
+RB_API int rb_event_free(rb_event_t ev);
+
+/* Recompute an existing event in place for new data and/or a new fiducial
+ * point -- e.g. after a reference-parameter search (Sec. II.C, "Reference
+ * parameters") -- keeping its grid and bin edges: fiducial waveform h0 on the
+ * full grid, summary data, tables and log L(theta_ref).  theta_ref_host: new
+ * theta_ref [13] or NULL to keep it.  data[d] ([n_freq][2]) / psd[d]
+ * ([n_freq]) for d < n_det, or both NULL to reuse the event's resident copy;
+ * with data_on_device = 1 they are device pointers read in place (no copy,
+ * they must stay valid until the stream reaches the rebuild), otherwise host
+ * pointers copied into the event.  Asynchronous on `stream`, allocates
+ * nothing; batch calls ordered after it on the same stream see the new
+ * tables, and the caller must not run batches of this event concurrently on
+ * other streams.  Errors: RB_EINVAL (NULL event, only one of data/psd,
+ * unphysical theta_ref), RB_ECUDA. */
+RB_API int rb_event_rebuild(rb_event_t ev, const double* theta_ref_host, const double* const* data,
+                            const double* const* psd, int data_on_device, void* stream);
+
+RB_API int rb_event_get_info(rb_event_t ev, rb_event_info* info);
+
+/* Copy the event's FP64 summary data and bin edges to host buffers:
+ * A0, A1: [n_det][n_bins][2]; B0, B1: [n_det][n_bins]; edges: [n_bins+1]
+ * grid indices (0 .. n_freq-1).  Any pointer may be NULL.  Synchronous. */
+RB_API int rb_event_get_summary(rb_event_t ev, double* A0, double* A1, double* B0, double* B1, int64_t* edges);
+
+/* Batched RB log-likelihood.  theta_dev: device [W][13] row-major FP64;
+ * logl_dev: device [W] FP64.  mode: RB_MIXED, RB_FP64 or RB_MIXED_F64PHASE.
+ * Asynchronous on `stream` (cudaStream_t).  W = 0 is a no-op.
+ * Errors: RB_EINVAL (NULL event/pointers with W > 0, W < 0, bad mode),
+ * RB_ENOMEM (stream-ordered workspace allocation), RB_ECUDA. */
+RB_API int rb_loglike_batch(rb_event_t ev, const double* theta_dev, int64_t W, double* logl_dev, int mode,
+                     void* stream);
+
+/* Batched RB log-likelihood and its gradient with respect to the 13
+ * parameters (hand-written reverse sweep over bins and edges, then the chain
+ * rule through the per-walker set-up).  grad_dev: device [W][13] FP64.
+ * Same conventions and errors as rb_loglike_batch. */
+RB_API int rb_loglike_grad_batch(rb_event_t ev, const double* theta_dev, int64_t W, double* logl_dev, double* grad_dev,
+                          int mode, void* stream);
+
+/* End-to-end convenience form of rb_loglike_grad_batch for host buffers:
+ * copies theta_host [W][13] to the device, evaluates, copies logl_host [W]
+ * (and grad_host [W][13] unless NULL) back, and synchronises the stream.
+ * theta_host/logl_host/grad_host should be pinned for full copy bandwidth. */
+RB_API int rb_loglike_grad_host(rb_event_t ev, const double* theta_host, int64_t W, double* logl_host, double* grad_host,
+                         int mode, void* stream);
+
+/* TaylorF2 + tidal detector strain h_d(f; theta) (FP64) on the grid
+ * f_k = (kmin + k)/T, k = 0..n_freq-1, for one source: geom = {lat, lon,
+ * elev_m, xarm_az, yarm_az}, theta_host [13].  h_dev: device [n_freq][2].
+ * Asynchronous on `stream`.  Used to inject signals and as the fiducial
+ * waveform kernel of rb_build_summary.  Errors: RB_EINVAL, RB_ECUDA. */
+RB_API int rb_strain(const double* geom, double gmst, const double* theta_host, double T, int64_t kmin, int64_t n_freq,
+              double* h_dev, void* stream);
+
+/* ---- serving loop (continuous batching) ----------------------------------
+ * A server owns a scheduler thread, a set of CUDA streams ("slots") and
+ * pinned staging buffers.  Clients submit likelihood(+gradient) requests for
+ * resident events from any thread; requests that arrive while others are on
+ * the GPU are admitted as soon as a slot and enough of the device-memory
+ * budget are free, and run concurrently on separate streams.  Each slot
+ * launch is a CUDA-graph replay of the captured (set-up, likelihood) pair for
+ * the request's event and walker-count bucket.  Results are returned by
+ * rb_poll; each is identical to the same request evaluated alone. */
+typedef struct {
+  size_t hbm_budget_bytes;  /* device bytes the in-flight requests may hold (0 = 1 GiB) */
+  int32_t max_slots;        /* concurrent requests on the GPU (streams), 1..64 (0 = 8) */
+  int32_t max_queue;        /* pending requests before rb_submit returns RB_EBUSY (0 = 4096) */
+  int32_t use_graphs;       /* 1 = replay captured CUDA graphs (default), 0 = plain launches */
+  int32_t mode;             /* RB_MIXED / RB_FP64 / RB_MIXED_F64PHASE */
+  int64_t max_walkers;      /* largest request accepted (0 = 65536) */
+} rb_server_opts;
+
+typedef struct {
+  uint64_t submitted, completed, rejected, graph_launches, plain_launches, graphs_captured;
+  int32_t in_flight, queued;
+  size_t hbm_in_use;
+} rb_server_stats;
+
+RB_API int rb_server_create(const rb_server_opts* opts, rb_server_t* out);
+/* Stops the scheduler after the in-flight requests finish; pending requests
+ * fail with RB_ECLOSED. */
+RB_API int rb_server_destroy(rb_server_t srv);
+/* Enqueue a request: theta_host [W][13] is copied before return.  *ticket
+ * identifies it for rb_poll.  RB_EBUSY if the queue is full, RB_EINVAL for
+ * W < 1, W > max_walkers or a NULL event. */
+RB_API int rb_submit(rb_server_t srv, rb_event_t ev, const double* theta_host, int64_t W, int want_grad,
+              uint64_t* ticket);
+/* Wait up to timeout_us (0 = do not wait, < 0 = wait without limit) for a
+ * request; on RB_OK copies logl_out [W] and, if the request wanted it and
+ * grad_out != NULL, grad_out [W][13], and forgets the ticket.  Returns
+ * RB_PENDING (timeout_us == 0 and not done), RB_ETIMEDOUT, RB_ENOTFOUND, or
+ * the request's own error status. */
+RB_API int rb_poll(rb_server_t srv, uint64_t ticket, int64_t timeout_us, double* logl_out, double* grad_out);
+RB_API int rb_server_get_stats(rb_server_t srv, rb_server_stats* stats);
+
+/* ---- diagnostics ---------------------------------------------------------- */
+RB_API const char* rb_strerror(int status);
+RB_API const char* rb_last_error(void);
+/* Tracing: record the CUDA events before_main / after_main (cudaEvent_t, or
+ * NULL to stop) on the launch stream immediately before and after the main
+ * likelihood kernel of every subsequent batch call (process-wide). */
+RB_API void rb_set_trace_events(void* before_main, void* after_main);
+/* Number of this library's kernel launches on the calling process so far
+ * (all entry points, all threads). */
+RB_API uint64_t rb_kernel_launch_count(void);
+RB_API int rb_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RB_H_ */

@@ -1,0 +1,284 @@
+"""Python binding of librb: events, batched relative-binning likelihood and
+gradient, strain generation, the serving loop, and a torch.autograd.Function.
+
+PyTorch is used for device memory and streams only: tensors are passed to the
+C ABI as raw device pointers together with the current CUDA stream.  Every
+step of the likelihood runs in librb's kernels; nothing here computes it.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import MODES, NPAR, check, load
+
+
+def _stream_handle(stream: Optional[torch.cuda.Stream]) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _mode(mode) -> int:
+    if isinstance(mode, str):
+        return MODES[mode]
+    return int(mode)
+
+
+def _theta_dev(theta: torch.Tensor) -> torch.Tensor:
+    if not (isinstance(theta, torch.Tensor) and theta.is_cuda):
+        raise TypeError("theta must be a CUDA tensor [W, 13]")
+    if theta.dim() != 2 or theta.shape[1] != NPAR:
+        raise ValueError("theta must have shape [W, 13]")
+    return theta.to(torch.float64).contiguous()
+
+
+class Event:
+    """A device-resident event: grid, bin edges, summary data and tables.
+
+    geom: [D][5] site rows (lat, lon [rad], elevation [m], x/y arm azimuth [rad]);
+    data: [D][N] complex strain and psd: [D][N] one-sided PSD, either numpy
+    arrays (host) or CUDA tensors (data complex128, psd float64).
+    """
+
+    def __init__(self, geom, gmst: float, T: float, f_low: float, f_high: float, data, psd, n_bins: int,
+                 theta_ref, stream: Optional[torch.cuda.Stream] = None):
+        lib = load()
+        geom = np.asarray(geom, dtype=np.float64).reshape(-1, 5)
+        D = geom.shape[0]
+        desc = _lib.EventDesc()
+        desc.n_det = D
+        desc.n_bins = int(n_bins)
+        desc.T, desc.f_low, desc.f_high, desc.gmst = float(T), float(f_low), float(f_high), float(gmst)
+        on_device = isinstance(data, torch.Tensor) and data.is_cuda
+        desc.data_on_device = 1 if on_device else 0
+        keep = []
+        for d in range(D):
+            row = desc.det[d]
+            row.lat, row.lon, row.elev_m, row.xarm_az, row.yarm_az = map(float, geom[d])
+            if on_device:
+                dd = torch.view_as_real(data[d].to(torch.complex128).contiguous()).contiguous()
+                pp = psd[d].to(torch.float64).contiguous()
+                keep += [dd, pp]
+                row.data, row.psd = dd.data_ptr(), pp.data_ptr()
+            else:
+                dd = np.ascontiguousarray(np.stack([np.real(data[d]), np.imag(data[d])], axis=-1), dtype=np.float64)
+                pp = np.ascontiguousarray(psd[d], dtype=np.float64)
+                keep += [dd, pp]
+                row.data, row.psd = dd.ctypes.data, pp.ctypes.data
+        th = np.asarray(theta_ref, dtype=np.float64).reshape(NPAR)
+        for j in range(NPAR):
+            desc.theta_ref[j] = float(th[j])
+        desc.cuda_stream = _stream_handle(stream).value if torch.cuda.is_available() else None
+        handle = ctypes.c_void_p()
+        check(lib.rb_build_summary(ctypes.byref(desc), ctypes.byref(handle)), "rb_build_summary")
+        del keep
+        self._h = handle
+        self.n_det = D
+        self.n_bins = int(n_bins)
+        self.theta_ref = th.copy()
+
+    @classmethod
+    def from_synth(cls, ev: dict, n_bins: Optional[int] = None, theta_ref=None, stream=None) -> "Event":
+        """Build from a ``synth.make_event`` dict that carries ``data``."""
+        return cls(ev["geom"], ev["gmst"], ev["T"], ev["f_low"], ev["f_high"], ev["data"], ev["psd"],
+                   n_bins if n_bins is not None else ev["n_bins"],
+                   ev["theta_inj"] if theta_ref is None else theta_ref, stream=stream)
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise RuntimeError("event has been freed")
+        return self._h
+
+    def rebuild(self, theta_ref=None, data=None, psd=None, stream=None) -> None:
+        """Recompute the summary data in place (asynchronous, allocation-free).
+
+        data/psd: per-detector CUDA tensors (read in place), host numpy arrays
+        (copied in), or None to reuse the event's resident copy."""
+        lib = load()
+        th_p = None
+        if theta_ref is not None:
+            th = np.ascontiguousarray(theta_ref, dtype=np.float64).reshape(NPAR)
+            th_p = th.ctypes.data_as(_lib.c_double_p)
+            self.theta_ref = th.copy()
+        dp = pp = None
+        on_dev = 0
+        keep = []
+        if data is not None:
+            D = self.n_det
+            dp = (ctypes.c_void_p * D)()
+            pp = (ctypes.c_void_p * D)()
+            for d in range(D):
+                if isinstance(data[d], torch.Tensor):
+                    on_dev = 1
+                    dd, ps = data[d], psd[d]
+                    if not (dd.is_contiguous() and ps.is_contiguous() and dd.dtype == torch.float64
+                            and ps.dtype == torch.float64):
+                        raise ValueError("device data must be contiguous float64 [N][2] / [N]")
+                    dp[d], pp[d] = dd.data_ptr(), ps.data_ptr()
+                else:
+                    dd = np.ascontiguousarray(data[d], dtype=np.float64)
+                    ps = np.ascontiguousarray(psd[d], dtype=np.float64)
+                    dp[d], pp[d] = dd.ctypes.data, ps.ctypes.data
+                keep += [dd, ps]
+        check(lib.rb_event_rebuild(self.handle, th_p, dp, pp, on_dev, _stream_handle(stream)), "rb_event_rebuild")
+
+    def info(self) -> dict:
+        lib = load()
+        inf = _lib.EventInfo()
+        check(lib.rb_event_get_info(self.handle, ctypes.byref(inf)), "rb_event_get_info")
+        return {f: getattr(inf, f) for f, _ in _lib.EventInfo._fields_}
+
+    def summary(self) -> dict:
+        """FP64 summary data and bin edges copied to the host."""
+        lib = load()
+        D, B = self.n_det, self.n_bins
+        A0 = np.zeros((D, B, 2))
+        A1 = np.zeros((D, B, 2))
+        B0 = np.zeros((D, B))
+        B1 = np.zeros((D, B))
+        edges = np.zeros(B + 1, dtype=np.int64)
+        p = lambda a: a.ctypes.data_as(_lib.c_double_p)
+        check(lib.rb_event_get_summary(self.handle, p(A0), p(A1), p(B0), p(B1),
+                                       edges.ctypes.data_as(_lib.c_int64_p)), "rb_event_get_summary")
+        return {"A0": A0[..., 0] + 1j * A0[..., 1], "A1": A1[..., 0] + 1j * A1[..., 1], "B0": B0, "B1": B1,
+                "edges": edges}
+
+    def free(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            load().rb_event_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def loglike(event: Event, theta: torch.Tensor, mode="mixed", stream=None) -> torch.Tensor:
+    """Batched RB log-likelihood [W] (float64, on theta's device)."""
+    th = _theta_dev(theta)
+    out = torch.empty(th.shape[0], dtype=torch.float64, device=th.device)
+    check(load().rb_loglike_batch(event.handle, ctypes.c_void_p(th.data_ptr()), th.shape[0],
+                                  ctypes.c_void_p(out.data_ptr()), _mode(mode), _stream_handle(stream)),
+          "rb_loglike_batch")
+    return out
+
+
+def loglike_grad(event: Event, theta: torch.Tensor, mode="mixed", stream=None):
+    """Batched RB log-likelihood [W] and gradient [W, 13]."""
+    th = _theta_dev(theta)
+    W = th.shape[0]
+    out = torch.empty(W, dtype=torch.float64, device=th.device)
+    grad = torch.empty(W, NPAR, dtype=torch.float64, device=th.device)
+    check(load().rb_loglike_grad_batch(event.handle, ctypes.c_void_p(th.data_ptr()), W,
+                                       ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(grad.data_ptr()),
+                                       _mode(mode), _stream_handle(stream)), "rb_loglike_grad_batch")
+    return out, grad
+
+
+def loglike_grad_host(event: Event, theta: np.ndarray, logl_out: np.ndarray, grad_out: Optional[np.ndarray],
+                      mode="mixed", stream=None) -> None:
+    """End-to-end call on host buffers (copies in, evaluates, copies out, syncs)."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    W = th.shape[0]
+    check(load().rb_loglike_grad_host(event.handle, ctypes.c_void_p(th.ctypes.data), W,
+                                      ctypes.c_void_p(logl_out.ctypes.data),
+                                      ctypes.c_void_p(grad_out.ctypes.data) if grad_out is not None else None,
+                                      _mode(mode), _stream_handle(stream)), "rb_loglike_grad_host")
+
+
+def strain(geom, gmst: float, theta, T: float, kmin: int, n_freq: int, device="cuda", stream=None) -> torch.Tensor:
+    """Detector strain h_d(f) [n_freq] complex128 on the device (librb kernel)."""
+    g = np.ascontiguousarray(geom, dtype=np.float64).reshape(5)
+    th = np.ascontiguousarray(theta, dtype=np.float64).reshape(NPAR)
+    out = torch.empty(n_freq, 2, dtype=torch.float64, device=device)
+    check(load().rb_strain(g.ctypes.data_as(_lib.c_double_p), float(gmst), th.ctypes.data_as(_lib.c_double_p),
+                           float(T), int(kmin), int(n_freq), ctypes.c_void_p(out.data_ptr()),
+                           _stream_handle(stream)), "rb_strain")
+    return torch.view_as_complex(out)
+
+
+def kernel_launch_count() -> int:
+    return int(load().rb_kernel_launch_count())
+
+
+def set_trace_events(before: Optional[torch.cuda.Event], after: Optional[torch.cuda.Event]) -> None:
+    """Record `before`/`after` around the main likelihood kernel of every batch call."""
+    b = ctypes.c_void_p(before.cuda_event) if before is not None else None
+    a = ctypes.c_void_p(after.cuda_event) if after is not None else None
+    load().rb_set_trace_events(b, a)
+
+
+class RBLogLikelihood(torch.autograd.Function):
+    """log L(theta) with the hand-written adjoint as its backward.
+
+    forward evaluates log L and d log L / d theta in one pass of the fused
+    kernel; backward returns grad_output[:, None] * (d log L / d theta).
+    """
+
+    @staticmethod
+    def forward(ctx, theta: torch.Tensor, event: Event, mode="mixed"):
+        logl, grad = loglike_grad(event, theta.detach(), mode)
+        ctx.save_for_backward(grad)
+        return logl
+
+    @staticmethod
+    def backward(ctx, grad_output):
+        (grad,) = ctx.saved_tensors
+        return grad_output.to(grad.dtype)[:, None] * grad, None, None
+
+
+def rb_loglike(theta: torch.Tensor, event: Event, mode="mixed") -> torch.Tensor:
+    return RBLogLikelihood.apply(theta, event, mode)
+
+
+class Server:
+    """Continuous-batching request loop (rb_server_* in the C ABI)."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, max_slots: int = 8, max_queue: int = 0, use_graphs: bool = True,
+                 mode="mixed", max_walkers: int = 0):
+        lib = load()
+        o = _lib.ServerOpts(hbm_budget_bytes, max_slots, max_queue, 1 if use_graphs else 0, _mode(mode), max_walkers)
+        h = ctypes.c_void_p()
+        check(lib.rb_server_create(ctypes.byref(o), ctypes.byref(h)), "rb_server_create")
+        self._h = h
+
+    def submit(self, event: Event, theta: np.ndarray, want_grad: bool = True) -> int:
+        th = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1, NPAR)
+        t = ctypes.c_uint64()
+        check(load().rb_submit(self._h, event.handle, th.ctypes.data_as(_lib.c_double_p), th.shape[0],
+                               1 if want_grad else 0, ctypes.byref(t)), "rb_submit")
+        return t.value
+
+    def poll(self, ticket: int, W: int, timeout_us: int = -1, want_grad: bool = True):
+        """Returns (status, logl, grad); status RB_OK, RB_PENDING or RB_ETIMEDOUT (others raise)."""
+        logl = np.zeros(W)
+        grad = np.zeros((W, NPAR)) if want_grad else None
+        st = load().rb_poll(self._h, ticket, int(timeout_us), logl.ctypes.data_as(_lib.c_double_p),
+                            grad.ctypes.data_as(_lib.c_double_p) if grad is not None else None)
+        if st in (_lib.RB_PENDING, _lib.RB_ETIMEDOUT):
+            return st, None, None
+        check(st, "rb_poll")
+        return st, logl, grad
+
+    def stats(self) -> dict:
+        s = _lib.ServerStats()
+        check(load().rb_server_get_stats(self._h, ctypes.byref(s)), "rb_server_get_stats")
+        return {f: getattr(s, f) for f, _ in _lib.ServerStats._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            load().rb_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

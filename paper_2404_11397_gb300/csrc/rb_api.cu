@@ -1,0 +1,489 @@
+// rb_api.cu -- the C ABI of librb (declared in include/rb.h): event build,
+// batched likelihood / gradient calls, strain generation, diagnostics.
+// Host code only orchestrates: every step of the computation runs in the
+// kernels of rb_setup.cu, rb_loglike.cu and rb_summary.cu.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "rb.h"
+#include "rb_api_internal.h"
+#include "rb_internal.cuh"
+
+namespace rb {
+
+// ---- launchers defined in the kernel translation units ----
+cudaError_t launch_ref_values(const double* theta_ref_dev, const EventConst& ec, RefValues* out, cudaStream_t s);
+cudaError_t launch_setup_mixed(const double* theta, int64_t W, const EventConst& ec, const RefValues* ref,
+                               WalkerMixed* ws, WalkerTan<float>* tan, bool grad, cudaStream_t s);
+cudaError_t launch_setup_f64(const double* theta, int64_t W, const EventConst& ec, const RefValues* ref,
+                             WalkerF64* ws, void* tan, bool grad, bool tan_f32, cudaStream_t s);
+cudaError_t launch_rb_mixed(const EventDev& ev, const void* ws, const void* tan, int64_t W, double* logl,
+                            double* grad, bool phase64, cudaStream_t s, int n_sm);
+cudaError_t launch_rb_f64(const EventDev& ev, const void* ws, const void* tan, int64_t W, double* logl, double* grad,
+                          cudaStream_t s, int n_sm);
+cudaError_t launch_bin_edges(double f_low, double f_high, double T, int64_t kmin, int64_t N, int B, int64_t* edges,
+                             cudaStream_t s);
+cudaError_t launch_summary(const DataPtrs& in, int64_t kmin, int64_t N, double T, int D, int B,
+                           const int64_t* edges, const RefValues* ref, double* out, cudaStream_t s);
+cudaError_t launch_tables(int64_t kmin, double T, int D, int B, int Ep, int Bp, const int64_t* edges,
+                          const double* summ, float* tab32, size_t edge32_floats, double* tab64, double* base,
+                          cudaStream_t s);
+cudaError_t launch_strain(const RefValues* src, int64_t kmin, int64_t N, double T, double* h, cudaStream_t s);
+
+// ---- diagnostics ----
+static thread_local char g_err[512] = "no error";
+static std::atomic<uint64_t> g_launches{0};
+static std::atomic<uint64_t> g_event_uid{0};
+
+int set_error(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) return set_error(RB_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+  return set_error(RB_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int sm_count() {
+  static std::once_flag once;
+  static int n = 0;
+  std::call_once(once, [] {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 1;
+  });
+  return n;
+}
+
+// ---- site geometry (host) ----
+static void arm_unit(double lat, double lon, double az, double a[3]) {
+  const double n[3] = {-std::sin(lat) * std::cos(lon), -std::sin(lat) * std::sin(lon), std::cos(lat)};  // North
+  const double e[3] = {-std::sin(lon), std::cos(lon), 0.0};                                            // East
+  for (int i = 0; i < 3; ++i) a[i] = std::cos(az) * n[i] + std::sin(az) * e[i];
+}
+
+DetGeom make_geom(double lat, double lon, double elev, double xaz, double yaz) {
+  DetGeom g;
+  double x[3], y[3];
+  arm_unit(lat, lon, xaz, x);
+  arm_unit(lat, lon, yaz, y);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) g.D[i][j] = 0.5 * (x[i] * x[j] - y[i] * y[j]);
+  // WGS-84 geodetic -> Earth-fixed Cartesian
+  const double a = 6378137.0, e2 = 6.69437999014e-3;
+  const double s = std::sin(lat), c = std::cos(lat);
+  const double Nr = a / std::sqrt(1.0 - e2 * s * s);
+  g.r[0] = (Nr + elev) * c * std::cos(lon);
+  g.r[1] = (Nr + elev) * c * std::sin(lon);
+  g.r[2] = (Nr * (1.0 - e2) + elev) * s;
+  return g;
+}
+
+static bool theta_ok(const double* th) {
+  for (int j = 0; j < kNPar; ++j)
+    if (!std::isfinite(th[j])) return false;
+  return th[0] > 0.0 && th[1] > 0.0 && th[1] <= 1.0 && th[6] > 0.0;
+}
+
+static int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+}  // namespace rb
+
+using namespace rb;
+
+struct rb_event_s {
+  rb::EventEntry e;
+};
+
+namespace rb {
+const EventEntry* event_entry(::rb_event_s* ev) { return ev ? &ev->e : nullptr; }
+}  // namespace rb
+
+extern "C" {
+
+int rb_abi_version(void) { return 1; }
+
+const char* rb_last_error(void) { return g_err; }
+
+uint64_t rb_kernel_launch_count(void) { return g_launches.load(); }
+
+const char* rb_strerror(int status) {
+  switch (status) {
+    case RB_OK: return "ok";
+    case RB_PENDING: return "pending";
+    case RB_EINVAL: return "invalid argument";
+    case RB_ENOMEM: return "out of memory";
+    case RB_ECUDA: return "CUDA error";
+    case RB_ETIMEDOUT: return "timed out";
+    case RB_EBUSY: return "busy: admission refused";
+    case RB_ENOTFOUND: return "unknown ticket";
+    case RB_ECLOSED: return "server closed";
+    default: return "unknown status";
+  }
+}
+
+int rb_event_free(rb_event_t ev) {
+  if (!ev) return RB_OK;
+  EventEntry& e = ev->e;
+  cudaFree(e.d_edges);
+  cudaFree(e.d_summ);
+  cudaFree(e.d_tab32);
+  cudaFree(e.d_tab64);
+  cudaFree(e.d_ref);
+  cudaFree(e.d_base);
+  cudaFree(e.d_data);
+  cudaFree(e.d_psd);
+  cudaFree(e.d_theta_ref);
+  delete ev;
+  return RB_OK;
+}
+
+int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
+  if (!desc || !out) return set_error(RB_EINVAL, "rb_build_summary: NULL descriptor or output");
+  *out = nullptr;
+  const int D = desc->n_det, B = desc->n_bins;
+  if (D < 1 || D > RB_MAX_DET) return set_error(RB_EINVAL, "rb_build_summary: n_det=%d not in 1..%d", D, RB_MAX_DET);
+  if (!(desc->T > 0.0) || !std::isfinite(desc->T) || !(desc->f_low > 0.0) || !(desc->f_high > desc->f_low) ||
+      !std::isfinite(desc->f_high) || !std::isfinite(desc->gmst))
+    return set_error(RB_EINVAL, "rb_build_summary: invalid T/f_low/f_high/gmst");
+  const int64_t kmin = (int64_t)std::ceil(desc->f_low * desc->T - 1e-9);
+  const int64_t kmax = (int64_t)std::floor(desc->f_high * desc->T + 1e-9);
+  const int64_t N = kmax - kmin + 1;
+  if (N < 2) return set_error(RB_EINVAL, "rb_build_summary: grid has %lld points", (long long)N);
+  if (B < 1 || B > N - 1) return set_error(RB_EINVAL, "rb_build_summary: n_bins=%d not in 1..%lld", B, (long long)(N - 1));
+  if ((int64_t)B + 1 > (int64_t)1 << 20) return set_error(RB_EINVAL, "rb_build_summary: too many bins");
+  for (int d = 0; d < D; ++d)
+    if (!desc->det[d].data || !desc->det[d].psd) return set_error(RB_EINVAL, "rb_build_summary: detector %d has NULL data/psd", d);
+  if (!theta_ok(desc->theta_ref)) return set_error(RB_EINVAL, "rb_build_summary: unphysical theta_ref");
+
+  rb_event_t ev = new (std::nothrow) rb_event_s();
+  if (!ev) return set_error(RB_ENOMEM, "rb_build_summary: host allocation");
+  EventEntry& e = ev->e;
+  cudaStream_t s = (cudaStream_t)desc->cuda_stream;
+  e.uid = ++g_event_uid;
+  e.n_det = D;
+  e.n_bins = B;
+  e.kmin = kmin;
+  e.N = N;
+  e.T = desc->T;
+  e.f_low = desc->f_low;
+  e.f_high = desc->f_high;
+  e.gmst = desc->gmst;
+  std::memcpy(e.theta_ref, desc->theta_ref, sizeof(e.theta_ref));
+  e.ec.n_det = D;
+  e.ec.pad = 0;
+  e.ec.gmst = desc->gmst;
+  for (int d = 0; d < RB_MAX_DET; ++d) {
+    if (d < D) {
+      const rb_detector_desc& dd = desc->det[d];
+      e.ec.det[d] = make_geom(dd.lat, dd.lon, dd.elev_m, dd.xarm_az, dd.yarm_az);
+    } else {
+      std::memset(&e.ec.det[d], 0, sizeof(DetGeom));
+    }
+  }
+  const int E = B + 1;
+  const int Ep = round_up(E, 4), Bp = round_up(B, 4);
+  const size_t edge32 = (size_t)(2 * kNBasis + 2) * Ep;
+  const size_t tab32 = edge32 + (size_t)D * 6 * Bp;
+  const size_t tab64 = (size_t)(kNBasis + 1) * Ep + (size_t)D * 6 * Bp;
+  {
+    // the batch kernels stage all edge and bin tables in shared memory
+    int dev = 0, smem_max = 0;
+    cudaError_t qerr = cudaGetDevice(&dev);
+    if (qerr == cudaSuccess) qerr = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (qerr != cudaSuccess) {
+      delete ev;
+      return cuda_fail(qerr, "rb_build_summary: device query");
+    }
+    const size_t need = std::max(tab32 * sizeof(float), (size_t)(kNBasis + 1) * Ep * sizeof(double) +
+                                                            (size_t)D * 6 * Bp * sizeof(float));
+    if (need > (size_t)smem_max) {
+      delete ev;
+      return set_error(RB_EINVAL, "rb_build_summary: %d bins x %d detectors need %zu B of shared memory (max %d)",
+                       B, D, need, smem_max);
+    }
+  }
+
+  int rc = RB_OK;
+  cudaError_t err;
+  do {
+    struct { void** p; size_t n; const char* what; } allocs[] = {
+        {(void**)&e.d_edges, sizeof(int64_t) * E, "edges"},
+        {(void**)&e.d_summ, sizeof(double) * 6 * D * B, "summary"},
+        {(void**)&e.d_tab32, sizeof(float) * tab32, "tab32"},
+        {(void**)&e.d_tab64, sizeof(double) * tab64, "tab64"},
+        {(void**)&e.d_ref, sizeof(RefValues), "ref"},
+        {(void**)&e.d_base, sizeof(double), "base"},
+        {(void**)&e.d_data, sizeof(double) * 2 * D * N, "strain"},
+        {(void**)&e.d_psd, sizeof(double) * D * N, "psd"},
+        {(void**)&e.d_theta_ref, sizeof(double) * kNPar, "theta_ref"}};
+    for (auto& a : allocs) {
+      if ((err = cudaMalloc(a.p, a.n)) != cudaSuccess) { rc = cuda_fail(err, a.what); break; }
+      e.device_bytes += a.n;
+    }
+    if (rc != RB_OK) break;
+    e.dev.n_det = D;
+    e.dev.n_bins = B;
+    e.dev.n_edges = E;
+    e.dev.e_pad = Ep;
+    e.dev.b_pad = Bp;
+    e.dev.kmin = kmin;
+    e.dev.n_freq = N;
+    e.dev.T = e.T;
+    e.dev.base_logl = e.d_base;
+    e.dev.tab32 = e.d_tab32;
+    e.dev.tab32_floats = tab32;
+    e.dev.edge32_floats = edge32;
+    e.dev.tab64 = e.d_tab64;
+    e.dev.ref = e.d_ref;
+    const cudaMemcpyKind kind = desc->data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    for (int d = 0; d < D && rc == RB_OK; ++d) {
+      if ((err = cudaMemcpyAsync(e.d_data + 2 * (size_t)d * N, desc->det[d].data, sizeof(double) * 2 * N, kind, s)) != cudaSuccess) rc = cuda_fail(err, "copy strain");
+      else if ((err = cudaMemcpyAsync(e.d_psd + (size_t)d * N, desc->det[d].psd, sizeof(double) * N, kind, s)) != cudaSuccess) rc = cuda_fail(err, "copy psd");
+    }
+    if (rc != RB_OK) break;
+    if ((err = cudaMemcpyAsync(e.d_theta_ref, e.theta_ref, sizeof(double) * kNPar, cudaMemcpyHostToDevice, s)) != cudaSuccess) { rc = cuda_fail(err, "copy theta_ref"); break; }
+    if ((err = launch_bin_edges(e.f_low, e.f_high, e.T, kmin, N, B, e.d_edges, s)) != cudaSuccess) { rc = cuda_fail(err, "bin edge kernels"); break; }
+    count_launches(2);
+    if ((rc = rebuild_event(e, nullptr, s)) != RB_OK) break;
+    if ((err = cudaStreamSynchronize(s)) != cudaSuccess) { rc = cuda_fail(err, "build synchronise"); break; }
+  } while (false);
+  if (rc != RB_OK) {
+    cudaStreamSynchronize(s);
+    rb_event_free(ev);
+    return rc;
+  }
+  *out = ev;
+  return RB_OK;
+}
+
+int rb_event_rebuild(rb_event_t ev, const double* theta_ref_host, const double* const* data, const double* const* psd,
+                     int data_on_device, void* stream) {
+  if (!ev) return set_error(RB_EINVAL, "rb_event_rebuild: NULL event");
+  EventEntry& e = ev->e;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t err;
+  if (theta_ref_host) {
+    if (!theta_ok(theta_ref_host)) return set_error(RB_EINVAL, "rb_event_rebuild: unphysical theta_ref");
+    std::memcpy(e.theta_ref, theta_ref_host, sizeof(e.theta_ref));
+    if ((err = cudaMemcpyAsync(e.d_theta_ref, theta_ref_host, sizeof(double) * kNPar, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      return cuda_fail(err, "rb_event_rebuild: copy theta_ref");
+  }
+  DataPtrs in{};
+  bool have = false;
+  if (data || psd) {
+    if (!data || !psd) return set_error(RB_EINVAL, "rb_event_rebuild: data and psd must both be given");
+    for (int d = 0; d < e.n_det; ++d)
+      if (!data[d] || !psd[d]) return set_error(RB_EINVAL, "rb_event_rebuild: detector %d has NULL data/psd", d);
+    const int64_t N = e.N;
+    if (data_on_device) {  // read in place, no copy
+      for (int d = 0; d < e.n_det; ++d) {
+        in.data[d] = data[d];
+        in.psd[d] = psd[d];
+      }
+      have = true;
+    } else {  // stage into the event's resident copy
+      for (int d = 0; d < e.n_det; ++d) {
+        if ((err = cudaMemcpyAsync(e.d_data + 2 * (size_t)d * N, data[d], sizeof(double) * 2 * N, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+          return cuda_fail(err, "rb_event_rebuild: copy strain");
+        if ((err = cudaMemcpyAsync(e.d_psd + (size_t)d * N, psd[d], sizeof(double) * N, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+          return cuda_fail(err, "rb_event_rebuild: copy psd");
+      }
+    }
+  }
+  return rebuild_event(e, have ? &in : nullptr, s);
+}
+
+void rb_set_trace_events(void* before_main, void* after_main) { set_trace_events(before_main, after_main); }
+
+int rb_event_get_info(rb_event_t ev, rb_event_info* info) {
+  if (!ev || !info) return set_error(RB_EINVAL, "rb_event_get_info: NULL argument");
+  const EventEntry& e = ev->e;
+  info->n_det = e.n_det;
+  info->n_bins = e.n_bins;
+  info->kmin = e.kmin;
+  info->n_freq = e.N;
+  info->T = e.T;
+  info->gmst = e.gmst;
+  info->device_bytes = e.device_bytes;
+  cudaError_t err = cudaMemcpy(&info->base_logl, e.d_base, sizeof(double), cudaMemcpyDeviceToHost);
+  if (err != cudaSuccess) return cuda_fail(err, "rb_event_get_info: read base");
+  return RB_OK;
+}
+
+int rb_event_get_summary(rb_event_t ev, double* A0, double* A1, double* B0, double* B1, int64_t* edges) {
+  if (!ev) return set_error(RB_EINVAL, "rb_event_get_summary: NULL event");
+  const EventEntry& e = ev->e;
+  const int D = e.n_det, B = e.n_bins;
+  std::vector<double> s((size_t)6 * D * B);
+  cudaError_t err = cudaMemcpy(s.data(), e.d_summ, sizeof(double) * s.size(), cudaMemcpyDeviceToHost);
+  if (err != cudaSuccess) return cuda_fail(err, "copy summary");
+  if (edges && (err = cudaMemcpy(edges, e.d_edges, sizeof(int64_t) * (B + 1), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(err, "copy edges");
+  for (size_t i = 0; i < (size_t)D * B; ++i) {
+    if (A0) { A0[2 * i] = s[6 * i]; A0[2 * i + 1] = s[6 * i + 1]; }
+    if (A1) { A1[2 * i] = s[6 * i + 2]; A1[2 * i + 1] = s[6 * i + 3]; }
+    if (B0) B0[i] = s[6 * i + 4];
+    if (B1) B1[i] = s[6 * i + 5];
+  }
+  return RB_OK;
+}
+
+int rb_loglike_grad_batch(rb_event_t ev, const double* theta_dev, int64_t W, double* logl_dev, double* grad_dev,
+                          int mode, void* stream) {
+  return rb::run_batch(event_entry(ev), theta_dev, W, logl_dev, grad_dev, mode, (cudaStream_t)stream, nullptr);
+}
+
+int rb_loglike_batch(rb_event_t ev, const double* theta_dev, int64_t W, double* logl_dev, int mode, void* stream) {
+  return rb::run_batch(event_entry(ev), theta_dev, W, logl_dev, nullptr, mode, (cudaStream_t)stream, nullptr);
+}
+
+int rb_loglike_grad_host(rb_event_t ev, const double* theta_host, int64_t W, double* logl_host, double* grad_host,
+                         int mode, void* stream) {
+  if (!ev) return set_error(RB_EINVAL, "rb_loglike_grad_host: NULL event");
+  if (W < 0) return set_error(RB_EINVAL, "rb_loglike_grad_host: W < 0");
+  if (W == 0) return RB_OK;
+  if (!theta_host || !logl_host) return set_error(RB_EINVAL, "rb_loglike_grad_host: NULL buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  double *d_theta = nullptr, *d_logl = nullptr, *d_grad = nullptr;
+  int rc = RB_OK;
+  cudaError_t err;
+  do {
+    if ((err = cudaMallocAsync(&d_theta, sizeof(double) * kNPar * W, s)) != cudaSuccess) { rc = cuda_fail(err, "cudaMallocAsync theta"); break; }
+    if ((err = cudaMallocAsync(&d_logl, sizeof(double) * W, s)) != cudaSuccess) { rc = cuda_fail(err, "cudaMallocAsync logl"); break; }
+    if (grad_host && (err = cudaMallocAsync(&d_grad, sizeof(double) * kNPar * W, s)) != cudaSuccess) { rc = cuda_fail(err, "cudaMallocAsync grad"); break; }
+    if ((err = cudaMemcpyAsync(d_theta, theta_host, sizeof(double) * kNPar * W, cudaMemcpyHostToDevice, s)) != cudaSuccess) { rc = cuda_fail(err, "copy theta"); break; }
+    rc = rb::run_batch(&ev->e, d_theta, W, d_logl, d_grad, mode, s, nullptr);
+    if (rc != RB_OK) break;
+    if ((err = cudaMemcpyAsync(logl_host, d_logl, sizeof(double) * W, cudaMemcpyDeviceToHost, s)) != cudaSuccess) { rc = cuda_fail(err, "copy logl"); break; }
+    if (grad_host && (err = cudaMemcpyAsync(grad_host, d_grad, sizeof(double) * kNPar * W, cudaMemcpyDeviceToHost, s)) != cudaSuccess) { rc = cuda_fail(err, "copy grad"); break; }
+  } while (false);
+  if (d_theta) cudaFreeAsync(d_theta, s);
+  if (d_logl) cudaFreeAsync(d_logl, s);
+  if (d_grad) cudaFreeAsync(d_grad, s);
+  err = cudaStreamSynchronize(s);
+  if (rc == RB_OK && err != cudaSuccess) rc = cuda_fail(err, "synchronise");
+  return rc;
+}
+
+int rb_strain(const double* geom, double gmst, const double* theta_host, double T, int64_t kmin, int64_t n_freq,
+              double* h_dev, void* stream) {
+  if (!geom || !theta_host || !h_dev) return set_error(RB_EINVAL, "rb_strain: NULL argument");
+  if (!(T > 0.0) || n_freq < 1 || kmin < 1) return set_error(RB_EINVAL, "rb_strain: invalid grid");
+  cudaStream_t s = (cudaStream_t)stream;
+  EventConst ec;
+  std::memset(&ec, 0, sizeof(ec));
+  ec.n_det = 1;
+  ec.gmst = gmst;
+  ec.det[0] = make_geom(geom[0], geom[1], geom[2], geom[3], geom[4]);
+  double* d_theta = nullptr;
+  RefValues* d_src = nullptr;
+  int rc = RB_OK;
+  cudaError_t err;
+  do {
+    if ((err = cudaMallocAsync(&d_theta, sizeof(double) * kNPar, s)) != cudaSuccess) { rc = cuda_fail(err, "cudaMallocAsync theta"); break; }
+    if ((err = cudaMallocAsync(&d_src, sizeof(RefValues), s)) != cudaSuccess) { rc = cuda_fail(err, "cudaMallocAsync values"); break; }
+    if ((err = cudaMemcpyAsync(d_theta, theta_host, sizeof(double) * kNPar, cudaMemcpyHostToDevice, s)) != cudaSuccess) { rc = cuda_fail(err, "copy theta"); break; }
+    if ((err = launch_ref_values(d_theta, ec, d_src, s)) != cudaSuccess) { rc = cuda_fail(err, "values kernel"); break; }
+    if ((err = launch_strain(d_src, kmin, n_freq, T, h_dev, s)) != cudaSuccess) { rc = cuda_fail(err, "strain kernel"); break; }
+    count_launches(2);
+  } while (false);
+  if (d_theta) cudaFreeAsync(d_theta, s);
+  if (d_src) cudaFreeAsync(d_src, s);
+  return rc;
+}
+
+}  // extern "C"
+
+namespace rb {
+
+int rebuild_event(EventEntry& e, const DataPtrs* in_opt, cudaStream_t s) {
+  cudaError_t err;
+  DataPtrs in{};
+  if (in_opt) {
+    in = *in_opt;
+  } else {
+    for (int d = 0; d < e.n_det; ++d) {
+      in.data[d] = e.d_data + 2 * (size_t)d * e.N;
+      in.psd[d] = e.d_psd + (size_t)d * e.N;
+    }
+  }
+  if ((err = launch_ref_values(e.d_theta_ref, e.ec, e.d_ref, s)) != cudaSuccess) return cuda_fail(err, "reference values kernel");
+  if ((err = launch_summary(in, e.kmin, e.N, e.T, e.n_det, e.n_bins, e.d_edges, e.d_ref, e.d_summ, s)) != cudaSuccess)
+    return cuda_fail(err, "summary kernel");
+  if ((err = launch_tables(e.kmin, e.T, e.n_det, e.n_bins, e.dev.e_pad, e.dev.b_pad, e.d_edges, e.d_summ, e.d_tab32,
+                           e.dev.edge32_floats, e.d_tab64, e.d_base, s)) != cudaSuccess)
+    return cuda_fail(err, "table kernels");
+  count_launches(4);
+  return RB_OK;
+}
+
+static std::atomic<void*> g_trace_before{nullptr}, g_trace_after{nullptr};
+void set_trace_events(void* before, void* after) {
+  g_trace_before.store(before);
+  g_trace_after.store(after);
+}
+
+size_t walker_ws_bytes(int mode, bool grad) {
+  size_t b = (mode == RB_MIXED) ? sizeof(WalkerMixed) : sizeof(WalkerF64);
+  if (grad) b += (mode == RB_FP64) ? sizeof(WalkerTan<double>) : sizeof(WalkerTan<float>);
+  return b;
+}
+
+// Set-up kernel + likelihood kernel for one batch.  If `scratch` is NULL the
+// per-walker workspace is taken from the stream-ordered pool of `s`.
+int run_batch(const EventEntry* e, const double* theta, int64_t W, double* logl, double* grad, int mode,
+              cudaStream_t s, void* scratch) {
+  if (!e) return set_error(RB_EINVAL, "NULL event");
+  if (W < 0) return set_error(RB_EINVAL, "W < 0");
+  if (mode != RB_MIXED && mode != RB_FP64 && mode != RB_MIXED_F64PHASE) return set_error(RB_EINVAL, "bad mode %d", mode);
+  if (W == 0) return RB_OK;
+  if (!theta || !logl) return set_error(RB_EINVAL, "NULL theta or logl");
+  const bool want_grad = grad != nullptr;
+  const size_t ws_bytes = (mode == RB_MIXED) ? sizeof(WalkerMixed) * W : sizeof(WalkerF64) * W;
+  const size_t tan_bytes = !want_grad ? 0 : (mode == RB_FP64 ? sizeof(WalkerTan<double>) : sizeof(WalkerTan<float>)) * W;
+  void* buf = scratch;
+  cudaError_t err;
+  if (!buf) {
+    err = cudaMallocAsync(&buf, ws_bytes + tan_bytes, s);
+    if (err != cudaSuccess) return cuda_fail(err, "cudaMallocAsync workspace");
+  }
+  void* ws = buf;
+  void* tan = want_grad ? static_cast<void*>(static_cast<char*>(buf) + ws_bytes) : nullptr;
+  int rc = RB_OK;
+  const int n_sm = sm_count();
+  cudaEvent_t tb = static_cast<cudaEvent_t>(g_trace_before.load());
+  cudaEvent_t ta = static_cast<cudaEvent_t>(g_trace_after.load());
+  if (mode == RB_MIXED)
+    err = launch_setup_mixed(theta, W, e->ec, e->d_ref, static_cast<WalkerMixed*>(ws),
+                             static_cast<WalkerTan<float>*>(tan), want_grad, s);
+  else
+    err = launch_setup_f64(theta, W, e->ec, e->d_ref, static_cast<WalkerF64*>(ws), tan, want_grad,
+                           mode == RB_MIXED_F64PHASE, s);
+  if (err == cudaSuccess && tb) err = cudaEventRecord(tb, s);
+  if (err == cudaSuccess) {
+    if (mode == RB_FP64)
+      err = launch_rb_f64(e->dev, ws, tan, W, logl, grad, s, n_sm);
+    else
+      err = launch_rb_mixed(e->dev, ws, tan, W, logl, grad, mode == RB_MIXED_F64PHASE, s, n_sm);
+  }
+  if (err == cudaSuccess && ta) err = cudaEventRecord(ta, s);
+  if (err != cudaSuccess) rc = cuda_fail(err, "likelihood kernels");
+  else count_launches(2);
+  if (!scratch) cudaFreeAsync(buf, s);
+  return rc;
+}
+
+}  // namespace rb

@@ -1,0 +1,58 @@
+// rb_api_internal.h -- host-side structures shared by the C ABI translation
+// units (rb_api.cu, rb_server.cpp).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "rb.h"
+#include "rb_internal.cuh"
+
+namespace rb {
+
+// Host record of one event and the device memory it owns.
+struct EventEntry {
+  int n_det = 0, n_bins = 0;
+  int64_t kmin = 0, N = 0;
+  double T = 0, f_low = 0, f_high = 0, gmst = 0;
+  double theta_ref[kNPar] = {};
+  EventConst ec{};
+  EventDev dev{};
+  int64_t* d_edges = nullptr;
+  double* d_summ = nullptr;
+  float* d_tab32 = nullptr;
+  double* d_tab64 = nullptr;
+  RefValues* d_ref = nullptr;
+  double* d_base = nullptr;
+  double* d_data = nullptr;   // resident strain [D][N][2]
+  double* d_psd = nullptr;    // resident PSD [D][N]
+  double* d_theta_ref = nullptr;
+  size_t device_bytes = 0;
+  uint64_t uid = 0;  // unique per built event (never reused within a process)
+};
+
+const EventEntry* event_entry(::rb_event_s* ev);
+
+int set_error(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+void count_launches(uint64_t n);
+int sm_count();
+
+// Per-walker workspace of one batch, in bytes per walker.
+size_t walker_ws_bytes(int mode, bool grad);
+
+// Set-up + likelihood kernels for one batch; scratch = NULL takes the
+// workspace from the stream-ordered allocator.
+int run_batch(const EventEntry* e, const double* theta, int64_t W, double* logl, double* grad, int mode,
+              cudaStream_t s, void* scratch);
+
+// Fiducial values, summary data, tables and base of an event from the given
+// device strain/PSD (NULL: the event's resident copy); no allocation, no
+// synchronisation.
+int rebuild_event(EventEntry& e, const DataPtrs* in, cudaStream_t s);
+
+// Events recorded on the launch stream right before / after the main
+// likelihood kernel of every batch (NULL disables).
+void set_trace_events(void* before, void* after);
+
+}  // namespace rb

@@ -1,0 +1,210 @@
+// rb_internal.cuh -- layouts and device helpers shared by the librb kernels.
+//
+// Method: relative-binning likelihood of arXiv:2404.11397, Sec. II.A-II.C
+// (Eqs. 2-5), with TaylorF2 + tides (Sec. II.B) at the bin edges.
+//
+// Phase factorisation used by every kernel.  With v = (pi M f)^{1/3}, the
+// TaylorF2 phase Psi(f) = 2 pi f t_c - phi_c - pi/4 + 3/(128 eta v^5) sum_k phi_k v^k
+// is written as
+//     Psi(f) = Phi0 + sum_{k<10} c_k g_k(f) + 2 pi f t_c,
+// with the ten frequency functions (the PN powers v^{k-5}, the 2.5PN and 3PN
+// logarithms split into ln f parts)
+//     g = { f^-5/3, f^-1, f^-2/3, f^-1/3, ln f, f^1/3, f^1/3 ln f, f^2/3, f^5/3, f^7/3 }
+// and per-source coefficients c_k(theta) and constant Phi0(theta).  The
+// detector delay adds 2 pi f dt_d, so each detector's phase difference to the
+// fiducial waveform at a bin edge is
+//     dPsi_d(f_e) = sum_k (c_k - c_k,ref) g_k(f_e) + 2 pi f_e (tau_d - tau_d,ref),
+// tau_d = t_c + dt_d.  The kernels work in turns: x = dPsi / (2 pi), and the
+// edge tables hold g_k(f_e) / (2 pi).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rb {
+
+constexpr int kNPar = 13;
+constexpr int kMaxDet = 3;
+constexpr int kNBasis = 10;
+constexpr int kNTanIntr = 6;  // Mc, q, chi1, chi2, Lambda1, Lambda2
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+constexpr double kTwoPi = 6.283185307179586476925286766559005768;
+constexpr double kEulerGamma = 0.577215664901532860606512090082402431;
+constexpr double kMsunS = 4.925490947641266978e-6;   // G M_sun / c^3 [s]
+constexpr double kClight = 299792458.0;               // [m/s]
+constexpr double kMpcS = 3.085677581491367e22 / 299792458.0;  // 1 Mpc / c [s]
+
+// Per-detector constant geometry (built on the host from the site row).
+struct DetGeom {
+  double D[3][3];   // response tensor (x x^T - y y^T)/2
+  double r[3];      // vertex [m], Earth-fixed
+};
+
+// Constant event data needed by the per-walker set-up kernel.
+struct EventConst {
+  int n_det;
+  int pad;
+  double gmst;
+  DetGeom det[kMaxDet];
+};
+
+// Absolute per-source quantities (FP64).  Produced by one noinline device
+// function so that theta and theta_ref go through identical instructions.
+struct Values {
+  double c[kNBasis];     // phase-basis coefficients [rad]
+  double phi0;           // constant phase [rad]
+  double tau[kMaxDet];   // t_c + dt_d [s]
+  double amp;            // Mc^{5/6} / d_L (Msun^{5/6} / Mpc)
+  double P64[kMaxDet][2];  // F+ (1+cos^2 i)/2 - i Fx cos i   (FP64, only if requested)
+  float P32[kMaxDet][2];   // same, FP32 trigonometry
+  int valid;
+  int pad;
+};
+
+// Per-detector strain [N][2] and PSD [N] pointers (device).
+struct DataPtrs {
+  const double* data[kMaxDet];
+  const double* psd[kMaxDet];
+};
+
+// Fiducial (theta_ref) values of an event, written once by the set-up kernel.
+struct RefValues {
+  Values v;
+};
+
+// Per-walker set-up output for the mixed (float-float) path.
+struct WalkerMixed {
+  float dc_hi[kNBasis], dc_lo[kNBasis];  // c_k - c_k,ref as float pairs
+  float tau_hi[kMaxDet], tau_lo[kMaxDet];  // tau_d - tau_d,ref [s] as float pairs
+  float rho[kMaxDet][2];   // C_d(theta) / C_d(theta_ref)
+  float sig[kMaxDet][2];   // rho - 1, computed as (Q - Q_ref) / Q_ref
+  int valid;
+  int pad[3];
+};
+
+// Per-walker set-up output for the FP64 and FP64-phase paths.
+struct WalkerF64 {
+  double dc[kNBasis];
+  double tau[kMaxDet];
+  double rho[kMaxDet][2];
+  double sig[kMaxDet][2];
+  int valid;
+  int pad;
+};
+
+// Tangents for the chain rule (T = float for the mixed paths, double for FP64).
+template <class T>
+struct WalkerTan {
+  T dc[kNBasis][kNTanIntr];      // d c_k / d(Mc, q, chi1, chi2, L1, L2)
+  T dphi0[2];                    // d Phi0 / d(Mc, q)
+  T dtd[kMaxDet][2];             // d dt_d / d(ra, dec)
+  T dlnP[kMaxDet][4][2];         // d ln P_d / d(iota, psi, ra, dec), complex
+  T lnamp_Mc, lnamp_dL;          // d ln(Mc^{5/6}/d_L) / d(Mc, dL)
+};
+
+// Device-side event tables.  Offsets are in elements of the table type.
+struct EventDev {
+  int n_det, n_bins, n_edges, e_pad, b_pad;
+  int64_t kmin, n_freq;
+  double T;
+  const double* base_logl;  // device: sum_d (Re sum_b A0 - sum_b B0 / 2) = log L(theta_ref)
+  // float image copied to shared memory by the mixed kernels:
+  //   [0 .. 10*Ep)       g_hi[k][e]  (g_k(f_e)/2pi, high part)
+  //   [10*Ep .. 20*Ep)   g_lo[k][e]
+  //   [20*Ep .. 21*Ep)   f_hi[e], [21*Ep .. 22*Ep) f_lo[e]
+  //   then per detector 6 rows of Bp: a0r, a0i, a1r, a1i, b0, b1
+  //   (alpha0 = A0/2, alpha1 = A1/df_b, beta0 = B0/2, beta1 = B1/df_b)
+  const float* tab32;
+  size_t tab32_floats;   // multiple of 4
+  size_t edge32_floats;  // length of the edge part (22*Ep)
+  // FP64 tables: g[k][e] (10*Ep), f[e] (Ep), then per detector 6 rows of Bp
+  const double* tab64;
+  const RefValues* ref;
+};
+
+// ---------------------------------------------------------------------------
+// Float-float helpers (all operations rounded explicitly: no contraction or
+// reassociation may touch the error-free transformations).
+// ---------------------------------------------------------------------------
+struct f2x {
+  float hi, lo;
+};
+
+__device__ __forceinline__ f2x f2x_from(double x) {
+  float h = __double2float_rn(x);
+  float l = __double2float_rn(x - (double)h);
+  return {h, l};
+}
+
+// s += a * b, with a, b float pairs; (s_hi, s_lo) is an unnormalised pair.
+// Product: hi*hi exactly by FMA (Dekker), cross terms folded into the error;
+// lo*lo (< 2^-48 relative) is dropped.  Sum: Knuth two-sum on the high parts.
+__device__ __forceinline__ void f2x_fma_acc(float a_hi, float a_lo, float b_hi, float b_lo, float& s_hi,
+                                            float& s_lo) {
+  float p = __fmul_rn(a_hi, b_hi);
+  float e = __fmaf_rn(a_hi, b_hi, -p);
+  e = __fmaf_rn(a_hi, b_lo, e);
+  e = __fmaf_rn(a_lo, b_hi, e);
+  float s = __fadd_rn(s_hi, p);
+  float bb = __fadd_rn(s, -s_hi);
+  float err = __fadd_rn(__fadd_rn(s_hi, -__fadd_rn(s, -bb)), __fadd_rn(p, -bb));
+  s_hi = s;
+  s_lo = __fadd_rn(s_lo, __fadd_rn(err, e));
+}
+
+// Round to nearest integer on the FMA pipe (valid for |x| < 2^22; larger
+// inputs still give an integer within 1 of x, which the second stage of
+// frac_turns absorbs).
+__device__ __forceinline__ float round_fma_pipe(float x) {
+  const float magic = 12582912.0f;  // 1.5 * 2^23
+  return __fadd_rn(__fadd_rn(x, magic), -magic);
+}
+
+// Fractional part in [-1/2, 1/2] (up to rounding) of the float pair (hi, lo), in turns.
+__device__ __forceinline__ float frac_turns(float hi, float lo) {
+  float r = __fadd_rn(hi, -round_fma_pipe(hi));  // exact
+  float y = __fadd_rn(r, lo);
+  return __fadd_rn(y, -round_fma_pipe(y));
+}
+
+// Half-angle sine and cosine: s = sin(pi y), c = cos(pi y) for |y| <= 1/2, by
+// the Taylor series of sin and cos about 0 (terms 1/n!, truncated where the
+// remainder is below 1e-9 at |pi y| = pi/2).  pi is applied as a float pair.
+__device__ __forceinline__ void sincos_pi_half(float y, float& s, float& c) {
+  const float pi_hi = 3.14159274101257324f;
+  const float pi_lo = -8.74227765734758577e-8f;
+  float z = __fmaf_rn(y, pi_hi, y * pi_lo);
+  float w = z * z;
+  // sin z = z (1 - w/3! + w^2/5! - ... + w^6/13!)
+  float ps = 1.6059043836821613e-10f;          // 1/13!
+  ps = fmaf(ps, w, -2.5052108385441720e-08f);  // -1/11!
+  ps = fmaf(ps, w, 2.7557319223985893e-06f);   // 1/9!
+  ps = fmaf(ps, w, -1.9841269841269841e-04f);  // -1/7!
+  ps = fmaf(ps, w, 8.3333333333333333e-03f);   // 1/5!
+  ps = fmaf(ps, w, -1.6666666666666667e-01f);  // -1/3!
+  s = fmaf(ps * w, z, z);
+  // cos z = 1 - w/2! + w^2/4! - ... + w^7/14!
+  float pc = -1.1470745597729725e-11f;         // -1/14!
+  pc = fmaf(pc, w, 2.0876756987868099e-09f);   // 1/12!
+  pc = fmaf(pc, w, -2.7557319223985891e-07f);  // -1/10!
+  pc = fmaf(pc, w, 2.4801587301587302e-05f);   // 1/8!
+  pc = fmaf(pc, w, -1.3888888888888889e-03f);  // -1/6!
+  pc = fmaf(pc, w, 4.1666666666666667e-02f);   // 1/4!
+  pc = fmaf(pc, w, -0.5f);                     // -1/2!
+  c = fmaf(pc, w, 1.0f);
+}
+
+// Sum a float over the warp in FP64 (all lanes get the total).
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum_f32(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace rb

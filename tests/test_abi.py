@@ -1,0 +1,77 @@
+"""The C ABI library loads without a GPU, exports exactly what include/rb.h
+declares, and rejects malformed arguments on the host before touching CUDA."""
+import ctypes
+import re
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2404_11397_gb300 import _lib
+    if not _lib.LIB_PATH.exists():
+        from paper_2404_11397_gb300 import build
+        build.build()
+    return _lib.load()
+
+
+def _declared():
+    src = (ROOT / "include" / "rb.h").read_text()
+    return sorted(set(re.findall(r"RB_API\s+[\w\s\*]+?\b(rb_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("rb_build_summary", "rb_event_free", "rb_loglike_batch", "rb_loglike_grad_batch", "rb_submit",
+                     "rb_poll", "rb_server_create", "rb_strerror"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2404_11397_gb300 import _lib
+    for name in _declared():
+        assert hasattr(lib, name), name
+        assert name in _lib.SIGNATURES, f"{name} missing from the Python binding"
+
+
+def test_status_strings_and_version(lib):
+    assert lib.rb_abi_version() == 1
+    assert lib.rb_strerror(0) == b"ok"
+    assert lib.rb_strerror(-5).startswith(b"busy")
+    assert lib.rb_strerror(12345) == b"unknown status"
+
+
+def test_host_side_validation(lib):
+    from paper_2404_11397_gb300 import _lib
+    h = ctypes.c_void_p()
+    assert lib.rb_build_summary(None, ctypes.byref(h)) == _lib.RB_EINVAL
+    desc = _lib.EventDesc()
+    desc.n_det = 0
+    assert lib.rb_build_summary(ctypes.byref(desc), ctypes.byref(h)) == _lib.RB_EINVAL
+    assert b"n_det" in lib.rb_last_error()
+    desc.n_det, desc.n_bins, desc.T, desc.f_low, desc.f_high = 1, 10, 4.0, 20.0, 10.0
+    assert lib.rb_build_summary(ctypes.byref(desc), ctypes.byref(h)) == _lib.RB_EINVAL  # f_high < f_low
+    desc.f_high, desc.n_bins = 30.0, 100  # 41 grid points < 101 edges
+    assert lib.rb_build_summary(ctypes.byref(desc), ctypes.byref(h)) == _lib.RB_EINVAL
+    assert b"n_bins" in lib.rb_last_error()
+    assert lib.rb_loglike_batch(None, None, 4, None, 0, None) == _lib.RB_EINVAL
+    assert lib.rb_loglike_grad_batch(None, None, 4, None, None, 0, None) == _lib.RB_EINVAL
+    assert lib.rb_event_rebuild(None, None, None, None, 0, None) == _lib.RB_EINVAL
+    assert lib.rb_event_free(None) == _lib.RB_OK
+    t = ctypes.c_uint64()
+    th = np.zeros(13)
+    assert lib.rb_submit(None, None, th.ctypes.data_as(_lib.c_double_p), 1, 1, ctypes.byref(t)) == _lib.RB_EINVAL
+    assert lib.rb_poll(None, 1, 0, None, None) == _lib.RB_EINVAL
+    assert lib.rb_server_get_stats(None, None) == _lib.RB_EINVAL
+
+
+def test_package_fails_loudly_without_library(monkeypatch, tmp_path):
+    from paper_2404_11397_gb300 import _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_PATH", tmp_path / "librb.so")
+    with pytest.raises(RuntimeError, match="missing"):
+        _lib.load()

@@ -1,0 +1,293 @@
+"""GPU path (librb, through the C ABI) vs the FP64 oracle on the same seeded inputs.
+
+Tolerances (stated in the library's design notes):
+* bin edges: bit-exact (integer work);
+* summary data A0, A1, B0, B1 (FP64 on both sides): 1e-9 of the largest |entry| per detector;
+* log L, mixed precision: |dlogL| <= max(1e-3, 2e-6 (|<d|h>| + <h|h>/2));
+  FP64 path: 1e-9 of the same scale (plus 1e-8 absolute);
+* gradient: |dg_j| <= 1e-4 max(|g_j|, 1e-2 max_j |g_j|)  (mixed), 1e-8 (FP64);
+* at the fiducial point every mode returns the FP64 constant exactly.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests._events import inject
+
+pytestmark = pytest.mark.gpu
+
+MODES = ("mixed", "mixed_f64phase", "fp64")
+
+
+@pytest.fixture(scope="module")
+def rb():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    import paper_2404_11397_gb300 as m
+    m.load()
+    return m
+
+
+def _terms(ev, s, theta):
+    """Oracle RB log L, <d|h> and <h|h> (the latter from the data-free summary)."""
+    zero = dict(s)
+    zero["A0"] = np.zeros_like(s["A0"])
+    zero["A1"] = np.zeros_like(s["A1"])
+    hh = -2.0 * oracle.loglike_rb(ev, zero, theta)
+    L = oracle.loglike_rb(ev, s, theta)
+    return L, L + 0.5 * hh, hh
+
+
+def _tol(mode, dh, hh):
+    scale = np.abs(dh) + 0.5 * hh
+    if mode == "fp64":
+        return 1e-9 * scale + 1e-8
+    return np.maximum(1e-3, 2e-6 * scale)
+
+
+def _gtol(mode, g):
+    rel = 1e-8 if mode == "fp64" else 1e-4
+    return rel * np.maximum(np.abs(g), 1e-2 * np.max(np.abs(g), axis=1, keepdims=True))
+
+
+class Case:
+    def __init__(self, rb, cfg, n_bins=None, **kw):
+        self.ev = inject(synth.make_event(cfg, **kw))
+        self.n_bins = n_bins or self.ev["n_bins"]
+        self.edges = oracle.bin_edges(self.ev, self.n_bins)
+        self.s = oracle.summary(self.ev, self.ev["theta_inj"], self.edges)
+        self.event = rb.Event.from_synth(self.ev, n_bins=self.n_bins)
+
+
+@pytest.fixture(scope="module")
+def c1(rb):
+    return Case(rb, "C1")
+
+
+@pytest.fixture(scope="module")
+def c2(rb):
+    return Case(rb, "C2")
+
+
+@pytest.fixture(scope="module")
+def small(rb):
+    # a few thousand grid points, 3 detectors, 45 bins (several 31-bin chunks + a ragged tail)
+    return Case(rb, "C2", n_bins=45, T=8.0, f_low=20.0, f_high=512.0)
+
+
+def test_grid_and_info(rb, c1, c2):
+    for c in (c1, c2):
+        inf = c.event.info()
+        assert inf["n_freq"] == c.ev["N"] and inf["kmin"] == c.ev["kmin"]
+        assert inf["n_bins"] == c.n_bins and inf["n_det"] == c.ev["geom"].shape[0]
+
+
+@pytest.mark.parametrize("cfg,n_bins,kw", [("C1", None, {}), ("C2", None, {}), ("C2", 45, dict(T=8.0, f_high=512.0)),
+                                           ("C4", None, {}), ("C2", 1, dict(T=4.0, f_high=256.0)),
+                                           ("C2", 1000, dict(T=16.0))])
+def test_bin_edges_bit_exact(rb, cfg, n_bins, kw):
+    ev = inject(synth.make_event(cfg, **kw))
+    B = n_bins or ev["n_bins"]
+    event = rb.Event.from_synth(ev, n_bins=B)
+    np.testing.assert_array_equal(event.summary()["edges"], oracle.bin_edges(ev, B))
+    event.free()
+
+
+def test_bin_edges_one_point_per_bin(rb):
+    ev = inject(synth.make_event("C2", T=1.0, f_low=30.0, f_high=94.0))
+    event = rb.Event.from_synth(ev, n_bins=ev["N"] - 1)
+    np.testing.assert_array_equal(event.summary()["edges"], np.arange(ev["N"]))
+
+
+def test_summary_data_matches_oracle(rb, c1, c2, small):
+    for c in (c1, c2, small):
+        g = c.event.summary()
+        for key in ("A0", "A1", "B0", "B1"):
+            ref = c.s[key]
+            scale = np.max(np.abs(ref), axis=1, keepdims=True)
+            assert np.all(np.abs(g[key] - ref) <= 1e-9 * scale), key
+
+
+def test_strain_kernel_matches_oracle(rb, c2):
+    ev = c2.ev
+    th = synth.draw_prior(synth.PRIOR_GW170817, 3, seed=21)
+    for w in range(3):
+        for d in range(3):
+            h = rb.strain(ev["geom"][d], ev["gmst"], th[w], ev["T"], ev["kmin"], ev["N"]).cpu().numpy()
+            ref = oracle.strain(th[w], ev["geom"][d], ev["gmst"], ev["f"])
+            assert np.max(np.abs(h - ref)) <= 1e-9 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_exact_at_reference(rb, c1, c2, small, mode):
+    for c in (c1, c2, small):
+        th = torch.tensor(np.tile(c.ev["theta_inj"], (33, 1)), device="cuda")
+        L = rb.loglike(c.event, th, mode=mode).cpu().numpy()
+        Lg, G = rb.loglike_grad(c.event, th, mode=mode)
+        base = c.event.info()["base_logl"]
+        assert np.all(L == base) and np.all(Lg.cpu().numpy() == base)
+        full = oracle.loglike_full(c.ev, c.ev["theta_inj"])[0]
+        assert abs(base - full) <= 1e-9 * abs(full)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_loglike_box_walkers(rb, c1, small, mode):
+    for c, W in ((c1, 1000), (small, 777)):
+        th = synth.walkers("C1", W) if c is c1 else synth.draw_box(c.ev["theta_inj"], W, seed=31, rel=0.01,
+                                                                   abs_width=1e-2 * synth.PRIOR_WIDTH)
+        L = rb.loglike(c.event, torch.tensor(th, device="cuda"), mode=mode).cpu().numpy()
+        ref, dh, hh = _terms(c.ev, c.s, th)
+        err = np.abs(L - ref)
+        assert np.all(err <= _tol(mode, dh, hh)), (mode, err.max())
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_loglike_posterior_scale(rb, c1, c2, mode):
+    for c in (c1, c2):
+        th = synth.posterior_box(c.ev["theta_inj"], 256, seed=41)
+        L = rb.loglike(c.event, torch.tensor(th, device="cuda"), mode=mode).cpu().numpy()
+        ref, dh, hh = _terms(c.ev, c.s, th)
+        assert np.all(np.abs(L - ref) <= _tol(mode, dh, hh))
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_loglike_prior_draws_full_batch(rb, c2, mode):
+    """C2 at its full size (4096 prior draws, the benchmark's launch), every walker checked."""
+    th = synth.walkers("C2")
+    L = rb.loglike(c2.event, torch.tensor(th, device="cuda"), mode=mode).cpu().numpy()
+    ref, dh, hh = _terms(c2.ev, c2.s, th)
+    err = np.abs(L - ref)
+    assert np.all(err <= _tol(mode, dh, hh)), (mode, err.max())
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_gradient_matches_oracle(rb, c1, small, mode):
+    for c, W in ((c1, 64), (small, 40)):
+        th = synth.draw_box(c.ev["theta_inj"], W, seed=51, rel=3e-3, abs_width=3e-3 * synth.PRIOR_WIDTH)
+        L, G = rb.loglike_grad(c.event, torch.tensor(th, device="cuda"), mode=mode)
+        ref_L, ref_G = oracle.loglike_rb(c.ev, c.s, th, grad=True)
+        _, dh, hh = _terms(c.ev, c.s, th)
+        assert np.all(np.abs(L.cpu().numpy() - ref_L) <= _tol(mode, dh, hh))
+        G = G.cpu().numpy()
+        bad = np.abs(G - ref_G) > _gtol(mode, ref_G)
+        assert not bad.any(), (mode, np.argwhere(bad)[:5], (np.abs(G - ref_G) / _gtol(mode, ref_G) * 1e-4).max())
+
+
+def test_gradient_prior_draws(rb, c2):
+    th = synth.walkers("C2", 4096)[:48]
+    for mode in MODES:
+        L, G = rb.loglike_grad(c2.event, torch.tensor(th, device="cuda"), mode=mode)
+        ref_L, ref_G = oracle.loglike_rb(c2.ev, c2.s, th, grad=True)
+        G = G.cpu().numpy()
+        assert np.all(np.abs(G - ref_G) <= _gtol(mode, ref_G) * (1 if mode == "fp64" else 10)), mode
+
+
+def test_fp64_gradient_vs_finite_differences(rb, small):
+    th0 = synth.draw_box(small.ev["theta_inj"], 4, seed=61, rel=3e-3, abs_width=3e-3 * synth.PRIOR_WIDTH)
+    _, G = rb.loglike_grad(small.event, torch.tensor(th0, device="cuda"), mode="fp64")
+    G = G.cpu().numpy()
+    for j in range(13):
+        h = 1e-6 * np.maximum(np.abs(th0[:, j]), synth.PRIOR_WIDTH[j])
+
+        def cd(step):
+            tp, tm = th0.copy(), th0.copy()
+            tp[:, j] += step
+            tm[:, j] -= step
+            Lp = rb.loglike(small.event, torch.tensor(tp, device="cuda"), mode="fp64").cpu().numpy()
+            Lm = rb.loglike(small.event, torch.tensor(tm, device="cuda"), mode="fp64").cpu().numpy()
+            return (Lp - Lm) / (2 * step)
+        fd = (4 * cd(h / 2) - cd(h)) / 3
+        scale = np.maximum(np.abs(G[:, j]), 1e-2 * np.max(np.abs(G), axis=1))
+        assert np.all(np.abs(fd - G[:, j]) <= 1e-6 * scale), j
+
+
+def test_unphysical_walkers(rb, small):
+    th = np.tile(small.ev["theta_inj"], (6, 1))
+    th[0, 1] = 1.5
+    th[1, 1] = -0.1
+    th[2, 6] = 0.0
+    th[3, 0] = np.nan
+    th[4, 11] = np.inf
+    for mode in MODES:
+        L, G = rb.loglike_grad(small.event, torch.tensor(th, device="cuda"), mode=mode)
+        L, G = L.cpu().numpy(), G.cpu().numpy()
+        assert np.all(np.isneginf(L[:5])) and np.isfinite(L[5])
+        assert np.all(G[:5] == 0.0)
+
+
+def test_edge_cases_batch_shapes(rb, small):
+    th = synth.draw_box(small.ev["theta_inj"], 70, seed=71, rel=1e-3, abs_width=1e-3 * synth.PRIOR_WIDTH)
+    full = rb.loglike(small.event, torch.tensor(th, device="cuda")).cpu().numpy()
+    # W = 0 is a no-op; W = 1 and ragged W give the same per-walker values (warp per walker)
+    empty = rb.loglike(small.event, torch.zeros(0, 13, dtype=torch.float64, device="cuda"))
+    assert empty.numel() == 0
+    one = rb.loglike(small.event, torch.tensor(th[5:6], device="cuda")).cpu().numpy()
+    assert one[0] == full[5]
+    part = rb.loglike(small.event, torch.tensor(th[3:40], device="cuda")).cpu().numpy()
+    np.testing.assert_array_equal(part, full[3:40])
+
+
+def test_one_bin_and_one_point_per_bin(rb):
+    for n_bins, kw in ((1, dict(T=4.0, f_high=256.0)), (None, dict(T=1.0, f_low=30.0, f_high=94.0))):
+        ev = inject(synth.make_event("C2", **kw))
+        B = n_bins or ev["N"] - 1
+        edges = oracle.bin_edges(ev, B)
+        s = oracle.summary(ev, ev["theta_inj"], edges)
+        event = rb.Event.from_synth(ev, n_bins=B)
+        th = synth.draw_box(ev["theta_inj"], 50, seed=81, rel=0.01, abs_width=1e-2 * synth.PRIOR_WIDTH)
+        for mode in MODES:
+            L = rb.loglike(event, torch.tensor(th, device="cuda"), mode=mode).cpu().numpy()
+            ref, dh, hh = _terms(ev, s, th)
+            assert np.all(np.abs(L - ref) <= _tol(mode, dh, hh)), (B, mode)
+        event.free()
+
+
+def test_heavy_config_full_size_sampled(rb):
+    """C4 (T = 256 s, 1000 bins, 16384 walkers) in one launch; 256 sampled walkers vs the oracle."""
+    ev = inject(synth.make_event("C4"))
+    edges = oracle.bin_edges(ev, 1000)
+    event = rb.Event.from_synth(ev, n_bins=1000)
+    np.testing.assert_array_equal(event.summary()["edges"], edges)
+    s = oracle.summary(ev, ev["theta_inj"], edges)
+    th = synth.walkers("C4")
+    L, G = rb.loglike_grad(event, torch.tensor(th, device="cuda"), mode="mixed")
+    idx = np.linspace(0, th.shape[0] - 1, 256).astype(int)
+    ref, dh, hh = _terms(ev, s, th[idx])
+    assert np.all(np.abs(L.cpu().numpy()[idx] - ref) <= _tol("mixed", dh, hh))
+    _, ref_G = oracle.loglike_rb(ev, s, th[idx[:16]], grad=True)
+    assert np.all(np.abs(G.cpu().numpy()[idx[:16]] - ref_G) <= 10 * _gtol("mixed", ref_G))
+    event.free()
+
+
+def test_autograd_function(rb, small):
+    th = torch.tensor(synth.draw_box(small.ev["theta_inj"], 16, seed=91, rel=1e-3,
+                                     abs_width=1e-3 * synth.PRIOR_WIDTH), device="cuda", requires_grad=True)
+    L = rb.rb_loglike(th, small.event, "mixed")
+    w = torch.linspace(0.5, 2.0, 16, dtype=torch.float64, device="cuda")
+    (L * w).sum().backward()
+    _, G = rb.loglike_grad(small.event, th.detach(), mode="mixed")
+    torch.testing.assert_close(th.grad, w[:, None] * G, rtol=0, atol=0)
+
+
+def test_host_entry_point_matches_device(rb, small):
+    th = synth.draw_box(small.ev["theta_inj"], 100, seed=101, rel=1e-3, abs_width=1e-3 * synth.PRIOR_WIDTH)
+    Ld, Gd = rb.loglike_grad(small.event, torch.tensor(th, device="cuda"), mode="mixed")
+    Lh = np.zeros(100)
+    Gh = np.zeros((100, 13))
+    rb.loglike_grad_host(small.event, th, Lh, Gh, mode="mixed")
+    np.testing.assert_array_equal(Lh, Ld.cpu().numpy())
+    np.testing.assert_array_equal(Gh, Gd.cpu().numpy())
+
+
+def test_library_errors(rb, small):
+    with pytest.raises(rb.RBError) as e:
+        rb.loglike(small.event, torch.zeros(4, 13, dtype=torch.float64, device="cuda"), mode=7)
+    assert e.value.status == rb.RB_EINVAL
+    ev = dict(small.ev)
+    with pytest.raises(rb.RBError):
+        rb.Event.from_synth(ev, n_bins=ev["N"])  # more bins than grid intervals
+    bad = np.array(ev["theta_inj"])
+    bad[1] = 2.0
+    with pytest.raises(rb.RBError):
+        rb.Event.from_synth(ev, n_bins=10, theta_ref=bad)
