@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--profile", action="store_true",
+                   help="fixed short warm-up and no extra legs (for profiler launch lists)")
     return p.parse_args()
 
 
@@ -211,7 +213,7 @@ def run_gb300(args, dist: Dist):
     import ctypes
 
     def step(mode):
-        event.rebuild(data=data_rows, psd=psd_rows)
+        event.rebuild(data=data_rows, psd=psd_rows, mode=mode)
         rc = lib.rb_loglike_grad_batch(event.handle, ctypes.c_void_p(theta.data_ptr()), W,
                                        ctypes.c_void_p(logl.data_ptr()), ctypes.c_void_p(grad.data_ptr()),
                                        rb.MODES[mode], ctypes.c_void_p(stream.cuda_stream))
@@ -254,7 +256,7 @@ def run_gb300(args, dist: Dist):
         step(args.mode)
     sampler.start()
     t0 = time.perf_counter()
-    while time.perf_counter() - t0 < 0.5:
+    while not args.profile and time.perf_counter() - t0 < 0.5:
         step(args.mode)
         torch.cuda.synchronize()
     step_ms, main_ms, launches = timed(args.mode, args.steps, 0)
@@ -317,7 +319,7 @@ def run_e2e(rb, torch, event, ev, data, psd, theta, W, args, dist, device):
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
     def step():
-        rc = lib.rb_event_rebuild(event.handle, None, dp, pp, 0, stream)
+        rc = lib.rb_event_rebuild(event.handle, None, dp, pp, 0, rb.MODES[args.mode], stream)
         if rc == 0:
             rc = lib.rb_loglike_grad_host(event.handle, ctypes.c_void_p(h_theta.data_ptr()), W,
                                           ctypes.c_void_p(h_logl.data_ptr()), ctypes.c_void_p(h_grad.data_ptr()),
@@ -496,6 +498,8 @@ def run_reference(args, dist: Dist):
 
 def main():
     args = parse()
+    if args.profile:
+        args.no_e2e = args.no_cpu = args.no_serving = args.no_fp64 = True
     dist = Dist()
     if args.impl == "reference":
         dist.init("gloo")

@@ -139,13 +139,18 @@ RB_API int rb_event_free(rb_event_t ev);
  * ([n_freq]) for d < n_det, or both NULL to reuse the event's resident copy;
  * with data_on_device = 1 they are device pointers read in place (no copy,
  * they must stay valid until the stream reaches the rebuild), otherwise host
- * pointers copied into the event.  Asynchronous on `stream`, allocates
- * nothing; batch calls ordered after it on the same stream see the new
- * tables, and the caller must not run batches of this event concurrently on
- * other streams.  Errors: RB_EINVAL (NULL event, only one of data/psd,
- * unphysical theta_ref), RB_ECUDA. */
+ * pointers copied into the event.  mode RB_FP64: the summary sums are formed
+ * in FP64 (as rb_build_summary does); RB_MIXED / RB_MIXED_F64PHASE: the
+ * fiducial phase is expanded in a Taylor series per 32-point chunk of the
+ * grid (coefficients in FP64) and every grid point is evaluated in FP32 and
+ * float-pair arithmetic, which keeps the build bound by memory bandwidth
+ * (used when T f_low >= 1024, otherwise the FP64 sums are used).
+ * Asynchronous on `stream`, allocates nothing; batch calls ordered after it
+ * on the same stream see the new tables, and the caller must not run batches
+ * of this event concurrently on other streams.  Errors: RB_EINVAL (NULL
+ * event, only one of data/psd, unphysical theta_ref, bad mode), RB_ECUDA. */
 RB_API int rb_event_rebuild(rb_event_t ev, const double* theta_ref_host, const double* const* data,
-                            const double* const* psd, int data_on_device, void* stream);
+                            const double* const* psd, int data_on_device, int mode, void* stream);
 
 RB_API int rb_event_get_info(rb_event_t ev, rb_event_info* info);
 

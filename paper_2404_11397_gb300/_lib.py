@@ -55,7 +55,7 @@ SIGNATURES = {
     "rb_build_summary": (ctypes.c_int, [ctypes.POINTER(EventDesc), ctypes.POINTER(ctypes.c_void_p)]),
     "rb_event_free": (ctypes.c_int, [ctypes.c_void_p]),
     "rb_event_rebuild": (ctypes.c_int, [ctypes.c_void_p, c_double_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
-                                        ctypes.c_void_p]),
+                                        ctypes.c_int, ctypes.c_void_p]),
     "rb_event_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(EventInfo)]),
     "rb_event_get_summary": (ctypes.c_int, [ctypes.c_void_p, c_double_p, c_double_p, c_double_p, c_double_p,
                                             c_int64_p]),

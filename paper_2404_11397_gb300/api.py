@@ -94,7 +94,7 @@ class Event:
             raise RuntimeError("event has been freed")
         return self._h
 
-    def rebuild(self, theta_ref=None, data=None, psd=None, stream=None) -> None:
+    def rebuild(self, theta_ref=None, data=None, psd=None, mode="mixed", stream=None) -> None:
         """Recompute the summary data in place (asynchronous, allocation-free).
 
         data/psd: per-detector CUDA tensors (read in place), host numpy arrays
@@ -125,7 +125,8 @@ class Event:
                     ps = np.ascontiguousarray(psd[d], dtype=np.float64)
                     dp[d], pp[d] = dd.ctypes.data, ps.ctypes.data
                 keep += [dd, ps]
-        check(lib.rb_event_rebuild(self.handle, th_p, dp, pp, on_dev, _stream_handle(stream)), "rb_event_rebuild")
+        check(lib.rb_event_rebuild(self.handle, th_p, dp, pp, on_dev, _mode(mode), _stream_handle(stream)),
+              "rb_event_rebuild")
 
     def info(self) -> dict:
         lib = load()

@@ -36,6 +36,10 @@ cudaError_t launch_tables(int64_t kmin, double T, int D, int B, int Ep, int Bp, 
                           const double* summ, float* tab32, size_t edge32_floats, double* tab64, double* base,
                           cudaStream_t s);
 cudaError_t launch_strain(const RefValues* src, int64_t kmin, int64_t N, double T, double* h, cudaStream_t s);
+cudaError_t launch_summary_fast(const DataPtrs& in, int64_t kmin, int64_t N, double T, int D, int B,
+                                const int64_t* edges, const RefValues* ref, void* chunk_scratch, double* out,
+                                cudaStream_t s);
+size_t chunk_scratch_bytes(int64_t N);
 
 // ---- diagnostics ----
 static thread_local char g_err[512] = "no error";
@@ -146,6 +150,7 @@ int rb_event_free(rb_event_t ev) {
   cudaFree(e.d_data);
   cudaFree(e.d_psd);
   cudaFree(e.d_theta_ref);
+  cudaFree(e.d_chunks);
   delete ev;
   return RB_OK;
 }
@@ -228,7 +233,8 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
         {(void**)&e.d_base, sizeof(double), "base"},
         {(void**)&e.d_data, sizeof(double) * 2 * D * N, "strain"},
         {(void**)&e.d_psd, sizeof(double) * D * N, "psd"},
-        {(void**)&e.d_theta_ref, sizeof(double) * kNPar, "theta_ref"}};
+        {(void**)&e.d_theta_ref, sizeof(double) * kNPar, "theta_ref"},
+        {(void**)&e.d_chunks, chunk_scratch_bytes(N), "chunk coefficients"}};
     for (auto& a : allocs) {
       if ((err = cudaMalloc(a.p, a.n)) != cudaSuccess) { rc = cuda_fail(err, a.what); break; }
       e.device_bytes += a.n;
@@ -257,7 +263,7 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
     if ((err = cudaMemcpyAsync(e.d_theta_ref, e.theta_ref, sizeof(double) * kNPar, cudaMemcpyHostToDevice, s)) != cudaSuccess) { rc = cuda_fail(err, "copy theta_ref"); break; }
     if ((err = launch_bin_edges(e.f_low, e.f_high, e.T, kmin, N, B, e.d_edges, s)) != cudaSuccess) { rc = cuda_fail(err, "bin edge kernels"); break; }
     count_launches(2);
-    if ((rc = rebuild_event(e, nullptr, s)) != RB_OK) break;
+    if ((rc = rebuild_event(e, nullptr, RB_FP64, s)) != RB_OK) break;
     if ((err = cudaStreamSynchronize(s)) != cudaSuccess) { rc = cuda_fail(err, "build synchronise"); break; }
   } while (false);
   if (rc != RB_OK) {
@@ -270,8 +276,9 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
 }
 
 int rb_event_rebuild(rb_event_t ev, const double* theta_ref_host, const double* const* data, const double* const* psd,
-                     int data_on_device, void* stream) {
+                     int data_on_device, int mode, void* stream) {
   if (!ev) return set_error(RB_EINVAL, "rb_event_rebuild: NULL event");
+  if (mode != RB_MIXED && mode != RB_FP64 && mode != RB_MIXED_F64PHASE) return set_error(RB_EINVAL, "rb_event_rebuild: bad mode %d", mode);
   EventEntry& e = ev->e;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t err;
@@ -303,7 +310,7 @@ int rb_event_rebuild(rb_event_t ev, const double* theta_ref_host, const double* 
       }
     }
   }
-  return rebuild_event(e, have ? &in : nullptr, s);
+  return rebuild_event(e, have ? &in : nullptr, mode, s);
 }
 
 void rb_set_trace_events(void* before_main, void* after_main) { set_trace_events(before_main, after_main); }
@@ -409,7 +416,7 @@ int rb_strain(const double* geom, double gmst, const double* theta_host, double 
 
 namespace rb {
 
-int rebuild_event(EventEntry& e, const DataPtrs* in_opt, cudaStream_t s) {
+int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t s) {
   cudaError_t err;
   DataPtrs in{};
   if (in_opt) {
@@ -421,8 +428,13 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, cudaStream_t s) {
     }
   }
   if ((err = launch_ref_values(e.d_theta_ref, e.ec, e.d_ref, s)) != cudaSuccess) return cuda_fail(err, "reference values kernel");
-  if ((err = launch_summary(in, e.kmin, e.N, e.T, e.n_det, e.n_bins, e.d_edges, e.d_ref, e.d_summ, s)) != cudaSuccess)
-    return cuda_fail(err, "summary kernel");
+  const bool fast = mode != RB_FP64 && e.kmin >= 1024;
+  if (fast)
+    err = launch_summary_fast(in, e.kmin, e.N, e.T, e.n_det, e.n_bins, e.d_edges, e.d_ref, e.d_chunks, e.d_summ, s);
+  else
+    err = launch_summary(in, e.kmin, e.N, e.T, e.n_det, e.n_bins, e.d_edges, e.d_ref, e.d_summ, s);
+  if (err != cudaSuccess) return cuda_fail(err, "summary kernel");
+  if (fast) count_launches(1);
   if ((err = launch_tables(e.kmin, e.T, e.n_det, e.n_bins, e.dev.e_pad, e.dev.b_pad, e.d_edges, e.d_summ, e.d_tab32,
                            e.dev.edge32_floats, e.d_tab64, e.d_base, s)) != cudaSuccess)
     return cuda_fail(err, "table kernels");

@@ -27,6 +27,7 @@ struct EventEntry {
   double* d_data = nullptr;   // resident strain [D][N][2]
   double* d_psd = nullptr;    // resident PSD [D][N]
   double* d_theta_ref = nullptr;
+  void* d_chunks = nullptr;   // per-chunk Taylor coefficients of the fast summary build
   size_t device_bytes = 0;
   uint64_t uid = 0;  // unique per built event (never reused within a process)
 };
@@ -49,7 +50,9 @@ int run_batch(const EventEntry* e, const double* theta, int64_t W, double* logl,
 // Fiducial values, summary data, tables and base of an event from the given
 // device strain/PSD (NULL: the event's resident copy); no allocation, no
 // synchronisation.
-int rebuild_event(EventEntry& e, const DataPtrs* in, cudaStream_t s);
+// mode RB_FP64 uses the FP64 summary kernel; the mixed modes use the fast
+// Taylor-chunk kernel when T f_low >= 1024 (FP64 kernel otherwise).
+int rebuild_event(EventEntry& e, const DataPtrs* in, int mode, cudaStream_t s);
 
 // Events recorded on the launch stream right before / after the main
 // likelihood kernel of every batch (NULL disables).

@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(128) k_setup_mixed(const double* __restrict__ 
   double th[kNPar];
   load_theta(theta, w, th);
   Values v;
-  walker_values(th, ec, 0, v);
+  walker_values(th, ec, 1, v);
   WalkerMixed o;
   o.valid = v.valid;
   o.pad[0] = o.pad[1] = o.pad[2] = 0;
@@ -326,26 +326,28 @@ __global__ void __launch_bounds__(128) k_setup_mixed(const double* __restrict__ 
       o.dc_hi[k] = c.hi;
       o.dc_lo[k] = c.lo;
     }
-    const float dphi0 = (float)wrap_pi(v.phi0 - r.phi0);
-    float sp, cp;
-    sincosf(dphi0, &sp, &cp);
-    const float ampr = (float)(v.amp / r.amp);
+    // The prefactor ratio is formed in FP64: F+ = D:(XX - YY) cancels, and
+    // an FP32 antenna pattern can be off by ~1e-7 absolute, i.e. up to ~1e-5
+    // relative, which moves log L by ~1e-3 at SNR ~ 100.
+    double sp, cp;
+    sincos(wrap_pi(v.phi0 - r.phi0), &sp, &cp);
+    const double ampr = v.amp / r.amp;
     for (int d = 0; d < kMaxDet; ++d) {
       if (d < ec.n_det) {
         f2x t = f2x_from(v.tau[d] - r.tau[d]);
         o.tau_hi[d] = t.hi;
         o.tau_lo[d] = t.lo;
         // Q = ampr P e^{-i dphi0};  rho = Q / P_ref;  sig = (Q - P_ref) / P_ref
-        const float pr = v.P32[d][0], pi = v.P32[d][1];
-        const float qr = ampr * (pr * cp + pi * sp);
-        const float qi = ampr * (pi * cp - pr * sp);
-        const float rr = r.P32[d][0], ri = r.P32[d][1];
-        const float den = rr * rr + ri * ri;
-        o.rho[d][0] = (qr * rr + qi * ri) / den;
-        o.rho[d][1] = (qi * rr - qr * ri) / den;
-        const float er = qr - rr, ei = qi - ri;
-        o.sig[d][0] = (er * rr + ei * ri) / den;
-        o.sig[d][1] = (ei * rr - er * ri) / den;
+        const double pr = v.P64[d][0], pi = v.P64[d][1];
+        const double qr = ampr * (pr * cp + pi * sp);
+        const double qi = ampr * (pi * cp - pr * sp);
+        const double rr = r.P64[d][0], ri = r.P64[d][1];
+        const double den = rr * rr + ri * ri;
+        o.rho[d][0] = (float)((qr * rr + qi * ri) / den);
+        o.rho[d][1] = (float)((qi * rr - qr * ri) / den);
+        const double er = qr - rr, ei = qi - ri;
+        o.sig[d][0] = (float)((er * rr + ei * ri) / den);
+        o.sig[d][1] = (float)((ei * rr - er * ri) / den);
       } else {
         o.tau_hi[d] = o.tau_lo[d] = 0.f;
         o.rho[d][0] = o.rho[d][1] = o.sig[d][0] = o.sig[d][1] = 0.f;

@@ -60,7 +60,7 @@ def test_host_side_validation(lib):
     assert b"n_bins" in lib.rb_last_error()
     assert lib.rb_loglike_batch(None, None, 4, None, 0, None) == _lib.RB_EINVAL
     assert lib.rb_loglike_grad_batch(None, None, 4, None, None, 0, None) == _lib.RB_EINVAL
-    assert lib.rb_event_rebuild(None, None, None, None, 0, None) == _lib.RB_EINVAL
+    assert lib.rb_event_rebuild(None, None, None, None, 0, 0, None) == _lib.RB_EINVAL
     assert lib.rb_event_free(None) == _lib.RB_OK
     t = ctypes.c_uint64()
     th = np.zeros(13)
