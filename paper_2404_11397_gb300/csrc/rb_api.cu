@@ -20,10 +20,8 @@ namespace rb {
 
 // ---- launchers defined in the kernel translation units ----
 cudaError_t launch_ref_values(const double* theta_ref_dev, const EventConst& ec, RefValues* out, cudaStream_t s);
-cudaError_t launch_setup_mixed(const double* theta, int64_t W, const EventConst& ec, const RefValues* ref,
-                               WalkerMixed* ws, WalkerTan<float>* tan, bool grad, cudaStream_t s);
-cudaError_t launch_setup_f64(const double* theta, int64_t W, const EventConst& ec, const RefValues* ref,
-                             WalkerF64* ws, void* tan, bool grad, bool tan_f32, cudaStream_t s);
+cudaError_t launch_setup(int mode, const double* theta, int64_t W, const EventConst& ec, const RefValues* ref,
+                         void* ws, void* tan, bool grad, cudaStream_t s);
 cudaError_t launch_rb_mixed(const EventDev& ev, const void* ws, const void* tan, int64_t W, double* logl,
                             double* grad, bool phase64, cudaStream_t s, int n_sm);
 cudaError_t launch_rb_f64(const EventDev& ev, const void* ws, const void* tan, int64_t W, double* logl, double* grad,
@@ -31,15 +29,16 @@ cudaError_t launch_rb_f64(const EventDev& ev, const void* ws, const void* tan, i
 cudaError_t launch_bin_edges(double f_low, double f_high, double T, int64_t kmin, int64_t N, int B, int64_t* edges,
                              cudaStream_t s);
 cudaError_t launch_summary(const DataPtrs& in, int64_t kmin, int64_t N, double T, int D, int B,
-                           const int64_t* edges, const RefValues* ref, double* out, cudaStream_t s);
-cudaError_t launch_tables(int64_t kmin, double T, int D, int B, int Ep, int Bp, const int64_t* edges,
-                          const double* summ, float* tab32, size_t edge32_floats, double* tab64, double* base,
-                          cudaStream_t s);
+                           const int64_t* edges, const RefValues* ref, const SummaryOut& so, cudaStream_t s);
+cudaError_t launch_edge_tables(int64_t kmin, double T, int D, int B, int Ep, int Bp, const int64_t* edges,
+                               float* tab32, size_t edge32_floats, double* tab64, double* inv_df, cudaStream_t s);
+cudaError_t launch_chunk_q(int64_t kmin, double T, int64_t N, void* cq, cudaStream_t s);
+size_t chunk_q_bytes(int64_t N);
+size_t chunk_coef_bytes(int64_t N);
 cudaError_t launch_strain(const RefValues* src, int64_t kmin, int64_t N, double T, double* h, cudaStream_t s);
-cudaError_t launch_summary_fast(const DataPtrs& in, int64_t kmin, int64_t N, double T, int D, int B,
-                                const int64_t* edges, const RefValues* ref, void* chunk_scratch, double* out,
+cudaError_t launch_summary_fast(const DataPtrs& in, int64_t N, double T, int D, int B, const int64_t* edges,
+                                const RefValues* ref, const void* cq, void* chunk_coef, const SummaryOut& so,
                                 cudaStream_t s);
-size_t chunk_scratch_bytes(int64_t N);
 
 // ---- diagnostics ----
 static thread_local char g_err[512] = "no error";
@@ -150,7 +149,11 @@ int rb_event_free(rb_event_t ev) {
   cudaFree(e.d_data);
   cudaFree(e.d_psd);
   cudaFree(e.d_theta_ref);
+  cudaFree(e.d_chunkq);
   cudaFree(e.d_chunks);
+  cudaFree(e.d_invdf);
+  cudaFree(e.d_share);
+  cudaFree(e.d_counter);
   delete ev;
   return RB_OK;
 }
@@ -234,7 +237,11 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
         {(void**)&e.d_data, sizeof(double) * 2 * D * N, "strain"},
         {(void**)&e.d_psd, sizeof(double) * D * N, "psd"},
         {(void**)&e.d_theta_ref, sizeof(double) * kNPar, "theta_ref"},
-        {(void**)&e.d_chunks, chunk_scratch_bytes(N), "chunk coefficients"}};
+        {(void**)&e.d_chunkq, chunk_q_bytes(N), "chunk matrices"},
+        {(void**)&e.d_chunks, chunk_coef_bytes(N), "chunk coefficients"},
+        {(void**)&e.d_invdf, sizeof(double) * B, "bin widths"},
+        {(void**)&e.d_share, sizeof(double) * D * B, "base shares"},
+        {(void**)&e.d_counter, sizeof(unsigned), "block counter"}};
     for (auto& a : allocs) {
       if ((err = cudaMalloc(a.p, a.n)) != cudaSuccess) { rc = cuda_fail(err, a.what); break; }
       e.device_bytes += a.n;
@@ -261,8 +268,11 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
     }
     if (rc != RB_OK) break;
     if ((err = cudaMemcpyAsync(e.d_theta_ref, e.theta_ref, sizeof(double) * kNPar, cudaMemcpyHostToDevice, s)) != cudaSuccess) { rc = cuda_fail(err, "copy theta_ref"); break; }
+    if ((err = cudaMemsetAsync(e.d_counter, 0, sizeof(unsigned), s)) != cudaSuccess) { rc = cuda_fail(err, "zero counter"); break; }
     if ((err = launch_bin_edges(e.f_low, e.f_high, e.T, kmin, N, B, e.d_edges, s)) != cudaSuccess) { rc = cuda_fail(err, "bin edge kernels"); break; }
-    count_launches(2);
+    if ((err = launch_edge_tables(kmin, e.T, D, B, Ep, Bp, e.d_edges, e.d_tab32, edge32, e.d_tab64, e.d_invdf, s)) != cudaSuccess) { rc = cuda_fail(err, "edge table kernel"); break; }
+    if ((err = launch_chunk_q(kmin, e.T, N, e.d_chunkq, s)) != cudaSuccess) { rc = cuda_fail(err, "chunk matrix kernel"); break; }
+    count_launches(4);
     if ((rc = rebuild_event(e, nullptr, RB_FP64, s)) != RB_OK) break;
     if ((err = cudaStreamSynchronize(s)) != cudaSuccess) { rc = cuda_fail(err, "build synchronise"); break; }
   } while (false);
@@ -430,15 +440,11 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
   if ((err = launch_ref_values(e.d_theta_ref, e.ec, e.d_ref, s)) != cudaSuccess) return cuda_fail(err, "reference values kernel");
   const bool fast = mode != RB_FP64 && e.kmin >= 1024;
   if (fast)
-    err = launch_summary_fast(in, e.kmin, e.N, e.T, e.n_det, e.n_bins, e.d_edges, e.d_ref, e.d_chunks, e.d_summ, s);
+    err = launch_summary_fast(in, e.N, e.T, e.n_det, e.n_bins, e.d_edges, e.d_ref, e.d_chunkq, e.d_chunks, e.out(), s);
   else
-    err = launch_summary(in, e.kmin, e.N, e.T, e.n_det, e.n_bins, e.d_edges, e.d_ref, e.d_summ, s);
+    err = launch_summary(in, e.kmin, e.N, e.T, e.n_det, e.n_bins, e.d_edges, e.d_ref, e.out(), s);
   if (err != cudaSuccess) return cuda_fail(err, "summary kernel");
-  if (fast) count_launches(1);
-  if ((err = launch_tables(e.kmin, e.T, e.n_det, e.n_bins, e.dev.e_pad, e.dev.b_pad, e.d_edges, e.d_summ, e.d_tab32,
-                           e.dev.edge32_floats, e.d_tab64, e.d_base, s)) != cudaSuccess)
-    return cuda_fail(err, "table kernels");
-  count_launches(4);
+  count_launches(fast ? 3 : 2);
   return RB_OK;
 }
 
@@ -478,12 +484,7 @@ int run_batch(const EventEntry* e, const double* theta, int64_t W, double* logl,
   const int n_sm = sm_count();
   cudaEvent_t tb = static_cast<cudaEvent_t>(g_trace_before.load());
   cudaEvent_t ta = static_cast<cudaEvent_t>(g_trace_after.load());
-  if (mode == RB_MIXED)
-    err = launch_setup_mixed(theta, W, e->ec, e->d_ref, static_cast<WalkerMixed*>(ws),
-                             static_cast<WalkerTan<float>*>(tan), want_grad, s);
-  else
-    err = launch_setup_f64(theta, W, e->ec, e->d_ref, static_cast<WalkerF64*>(ws), tan, want_grad,
-                           mode == RB_MIXED_F64PHASE, s);
+  err = launch_setup(mode, theta, W, e->ec, e->d_ref, ws, tan, want_grad, s);
   if (err == cudaSuccess && tb) err = cudaEventRecord(tb, s);
   if (err == cudaSuccess) {
     if (mode == RB_FP64)

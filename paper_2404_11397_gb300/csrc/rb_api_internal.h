@@ -27,9 +27,17 @@ struct EventEntry {
   double* d_data = nullptr;   // resident strain [D][N][2]
   double* d_psd = nullptr;    // resident PSD [D][N]
   double* d_theta_ref = nullptr;
-  void* d_chunks = nullptr;   // per-chunk Taylor coefficients of the fast summary build
+  void* d_chunkq = nullptr;   // event-constant per-chunk Taylor matrices (fast summary build)
+  void* d_chunks = nullptr;   // per-rebuild chunk coefficients (fast summary build)
+  double* d_invdf = nullptr;  // [B] 1 / bin width
+  double* d_share = nullptr;  // [D][B] per-bin shares of log L(theta_ref)
+  unsigned* d_counter = nullptr;
   size_t device_bytes = 0;
   uint64_t uid = 0;  // unique per built event (never reused within a process)
+  SummaryOut out() const {
+    return SummaryOut{d_summ, d_tab32 + dev.edge32_floats, d_tab64 + (size_t)(kNBasis + 1) * dev.e_pad, d_invdf,
+                      d_share, d_counter, d_base, dev.b_pad};
+  }
 };
 
 const EventEntry* event_entry(::rb_event_s* ev);

@@ -68,9 +68,14 @@ struct DataPtrs {
   const double* psd[kMaxDet];
 };
 
-// Fiducial (theta_ref) values of an event, written once by the set-up kernel.
+// Fiducial (theta_ref) values of an event, written by the reference kernel:
+// the FP64 values plus float-pair copies used by the FP32-pipe kernels.
 struct RefValues {
   Values v;
+  float chat[kNBasis][2];   // c_k / 2pi (turns), float pair
+  float phi0t[2];           // Phi0 / 2pi (turns), float pair
+  float taut[kMaxDet][2];   // tau_d [s], float pair
+  double K[kMaxDet][2];     // A_ref P_d: h0_d = K_d f^-7/6 exp(-2 pi i x_d(f))
 };
 
 // Per-walker set-up output for the mixed (float-float) path.
@@ -121,6 +126,18 @@ struct EventDev {
   // FP64 tables: g[k][e] (10*Ep), f[e] (Ep), then per detector 6 rows of Bp
   const double* tab64;
   const RefValues* ref;
+};
+
+// Outputs of the summary kernels (see summary_epilogue).
+struct SummaryOut {
+  double* summ;          // [D][B][6] FP64 summary: A0 re/im, A1 re/im, B0, B1
+  float* bin32;          // [D][6][Bp] bin tables (float)
+  double* bin64;         // [D][6][Bp] bin tables (FP64)
+  const double* inv_df;  // [B] 1 / (f_{b+1} - f_b)
+  double* share;         // [D][B] per-bin share of log L(theta_ref)
+  unsigned* counter;     // blocks finished; zero between builds
+  double* base;          // log L(theta_ref)
+  int Bp;
 };
 
 // ---------------------------------------------------------------------------

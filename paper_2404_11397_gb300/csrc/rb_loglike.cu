@@ -25,6 +25,10 @@
 // U - V from its own bin and U + V from the bin on its left (shuffle up); an
 // edge shared by two chunks collects the two halves in two passes, which is
 // exact because the adjoint is linear in the per-edge cotangent.
+#include <algorithm>
+#include <map>
+#include <mutex>
+
 #include "rb_internal.cuh"
 
 namespace rb {
@@ -405,18 +409,46 @@ size_t mixed_smem_bytes(const EventDev& ev, bool phase64) {
   return (size_t)(kNBasis + 1) * ev.e_pad * sizeof(double) + (ev.tab32_floats - ev.edge32_floats) * sizeof(float);
 }
 
+// Occupancy per (kernel, shared-memory size), cached: the query costs host
+// time on every launch otherwise.
+struct OccKey {
+  const void* fn;
+  size_t smem;
+  bool operator<(const OccKey& o) const { return fn < o.fn || (fn == o.fn && smem < o.smem); }
+};
+static std::mutex g_occ_mu;
+static std::map<OccKey, int> g_occ;
+
+static cudaError_t blocks_per_sm(const void* fn, int threads, size_t smem, int* out) {
+  {
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    auto it = g_occ.find({fn, smem});
+    if (it != g_occ.end()) {
+      *out = it->second;
+      return cudaSuccess;
+    }
+  }
+  cudaError_t err = cudaSuccess;
+  if (smem > 48 * 1024) err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  int n = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem);
+  if (err != cudaSuccess) return err;
+  std::lock_guard<std::mutex> lk(g_occ_mu);
+  g_occ[{fn, smem}] = n;
+  *out = n;
+  return cudaSuccess;
+}
+
 template <bool GRAD, bool PHASE64>
 static cudaError_t launch_mixed_t(const LaunchArgs& a, cudaStream_t s, int n_sm) {
   const size_t smem = mixed_smem_bytes(a.ev, PHASE64);
-  cudaError_t err = cudaFuncSetAttribute(k_rb_mixed<GRAD, PHASE64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-  if (err != cudaSuccess) return err;
+  const void* fn = reinterpret_cast<const void*>(k_rb_mixed<GRAD, PHASE64>);
   int per_sm = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rb_mixed<GRAD, PHASE64>, kThreads, smem);
+  cudaError_t err = blocks_per_sm(fn, kThreads, smem, &per_sm);
   if (err != cudaSuccess) return err;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const int64_t warps_needed = a.W;
-  const int64_t blocks_needed = (warps_needed * 32 + kThreads - 1) / kThreads;
+  const int64_t blocks_needed = (a.W * 32 + kThreads - 1) / kThreads;
   const int64_t grid = std::min<int64_t>(blocks_needed, (int64_t)per_sm * n_sm);
   k_rb_mixed<GRAD, PHASE64><<<(unsigned)grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();
@@ -434,8 +466,8 @@ cudaError_t launch_rb_f64(const EventDev& ev, const void* ws, const void* tan, i
   LaunchArgs a{ev, ws, tan, W, logl, grad};
   const int bs = 256;
   int per_sm = 0;
-  cudaError_t err = grad ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rb_f64<true>, bs, 0)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rb_f64<false>, bs, 0);
+  const void* fn = grad ? reinterpret_cast<const void*>(k_rb_f64<true>) : reinterpret_cast<const void*>(k_rb_f64<false>);
+  cudaError_t err = blocks_per_sm(fn, bs, 0, &per_sm);
   if (err != cudaSuccess) return err;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int64_t blocks_needed = (W * 32 + bs - 1) / bs;

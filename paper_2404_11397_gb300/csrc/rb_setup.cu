@@ -1,8 +1,6 @@
 // rb_setup.cu -- per-walker set-up (steps a1/a2): theta -> phase-basis
 // coefficients, constant phase, detector delays and complex prefactors, and
-// (for the gradient) their tangents.  One thread per walker: this is the only
-// FP64-heavy work of a batch, and on sm_103a the FP64 pipe is ~1/70 of the
-// FP32 rate, so it is spread over as many lanes as there are walkers.
+// (for the gradient) their tangents.
 //
 // Waveform (Sec. II.B; TaylorF2 from the PN literature cited there):
 //   h+ = A f^-7/6 (1+cos^2 i)/2 e^{-i Psi},  hx = -i A f^-7/6 cos i e^{-i Psi},
@@ -12,111 +10,152 @@
 // kappa = 1) terms, and 5PN/6PN tidal terms written per body (equivalent to
 // the Lambda-tilde / delta-Lambda-tilde form of the paper's appendix).
 // Detector response: h_d = (F+ h+ + Fx hx) e^{-2 pi i f dt_d}, dt_d = -n.r_d/c.
+//
+// On sm_103a an FP64 warp instruction occupies its SM sub-partition's FP64
+// unit for ~65 cycles whatever the number of active lanes, so what limits
+// this step is the number of FP64 instructions each warp issues.  A block
+// handles 32 walkers (one per lane) and splits each walker's FP64 work into
+// roles run by different warps, exchanging results through shared memory:
+//   phase 1  warp 0: ln(pi Mc), (pi Mc)^-5/3, (pi Mc)^1/3, Mc^5/6 / d_L
+//            warp 1: eta, ln eta, eta^-1/5
+//            warp 2: PN coefficients phi_k (polynomials in eta, X_i, chi_i, Lambda_i)
+//            warp 3: sky direction, detector delays tau_d = t_c + dt_d
+//            warp 4: polarisation and inclination sines/cosines
+//   phase 2  warp 0: basis coefficients c_k, constant phase Phi0, their
+//                    differences to the fiducial values, exp(-i dPhi0) - 1
+//            warps 1-3: antenna factor P_d = F+ (1+cos^2 i)/2 - i Fx cos i (FP64,
+//                    since F+ = D:(XX - YY) cancels)
+//            warp 4: delay differences
+//   phase 3  warps 1-3: prefactor ratio rho_d and rho_d - 1
+//   (gradient) warps 5, 6: tangents in FP32 (mixed) or FP64 dual numbers.
+// Every role is a noinline function, so a walker at theta_ref reproduces the
+// fiducial values bit for bit (the reference kernel runs the same roles).
+#include <type_traits>
+
+#include "rb.h"
 #include "rb_internal.cuh"
 
 namespace rb {
 
-// ---------------------------------------------------------------------------
-// Absolute per-source values.  noinline: one instruction sequence for every
-// caller, so theta == theta_ref reproduces the fiducial values bit for bit.
-// ---------------------------------------------------------------------------
-__device__ __noinline__ void walker_values(const double* th, const EventConst& ec, int need64, Values& out) {
-  const double Mc = th[0], q = th[1], chi1 = th[2], chi2 = th[3], L1 = th[4], L2 = th[5];
-  const double dL = th[6], tc = th[7], phic = th[8], iota = th[9], psi = th[10], ra = th[11], dec = th[12];
-  bool ok = true;
-  for (int j = 0; j < kNPar; ++j) ok = ok && isfinite(th[j]);
-  ok = ok && Mc > 0.0 && q > 0.0 && q <= 1.0 && dL > 0.0;
-  out.valid = ok ? 1 : 0;
-  if (!ok) return;
+constexpr int kSetupWalkers = 32;
+constexpr int kRoleThreads = 5 * 32;  // warps 0-4 take part in the FP64 phases
 
+// Barrier over the FP64-phase warps only (the tangent warps run on their own).
+__device__ __forceinline__ void roles_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kRoleThreads) : "memory"); }
+
+// ---------------------------------------------------------------------------
+// Roles (FP64).  noinline: one instruction sequence for every caller.
+// ---------------------------------------------------------------------------
+__device__ __noinline__ void role_mass(double Mc, double dL, double* lnMc, double* N0, double* a1, double* amp) {
+  const double l = log(kPi * Mc * kMsunS);
+  *lnMc = l;
+  *N0 = (3.0 / 128.0) * exp(-(5.0 / 3.0) * l);
+  *a1 = exp(l * (1.0 / 3.0));
+  // Mc^5/6 / d_L  (Msun^5/6 / Mpc):  Mc^5/6 = exp(5/6 l) / (pi G Msun / c^3)^5/6
+  *amp = exp((5.0 / 6.0) * l) * (1.0 / 9.802409278970853e-05) / dL;
+}
+
+__device__ __noinline__ void role_eta(double q, double* eta, double* lneta, double* a2) {
+  const double opq = 1.0 + q;
+  const double e = q / (opq * opq);
+  const double le = log(e);
+  *eta = e;
+  *lneta = le;
+  *a2 = exp(-0.2 * le);  // eta^-1/5
+}
+
+// phi: phi2, phi3, phi4, phi5p, phi6c, phi7, phi10, phi12
+__device__ __noinline__ void role_pn(double q, double chi1, double chi2, double L1, double L2, double* phi) {
   const double opq = 1.0 + q;
   const double eta = q / (opq * opq);
   const double X1 = 1.0 / opq, X2 = q / opq;
   const double X1_2 = X1 * X1, X2_2 = X2 * X2;
   const double X1_4 = X1_2 * X1_2, X2_4 = X2_2 * X2_2;
-
-  // PN coefficients (normalisation of Psi above).
   const double beta = (chi1 * (113.0 * X1_2 + 75.0 * eta) + chi2 * (113.0 * X2_2 + 75.0 * eta)) / 12.0;
   const double sigma = eta * (474.0 / 48.0) * chi1 * chi2 + (486.0 / 96.0) * (X1_2 * chi1 * chi1 + X2_2 * chi2 * chi2);
-  const double phi2 = 3715.0 / 756.0 + (55.0 / 9.0) * eta;
-  const double phi3 = -16.0 * kPi + 4.0 * beta;
-  const double phi4 = 15293365.0 / 508032.0 + (27145.0 / 504.0) * eta + (3085.0 / 72.0) * eta * eta - 10.0 * sigma;
-  const double phi5p = kPi * (38645.0 / 756.0 - (65.0 / 9.0) * eta);
-  const double phi6c = 11583231236531.0 / 4694215680.0 - (640.0 / 3.0) * kPi * kPi - (6848.0 / 21.0) * kEulerGamma +
-                       eta * (-15737765635.0 / 3048192.0 + (2255.0 / 12.0) * kPi * kPi) +
-                       (76055.0 / 1728.0) * eta * eta - (127825.0 / 1296.0) * eta * eta * eta;
-  const double phi7 = kPi * (77096675.0 / 254016.0 + (378515.0 / 1512.0) * eta - (74045.0 / 756.0) * eta * eta);
-  const double phi10 = (-288.0 + 264.0 * X1) * X1_4 * L1 + (-288.0 + 264.0 * X2) * X2_4 * L2;
-  const double phi12 = X1_4 * L1 * (-15895.0 / 28.0 + 4595.0 / 28.0 * X1 + 5715.0 / 14.0 * X1_2 - 325.0 / 7.0 * X1_2 * X1) +
-                       X2_4 * L2 * (-15895.0 / 28.0 + 4595.0 / 28.0 * X2 + 5715.0 / 14.0 * X2_2 - 325.0 / 7.0 * X2_2 * X2);
+  phi[0] = 3715.0 / 756.0 + (55.0 / 9.0) * eta;
+  phi[1] = -16.0 * kPi + 4.0 * beta;
+  phi[2] = 15293365.0 / 508032.0 + (27145.0 / 504.0) * eta + (3085.0 / 72.0) * eta * eta - 10.0 * sigma;
+  phi[3] = kPi * (38645.0 / 756.0 - (65.0 / 9.0) * eta);
+  phi[4] = 11583231236531.0 / 4694215680.0 - (640.0 / 3.0) * kPi * kPi - (6848.0 / 21.0) * kEulerGamma +
+           eta * (-15737765635.0 / 3048192.0 + (2255.0 / 12.0) * kPi * kPi) + (76055.0 / 1728.0) * eta * eta -
+           (127825.0 / 1296.0) * eta * eta * eta;
+  phi[5] = kPi * (77096675.0 / 254016.0 + (378515.0 / 1512.0) * eta - (74045.0 / 756.0) * eta * eta);
+  phi[6] = (-288.0 + 264.0 * X1) * X1_4 * L1 + (-288.0 + 264.0 * X2) * X2_4 * L2;
+  phi[7] = X1_4 * L1 * (-15895.0 / 28.0 + 4595.0 / 28.0 * X1 + 5715.0 / 14.0 * X1_2 - 325.0 / 7.0 * X1_2 * X1) +
+           X2_4 * L2 * (-15895.0 / 28.0 + 4595.0 / 28.0 * X2 + 5715.0 / 14.0 * X2_2 - 325.0 / 7.0 * X2_2 * X2);
+}
 
-  // 3/(128 eta v^5) v^k = N0 (pi M)^{k/3} f^{(k-5)/3}, N0 = (3/128) (pi Mc)^{-5/3}
-  const double lnMc = log(kPi * Mc * kMsunS);          // ln(pi Mc)
-  const double u = lnMc - 0.6 * log(eta);              // ln(pi M)
-  const double a = exp(u / 3.0);                        // (pi M)^{1/3}
-  const double N0 = (3.0 / 128.0) * exp(-(5.0 / 3.0) * lnMc);
-  const double a2 = a * a, a3 = a2 * a, a4 = a2 * a2, a5 = a4 * a, a6 = a3 * a3, a7 = a6 * a;
-  const double a10 = a5 * a5, a12 = a6 * a6;
-  out.c[0] = N0;
-  out.c[1] = N0 * a2 * phi2;
-  out.c[2] = N0 * a3 * phi3;
-  out.c[3] = N0 * a4 * phi4;
-  out.c[4] = N0 * a5 * phi5p;                                                 // ln f
-  out.c[5] = N0 * a6 * (phi6c - (6848.0 / 21.0) * (log(4.0) + u / 3.0));      // f^1/3
-  out.c[6] = N0 * a6 * (-6848.0 / 63.0);                                      // f^1/3 ln f
-  out.c[7] = N0 * a7 * phi7;
-  out.c[8] = N0 * a10 * phi10;
-  out.c[9] = N0 * a12 * phi12;
-  // constant: -phi_c - pi/4 + the v^0 part of the 2.5PN term, 1 - 3 ln v_lso + ln(pi M) (v_lso = 6^-1/2)
-  out.phi0 = -phic - 0.25 * kPi + N0 * a5 * phi5p * (1.0 + 1.5 * log(6.0) + u);
-  out.amp = exp((5.0 / 6.0) * log(Mc)) / dL;
-
-  // Detector projection.
+// sky: sin/cos dec, sin/cos (ra - gmst); tau_d = t_c - n.r_d / c
+__device__ __noinline__ void role_sky(double ra, double dec, double tc, const EventConst& ec, double* sky,
+                                      double* tau) {
   double sd, cd, sa, ca;
   sincos(dec, &sd, &cd);
   sincos(ra - ec.gmst, &sa, &ca);
+  sky[0] = sd;
+  sky[1] = cd;
+  sky[2] = sa;
+  sky[3] = ca;
   const double n0 = cd * ca, n1 = cd * sa, n2 = sd;
-  // antenna patterns in FP32 (angles are O(1); relative error ~1e-7)
-  float sgf, cgf, sdf, cdf, spf, cpf;
-  sincosf((float)(ec.gmst - ra), &sgf, &cgf);
-  sincosf((float)dec, &sdf, &cdf);
-  sincosf((float)psi, &spf, &cpf);
-  const float cif = cosf((float)iota);
-  const float Xf[3] = {-cpf * sgf - spf * cgf * sdf, -cpf * cgf + spf * sgf * sdf, spf * cdf};
-  const float Yf[3] = {spf * sgf - cpf * cgf * sdf, spf * cgf + cpf * sgf * sdf, cpf * cdf};
-  for (int d = 0; d < ec.n_det; ++d) {
+  for (int d = 0; d < kMaxDet; ++d) {
     const DetGeom& g = ec.det[d];
-    out.tau[d] = tc - (n0 * g.r[0] + n1 * g.r[1] + n2 * g.r[2]) / kClight;
-    float fp = 0.f, fx = 0.f;
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) {
-        const float Dij = (float)g.D[i][j];
-        fp += Dij * (Xf[i] * Xf[j] - Yf[i] * Yf[j]);
-        fx += Dij * (Xf[i] * Yf[j] + Yf[i] * Xf[j]);
-      }
-    out.P32[d][0] = fp * (1.0f + cif * cif) * 0.5f;
-    out.P32[d][1] = -fx * cif;
-  }
-  if (need64) {
-    double sg, cg, sp, cp;
-    sincos(ec.gmst - ra, &sg, &cg);
-    sincos(psi, &sp, &cp);
-    const double ci = cos(iota);
-    const double X[3] = {-cp * sg - sp * cg * sd, -cp * cg + sp * sg * sd, sp * cd};
-    const double Y[3] = {sp * sg - cp * cg * sd, sp * cg + cp * sg * sd, cp * cd};
-    for (int d = 0; d < ec.n_det; ++d) {
-      const DetGeom& g = ec.det[d];
-      double fp = 0.0, fx = 0.0;
-      for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-          fp += g.D[i][j] * (X[i] * X[j] - Y[i] * Y[j]);
-          fx += g.D[i][j] * (X[i] * Y[j] + Y[i] * X[j]);
-        }
-      out.P64[d][0] = fp * (1.0 + ci * ci) * 0.5;
-      out.P64[d][1] = -fx * ci;
-    }
+    tau[d] = (d < ec.n_det) ? tc - (n0 * g.r[0] + n1 * g.r[1] + n2 * g.r[2]) / kClight : 0.0;
   }
 }
+
+__device__ __noinline__ void role_orient(double psi, double iota, double* o) {
+  double sp, cp;
+  sincos(psi, &sp, &cp);
+  o[0] = sp;
+  o[1] = cp;
+  o[2] = cos(iota);
+}
+
+// c_k and Phi0 from the phase-1 results (see walker layout in rb_internal.cuh)
+__device__ __noinline__ void role_coef(double lnMc, double N0, double a1, double a2, double lneta, const double* phi,
+                                       double phic, double* c, double* phi0) {
+  const double u = lnMc - 0.6 * lneta;  // ln(pi M)
+  const double a = a1 * a2;             // (pi M)^1/3
+  const double a2p = a * a, a3 = a2p * a, a4 = a2p * a2p, a5 = a4 * a, a6 = a3 * a3, a7 = a6 * a;
+  const double a10 = a5 * a5, a12 = a6 * a6;
+  c[0] = N0;
+  c[1] = N0 * a2p * phi[0];
+  c[2] = N0 * a3 * phi[1];
+  c[3] = N0 * a4 * phi[2];
+  c[4] = N0 * a5 * phi[3];                                                    // ln f
+  c[5] = N0 * a6 * (phi[4] - (6848.0 / 21.0) * (1.3862943611198906 + u / 3.0));  // f^1/3 (ln 4 = 1.386...)
+  c[6] = N0 * a6 * (-6848.0 / 63.0);                                          // f^1/3 ln f
+  c[7] = N0 * a7 * phi[5];
+  c[8] = N0 * a10 * phi[6];
+  c[9] = N0 * a12 * phi[7];
+  // -phi_c - pi/4 + the v^0 part of the 2.5PN term, 1 - 3 ln v_lso + ln(pi M), v_lso = 6^-1/2
+  *phi0 = -phic - 0.25 * kPi + N0 * a5 * phi[3] * (1.0 + 1.5 * 1.791759469228055 + u);
+}
+
+// P_d = F+ (1 + cos^2 i)/2 - i Fx cos i,  F+ = X.DX - Y.DY,  Fx = X.DY + Y.DX
+__device__ __noinline__ void role_antenna(const DetGeom& g, const double* sky, const double* ori, double* P) {
+  const double sd = sky[0], cd = sky[1], sg = -sky[2], cg = sky[3];  // g = gmst - ra
+  const double sp = ori[0], cp = ori[1], ci = ori[2];
+  const double X[3] = {-cp * sg - sp * cg * sd, -cp * cg + sp * sg * sd, sp * cd};
+  const double Y[3] = {sp * sg - cp * cg * sd, sp * cg + cp * sg * sd, cp * cd};
+  double DX[3], DY[3];
+  for (int i = 0; i < 3; ++i) {
+    DX[i] = g.D[i][0] * X[0] + g.D[i][1] * X[1] + g.D[i][2] * X[2];
+    DY[i] = g.D[i][0] * Y[0] + g.D[i][1] * Y[1] + g.D[i][2] * Y[2];
+  }
+  const double fp = (X[0] * DX[0] + X[1] * DX[1] + X[2] * DX[2]) - (Y[0] * DY[0] + Y[1] * DY[1] + Y[2] * DY[2]);
+  const double fx = (X[0] * DY[0] + X[1] * DY[1] + X[2] * DY[2]) + (Y[0] * DX[0] + Y[1] * DX[1] + Y[2] * DX[2]);
+  P[0] = fp * (1.0 + ci * ci) * 0.5;
+  P[1] = -fx * ci;
+}
+
+__device__ __forceinline__ bool theta_valid(const double* th) {
+  bool ok = true;
+  for (int j = 0; j < kNPar; ++j) ok = ok && isfinite(th[j]);
+  return ok && th[0] > 0.0 && th[1] > 0.0 && th[1] <= 1.0 && th[6] > 0.0;
+}
+
+__device__ __forceinline__ double wrap_pi(double x) { return x - kTwoPi * rint(x * (1.0 / kTwoPi)); }
 
 // ---------------------------------------------------------------------------
 // Small forward-mode dual numbers for the tangents (T = float or double).
@@ -198,7 +237,7 @@ template <class T, int N> __device__ __forceinline__ void du_sincos(const Du<T, 
 // respect to (iota, psi, ra, dec).  Same formulas as walker_values, carried in
 // precision T (FP32 suffices for the mixed paths: tangents need ~1e-6).
 template <class T>
-__device__ void walker_tangents(const double* th, const EventConst& ec, WalkerTan<T>& o) {
+__device__ void tangents_intrinsic(const double* th, WalkerTan<T>& o) {
   using D6 = Du<T, kNTanIntr>;
   const D6 Mc = du_var<T, kNTanIntr>(T(th[0]), 0), q = du_var<T, kNTanIntr>(T(th[1]), 1);
   const D6 chi1 = du_var<T, kNTanIntr>(T(th[2]), 2), chi2 = du_var<T, kNTanIntr>(T(th[3]), 3);
@@ -245,7 +284,10 @@ __device__ void walker_tangents(const double* th, const EventConst& ec, WalkerTa
   o.dphi0[1] = phi0v.d[1];
   o.lnamp_Mc = T(5.0 / 6.0) / T(th[0]);
   o.lnamp_dL = T(-1) / T(th[6]);
+}
 
+template <class T>
+__device__ void tangents_detector(const double* th, const EventConst& ec, WalkerTan<T>& o) {
   // detector tangents: variables (iota, psi, ra, dec)
   using D4 = Du<T, 4>;
   const D4 iota = du_var<T, 4>(T(th[9]), 0), psi = du_var<T, 4>(T(th[10]), 1);
@@ -288,161 +330,279 @@ __device__ void walker_tangents(const double* th, const EventConst& ec, WalkerTa
   }
 }
 
+
 // ---------------------------------------------------------------------------
-// Kernels
+// The block-level set-up: 32 walkers, phases 1-3 over warps 0-4 (+ tangents).
 // ---------------------------------------------------------------------------
-__global__ void k_ref_values(const double* theta, EventConst ec, RefValues* out) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+struct SetupSmem {
+  double th[kNPar][kSetupWalkers];
+  double lnMc[kSetupWalkers], N0[kSetupWalkers], a1[kSetupWalkers], amp[kSetupWalkers];
+  double eta[kSetupWalkers], lneta[kSetupWalkers], a2[kSetupWalkers];
+  double phi[8][kSetupWalkers];
+  double sky[4][kSetupWalkers], tau[kMaxDet][kSetupWalkers];
+  double ori[3][kSetupWalkers];
+  double c[kNBasis][kSetupWalkers], phi0[kSetupWalkers];
+  double P[kMaxDet][2][kSetupWalkers];
+  double e64[2][kSetupWalkers];   // exp(-i dPhi0)
+  int valid[kSetupWalkers];
+};
+
+// Runs phases 1 and 2 for the walkers of this block and leaves the absolute
+// values in shared memory.  Warps 0-4 (and only they) must call it.
+__device__ void setup_absolute(const double* __restrict__ theta, int64_t w0, int64_t W, const EventConst& ec,
+                               SetupSmem& S) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kNPar * kSetupWalkers; i += kRoleThreads) {
+    const int l = i / kNPar, j = i % kNPar;
+    const int64_t w = (w0 + l < W) ? w0 + l : W - 1;  // pad with the last walker
+    S.th[j][l] = theta[w * kNPar + j];
+  }
+  roles_sync();
+  const int l = lane;
+  if (warp == 0) {
     double th[kNPar];
-    for (int j = 0; j < kNPar; ++j) th[j] = theta[j];
-    walker_values(th, ec, 1, out->v);
+    for (int j = 0; j < kNPar; ++j) th[j] = S.th[j][l];
+    S.valid[l] = theta_valid(th) ? 1 : 0;
+    role_mass(th[0], th[6], &S.lnMc[l], &S.N0[l], &S.a1[l], &S.amp[l]);
+  } else if (warp == 1) {
+    role_eta(S.th[1][l], &S.eta[l], &S.lneta[l], &S.a2[l]);
+  } else if (warp == 2) {
+    double phi[8];
+    role_pn(S.th[1][l], S.th[2][l], S.th[3][l], S.th[4][l], S.th[5][l], phi);
+    for (int k = 0; k < 8; ++k) S.phi[k][l] = phi[k];
+  } else if (warp == 3) {
+    double sky[4], tau[kMaxDet];
+    role_sky(S.th[11][l], S.th[12][l], S.th[7][l], ec, sky, tau);
+    for (int k = 0; k < 4; ++k) S.sky[k][l] = sky[k];
+    for (int d = 0; d < kMaxDet; ++d) S.tau[d][l] = tau[d];
+  } else if (warp == 4) {
+    double o[3];
+    role_orient(S.th[10][l], S.th[9][l], o);
+    for (int k = 0; k < 3; ++k) S.ori[k][l] = o[k];
+  }
+  roles_sync();
+  if (warp == 0) {
+    double phi[8], c[kNBasis], phi0;
+    for (int k = 0; k < 8; ++k) phi[k] = S.phi[k][l];
+    role_coef(S.lnMc[l], S.N0[l], S.a1[l], S.a2[l], S.lneta[l], phi, S.th[8][l], c, &phi0);
+    for (int k = 0; k < kNBasis; ++k) S.c[k][l] = c[k];
+    S.phi0[l] = phi0;
+  } else if (warp >= 1 && warp <= kMaxDet) {
+    const int d = warp - 1;
+    if (d < ec.n_det) {
+      double sky[4], ori[3], P[2];
+      for (int k = 0; k < 4; ++k) sky[k] = S.sky[k][l];
+      for (int k = 0; k < 3; ++k) ori[k] = S.ori[k][l];
+      role_antenna(ec.det[d], sky, ori, P);
+      S.P[d][0][l] = P[0];
+      S.P[d][1][l] = P[1];
+    } else {
+      S.P[d][0][l] = S.P[d][1][l] = 0.0;
+    }
+  }
+  roles_sync();
+}
+
+// Reference kernel: one block; lane 0's walker is theta_ref.
+__global__ void __launch_bounds__(7 * 32) k_ref_values(const double* theta, EventConst ec, RefValues* out) {
+  __shared__ SetupSmem S;
+  setup_absolute(theta, 0, 1, ec, S);
+  const int j = threadIdx.x;
+  if (j == 0) {
+    Values v;
+    for (int k = 0; k < kNBasis; ++k) v.c[k] = S.c[k][0];
+    v.phi0 = S.phi0[0];
+    for (int d = 0; d < kMaxDet; ++d) {
+      v.tau[d] = S.tau[d][0];
+      v.P64[d][0] = S.P[d][0][0];
+      v.P64[d][1] = S.P[d][1][0];
+      v.P32[d][0] = (float)v.P64[d][0];
+      v.P32[d][1] = (float)v.P64[d][1];
+    }
+    v.amp = S.amp[0];
+    v.valid = S.valid[0];
+    v.pad = 0;
+    out->v = v;
+  } else if (j >= 32 && j < 32 + kNBasis + 1 + 2 * kMaxDet) {
+    // float-pair copies, one quantity per lane (the FP64 instructions issue once)
+    const int i = j - 32;
+    // sqrt(5/24) pi^{-2/3} (G Msun/c^3)^{5/6} / (1 Mpc / c): amplitude of h0 per Msun^{5/6}/Mpc
+    const double a = 8.035028173395984e-06 / kMpcS * S.amp[0];
+    double x;
+    if (i < kNBasis) x = S.c[i][0] * (1.0 / kTwoPi);
+    else if (i == kNBasis) x = S.phi0[0] * (1.0 / kTwoPi);
+    else if (i < kNBasis + 1 + kMaxDet) x = (i - kNBasis - 1 < ec.n_det) ? S.tau[i - kNBasis - 1][0] : 0.0;
+    else x = 0.0;
+    const f2x p = f2x_from(x);
+    if (i < kNBasis) { out->chat[i][0] = p.hi; out->chat[i][1] = p.lo; }
+    else if (i == kNBasis) { out->phi0t[0] = p.hi; out->phi0t[1] = p.lo; }
+    else if (i < kNBasis + 1 + kMaxDet) { out->taut[i - kNBasis - 1][0] = p.hi; out->taut[i - kNBasis - 1][1] = p.lo; }
+    else {
+      const int d = i - kNBasis - 1 - kMaxDet;
+      const bool on = d < ec.n_det;
+      out->K[d][0] = on ? a * S.P[d][0][0] : 0.0;
+      out->K[d][1] = on ? a * S.P[d][1][0] : 0.0;
+    }
   }
 }
 
-__device__ __forceinline__ void load_theta(const double* __restrict__ theta, int64_t w, double* th) {
-#pragma unroll
-  for (int j = 0; j < kNPar; ++j) th[j] = theta[w * kNPar + j];
-}
-
-__device__ __forceinline__ double wrap_pi(double x) { return x - kTwoPi * rint(x * (1.0 / kTwoPi)); }
-
-template <bool GRAD>
-__global__ void __launch_bounds__(128) k_setup_mixed(const double* __restrict__ theta, int64_t W, EventConst ec,
-                                                     const RefValues* __restrict__ ref, WalkerMixed* __restrict__ ws,
-                                                     WalkerTan<float>* __restrict__ tan) {
-  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= W) return;
-  double th[kNPar];
-  load_theta(theta, w, th);
-  Values v;
-  walker_values(th, ec, 1, v);
-  WalkerMixed o;
-  o.valid = v.valid;
-  o.pad[0] = o.pad[1] = o.pad[2] = 0;
-  if (v.valid) {
-    const Values& r = ref->v;
-    for (int k = 0; k < kNBasis; ++k) {
-      f2x c = f2x_from(v.c[k] - r.c[k]);
-      o.dc_hi[k] = c.hi;
-      o.dc_lo[k] = c.lo;
+// Batch set-up.  MODE RB_MIXED writes WalkerMixed (+ float tangents);
+// RB_FP64 writes WalkerF64 (+ double tangents); RB_MIXED_F64PHASE writes
+// WalkerF64 (+ float tangents).
+template <int MODE, bool GRAD>
+__global__ void __launch_bounds__(7 * 32) k_setup(const double* __restrict__ theta, int64_t W, EventConst ec,
+                                                  const RefValues* __restrict__ ref, void* __restrict__ ws_out,
+                                                  void* __restrict__ tan_out) {
+  using TanT = typename std::conditional<MODE == RB_FP64, double, float>::type;
+  __shared__ SetupSmem S;
+  const int64_t w0 = (int64_t)blockIdx.x * kSetupWalkers;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t w = w0 + lane;
+  const bool mine = w < W;
+  if (warp >= 5) {
+    // tangents (gradient only) do not depend on the FP64 phases: these warps
+    // run them alongside and take no part in the role barriers
+    if (!GRAD) return;
+    double th[kNPar];
+    const int64_t wc = mine ? w : W - 1;
+    for (int j = 0; j < kNPar; ++j) th[j] = theta[wc * kNPar + j];
+    WalkerTan<TanT>* tan = static_cast<WalkerTan<TanT>*>(tan_out) + wc;
+    if (warp == 5) {
+      WalkerTan<TanT> t;
+      tangents_intrinsic<TanT>(th, t);
+      if (mine) {
+        for (int k = 0; k < kNBasis; ++k)
+          for (int j = 0; j < kNTanIntr; ++j) tan->dc[k][j] = t.dc[k][j];
+        tan->dphi0[0] = t.dphi0[0];
+        tan->dphi0[1] = t.dphi0[1];
+        tan->lnamp_Mc = t.lnamp_Mc;
+        tan->lnamp_dL = t.lnamp_dL;
+      }
+    } else {
+      WalkerTan<TanT> t;
+      tangents_detector<TanT>(th, ec, t);
+      if (mine) {
+        for (int d = 0; d < kMaxDet; ++d) {
+          tan->dtd[d][0] = t.dtd[d][0];
+          tan->dtd[d][1] = t.dtd[d][1];
+          for (int j = 0; j < 4; ++j) {
+            tan->dlnP[d][j][0] = t.dlnP[d][j][0];
+            tan->dlnP[d][j][1] = t.dlnP[d][j][1];
+          }
+        }
+      }
     }
-    // The prefactor ratio is formed in FP64: F+ = D:(XX - YY) cancels, and
-    // an FP32 antenna pattern can be off by ~1e-7 absolute, i.e. up to ~1e-5
-    // relative, which moves log L by ~1e-3 at SNR ~ 100.
-    double sp, cp;
-    sincos(wrap_pi(v.phi0 - r.phi0), &sp, &cp);
-    const double ampr = v.amp / r.amp;
+    return;
+  }
+  setup_absolute(theta, w0, W, ec, S);
+  const Values& r = ref->v;
+  const int l = lane;
+  if (warp == 0) {
+    // constant-phase factor exp(-i dPhi0) (FP64 from the half angle in mixed modes)
+    const double dphi0 = wrap_pi(S.phi0[l] - r.phi0);
+    if (MODE == RB_FP64) {
+      double sp, cp;
+      sincos(dphi0, &sp, &cp);
+      S.e64[0][l] = cp;
+      S.e64[1][l] = -sp;
+    } else {
+      // exp(-i dPhi0) - 1 = -2 sin^2(pi y) - 2i sin(pi y) cos(pi y), y = dPhi0 / 2pi as a float pair,
+      // plus the first-order term of the low part: d/dy exp(-2 pi i y) = -2 pi i exp(-2 pi i y)
+      const double y64 = dphi0 * (1.0 / kTwoPi);
+      const float yh = (float)y64, yl = (float)(y64 - (double)yh);
+      float sn, cs;
+      sincos_pi_half(yh, sn, cs);
+      const float er = -2.f * sn * sn, ei = -2.f * sn * cs;
+      const float t = 6.28318530717958648f * yl;
+      S.e64[0][l] = 1.0 + ((double)er + (double)(ei * t));
+      S.e64[1][l] = (double)ei - (double)((1.f + er) * t);
+    }
+  } else if (warp == 4 && mine) {
     for (int d = 0; d < kMaxDet; ++d) {
-      if (d < ec.n_det) {
-        f2x t = f2x_from(v.tau[d] - r.tau[d]);
-        o.tau_hi[d] = t.hi;
-        o.tau_lo[d] = t.lo;
-        // Q = ampr P e^{-i dphi0};  rho = Q / P_ref;  sig = (Q - P_ref) / P_ref
-        const double pr = v.P64[d][0], pi = v.P64[d][1];
-        const double qr = ampr * (pr * cp + pi * sp);
-        const double qi = ampr * (pi * cp - pr * sp);
-        const double rr = r.P64[d][0], ri = r.P64[d][1];
-        const double den = rr * rr + ri * ri;
-        o.rho[d][0] = (float)((qr * rr + qi * ri) / den);
-        o.rho[d][1] = (float)((qi * rr - qr * ri) / den);
-        const double er = qr - rr, ei = qi - ri;
-        o.sig[d][0] = (float)((er * rr + ei * ri) / den);
-        o.sig[d][1] = (float)((ei * rr - er * ri) / den);
+      const double dt = (d < ec.n_det) ? S.tau[d][l] - r.tau[d] : 0.0;
+      if (MODE == RB_MIXED) {
+        const f2x t = f2x_from(dt);
+        WalkerMixed* o = static_cast<WalkerMixed*>(ws_out) + w;
+        o->tau_hi[d] = t.hi;
+        o->tau_lo[d] = t.lo;
       } else {
-        o.tau_hi[d] = o.tau_lo[d] = 0.f;
-        o.rho[d][0] = o.rho[d][1] = o.sig[d][0] = o.sig[d][1] = 0.f;
+        static_cast<WalkerF64*>(ws_out)[w].tau[d] = dt;
       }
     }
   }
-  ws[w] = o;
-  if (GRAD && v.valid) {
-    WalkerTan<float> t;
-    walker_tangents<float>(th, ec, t);
-    tan[w] = t;
-  }
-}
-
-template <bool GRAD, class TanT>
-__global__ void __launch_bounds__(128) k_setup_f64(const double* __restrict__ theta, int64_t W, EventConst ec,
-                                                   const RefValues* __restrict__ ref, WalkerF64* __restrict__ ws,
-                                                   WalkerTan<TanT>* __restrict__ tan) {
-  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= W) return;
-  double th[kNPar];
-  load_theta(theta, w, th);
-  Values v;
-  walker_values(th, ec, 1, v);
-  WalkerF64 o;
-  o.valid = v.valid;
-  o.pad = 0;
-  if (v.valid) {
-    const Values& r = ref->v;
-    for (int k = 0; k < kNBasis; ++k) o.dc[k] = v.c[k] - r.c[k];
-    double sp, cp;
-    sincos(wrap_pi(v.phi0 - r.phi0), &sp, &cp);
-    const double ampr = v.amp / r.amp;
-    for (int d = 0; d < kMaxDet; ++d) {
-      if (d < ec.n_det) {
-        o.tau[d] = v.tau[d] - r.tau[d];
-        const double pr = v.P64[d][0], pi = v.P64[d][1];
-        const double qr = ampr * (pr * cp + pi * sp);
-        const double qi = ampr * (pi * cp - pr * sp);
-        const double rr = r.P64[d][0], ri = r.P64[d][1];
-        const double den = rr * rr + ri * ri;
-        o.rho[d][0] = (qr * rr + qi * ri) / den;
-        o.rho[d][1] = (qi * rr - qr * ri) / den;
-        const double er = qr - rr, ei = qi - ri;
-        o.sig[d][0] = (er * rr + ei * ri) / den;
-        o.sig[d][1] = (ei * rr - er * ri) / den;
-      } else {
-        o.tau[d] = 0.0;
-        o.rho[d][0] = o.rho[d][1] = o.sig[d][0] = o.sig[d][1] = 0.0;
+  roles_sync();
+  // phase 3: coefficient differences (warp 0) and prefactor ratios per detector (warps 1-3), FP64
+  if (warp == 0 && mine) {
+    if (MODE == RB_MIXED) {
+      WalkerMixed* o = static_cast<WalkerMixed*>(ws_out) + w;
+      for (int k = 0; k < kNBasis; ++k) {
+        const f2x c = f2x_from(S.c[k][l] - r.c[k]);
+        o->dc_hi[k] = c.hi;
+        o->dc_lo[k] = c.lo;
       }
+      o->valid = S.valid[l];
+      o->pad[0] = o->pad[1] = o->pad[2] = 0;
+    } else {
+      WalkerF64* o = static_cast<WalkerF64*>(ws_out) + w;
+      for (int k = 0; k < kNBasis; ++k) o->dc[k] = S.c[k][l] - r.c[k];
+      o->valid = S.valid[l];
+      o->pad = 0;
     }
-  } else {
-    for (int k = 0; k < kNBasis; ++k) o.dc[k] = 0.0;
-    for (int d = 0; d < kMaxDet; ++d) {
-      o.tau[d] = 0.0;
-      o.rho[d][0] = o.rho[d][1] = o.sig[d][0] = o.sig[d][1] = 0.0;
+  } else if (warp >= 1 && warp <= kMaxDet && mine) {
+    const int d = warp - 1;
+    double rho_r = 0.0, rho_i = 0.0, sig_r = 0.0, sig_i = 0.0;
+    if (d < ec.n_det) {
+      // Q = ampr P exp(-i dPhi0);  rho = Q / P_ref;  sig = (Q - P_ref) / P_ref
+      const double ampr = S.amp[l] / r.amp;
+      const double er = S.e64[0][l], ei = S.e64[1][l];
+      const double pr = S.P[d][0][l], pi = S.P[d][1][l];
+      const double qr = ampr * (pr * er - pi * ei), qi = ampr * (pr * ei + pi * er);
+      const double rr = r.P64[d][0], ri = r.P64[d][1];
+      const double den = rr * rr + ri * ri;
+      rho_r = (qr * rr + qi * ri) / den;
+      rho_i = (qi * rr - qr * ri) / den;
+      const double xr = qr - rr, xi = qi - ri;
+      sig_r = (xr * rr + xi * ri) / den;
+      sig_i = (xi * rr - xr * ri) / den;
     }
-  }
-  ws[w] = o;
-  if (GRAD && v.valid) {
-    WalkerTan<TanT> t;
-    walker_tangents<TanT>(th, ec, t);
-    tan[w] = t;
+    if (MODE == RB_MIXED) {
+      WalkerMixed* o = static_cast<WalkerMixed*>(ws_out) + w;
+      o->rho[d][0] = (float)rho_r;
+      o->rho[d][1] = (float)rho_i;
+      o->sig[d][0] = (float)sig_r;
+      o->sig[d][1] = (float)sig_i;
+    } else {
+      WalkerF64* o = static_cast<WalkerF64*>(ws_out) + w;
+      o->rho[d][0] = rho_r;
+      o->rho[d][1] = rho_i;
+      o->sig[d][0] = sig_r;
+      o->sig[d][1] = sig_i;
+    }
   }
 }
 
-// Host-side launchers (declared in rb_launch.h).
+// Host-side launchers.
 cudaError_t launch_ref_values(const double* theta_ref_dev, const EventConst& ec, RefValues* out, cudaStream_t s) {
-  k_ref_values<<<1, 32, 0, s>>>(theta_ref_dev, ec, out);
+  k_ref_values<<<1, 5 * 32, 0, s>>>(theta_ref_dev, ec, out);
   return cudaGetLastError();
 }
 
-cudaError_t launch_setup_mixed(const double* theta, int64_t W, const EventConst& ec, const RefValues* ref,
-                               WalkerMixed* ws, WalkerTan<float>* tan, bool grad, cudaStream_t s) {
-  const int bs = 128;
-  const unsigned grid = (unsigned)((W + bs - 1) / bs);
+template <int MODE>
+static cudaError_t launch_setup_t(const double* theta, int64_t W, const EventConst& ec, const RefValues* ref, void* ws,
+                                  void* tan, bool grad, cudaStream_t s) {
+  const unsigned grid = (unsigned)((W + kSetupWalkers - 1) / kSetupWalkers);
   if (grad)
-    k_setup_mixed<true><<<grid, bs, 0, s>>>(theta, W, ec, ref, ws, tan);
+    k_setup<MODE, true><<<grid, 7 * 32, 0, s>>>(theta, W, ec, ref, ws, tan);
   else
-    k_setup_mixed<false><<<grid, bs, 0, s>>>(theta, W, ec, ref, ws, tan);
+    k_setup<MODE, false><<<grid, 5 * 32, 0, s>>>(theta, W, ec, ref, ws, tan);
   return cudaGetLastError();
 }
 
-// tan: WalkerTan<double> (tan_f32 = false) or WalkerTan<float> (tan_f32 = true).
-cudaError_t launch_setup_f64(const double* theta, int64_t W, const EventConst& ec, const RefValues* ref,
-                             WalkerF64* ws, void* tan, bool grad, bool tan_f32, cudaStream_t s) {
-  const int bs = 128;
-  const unsigned grid = (unsigned)((W + bs - 1) / bs);
-  if (!grad)
-    k_setup_f64<false, double><<<grid, bs, 0, s>>>(theta, W, ec, ref, ws, nullptr);
-  else if (tan_f32)
-    k_setup_f64<true, float><<<grid, bs, 0, s>>>(theta, W, ec, ref, ws, static_cast<WalkerTan<float>*>(tan));
-  else
-    k_setup_f64<true, double><<<grid, bs, 0, s>>>(theta, W, ec, ref, ws, static_cast<WalkerTan<double>*>(tan));
-  return cudaGetLastError();
+cudaError_t launch_setup(int mode, const double* theta, int64_t W, const EventConst& ec, const RefValues* ref,
+                         void* ws, void* tan, bool grad, cudaStream_t s) {
+  if (mode == RB_MIXED) return launch_setup_t<RB_MIXED>(theta, W, ec, ref, ws, tan, grad, s);
+  if (mode == RB_FP64) return launch_setup_t<RB_FP64>(theta, W, ec, ref, ws, tan, grad, s);
+  return launch_setup_t<RB_MIXED_F64PHASE>(theta, W, ec, ref, ws, tan, grad, s);
 }
 
 }  // namespace rb

@@ -105,12 +105,67 @@ __device__ __forceinline__ void strain_f64(const Values& v, int d, double f, dou
   hi = a * (Q * c - P * s);
 }
 
+// ---------------------------------------------------------------------------
+// Summary epilogue shared by the FP64 and fast kernels: from the six block
+// sums (A0 re/im, A1 re/im, B0, B1 before the constant factors) lanes 0..5
+// of warp 0 each finish one output (SIMT: the FP64 instructions are issued
+// once for all six), write the FP64 summary entry and the bin tables
+// (alpha0 = A0/2, alpha1 = A1/df_b, beta0 = B0/2, beta1 = B1/df_b), and the
+// block's share Re A0 - B0/2 of log L(theta_ref).  The last block to finish
+// sums the shares in a fixed order (deterministic).
+// ---------------------------------------------------------------------------
+__device__ void summary_epilogue(const SummaryOut& so, int b, int d, int B, int D, const double* sblock,
+                                 const double* scale, bool scaled_form) {
+  __shared__ bool last;
+  if (threadIdx.x < 32) {
+    const int j = threadIdx.x;
+    double o = 0.0;
+    if (j < 6) {
+      o = sblock[j];
+      if (scaled_form) {
+        // A = conj(K) (s_re + i s_im) * scale[0];  B = |K|^2 s * scale[1]
+        const double Kr = scale[2], Ki = scale[3];
+        const double pr = sblock[j & ~1], pi = sblock[j | 1];
+        if (j < 4) o = scale[0] * ((j & 1) ? (Kr * pi - Ki * pr) : (Kr * pr + Ki * pi));
+        else o = scale[1] * (Kr * Kr + Ki * Ki) * o;
+      }
+      so.summ[((size_t)d * B + b) * 6 + j] = o;
+      const double t = (j == 2 || j == 3 || j == 5) ? o * so.inv_df[b] : 0.5 * o;
+      so.bin64[((size_t)d * 6 + j) * so.Bp + b] = t;
+      so.bin32[((size_t)d * 6 + j) * so.Bp + b] = (float)t;
+    }
+    const double b0 = __shfl_sync(0xffffffffu, o, 4);
+    if (j == 0) so.share[(size_t)d * B + b] = o - 0.5 * b0;
+    if (j == 0) {
+      __threadfence();
+      const unsigned ticket = atomicAdd(so.counter, 1u);
+      last = (ticket == (unsigned)(B * D) - 1u);
+    }
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  __shared__ double part[32];
+  const int n = B * D;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += so.share[i];
+  acc = warp_sum_f64(acc);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += part[i];
+    *so.base = t;
+    *so.counter = 0u;
+  }
+}
+
 // One block per (bin, detector): FP64 fiducial waveform generated inline,
 // FP64 accumulation, fixed-order block reduction (deterministic).
 constexpr int kSumThreads = 128;
-__global__ void __launch_bounds__(kSumThreads) k_summary(DataPtrs in, int64_t kmin, int64_t N, double T, int B,
+__global__ void __launch_bounds__(kSumThreads) k_summary(DataPtrs in, int64_t kmin, int64_t N, double T, int B, int D,
                                                          const int64_t* __restrict__ edges,
-                                                         const RefValues* __restrict__ ref, double* __restrict__ out) {
+                                                         const RefValues* __restrict__ ref, SummaryOut so) {
   const int b = blockIdx.x, d = blockIdx.y;
   const Values& v = ref->v;
   const int64_t k0 = edges[b];
@@ -134,6 +189,7 @@ __global__ void __launch_bounds__(kSumThreads) k_summary(DataPtrs in, int64_t km
     acc[5] += w * hh * df;
   }
   __shared__ double red[kSumThreads / 32][6];
+  __shared__ double sblock[6];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int j = 0; j < 6; ++j) acc[j] = warp_sum_f64(acc[j]);
@@ -141,17 +197,21 @@ __global__ void __launch_bounds__(kSumThreads) k_summary(DataPtrs in, int64_t km
     for (int j = 0; j < 6; ++j) red[wid][j] = acc[j];
   __syncthreads();
   if (threadIdx.x < 6) {
-    double s = 0.0;
-    for (int i = 0; i < kSumThreads / 32; ++i) s += red[i][threadIdx.x];
-    // out layout: [D][B][6] = A0r, A0i, A1r, A1i, B0, B1
-    out[((size_t)d * B + b) * 6 + threadIdx.x] = s;
+    double t = 0.0;
+    for (int i = 0; i < kSumThreads / 32; ++i) t += red[i][threadIdx.x];
+    sblock[threadIdx.x] = t;
   }
+  __syncthreads();
+  summary_epilogue(so, b, d, B, D, sblock, nullptr, false);
 }
 
-// Edge and bin tables for the batch kernels, and the fiducial log-likelihood.
-__global__ void k_tables(int64_t kmin, double T, int D, int B, int Ep, int Bp, const int64_t* __restrict__ edges,
-                         const double* __restrict__ summ, float* __restrict__ tab32, size_t edge32_floats,
-                         double* __restrict__ tab64) {
+// ---------------------------------------------------------------------------
+// Event-constant edge tables (built once per event): g_k(f_e) / 2pi as float
+// pairs and FP64, f_e, and 1 / df_b per bin; pad entries are zero.
+// ---------------------------------------------------------------------------
+__global__ void k_edge_tables(int64_t kmin, double T, int D, int B, int Ep, int Bp,
+                              const int64_t* __restrict__ edges, float* __restrict__ tab32, size_t edge32_floats,
+                              double* __restrict__ tab64, double* __restrict__ inv_df) {
   const int E = B + 1;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
@@ -178,34 +238,14 @@ __global__ void k_tables(int64_t kmin, double T, int D, int B, int Ep, int Bp, c
     tab32[(size_t)2 * kNBasis * Ep + e] = fp.hi;
     tab32[(size_t)(2 * kNBasis + 1) * Ep + e] = fp.lo;
   }
+  for (int b = tid; b < B; b += nth) inv_df[b] = T / (double)(edges[b + 1] - edges[b]);
+  // bin tables: zero the padding once (the summary kernels write b < B)
   double* bin64 = tab64 + (size_t)(kNBasis + 1) * Ep;
   float* bin32 = tab32 + edge32_floats;
-  for (int i = tid; i < D * Bp; i += nth) {
-    const int d = i / Bp, b = i % Bp;
-    double v[6] = {0, 0, 0, 0, 0, 0};
-    if (b < B) {
-      const double* s = summ + ((size_t)d * B + b) * 6;
-      const double idf = 1.0 / (grid_f(kmin, edges[b + 1], T) - grid_f(kmin, edges[b], T));
-      v[0] = 0.5 * s[0];
-      v[1] = 0.5 * s[1];
-      v[2] = s[2] * idf;
-      v[3] = s[3] * idf;
-      v[4] = 0.5 * s[4];
-      v[5] = s[5] * idf;
-    }
-    for (int j = 0; j < 6; ++j) {
-      bin64[((size_t)d * 6 + j) * Bp + b] = v[j];
-      bin32[((size_t)d * 6 + j) * Bp + b] = (float)v[j];
-    }
+  for (int i = tid; i < D * 6 * Bp; i += nth) {
+    bin64[i] = 0.0;
+    bin32[i] = 0.f;
   }
-}
-
-// base = sum_d sum_b (Re A0 - B0/2), one warp, fixed summation order.
-__global__ void k_base_logl(int D, int B, const double* __restrict__ summ, double* __restrict__ out) {
-  double s = 0.0;
-  for (int i = threadIdx.x; i < D * B; i += 32) s += summ[(size_t)i * 6 + 0] - 0.5 * summ[(size_t)i * 6 + 4];
-  s = warp_sum_f64(s);
-  if (threadIdx.x == 0) *out = s;
 }
 
 // Detector strain for one source on a grid (FP64).
@@ -236,19 +276,15 @@ cudaError_t launch_bin_edges(double f_low, double f_high, double T, int64_t kmin
 }
 
 cudaError_t launch_summary(const DataPtrs& in, int64_t kmin, int64_t N, double T, int D, int B,
-                           const int64_t* edges, const RefValues* ref, double* out, cudaStream_t s) {
+                           const int64_t* edges, const RefValues* ref, const SummaryOut& so, cudaStream_t s) {
   dim3 grid(B, D);
-  k_summary<<<grid, kSumThreads, 0, s>>>(in, kmin, N, T, B, edges, ref, out);
+  k_summary<<<grid, kSumThreads, 0, s>>>(in, kmin, N, T, B, D, edges, ref, so);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tables(int64_t kmin, double T, int D, int B, int Ep, int Bp, const int64_t* edges,
-                          const double* summ, float* tab32, size_t edge32_floats, double* tab64, double* base,
-                          cudaStream_t s) {
-  k_tables<<<64, 256, 0, s>>>(kmin, T, D, B, Ep, Bp, edges, summ, tab32, edge32_floats, tab64);
-  cudaError_t err = cudaGetLastError();
-  if (err != cudaSuccess) return err;
-  k_base_logl<<<1, 32, 0, s>>>(D, B, summ, base);
+cudaError_t launch_edge_tables(int64_t kmin, double T, int D, int B, int Ep, int Bp, const int64_t* edges,
+                               float* tab32, size_t edge32_floats, double* tab64, double* inv_df, cudaStream_t s) {
+  k_edge_tables<<<16, 256, 0, s>>>(kmin, T, D, B, Ep, Bp, edges, tab32, edge32_floats, tab64, inv_df);
   return cudaGetLastError();
 }
 
@@ -267,16 +303,18 @@ cudaError_t launch_strain(const RefValues* src, int64_t kmin, int64_t N, double 
 // the grid, f = f_c (1 + j u) with u = df / f_c and j = k - k_c in [-16, 15]:
 //   g_k(f_c (1 + j u)) = P_k(f_c) sum_n (alpha_kn + beta_kn ln f_c) (j u)^n,
 // the binomial series of the PN power laws (alpha = binom(p_k, n)) and of
-// ln(1 + j u) for the two logarithmic terms.  The coefficients X_n of j^n are
-// formed once per chunk in FP64 (orders 0-3; orders 4-8 in FP32, where the
-// terms are below 1e-5 turns), and each grid point then needs only FP32 and
+// ln(1 + j u) for the two logarithmic terms.  The event-constant matrices
+// Q_kn(c) = u^n P_k(f_c) (alpha_kn + beta_kn ln f_c) are built once per event
+// in FP64 and stored as float pairs (orders 0-2) and floats (orders 3-8); a
+// rebuild forms X_n(c) = sum_k (c_k / 2pi) Q_kn(c) with float-pair dot
+// products on the FP32 pipe.  Each grid point then needs only FP32 and
 // float-pair arithmetic: X0 + X1 j + X2 j^2 (float pairs) + j^3 (X3 + ... +
 // X8 j^5) (FP32 Horner), reduction to [-1/2, 1/2] turns, the half-angle
 // sin/cos, and the amplitude f^-7/6 = f_c^-7/6 (1 + j u)^-7/6 (FP32 series).
 // With T f_low >= 1024 the truncated terms are below 1e-10 turns.  Strain
 // and PSD are scaled by powers of two into FP32 range; per-thread partial
 // sums are FP32, the block reduction is in float pairs, and the epilogue
-// applies conj(K_d) = conj(A_ref P_d) and the scale factors in FP64.
+// applies conj(K_d) and the scale factors in FP64.
 // ===========================================================================
 constexpr int kChunk = 32;
 constexpr int kOrd = 8;
@@ -284,9 +322,20 @@ constexpr int kOrd = 8;
 struct TaylorTables {
   double alpha[kNBasis][kOrd + 1];
   double beta6[kOrd + 1];  // ln f_c coefficient of the f^1/3 ln f term
-  float amp[5];            // binom(-7/6, n)
+  double amp[5];           // binom(-7/6, n)
 };
 
+// Event-constant per-chunk matrices, stored field-major ([field][chunk]) so
+// that consecutive threads read consecutive chunks.  Fields:
+constexpr int kQ01 = 0;                       // (k*2 + n)*2 + h: orders 0, 1 as float pairs
+constexpr int kQ2 = kQ01 + kNBasis * 4;       // k*2 + h: order 2 as a float pair
+constexpr int kQh = kQ2 + kNBasis * 2;        // (n-3)*10 + k: orders 3..8
+constexpr int kQfc = kQh + (kOrd - 2) * kNBasis;  // f_c as a float pair
+constexpr int kQamp = kQfc + 2;               // f_c^-7/6, binom(-7/6, n) u^n (n = 1..4)
+constexpr int kQFields = kQamp + 5;
+static_assert(kQFields <= 128, "chunk matrix fields");
+
+// Per-rebuild chunk coefficients (128 bytes).
 struct ChunkCoef {
   float x0[kMaxDet][2];   // X0 + f_c tau_d, reduced to [-1/2, 1/2] turns, float pair
   float x1[kMaxDet][2];   // X1 + df tau_d, float pair
@@ -297,69 +346,91 @@ struct ChunkCoef {
 };
 static_assert(sizeof(ChunkCoef) == 128, "chunk record is one 128-byte line");
 
-__global__ void __launch_bounds__(128) k_chunk_coef(const RefValues* __restrict__ ref, int64_t kmin, double T, int D,
-                                                    int64_t n_chunks, TaylorTables tt, ChunkCoef* __restrict__ out) {
+__global__ void __launch_bounds__(128) k_chunk_q(int64_t kmin, double T, int64_t n_chunks, TaylorTables tt,
+                                                 float* __restrict__ q) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_chunks) return;
-  const Values& v = ref->v;
+  auto put = [&](int f, float v) { q[(size_t)f * n_chunks + c] = v; };
   const double nc = (double)(kmin + c * kChunk + kChunk / 2);
   const double fc = nc / T, u = 1.0 / nc;
   const double cf = cbrt(fc), lf = log(fc), icf = 1.0 / cf, icf2 = icf * icf;
   const double P[kNBasis] = {icf2 * icf2 * icf, 1.0 / fc, icf2, icf, 1.0, cf, cf, cf * cf, fc * cf * cf, fc * fc * cf};
-  double vk[kNBasis];
-#pragma unroll
-  for (int k = 0; k < kNBasis; ++k) vk[k] = v.c[k] * (1.0 / kTwoPi) * P[k];
-  double X[4];
   double un = 1.0;
-#pragma unroll
-  for (int n = 0; n < 4; ++n) {
-    double s = lf * vk[6] * tt.beta6[n];
-#pragma unroll
-    for (int k = 0; k < kNBasis; ++k) s = fma(vk[k], tt.alpha[k][n], s);
-    if (n == 0) s = fma(lf, vk[4], s);
-    X[n] = s * un;
+  for (int n = 0; n <= kOrd; ++n) {
+    for (int k = 0; k < kNBasis; ++k) {
+      double a = tt.alpha[k][n];
+      if (k == 6) a += tt.beta6[n] * lf;
+      if (k == 4 && n == 0) a = lf;
+      const double v = un * P[k] * a;
+      if (n < 2) {
+        const f2x p = f2x_from(v);
+        put(kQ01 + (k * 2 + n) * 2, p.hi);
+        put(kQ01 + (k * 2 + n) * 2 + 1, p.lo);
+      } else if (n == 2) {
+        const f2x p = f2x_from(v);
+        put(kQ2 + k * 2, p.hi);
+        put(kQ2 + k * 2 + 1, p.lo);
+      } else {
+        put(kQh + (n - 3) * kNBasis + k, (float)v);
+      }
+    }
     un *= u;
   }
-  ChunkCoef o;
-  float vf[kNBasis];
-#pragma unroll
-  for (int k = 0; k < kNBasis; ++k) vf[k] = (float)vk[k];
-  const float lff = (float)lf;
-  float unf = (float)un;  // u^4
-  const float uf = (float)u;
-#pragma unroll
-  for (int n = 4; n <= kOrd; ++n) {
-    float s = lff * vf[6] * (float)tt.beta6[n];
-#pragma unroll
-    for (int k = 0; k < kNBasis; ++k) s = fmaf(vf[k], (float)tt.alpha[k][n], s);
-    o.xh[n - 3] = s * unf;
-    unf *= uf;
+  const f2x fcp = f2x_from(fc);
+  put(kQfc, fcp.hi);
+  put(kQfc + 1, fcp.lo);
+  put(kQamp, (float)(sqrt(icf) / fc));  // f_c^-7/6
+  double ua = u;
+  for (int n = 1; n < 5; ++n) {
+    put(kQamp + n, (float)(tt.amp[n] * ua));
+    ua *= u;
   }
-  const double x0 = X[0] + v.phi0 * (1.0 / kTwoPi);
+}
+
+__global__ void __launch_bounds__(128) k_chunk_coef(const RefValues* __restrict__ ref, const float* __restrict__ q,
+                                                    float invT_hi, float invT_lo, int D, int64_t n_chunks,
+                                                    ChunkCoef* __restrict__ out) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_chunks) return;
+  const RefValues& r = *ref;
+  auto get = [&](int f) { return q[(size_t)f * n_chunks + c]; };
+  float x0h = r.phi0t[0], x0l = r.phi0t[1], x1h = 0.f, x1l = 0.f, x2h = 0.f, x2l = 0.f;
+  float xh[kOrd - 2];
+#pragma unroll
+  for (int n = 0; n < kOrd - 2; ++n) xh[n] = 0.f;
+#pragma unroll
+  for (int k = 0; k < kNBasis; ++k) {
+    const float ch = r.chat[k][0], cl = r.chat[k][1];
+    f2x_fma_acc(ch, cl, get(kQ01 + k * 4), get(kQ01 + k * 4 + 1), x0h, x0l);
+    f2x_fma_acc(ch, cl, get(kQ01 + k * 4 + 2), get(kQ01 + k * 4 + 3), x1h, x1l);
+    f2x_fma_acc(ch, cl, get(kQ2 + k * 2), get(kQ2 + k * 2 + 1), x2h, x2l);
+#pragma unroll
+    for (int n = 0; n < kOrd - 2; ++n) xh[n] = fmaf(ch, get(kQh + n * kNBasis + k), xh[n]);
+  }
+  const float fch = get(kQfc), fcl = get(kQfc + 1);
+  ChunkCoef o;
+#pragma unroll
   for (int d = 0; d < kMaxDet; ++d) {
     if (d < D) {
-      double a = fma(fc, v.tau[d], x0);
-      a -= rint(a);
-      const f2x p0 = f2x_from(a), p1 = f2x_from(X[1] + v.tau[d] / T);
-      o.x0[d][0] = p0.hi;
-      o.x0[d][1] = p0.lo;
-      o.x1[d][0] = p1.hi;
-      o.x1[d][1] = p1.lo;
+      float ah = x0h, al = x0l;
+      f2x_fma_acc(r.taut[d][0], r.taut[d][1], fch, fcl, ah, al);
+      const float rh = __fadd_rn(ah, -round_fma_pipe(ah));  // exact: drop whole turns
+      o.x0[d][0] = rh;
+      o.x0[d][1] = al;
+      float bh = x1h, bl = x1l;
+      f2x_fma_acc(r.taut[d][0], r.taut[d][1], invT_hi, invT_lo, bh, bl);
+      o.x1[d][0] = bh;
+      o.x1[d][1] = bl;
     } else {
       o.x0[d][0] = o.x0[d][1] = o.x1[d][0] = o.x1[d][1] = 0.f;
     }
   }
-  const f2x p2 = f2x_from(X[2]);
-  o.x2[0] = p2.hi;
-  o.x2[1] = p2.lo;
-  o.xh[0] = (float)X[3];
-  o.amp[0] = (float)(sqrt(icf) / fc);  // f_c^-7/6
-  float ua = uf;
+  o.x2[0] = x2h;
+  o.x2[1] = x2l;
 #pragma unroll
-  for (int n = 1; n < 5; ++n) {
-    o.amp[n] = tt.amp[n] * ua;
-    ua *= uf;
-  }
+  for (int n = 0; n < kOrd - 2; ++n) o.xh[n] = xh[n];
+#pragma unroll
+  for (int n = 0; n < 5; ++n) o.amp[n] = get(kQamp + n);
 #pragma unroll
   for (int i = 0; i < 7; ++i) o.pad[i] = 0.f;
   out[c] = o;
@@ -386,12 +457,52 @@ __device__ __forceinline__ void f2x_add(float& hi, float& lo, float v) {
   hi = s;
 }
 
+// One grid point of the fast summary sums.
+__device__ __forceinline__ void fast_point(const ChunkCoef& C, int d, int64_t k, double2 dv, double psd, int sd,
+                                           int sS, int64_t e01, float half_df, float* acc) {
+  const float jf = (float)((int)(k & (kChunk - 1)) - kChunk / 2);
+  const float dre = scaled_float(dv.x, sd), dim = scaled_float(dv.y, sd);
+  const float Sp = scaled_float(psd, sS);
+  float t = C.xh[5];
+#pragma unroll
+  for (int n = 4; n >= 0; --n) t = fmaf(t, jf, C.xh[n]);
+  const float j2 = jf * jf;
+  const float t3 = t * (j2 * jf);
+  const float p1 = __fmul_rn(C.x1[d][0], jf);
+  float e1e = __fmaf_rn(C.x1[d][0], jf, -p1);
+  e1e = __fmaf_rn(C.x1[d][1], jf, e1e);
+  const float p2 = __fmul_rn(C.x2[0], j2);
+  float e2e = __fmaf_rn(C.x2[0], j2, -p2);
+  e2e = __fmaf_rn(C.x2[1], j2, e2e);
+  float sh = C.x0[d][0], sl = C.x0[d][1];
+  f2x_add(sh, sl, p1);
+  f2x_add(sh, sl, p2);
+  sl = __fadd_rn(sl, __fadd_rn(__fadd_rn(e1e, e2e), t3));
+  const float y = frac_turns(sh, sl);
+  float sn, cs;
+  sincos_pi_half(y, sn, cs);
+  const float Cc = fmaf(-2.f * sn, sn, 1.f), Ss = 2.f * sn * cs;  // exp(+2 pi i y)
+  const float A = C.amp[0] * fmaf(jf, fmaf(jf, fmaf(jf, fmaf(jf, C.amp[4], C.amp[3]), C.amp[2]), C.amp[1]), 1.f);
+  const float wA = A / Sp;
+  const float dr = dre * wA, di = dim * wA;
+  const float qr = fmaf(dr, Cc, -di * Ss), qi = fmaf(dr, Ss, di * Cc);
+  const float dff = (float)(2 * k - e01) * half_df;  // f - f_m
+  acc[0] += qr;
+  acc[1] += qi;
+  acc[2] = fmaf(qr, dff, acc[2]);
+  acc[3] = fmaf(qi, dff, acc[3]);
+  const float hh = wA * A;
+  acc[4] += hh;
+  acc[5] = fmaf(hh, dff, acc[5]);
+}
+
 constexpr int kFastThreads = 128;
+constexpr int kFastUnroll = 4;
+constexpr int kSeg = 1024;  // points per staged segment
 __global__ void __launch_bounds__(kFastThreads) k_summary_fast(DataPtrs in, const ChunkCoef* __restrict__ ch,
-                                                               int64_t kmin, int64_t N, double T, int B,
+                                                               double T, int B, int D,
                                                                const int64_t* __restrict__ edges,
-                                                               const RefValues* __restrict__ ref,
-                                                               double* __restrict__ out) {
+                                                               const RefValues* __restrict__ ref, SummaryOut so) {
   const int b = blockIdx.x, d = blockIdx.y;
   const int64_t e0 = edges[b], e1 = edges[b + 1];
   const int64_t k0 = e0;
@@ -403,44 +514,38 @@ __global__ void __launch_bounds__(kFastThreads) k_summary_fast(DataPtrs in, cons
   const int sS = -ex, sd = -(ex / 2);
   const float half_df = (float)(0.5 / T);
   float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int64_t k = k0 + threadIdx.x; k < k1; k += kFastThreads) {
-    const ChunkCoef& C = ch[k >> 5];
-    const float jf = (float)((int)(k & (kChunk - 1)) - kChunk / 2);
-    const double2 dv = *reinterpret_cast<const double2*>(dat + 2 * k);
-    const float dre = scaled_float(dv.x, sd), dim = scaled_float(dv.y, sd);
-    const float Sp = scaled_float(psd[k], sS);
-    // phase in turns: float pairs for X0 + X1 j + X2 j^2, FP32 for the rest
-    float t = C.xh[5];
+  // The bin is processed in segments of kSeg points; the segment's chunk
+  // records are staged in shared memory first (coalesced 16-byte loads).
+  __shared__ __align__(16) ChunkCoef sch[kSeg / kChunk + 1];
+  for (int64_t s0 = k0; s0 < k1; s0 += kSeg) {
+    const int64_t s1 = (s0 + kSeg < k1) ? s0 + kSeg : k1;
+    const int64_t c0 = s0 >> 5, nch = ((s1 - 1) >> 5) - c0 + 1;
+    {
+      const float4* src = reinterpret_cast<const float4*>(ch + c0);
+      float4* dst = reinterpret_cast<float4*>(sch);
+      const int n4 = (int)nch * (int)(sizeof(ChunkCoef) / 16);
+      for (int i = threadIdx.x; i < n4; i += kFastThreads) dst[i] = src[i];
+    }
+    __syncthreads();
+    // issue the loads of kFastUnroll points before using any of them
+    for (int64_t kb = s0 + threadIdx.x; kb < s1; kb += kFastThreads * kFastUnroll) {
+      double2 dv[kFastUnroll];
+      double pv[kFastUnroll];
 #pragma unroll
-    for (int n = 4; n >= 0; --n) t = fmaf(t, jf, C.xh[n]);
-    const float j2 = jf * jf;
-    const float t3 = t * (j2 * jf);
-    const float p1 = __fmul_rn(C.x1[d][0], jf);
-    float e1e = __fmaf_rn(C.x1[d][0], jf, -p1);
-    e1e = __fmaf_rn(C.x1[d][1], jf, e1e);
-    const float p2 = __fmul_rn(C.x2[0], j2);
-    float e2e = __fmaf_rn(C.x2[0], j2, -p2);
-    e2e = __fmaf_rn(C.x2[1], j2, e2e);
-    float sh = C.x0[d][0], sl = C.x0[d][1];
-    f2x_add(sh, sl, p1);
-    f2x_add(sh, sl, p2);
-    sl = __fadd_rn(sl, __fadd_rn(__fadd_rn(e1e, e2e), t3));
-    const float y = frac_turns(sh, sl);
-    float sn, cs;
-    sincos_pi_half(y, sn, cs);
-    const float Cc = fmaf(-2.f * sn, sn, 1.f), Ss = 2.f * sn * cs;  // exp(+2 pi i y)
-    const float A = C.amp[0] * fmaf(jf, fmaf(jf, fmaf(jf, fmaf(jf, C.amp[4], C.amp[3]), C.amp[2]), C.amp[1]), 1.f);
-    const float wA = A / Sp;
-    const float dr = dre * wA, di = dim * wA;
-    const float qr = fmaf(dr, Cc, -di * Ss), qi = fmaf(dr, Ss, di * Cc);
-    const float dff = (float)(2 * k - e0 - e1) * half_df;  // f - f_m
-    acc[0] += qr;
-    acc[1] += qi;
-    acc[2] = fmaf(qr, dff, acc[2]);
-    acc[3] = fmaf(qi, dff, acc[3]);
-    const float hh = wA * A;
-    acc[4] += hh;
-    acc[5] = fmaf(hh, dff, acc[5]);
+      for (int u = 0; u < kFastUnroll; ++u) {
+        const int64_t k = kb + (int64_t)u * kFastThreads;
+        if (k < s1) {
+          dv[u] = *reinterpret_cast<const double2*>(dat + 2 * k);
+          pv[u] = psd[k];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kFastUnroll; ++u) {
+        const int64_t k = kb + (int64_t)u * kFastThreads;
+        if (k < s1) fast_point(sch[(k >> 5) - c0], d, k, dv[u], pv[u], sd, sS, e0 + e1, half_df, acc);
+      }
+    }
+    __syncthreads();
   }
   // float-pair block reduction (fixed order)
   float lo[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -455,6 +560,8 @@ __global__ void __launch_bounds__(kFastThreads) k_summary_fast(DataPtrs in, cons
     }
   }
   __shared__ float red[kFastThreads / 32][6][2];
+  __shared__ double sblock[6];
+  __shared__ double scale[4];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0)
     for (int j = 0; j < 6; ++j) {
@@ -462,29 +569,20 @@ __global__ void __launch_bounds__(kFastThreads) k_summary_fast(DataPtrs in, cons
       red[wid][j][1] = lo[j];
     }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double s[6];
-    for (int j = 0; j < 6; ++j) {
-      double t = 0.0;
-      for (int i = 0; i < kFastThreads / 32; ++i) t += (double)red[i][j][0] + (double)red[i][j][1];
-      s[j] = t;
+  if (threadIdx.x < 6) {
+    float h = red[0][threadIdx.x][0], l = red[0][threadIdx.x][1];
+    for (int i = 1; i < kFastThreads / 32; ++i) {
+      f2x_add(h, l, red[i][threadIdx.x][0]);
+      l = __fadd_rn(l, red[i][threadIdx.x][1]);
     }
-    const Values& v = ref->v;
-    const double kamp = 8.035028173395984e-06 / kMpcS;
-    const double a = kamp * v.amp;
-    const double Kr = a * v.P64[d][0], Ki = a * v.P64[d][1];
+    sblock[threadIdx.x] = (double)h + (double)l;
+  } else if (threadIdx.x >= 32 && threadIdx.x < 36) {
+    const int j = threadIdx.x - 32;
     const double w4 = 4.0 / T;
-    const double sq = ldexp(w4, sS - sd), sb = ldexp(w4, sS);
-    double* o = out + ((size_t)d * B + b) * 6;
-    // conj(K) (s0 + i s1)
-    o[0] = sq * (Kr * s[0] + Ki * s[1]);
-    o[1] = sq * (Kr * s[1] - Ki * s[0]);
-    o[2] = sq * (Kr * s[2] + Ki * s[3]);
-    o[3] = sq * (Kr * s[3] - Ki * s[2]);
-    const double K2 = Kr * Kr + Ki * Ki;
-    o[4] = sb * K2 * s[4];
-    o[5] = sb * K2 * s[5];
+    scale[j] = j == 0 ? ldexp(w4, sS - sd) : (j == 1 ? ldexp(w4, sS) : ref->K[d][j - 2]);
   }
+  __syncthreads();
+  summary_epilogue(so, b, d, B, D, sblock, scale, true);
 }
 
 static TaylorTables make_taylor_tables() {
@@ -512,25 +610,35 @@ static TaylorTables make_taylor_tables() {
   }
   double b = 1.0;
   for (int n = 0; n < 5; ++n) {
-    t.amp[n] = (float)b;
+    t.amp[n] = b;
     b *= (-7.0 / 6.0 - n) / (n + 1);
   }
   return t;
 }
 
-size_t chunk_scratch_bytes(int64_t N) { return sizeof(ChunkCoef) * (size_t)((N + kChunk - 1) / kChunk); }
+int64_t n_chunks_of(int64_t N) { return (N + kChunk - 1) / kChunk; }
+size_t chunk_q_bytes(int64_t N) { return sizeof(float) * 128 * (size_t)n_chunks_of(N); }
+size_t chunk_coef_bytes(int64_t N) { return sizeof(ChunkCoef) * (size_t)n_chunks_of(N); }
 
-cudaError_t launch_summary_fast(const DataPtrs& in, int64_t kmin, int64_t N, double T, int D, int B,
-                                const int64_t* edges, const RefValues* ref, void* chunk_scratch, double* out,
-                                cudaStream_t s) {
+cudaError_t launch_chunk_q(int64_t kmin, double T, int64_t N, void* cq, cudaStream_t s) {
   static const TaylorTables tt = make_taylor_tables();
-  const int64_t n_chunks = (N + kChunk - 1) / kChunk;
-  ChunkCoef* ch = static_cast<ChunkCoef*>(chunk_scratch);
-  k_chunk_coef<<<(unsigned)((n_chunks + 127) / 128), 128, 0, s>>>(ref, kmin, T, D, n_chunks, tt, ch);
+  const int64_t nc = n_chunks_of(N);
+  k_chunk_q<<<(unsigned)((nc + 127) / 128), 128, 0, s>>>(kmin, T, nc, tt, static_cast<float*>(cq));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_summary_fast(const DataPtrs& in, int64_t N, double T, int D, int B, const int64_t* edges,
+                                const RefValues* ref, const void* cq, void* chunk_coef, const SummaryOut& so,
+                                cudaStream_t s) {
+  const int64_t nc = n_chunks_of(N);
+  ChunkCoef* ch = static_cast<ChunkCoef*>(chunk_coef);
+  const double invT = 1.0 / T;
+  const float ih = (float)invT, il = (float)(invT - (double)ih);
+  k_chunk_coef<<<(unsigned)((nc + 127) / 128), 128, 0, s>>>(ref, static_cast<const float*>(cq), ih, il, D, nc, ch);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   dim3 grid(B, D);
-  k_summary_fast<<<grid, kFastThreads, 0, s>>>(in, ch, kmin, N, T, B, edges, ref, out);
+  k_summary_fast<<<grid, kFastThreads, 0, s>>>(in, ch, T, B, D, edges, ref, so);
   return cudaGetLastError();
 }
 
