@@ -211,6 +211,8 @@ typedef struct {
   uint64_t submitted, completed, rejected, graph_launches, plain_launches, graphs_captured;
   int32_t in_flight, queued;
   size_t hbm_in_use;
+  int32_t max_in_flight;  /* largest number of requests on the GPU at once so far */
+  int32_t reserved;
 } rb_server_stats;
 
 RB_API int rb_server_create(const rb_server_opts* opts, rb_server_t* out);

@@ -47,7 +47,7 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
                 ("graph_launches", ctypes.c_uint64), ("plain_launches", ctypes.c_uint64),
                 ("graphs_captured", ctypes.c_uint64), ("in_flight", ctypes.c_int32), ("queued", ctypes.c_int32),
-                ("hbm_in_use", ctypes.c_size_t)]
+                ("hbm_in_use", ctypes.c_size_t), ("max_in_flight", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 # name -> (restype, argtypes); the order follows include/rb.h

@@ -26,7 +26,6 @@
 // edge shared by two chunks collects the two halves in two passes, which is
 // exact because the adjoint is linear in the per-edge cotangent.
 #include <algorithm>
-#include <map>
 #include <mutex>
 
 #include "rb_internal.cuh"
@@ -409,33 +408,44 @@ size_t mixed_smem_bytes(const EventDev& ev, bool phase64) {
   return (size_t)(kNBasis + 1) * ev.e_pad * sizeof(double) + (ev.tab32_floats - ev.edge32_floats) * sizeof(float);
 }
 
-// Occupancy per (kernel, shared-memory size), cached: the query costs host
-// time on every launch otherwise.
-struct OccKey {
+// Occupancy per (kernel, shared-memory size), cached in a fixed table (no
+// heap allocation on the launch path): the query costs host time otherwise.
+struct OccEntry {
   const void* fn;
   size_t smem;
-  bool operator<(const OccKey& o) const { return fn < o.fn || (fn == o.fn && smem < o.smem); }
+  int blocks;
 };
+constexpr int kOccSlots = 256;
 static std::mutex g_occ_mu;
-static std::map<OccKey, int> g_occ;
+static OccEntry g_occ[kOccSlots];
+static int g_occ_n = 0;
+static const void* g_smem_raised[16];
+static int g_smem_raised_n = 0;
 
 static cudaError_t blocks_per_sm(const void* fn, int threads, size_t smem, int* out) {
-  {
-    std::lock_guard<std::mutex> lk(g_occ_mu);
-    auto it = g_occ.find({fn, smem});
-    if (it != g_occ.end()) {
-      *out = it->second;
+  std::lock_guard<std::mutex> lk(g_occ_mu);
+  for (int i = 0; i < g_occ_n; ++i)
+    if (g_occ[i].fn == fn && g_occ[i].smem == smem) {
+      *out = g_occ[i].blocks;
       return cudaSuccess;
     }
-  }
   cudaError_t err = cudaSuccess;
-  if (smem > 48 * 1024) err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
+  bool raised = false;
+  for (int i = 0; i < g_smem_raised_n; ++i) raised = raised || g_smem_raised[i] == fn;
+  if (!raised) {
+    // allow any dynamic shared-memory size up to the device limit once, so
+    // that launches for different events never shrink it for one another
+    int dev = 0, smem_max = 0;
+    err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (err == cudaSuccess) err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+    if (err != cudaSuccess) return err;
+    if (g_smem_raised_n < 16) g_smem_raised[g_smem_raised_n++] = fn;
+  }
   int n = 0;
   err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem);
   if (err != cudaSuccess) return err;
-  std::lock_guard<std::mutex> lk(g_occ_mu);
-  g_occ[{fn, smem}] = n;
+  if (g_occ_n < kOccSlots) g_occ[g_occ_n++] = OccEntry{fn, smem, n};
   *out = n;
   return cudaSuccess;
 }

@@ -12,6 +12,7 @@
 // first walker; every walker is computed independently by one warp, so each
 // result is bit-identical to the same request evaluated alone.
 #include <chrono>
+#include <cstdio>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -37,6 +38,7 @@ struct Request {
   std::vector<double> theta, logl, grad;
   int status = RB_OK;
   bool done = false;
+  char msg[256] = "";  // error detail (set on the scheduler thread)
 };
 
 struct Server;
@@ -167,11 +169,13 @@ void Server::run() {
     s->req = r;
     hbm_in_use += r->footprint;
     ++in_flight;
+    if (in_flight > stats.max_in_flight) stats.max_in_flight = in_flight;
     lk.unlock();
     const int rc = launch(s, r);
     lk.lock();
     if (rc != RB_OK) {
       // the host node never ran: release here
+      std::snprintf(r->msg, sizeof(r->msg), "%s", rb_last_error());
       r->status = rc;
       r->done = true;
       hbm_in_use -= r->footprint;
@@ -185,6 +189,7 @@ void Server::run() {
   cv.wait(lk, [&] { return in_flight == 0; });
   for (Request* r : pending) {
     r->status = RB_ECLOSED;
+    std::snprintf(r->msg, sizeof(r->msg), "server shut down before the request ran");
     r->done = true;
   }
   pending.clear();
@@ -326,6 +331,7 @@ int rb_poll(rb_server_t srv, uint64_t ticket, int64_t timeout_us, double* logl_o
     }
   }
   const int status = r->status;
+  if (status != RB_OK) set_error(status, "rb_poll: request failed: %s", r->msg);
   if (status == RB_OK) {
     if (logl_out) std::memcpy(logl_out, r->logl.data(), sizeof(double) * r->W);
     if (grad_out && r->want_grad) std::memcpy(grad_out, r->grad.data(), sizeof(double) * kNPar * r->W);
