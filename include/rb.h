@@ -181,6 +181,23 @@ RB_API int rb_loglike_grad_batch(rb_event_t ev, const double* theta_dev, int64_t
 RB_API int rb_loglike_grad_host(rb_event_t ev, const double* theta_host, int64_t W, double* logl_host, double* grad_host,
                          int mode, void* stream);
 
+/* Allocation-free form of rb_loglike_grad_batch (the paper has no
+ * counterpart: it is an interface for callers that cannot allocate device
+ * memory at call time -- e.g. inside a stream capture in global mode, or
+ * under a host framework that owns the device memory).  Same arguments,
+ * results and errors as rb_loglike_grad_batch (grad_dev may be NULL for log L
+ * only), but the per-walker workspace is a fixed device array inside the
+ * library (RB_STATIC_MAX_WALKERS records, about 7.5 MiB, held on every device
+ * that loads the library until exit), so the call allocates nothing.
+ * W > RB_STATIC_MAX_WALKERS returns RB_EINVAL.  The first call on a device
+ * looks up the array's address (cudaGetSymbolAddress) and should come before
+ * any stream capture.  All calls share the array: calls whose kernels can
+ * overlap on the GPU race and must be ordered by the caller.  Asynchronous on
+ * `stream`. */
+#define RB_STATIC_MAX_WALKERS 8192
+RB_API int rb_loglike_grad_batch_static(rb_event_t ev, const double* theta_dev, int64_t W, double* logl_dev,
+                                        double* grad_dev, int mode, void* stream);
+
 /* TaylorF2 + tidal detector strain h_d(f; theta) (FP64) on the grid
  * f_k = (kmin + k)/T, k = 0..n_freq-1, for one source: geom = {lat, lon,
  * elev_m, xarm_az, yarm_az}, theta_host [13].  h_dev: device [n_freq][2].

@@ -13,6 +13,7 @@ RB_MIXED, RB_FP64, RB_MIXED_F64PHASE = 0, 1, 2
 MODES = {"mixed": RB_MIXED, "fp64": RB_FP64, "mixed_f64phase": RB_MIXED_F64PHASE}
 NPAR = 13
 MAX_DET = 3
+RB_STATIC_MAX_WALKERS = 8192
 
 c_double_p = ctypes.POINTER(ctypes.c_double)
 c_int64_p = ctypes.POINTER(ctypes.c_int64)
@@ -63,6 +64,8 @@ SIGNATURES = {
                                         ctypes.c_int, ctypes.c_void_p]),
     "rb_loglike_grad_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "rb_loglike_grad_batch_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                                    ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "rb_loglike_grad_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "rb_strain": (ctypes.c_int, [c_double_p, ctypes.c_double, c_double_p, ctypes.c_double, ctypes.c_int64,
