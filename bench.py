@@ -205,19 +205,15 @@ def run_gb300(args, dist: Dist):
     theta = torch.tensor(synth.walkers("C2", W), device=device)
     logl = torch.empty(W, dtype=torch.float64, device=device)
     grad = torch.empty(W, 13, dtype=torch.float64, device=device)
-    data_rows = [data[d].contiguous() for d in range(D)]
-    psd_rows = [psd[d].contiguous() for d in range(D)]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
     lib = rb.load()
     import ctypes
-    dp = (ctypes.c_void_p * D)(*[t.data_ptr() for t in data_rows])
-    pp = (ctypes.c_void_p * D)(*[t.data_ptr() for t in psd_rows])
 
     def launch(mode, stream_handle, rebuild=True):
         """One step through the C ABI: rebuild the summary data from the
-        HBM-resident strain, then log L + gradient for the batch."""
+        event's HBM-resident strain and PSD, then log L + gradient for the batch."""
         m = rb.MODES[mode]
-        rc = lib.rb_event_rebuild(event.handle, None, dp, pp, 1, m, stream_handle) if rebuild else 0
+        rc = lib.rb_event_rebuild(event.handle, None, None, None, 0, m, stream_handle) if rebuild else 0
         if rc == 0:
             rc = lib.rb_loglike_grad_batch(event.handle, ctypes.c_void_p(theta.data_ptr()), W,
                                            ctypes.c_void_p(logl.data_ptr()), ctypes.c_void_p(grad.data_ptr()), m,

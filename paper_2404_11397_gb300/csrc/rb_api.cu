@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -34,11 +35,12 @@ cudaError_t launch_edge_tables(int64_t kmin, double T, int D, int B, int Ep, int
                                float* tab32, size_t edge32_floats, double* tab64, double* inv_df, cudaStream_t s);
 cudaError_t launch_chunk_q(int64_t kmin, double T, int64_t N, void* cq, cudaStream_t s);
 size_t chunk_q_bytes(int64_t N);
-size_t chunk_coef_bytes(int64_t N);
 cudaError_t launch_strain(const RefValues* src, int64_t kmin, int64_t N, double T, double* h, cudaStream_t s);
-cudaError_t launch_summary_fast(const DataPtrs& in, int64_t N, double T, int D, int B, const int64_t* edges,
-                                const RefValues* ref, const void* cq, void* chunk_coef, const SummaryOut& so,
-                                cudaStream_t s);
+cudaError_t launch_summary_fast(const void* w32, const float* is32, const int* exps, int64_t N, double T, int D, int B,
+                                const int64_t* edges, const RefValues* ref, const void* cq, void* chunk_coef,
+                                const SummaryOut& so, int n_parts, cudaStream_t s);
+cudaError_t launch_data32(const DataPtrs& in, int64_t N, int D, void* w32, float* is32, int* exps, cudaStream_t s);
+size_t chunk_coef_bytes(int64_t N);
 
 // ---- diagnostics ----
 static thread_local char g_err[512] = "no error";
@@ -137,6 +139,41 @@ const char* rb_strerror(int status) {
   }
 }
 
+// Split every bin into parts of at most kPartPoints grid points for the fast
+// summary build (bin edges are final here; they do not change on a rebuild).
+static int make_parts(EventEntry& e, cudaStream_t s) {
+  const int B = e.n_bins;
+  std::vector<int64_t> edges(B + 1);
+  cudaError_t err = cudaMemcpyAsync(edges.data(), e.d_edges, sizeof(int64_t) * (B + 1), cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) return cuda_fail(err, "rb_build_summary: read bin edges");
+  std::vector<PartDesc> parts;
+  for (int b = 0; b < B; ++b) {
+    const int64_t k0 = edges[b], k1 = (b == B - 1) ? edges[b + 1] + 1 : edges[b + 1];
+    const int np = (int)((k1 - k0 + kPartPoints - 1) / kPartPoints);
+    const int first = (int)parts.size();
+    for (int p = 0; p < np; ++p) {
+      PartDesc d{};
+      d.bin = b;
+      d.start = (int)(k0 + (int64_t)p * kPartPoints);
+      d.end = (int)std::min<int64_t>(k1, k0 + (int64_t)(p + 1) * kPartPoints);
+      d.first = first;
+      d.n_parts = np;
+      parts.push_back(d);
+    }
+  }
+  e.n_parts = (int)parts.size();
+  const size_t pb = sizeof(PartDesc) * parts.size(), sb = sizeof(float) * 2 * 7 * kMaxDet * parts.size();
+  if ((err = cudaMalloc((void**)&e.d_parts, pb)) != cudaSuccess) return cuda_fail(err, "parts");
+  e.device_bytes += pb;
+  if ((err = cudaMalloc((void**)&e.d_part_sums, sb)) != cudaSuccess) return cuda_fail(err, "part sums");
+  e.device_bytes += sb;
+  err = cudaMemcpyAsync(e.d_parts, parts.data(), pb, cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);  // `parts` is freed on return
+  if (err != cudaSuccess) return cuda_fail(err, "upload parts");
+  return RB_OK;
+}
+
 int rb_event_free(rb_event_t ev) {
   if (!ev) return RB_OK;
   EventEntry& e = ev->e;
@@ -153,7 +190,12 @@ int rb_event_free(rb_event_t ev) {
   cudaFree(e.d_chunks);
   cudaFree(e.d_invdf);
   cudaFree(e.d_share);
-  cudaFree(e.d_counter);
+  cudaFree(e.d_sync);
+  cudaFree(e.d_w32);
+  cudaFree(e.d_is32);
+  cudaFree(e.d_wexp);
+  cudaFree(e.d_parts);
+  cudaFree(e.d_part_sums);
   delete ev;
   return RB_OK;
 }
@@ -241,7 +283,10 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
         {(void**)&e.d_chunks, chunk_coef_bytes(N), "chunk coefficients"},
         {(void**)&e.d_invdf, sizeof(double) * B, "bin widths"},
         {(void**)&e.d_share, sizeof(double) * D * B, "base shares"},
-        {(void**)&e.d_counter, sizeof(unsigned), "block counter"}};
+        {(void**)&e.d_sync, offsetof(SummarySync, bin_parts_done) + sizeof(unsigned) * B, "build counters"},
+        {(void**)&e.d_w32, sizeof(float) * 2 * D * N, "FP32 data copy"},
+        {(void**)&e.d_is32, sizeof(float) * D * N, "FP32 inverse PSD copy"},
+        {(void**)&e.d_wexp, sizeof(int) * 2 * kMaxDet, "FP32 copy scales"}};
     for (auto& a : allocs) {
       if ((err = cudaMalloc(a.p, a.n)) != cudaSuccess) { rc = cuda_fail(err, a.what); break; }
       e.device_bytes += a.n;
@@ -268,8 +313,9 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
     }
     if (rc != RB_OK) break;
     if ((err = cudaMemcpyAsync(e.d_theta_ref, e.theta_ref, sizeof(double) * kNPar, cudaMemcpyHostToDevice, s)) != cudaSuccess) { rc = cuda_fail(err, "copy theta_ref"); break; }
-    if ((err = cudaMemsetAsync(e.d_counter, 0, sizeof(unsigned), s)) != cudaSuccess) { rc = cuda_fail(err, "zero counter"); break; }
+    if ((err = cudaMemsetAsync(e.d_sync, 0, offsetof(SummarySync, bin_parts_done) + sizeof(unsigned) * B, s)) != cudaSuccess) { rc = cuda_fail(err, "zero counters"); break; }
     if ((err = launch_bin_edges(e.f_low, e.f_high, e.T, kmin, N, B, e.d_edges, s)) != cudaSuccess) { rc = cuda_fail(err, "bin edge kernels"); break; }
+    if ((rc = make_parts(e, s)) != RB_OK) break;
     if ((err = launch_edge_tables(kmin, e.T, D, B, Ep, Bp, e.d_edges, e.d_tab32, edge32, e.d_tab64, e.d_invdf, s)) != cudaSuccess) { rc = cuda_fail(err, "edge table kernel"); break; }
     if ((err = launch_chunk_q(kmin, e.T, N, e.d_chunkq, s)) != cudaSuccess) { rc = cuda_fail(err, "chunk matrix kernel"); break; }
     count_launches(4);
@@ -312,6 +358,7 @@ int rb_event_rebuild(rb_event_t ev, const double* theta_ref_host, const double* 
       }
       have = true;
     } else {  // stage into the event's resident copy
+      e.w32_resident = false;
       for (int d = 0; d < e.n_det; ++d) {
         if ((err = cudaMemcpyAsync(e.d_data + 2 * (size_t)d * N, data[d], sizeof(double) * 2 * N, cudaMemcpyHostToDevice, s)) != cudaSuccess)
           return cuda_fail(err, "rb_event_rebuild: copy strain");
@@ -438,13 +485,26 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
     }
   }
   if ((err = launch_ref_values(e.d_theta_ref, e.ec, e.d_ref, s)) != cudaSuccess) return cuda_fail(err, "reference values kernel");
-  const bool fast = mode != RB_FP64 && e.kmin >= 1024;
-  if (fast)
-    err = launch_summary_fast(in, e.N, e.T, e.n_det, e.n_bins, e.d_edges, e.d_ref, e.d_chunkq, e.d_chunks, e.out(), s);
-  else
+  const bool fast = mode != RB_FP64 && e.kmin >= 1024 && e.N <= (int64_t(1) << 30);
+  int launches = 2;
+  if (fast) {
+    // the FP32 working copy follows the data the sums are taken over: data
+    // read in place are converted every time, the resident data only after
+    // they change
+    if (in_opt || !e.w32_resident) {
+      if ((err = launch_data32(in, e.N, e.n_det, e.d_w32, e.d_is32, e.d_wexp, s)) != cudaSuccess)
+        return cuda_fail(err, "data conversion kernel");
+      e.w32_resident = !in_opt;
+      ++launches;
+    }
+    err = launch_summary_fast(e.d_w32, e.d_is32, e.d_wexp, e.N, e.T, e.n_det, e.n_bins, e.d_edges, e.d_ref, e.d_chunkq,
+                              e.d_chunks, e.out(), e.n_parts, s);
+    ++launches;
+  } else {
     err = launch_summary(in, e.kmin, e.N, e.T, e.n_det, e.n_bins, e.d_edges, e.d_ref, e.out(), s);
+  }
   if (err != cudaSuccess) return cuda_fail(err, "summary kernel");
-  count_launches(fast ? 3 : 2);
+  count_launches(launches);
   return RB_OK;
 }
 

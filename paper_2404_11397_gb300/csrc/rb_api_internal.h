@@ -31,12 +31,19 @@ struct EventEntry {
   void* d_chunks = nullptr;   // per-rebuild chunk coefficients (fast summary build)
   double* d_invdf = nullptr;  // [B] 1 / bin width
   double* d_share = nullptr;  // [D][B] per-bin shares of log L(theta_ref)
-  unsigned* d_counter = nullptr;
+  SummarySync* d_sync = nullptr;  // build counters (zero between builds)
+  void* d_w32 = nullptr;          // fast build: FP32 copy w = d'/S' [D][N] (float2)
+  float* d_is32 = nullptr;        // fast build: FP32 copy 1/S' [D][N]
+  int* d_wexp = nullptr;          // fast build: power-of-two scales {sd, sS} per detector
+  bool w32_resident = false;      // the FP32 copy holds the resident data
+  PartDesc* d_parts = nullptr;    // fast build: parts of bins
+  float* d_part_sums = nullptr;   // fast build: per-part float-pair sums
+  int n_parts = 0;
   size_t device_bytes = 0;
   uint64_t uid = 0;  // unique per built event (never reused within a process)
   SummaryOut out() const {
     return SummaryOut{d_summ, d_tab32 + dev.edge32_floats, d_tab64 + (size_t)(kNBasis + 1) * dev.e_pad, d_invdf,
-                      d_share, d_counter, d_base, dev.b_pad};
+                      d_share, d_sync, d_base, dev.b_pad, d_parts, d_part_sums};
   }
 };
 
@@ -59,7 +66,7 @@ int run_batch(const EventEntry* e, const double* theta, int64_t W, double* logl,
 // device strain/PSD (NULL: the event's resident copy); no allocation, no
 // synchronisation.
 // mode RB_FP64 uses the FP64 summary kernel; the mixed modes use the fast
-// Taylor-chunk kernel when T f_low >= 1024 (FP64 kernel otherwise).
+// Taylor-chunk kernel when T f_low >= 1024 and N <= 2^30 (FP64 kernel otherwise).
 int rebuild_event(EventEntry& e, const DataPtrs* in, int mode, cudaStream_t s);
 
 // Events recorded on the launch stream right before / after the main

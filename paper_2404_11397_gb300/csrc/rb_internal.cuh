@@ -129,15 +129,36 @@ struct EventDev {
 };
 
 // Outputs of the summary kernels (see summary_epilogue).
+constexpr int kPartPoints = 512;  // grid points per part of a bin (fast summary build)
+
+// Part of a bin for the fast summary build (bins are split into parts of at
+// most kPartPoints grid points; the last part of a bin to finish combines
+// the parts' sums in index order).
+struct PartDesc {
+  int bin, start, end;  // grid points [start, end) of bin `bin`
+  int first, n_parts;   // index of the bin's first part, parts in the bin
+  int pad[3];
+};
+
+// Synchronisation words of an event's summary build (zero between builds).
+struct SummarySync {
+  unsigned counter;              // bins (or blocks) finished
+  unsigned overflow;             // a bin's share did not fit the fixed-point sum
+  unsigned long long base_acc;   // sum of the bins' shares, fixed point 2^-32
+  unsigned bin_parts_done[1];    // [B] parts finished per bin (allocated with B entries)
+};
+
 struct SummaryOut {
   double* summ;          // [D][B][6] FP64 summary: A0 re/im, A1 re/im, B0, B1
   float* bin32;          // [D][6][Bp] bin tables (float)
   double* bin64;         // [D][6][Bp] bin tables (FP64)
   const double* inv_df;  // [B] 1 / (f_{b+1} - f_b)
   double* share;         // [D][B] per-bin share of log L(theta_ref)
-  unsigned* counter;     // blocks finished; zero between builds
+  SummarySync* sync;     // counters, zero between builds
   double* base;          // log L(theta_ref)
   int Bp;
+  const PartDesc* parts;  // fast build: [n_parts]
+  float* part_sums;       // fast build: [n_parts][7 kMaxDet][2] float pairs
 };
 
 // ---------------------------------------------------------------------------

@@ -17,7 +17,8 @@
 //   exp(-2 pi i x) - 1 = -2 sin^2(pi x) - 2 i sin(pi x) cos(pi x),
 //   delta = rho (exp(-2 pi i x) - 1) + (rho - 1).
 //
-// Mapping: one warp per walker (persistent grid-stride loop over walkers);
+// Mapping: one warp per walker (persistent: each block takes a contiguous,
+// equal share of the walkers and its warps take them in turn);
 // lane l handles edge 31 c + l of chunk c and bin 31 c + l (lanes 0..30), so
 // each bin's right edge comes from the next lane by one shuffle and every
 // chunk overlaps the next by one edge.  Edge and bin tables live in shared
@@ -118,10 +119,15 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
   __syncthreads();
 
   const int lane = threadIdx.x & 31;
-  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  // each block takes a contiguous, equal share of the walkers (so every SM
+  // gets W / grid of them, +-1), its warps take them in turn
+  const int64_t per_blk = a.W / gridDim.x, rem_blk = a.W % gridDim.x;
+  const int64_t w_begin = (int64_t)blockIdx.x * per_blk + min((int64_t)blockIdx.x, rem_blk);
+  const int64_t w_end = w_begin + per_blk + ((int64_t)blockIdx.x < rem_blk ? 1 : 0);
+  const int64_t warp0 = w_begin + (threadIdx.x >> 5);
+  const int64_t nwarps = blockDim.x >> 5;
 
-  for (int64_t w = warp0; w < a.W; w += nwarps) {
+  for (int64_t w = warp0; w < w_end; w += nwarps) {
     // ---- per-walker constants (uniform across the warp) ----
     float dch[kNBasis], dcl[kNBasis];
     double dc64[kNBasis];
@@ -295,9 +301,14 @@ __global__ void __launch_bounds__(256) k_rb_f64(LaunchArgs a) {
   const double* __restrict__ f64 = ev.tab64 + (size_t)kNBasis * Ep;
   const double* __restrict__ bin64 = ev.tab64 + (size_t)(kNBasis + 1) * Ep;
   const int lane = threadIdx.x & 31;
-  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t w = warp0; w < a.W; w += nwarps) {
+  // each block takes a contiguous, equal share of the walkers (so every SM
+  // gets W / grid of them, +-1), its warps take them in turn
+  const int64_t per_blk = a.W / gridDim.x, rem_blk = a.W % gridDim.x;
+  const int64_t w_begin = (int64_t)blockIdx.x * per_blk + min((int64_t)blockIdx.x, rem_blk);
+  const int64_t w_end = w_begin + per_blk + ((int64_t)blockIdx.x < rem_blk ? 1 : 0);
+  const int64_t warp0 = w_begin + (threadIdx.x >> 5);
+  const int64_t nwarps = blockDim.x >> 5;
+  for (int64_t w = warp0; w < w_end; w += nwarps) {
     const WalkerF64* s = reinterpret_cast<const WalkerF64*>(a.ws) + w;
     if (!s->valid) {
       if (lane == 0) a.logl[w] = -INFINITY;

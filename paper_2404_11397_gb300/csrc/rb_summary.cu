@@ -106,57 +106,102 @@ __device__ __forceinline__ void strain_f64(const Values& v, int d, double f, dou
 }
 
 // ---------------------------------------------------------------------------
-// Summary epilogue shared by the FP64 and fast kernels: from the six block
-// sums (A0 re/im, A1 re/im, B0, B1 before the constant factors) lanes 0..5
-// of warp 0 each finish one output (SIMT: the FP64 instructions are issued
-// once for all six), write the FP64 summary entry and the bin tables
-// (alpha0 = A0/2, alpha1 = A1/df_b, beta0 = B0/2, beta1 = B1/df_b), and the
-// block's share Re A0 - B0/2 of log L(theta_ref).  The last block to finish
-// sums the shares in a fixed order (deterministic).
+// Summary epilogue shared by the FP64 and fast kernels: from the block sums
+// of nd detectors d0 .. d0+nd-1 (six each: A0 re/im, A1 re/im, B0, B1 before
+// the constant factors), lane j < 6 nd of warp 0 finishes output j % 6 of
+// detector d0 + j / 6 (SIMT: the FP64 instructions are issued once for all),
+// writes the FP64 summary entry and the bin tables (alpha0 = A0/2,
+// alpha1 = A1/df_b, beta0 = B0/2, beta1 = B1/df_b), and each detector's share
+// Re A0 - B0/2 of log L(theta_ref).  log L(theta_ref) is the sum of all
+// shares, formed deterministically in one of two ways:
+//   fixed_base = false: the last of the n_blocks blocks to finish sums the
+//     D x B shares in a fixed order (FP64);
+//   fixed_base = true: every block adds its bin's share (over the nd
+//     detectors) to a 64-bit fixed-point accumulator (2^-32 units; integer
+//     addition does not depend on the order) and the last block converts it;
+//     if a share does not fit (|share| >= 2^31) the last block falls back to
+//     the fixed-order FP64 sum.
 // ---------------------------------------------------------------------------
-__device__ void summary_epilogue(const SummaryOut& so, int b, int d, int B, int D, const double* sblock,
-                                 const double* scale, bool scaled_form) {
+__device__ void summary_epilogue(const SummaryOut& so, int b, int d0, int nd, int B, int D, const double* sblock,
+                                 const double* scale, bool scaled_form, unsigned n_blocks, double inv_df_b,
+                                 bool fixed_base) {
   __shared__ bool last;
+  SummarySync* sy = so.sync;
   if (threadIdx.x < 32) {
     const int j = threadIdx.x;
+    const int g = j / 6, f = j - 6 * g, d = d0 + g;
+    const bool mine = j < 6 * nd;
     double o = 0.0;
-    if (j < 6) {
+    if (mine) {
       o = sblock[j];
       if (scaled_form) {
         // A = conj(K) (s_re + i s_im) * scale[0];  B = |K|^2 s * scale[1]
-        const double Kr = scale[2], Ki = scale[3];
-        const double pr = sblock[j & ~1], pi = sblock[j | 1];
-        if (j < 4) o = scale[0] * ((j & 1) ? (Kr * pi - Ki * pr) : (Kr * pr + Ki * pi));
-        else o = scale[1] * (Kr * Kr + Ki * Ki) * o;
+        const double* sc = scale + 4 * g;
+        const double Kr = sc[2], Ki = sc[3];
+        const double pr = sblock[6 * g + (f & ~1)], pi = sblock[6 * g + (f | 1)];
+        if (f < 4) o = sc[0] * ((f & 1) ? (Kr * pi - Ki * pr) : (Kr * pr + Ki * pi));
+        else o = sc[1] * (Kr * Kr + Ki * Ki) * o;
       }
-      so.summ[((size_t)d * B + b) * 6 + j] = o;
-      const double t = (j == 2 || j == 3 || j == 5) ? o * so.inv_df[b] : 0.5 * o;
-      so.bin64[((size_t)d * 6 + j) * so.Bp + b] = t;
-      so.bin32[((size_t)d * 6 + j) * so.Bp + b] = (float)t;
+      so.summ[((size_t)d * B + b) * 6 + f] = o;
+      const double t = (f == 2 || f == 3 || f == 5) ? o * inv_df_b : 0.5 * o;
+      so.bin64[((size_t)d * 6 + f) * so.Bp + b] = t;
+      so.bin32[((size_t)d * 6 + f) * so.Bp + b] = (float)t;
     }
-    const double b0 = __shfl_sync(0xffffffffu, o, 4);
-    if (j == 0) so.share[(size_t)d * B + b] = o - 0.5 * b0;
+    const double b0 = __shfl_sync(0xffffffffu, o, (6 * g + 4) & 31);
+    const double sh = (mine && f == 0) ? o - 0.5 * b0 : 0.0;
+    if (mine && f == 0) so.share[(size_t)d * B + b] = sh;
+    if (fixed_base) {
+      double tot = __shfl_sync(0xffffffffu, sh, 0);  // detectors in order
+      for (int g2 = 1; g2 < nd; ++g2) tot += __shfl_sync(0xffffffffu, sh, 6 * g2);
+      if (j == 0) {
+        if (fabs(tot) < 2147483648.0)
+          atomicAdd(&sy->base_acc, (unsigned long long)__double2ll_rn(tot * 4294967296.0));
+        else
+          atomicOr(&sy->overflow, 1u);
+      }
+    }
+    __threadfence();
+    __syncwarp();
     if (j == 0) {
-      __threadfence();
-      const unsigned ticket = atomicAdd(so.counter, 1u);
-      last = (ticket == (unsigned)(B * D) - 1u);
+      const unsigned ticket = atomicAdd(&sy->counter, 1u);
+      last = (ticket == n_blocks - 1u);
     }
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
+  if (fixed_base && *reinterpret_cast<volatile unsigned*>(&sy->overflow) == 0u) {
+    if (threadIdx.x == 0) {
+      const unsigned long long acc = atomicExch(&sy->base_acc, 0ull);
+      *so.base = (double)(long long)acc * (1.0 / 4294967296.0);
+      sy->counter = 0u;
+    }
+    return;
+  }
   __shared__ double part[32];
   const int n = B * D;
+  // loads first (up to 8 per thread in flight), then a pairwise tree
   double acc = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += so.share[i];
+  for (int i0 = threadIdx.x; i0 < n; i0 += 8 * blockDim.x) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = i0 + u * (int)blockDim.x;
+      v[u] = i < n ? __ldcg(so.share + i) : 0.0;
+    }
+    acc += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+  }
   acc = warp_sum_f64(acc);
   if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
+    const int nw = (int)(blockDim.x >> 5);
     double t = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += part[i];
+    for (int i = 0; i < nw; ++i) t += part[i];
     *so.base = t;
-    *so.counter = 0u;
+    sy->counter = 0u;
+    sy->overflow = 0u;
+    sy->base_acc = 0ull;
   }
 }
 
@@ -202,7 +247,7 @@ __global__ void __launch_bounds__(kSumThreads) k_summary(DataPtrs in, int64_t km
     sblock[threadIdx.x] = t;
   }
   __syncthreads();
-  summary_epilogue(so, b, d, B, D, sblock, nullptr, false);
+  summary_epilogue(so, b, d, 1, B, D, sblock, nullptr, false, (unsigned)(B * D), so.inv_df[b], false);
 }
 
 // ---------------------------------------------------------------------------
@@ -325,32 +370,23 @@ struct TaylorTables {
   double amp[5];           // binom(-7/6, n)
 };
 
-// Event-constant per-chunk matrices, stored field-major ([field][chunk]) so
-// that consecutive threads read consecutive chunks.  Fields:
-constexpr int kQ01 = 0;                       // (k*2 + n)*2 + h: orders 0, 1 as float pairs
-constexpr int kQ2 = kQ01 + kNBasis * 4;       // k*2 + h: order 2 as a float pair
+// Event-constant per-chunk matrices, stored chunk-major ([chunk][128
+// floats], one 512-byte row per chunk, read with 16-byte vector loads).
+// Fields:
+constexpr int kQ01 = 0;                       // 4k + 2n + h: orders 0, 1 of basis k as float pairs
+constexpr int kQ2 = kQ01 + kNBasis * 4;       // 2k + h: order 2 as a float pair
 constexpr int kQh = kQ2 + kNBasis * 2;        // (n-3)*10 + k: orders 3..8
 constexpr int kQfc = kQh + (kOrd - 2) * kNBasis;  // f_c as a float pair
 constexpr int kQamp = kQfc + 2;               // f_c^-7/6, binom(-7/6, n) u^n (n = 1..4)
 constexpr int kQFields = kQamp + 5;
-static_assert(kQFields <= 128, "chunk matrix fields");
-
-// Per-rebuild chunk coefficients (128 bytes).
-struct ChunkCoef {
-  float x0[kMaxDet][2];   // X0 + f_c tau_d, reduced to [-1/2, 1/2] turns, float pair
-  float x1[kMaxDet][2];   // X1 + df tau_d, float pair
-  float x2[2];            // float pair
-  float xh[kOrd - 2];     // X3 .. X8
-  float amp[5];           // f_c^-7/6, then binom(-7/6, n) u^n, n = 1..4
-  float pad[7];
-};
-static_assert(sizeof(ChunkCoef) == 128, "chunk record is one 128-byte line");
+constexpr int kQRow = 128;
+static_assert(kQFields <= kQRow && kQ2 % 4 == 0 && kQh % 4 == 0 && kQfc % 4 == 0, "chunk matrix fields");
 
 __global__ void __launch_bounds__(128) k_chunk_q(int64_t kmin, double T, int64_t n_chunks, TaylorTables tt,
                                                  float* __restrict__ q) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_chunks) return;
-  auto put = [&](int f, float v) { q[(size_t)f * n_chunks + c] = v; };
+  auto put = [&](int f, float v) { q[(size_t)c * kQRow + f] = v; };
   const double nc = (double)(kmin + c * kChunk + kChunk / 2);
   const double fc = nc / T, u = 1.0 / nc;
   const double cf = cbrt(fc), lf = log(fc), icf = 1.0 / cf, icf2 = icf * icf;
@@ -387,67 +423,26 @@ __global__ void __launch_bounds__(128) k_chunk_q(int64_t kmin, double T, int64_t
   }
 }
 
-__global__ void __launch_bounds__(128) k_chunk_coef(const RefValues* __restrict__ ref, const float* __restrict__ q,
-                                                    float invT_hi, float invT_lo, int D, int64_t n_chunks,
-                                                    ChunkCoef* __restrict__ out) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n_chunks) return;
-  const RefValues& r = *ref;
-  auto get = [&](int f) { return q[(size_t)f * n_chunks + c]; };
-  float x0h = r.phi0t[0], x0l = r.phi0t[1], x1h = 0.f, x1l = 0.f, x2h = 0.f, x2l = 0.f;
-  float xh[kOrd - 2];
-#pragma unroll
-  for (int n = 0; n < kOrd - 2; ++n) xh[n] = 0.f;
-#pragma unroll
-  for (int k = 0; k < kNBasis; ++k) {
-    const float ch = r.chat[k][0], cl = r.chat[k][1];
-    f2x_fma_acc(ch, cl, get(kQ01 + k * 4), get(kQ01 + k * 4 + 1), x0h, x0l);
-    f2x_fma_acc(ch, cl, get(kQ01 + k * 4 + 2), get(kQ01 + k * 4 + 3), x1h, x1l);
-    f2x_fma_acc(ch, cl, get(kQ2 + k * 2), get(kQ2 + k * 2 + 1), x2h, x2l);
-#pragma unroll
-    for (int n = 0; n < kOrd - 2; ++n) xh[n] = fmaf(ch, get(kQh + n * kNBasis + k), xh[n]);
-  }
-  const float fch = get(kQfc), fcl = get(kQfc + 1);
-  ChunkCoef o;
-#pragma unroll
-  for (int d = 0; d < kMaxDet; ++d) {
-    if (d < D) {
-      float ah = x0h, al = x0l;
-      f2x_fma_acc(r.taut[d][0], r.taut[d][1], fch, fcl, ah, al);
-      const float rh = __fadd_rn(ah, -round_fma_pipe(ah));  // exact: drop whole turns
-      o.x0[d][0] = rh;
-      o.x0[d][1] = al;
-      float bh = x1h, bl = x1l;
-      f2x_fma_acc(r.taut[d][0], r.taut[d][1], invT_hi, invT_lo, bh, bl);
-      o.x1[d][0] = bh;
-      o.x1[d][1] = bl;
-    } else {
-      o.x0[d][0] = o.x0[d][1] = o.x1[d][0] = o.x1[d][1] = 0.f;
-    }
-  }
-  o.x2[0] = x2h;
-  o.x2[1] = x2l;
-#pragma unroll
-  for (int n = 0; n < kOrd - 2; ++n) o.xh[n] = xh[n];
-#pragma unroll
-  for (int n = 0; n < 5; ++n) o.amp[n] = get(kQamp + n);
-#pragma unroll
-  for (int i = 0; i < 7; ++i) o.pad[i] = 0.f;
-  out[c] = o;
+// FP64 -> FP32 of x * 2^s with integer operations only (the FP64 -> FP32
+// conversion instruction issues on the FP64 pipe): subtract the exponent
+// offset from the magnitude word, round the 64-bit magnitude on the first
+// dropped bit, and shift the top 32 bits into FP32 position.  `bias` is
+// (896 - s) << 20; zero and results below the FP32 normal range give a
+// signed zero, results above it give inf.
+__device__ __forceinline__ float scaled_float(double x, unsigned bias) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u;
+  const unsigned mag = hi & 0x7FFFFFFFu;
+  unsigned rlo, rhi;
+  asm("add.cc.u32 %0, %2, 0x10000000;\n\taddc.u32 %1, %3, 0;" : "=r"(rlo), "=r"(rhi) : "r"(lo), "r"(mag));
+  const unsigned bits = __funnelshift_l(rlo, rhi - bias, 3) | sign;
+  const unsigned lo_lim = bias + (1u << 20), hi_lim = bias + (255u << 20);
+  return __uint_as_float(mag < lo_lim ? sign : (mag >= hi_lim ? (sign | 0x7F800000u) : bits));
 }
 
-// FP64 -> FP32 of x * 2^s with integer operations only (the FP64 -> FP32
-// conversion instruction runs on the FP64 pipe, ~1/70 of the FP32 rate):
-// shift the exponent, keep the top 23 mantissa bits and round on the next
-// bit.  Zero and subnormal inputs give a signed zero, overflow gives inf.
-__device__ __forceinline__ float scaled_float(double x, int s) {
-  const int hi = __double2hiint(x);
-  const unsigned lo = (unsigned)__double2loint(x);
-  const unsigned sign = (unsigned)hi & 0x80000000u;
-  const int e = ((hi >> 20) & 0x7FF) - 1023 + 127 + s;
-  const unsigned m = (((unsigned)hi & 0xFFFFFu) << 3) | (lo >> 29);
-  const unsigned bits = (sign | ((unsigned)e << 23) | m) + ((lo >> 28) & 1u);
-  return __int_as_float((int)(e <= 0 ? sign : (e >= 255 ? (sign | 0x7f800000u) : bits)));
+// Small integer -> float on the FMA pipe (|i| < 2^22).
+__device__ __forceinline__ float small_int_float(int i) {
+  return __fadd_rn(__int_as_float(0x4B400000 + i), -12582912.0f);
 }
 
 __device__ __forceinline__ void f2x_add(float& hi, float& lo, float v) {
@@ -457,132 +452,317 @@ __device__ __forceinline__ void f2x_add(float& hi, float& lo, float v) {
   hi = s;
 }
 
-// One grid point of the fast summary sums.
-__device__ __forceinline__ void fast_point(const ChunkCoef& C, int d, int64_t k, double2 dv, double psd, int sd,
-                                           int sS, int64_t e01, float half_df, float* acc) {
-  const float jf = (float)((int)(k & (kChunk - 1)) - kChunk / 2);
-  const float dre = scaled_float(dv.x, sd), dim = scaled_float(dv.y, sd);
-  const float Sp = scaled_float(psd, sS);
-  float t = C.xh[5];
-#pragma unroll
-  for (int n = 4; n >= 0; --n) t = fmaf(t, jf, C.xh[n]);
-  const float j2 = jf * jf;
-  const float t3 = t * (j2 * jf);
-  const float p1 = __fmul_rn(C.x1[d][0], jf);
-  float e1e = __fmaf_rn(C.x1[d][0], jf, -p1);
-  e1e = __fmaf_rn(C.x1[d][1], jf, e1e);
-  const float p2 = __fmul_rn(C.x2[0], j2);
-  float e2e = __fmaf_rn(C.x2[0], j2, -p2);
-  e2e = __fmaf_rn(C.x2[1], j2, e2e);
-  float sh = C.x0[d][0], sl = C.x0[d][1];
-  f2x_add(sh, sl, p1);
-  f2x_add(sh, sl, p2);
-  sl = __fadd_rn(sl, __fadd_rn(__fadd_rn(e1e, e2e), t3));
-  const float y = frac_turns(sh, sl);
+// Per-rebuild chunk coefficients (32 floats, 16-byte aligned groups):
+//   [0 .. 3]    X0 (pair, whole turns dropped), X1 (pair): intrinsic phase
+//   [4 .. 11]   X2 (pair), X3 .. X8
+//   [12 .. 16]  f_c^-7/6, binom(-7/6, n) u^n (n = 1..4)
+//   [18 .. 23]  exp(+2 pi i f_c tau_d) per detector (cos, sin)
+// The detector delay enters the fiducial phase linearly, x_d(f) = x(f) +
+// f tau_d, so per grid point exp(2 pi i x_d) = exp(2 pi i x) exp(2 pi i f_c
+// tau_d) exp(2 pi i j df tau_d): one sine/cosine per point, the chunk factor
+// from this record and the offset factor from a 32-entry table per block.
+constexpr int kRec = 32;
+
+// sin, cos of 2 pi y from the half-angle series (|y| <= 1/2 turns).
+__device__ __forceinline__ float2 cis_turns(float y) {
   float sn, cs;
   sincos_pi_half(y, sn, cs);
-  const float Cc = fmaf(-2.f * sn, sn, 1.f), Ss = 2.f * sn * cs;  // exp(+2 pi i y)
-  const float A = C.amp[0] * fmaf(jf, fmaf(jf, fmaf(jf, fmaf(jf, C.amp[4], C.amp[3]), C.amp[2]), C.amp[1]), 1.f);
-  const float wA = A / Sp;
-  const float dr = dre * wA, di = dim * wA;
-  const float qr = fmaf(dr, Cc, -di * Ss), qi = fmaf(dr, Ss, di * Cc);
-  const float dff = (float)(2 * k - e01) * half_df;  // f - f_m
-  acc[0] += qr;
-  acc[1] += qi;
-  acc[2] = fmaf(qr, dff, acc[2]);
-  acc[3] = fmaf(qi, dff, acc[3]);
-  const float hh = wA * A;
-  acc[4] += hh;
-  acc[5] = fmaf(hh, dff, acc[5]);
+  return make_float2(fmaf(-2.f * sn, sn, 1.f), 2.f * sn * cs);
 }
 
-constexpr int kFastThreads = 128;
-constexpr int kFastUnroll = 4;
-constexpr int kSeg = 1024;  // points per staged segment
-__global__ void __launch_bounds__(kFastThreads) k_summary_fast(DataPtrs in, const ChunkCoef* __restrict__ ch,
-                                                               double T, int B, int D,
-                                                               const int64_t* __restrict__ edges,
-                                                               const RefValues* __restrict__ ref, SummaryOut so) {
-  const int b = blockIdx.x, d = blockIdx.y;
-  const int64_t e0 = edges[b], e1 = edges[b + 1];
-  const int64_t k0 = e0;
-  const int64_t k1 = (b == B - 1) ? e1 + 1 : e1;
-  const double* __restrict__ dat = in.data[d];
-  const double* __restrict__ psd = in.psd[d];
-  // power-of-two scales from the first PSD sample: S' = S 2^sS ~ 1, d' = d 2^sd
-  const int ex = ((__double2hiint(psd[0]) >> 20) & 0x7FF) - 1023;
+// X_n = sum_k (c_k / 2pi) Q_kn (float-pair dot products) for 32 chunks per
+// block: warp 0 forms orders 0 and 1 and the per-detector chunk factors,
+// warp 1 order 2 and the amplitude series, warp 2 orders 3..8.  Each lane
+// reads its chunk's matrix row with 16-byte loads issued before use.
+__global__ void __launch_bounds__(96) k_chunk_coef(const RefValues* __restrict__ ref, const float* __restrict__ q,
+                                                   int D, int n_chunks, float* __restrict__ out) {
+  const int c = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int task = threadIdx.x >> 5;
+  if (c >= n_chunks) return;
+  const float4* row = reinterpret_cast<const float4*>(q + (size_t)c * kQRow);
+  float* rec = out + (size_t)c * kRec;
+  if (task == 0) {
+    float4 m[kNBasis];
+#pragma unroll
+    for (int k = 0; k < kNBasis; ++k) m[k] = __ldcs(row + (kQ01 / 4) + k);
+    const float4 fc = __ldcs(row + kQfc / 4);
+    float x0h = ref->phi0t[0], x0l = ref->phi0t[1], x1h = 0.f, x1l = 0.f;
+#pragma unroll
+    for (int k = 0; k < kNBasis; ++k) {
+      const float ch = ref->chat[k][0], cl = ref->chat[k][1];
+      f2x_fma_acc(ch, cl, m[k].x, m[k].y, x0h, x0l);
+      f2x_fma_acc(ch, cl, m[k].z, m[k].w, x1h, x1l);
+    }
+    reinterpret_cast<float4*>(rec)[0] = make_float4(__fadd_rn(x0h, -round_fma_pipe(x0h)), x0l, x1h, x1l);
+#pragma unroll
+    for (int d = 0; d < kMaxDet; ++d) {
+      float ah = 0.f, al = 0.f;
+      if (d < D) f2x_fma_acc(ref->taut[d][0], ref->taut[d][1], fc.x, fc.y, ah, al);
+      reinterpret_cast<float2*>(rec)[9 + d] = cis_turns(frac_turns(ah, al));
+    }
+  } else if (task == 1) {
+    float4 m[kNBasis / 2];
+#pragma unroll
+    for (int i = 0; i < kNBasis / 2; ++i) m[i] = __ldcs(row + kQ2 / 4 + i);
+    const float4 a0 = __ldcs(row + kQfc / 4), a1 = __ldcs(row + kQfc / 4 + 1);
+    float xh = 0.f, xl = 0.f;
+#pragma unroll
+    for (int i = 0; i < kNBasis / 2; ++i) {
+      f2x_fma_acc(ref->chat[2 * i][0], ref->chat[2 * i][1], m[i].x, m[i].y, xh, xl);
+      f2x_fma_acc(ref->chat[2 * i + 1][0], ref->chat[2 * i + 1][1], m[i].z, m[i].w, xh, xl);
+    }
+    reinterpret_cast<float2*>(rec)[2] = make_float2(xh, xl);
+    reinterpret_cast<float4*>(rec)[3] = make_float4(a0.z, a0.w, a1.x, a1.y);
+    rec[16] = a1.z;
+  } else {
+    float4 m[(kOrd - 2) * kNBasis / 4];
+#pragma unroll
+    for (int i = 0; i < (kOrd - 2) * kNBasis / 4; ++i) m[i] = __ldcs(row + kQh / 4 + i);
+    const float* mf = reinterpret_cast<const float*>(m);
+    float xn[kOrd - 2];
+#pragma unroll
+    for (int n = 0; n < kOrd - 2; ++n) {
+      float t = 0.f;
+#pragma unroll
+      for (int k = 0; k < kNBasis; ++k) t = fmaf(ref->chat[k][0], mf[n * kNBasis + k], t);
+      xn[n] = t;
+    }
+    reinterpret_cast<float2*>(rec)[3] = make_float2(xn[0], xn[1]);
+    reinterpret_cast<float4*>(rec)[2] = make_float4(xn[2], xn[3], xn[4], xn[5]);
+  }
+}
+
+// Integer -> float on the FMA pipe (exact for |i| < 2^22; larger |i| < 2^31
+// are split in two parts and rounded once).
+__device__ __forceinline__ float int_float_fma(int i) {
+  const int hi = i >> 21, lo = i & ((1 << 21) - 1);
+  return __fmaf_rn(small_int_float(hi), 2097152.0f, small_int_float(lo));
+}
+
+// FP32 working copy of an event's data for the fast summary build, made
+// when the data change (not on every rebuild):
+//   w_d = d'_d / S'_d (complex) and is_d = 1 / S'_d,  d' = d 2^sd, S' = S 2^sS,
+// with power-of-two scales from the detector's first PSD sample (S' ~ 1 and
+// d' ~ sqrt(T/4)); exps[d] = {sd, sS}.  One thread per (point, detector);
+// the FP64 -> FP32 conversion uses integer operations (scaled_float).
+__global__ void __launch_bounds__(256) k_data32(DataPtrs in, int64_t N, int D, float2* __restrict__ w32,
+                                                float* __restrict__ is32, int* __restrict__ exps) {
+  const int d = blockIdx.y;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int ex = ((__double2hiint(__ldg(in.psd[d])) >> 20) & 0x7FF) - 1023;
   const int sS = -ex, sd = -(ex / 2);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    exps[2 * d] = sd;
+    exps[2 * d + 1] = sS;
+  }
+  if (k >= N) return;
+  const double2 dv = __ldcs(reinterpret_cast<const double2*>(in.data[d]) + k);
+  const float Sp = scaled_float(__ldcs(in.psd[d] + k), (unsigned)(896 - sS) << 20);
+  const float is = __frcp_rn(Sp);
+  const unsigned bd = (unsigned)(896 - sd) << 20;
+  w32[(size_t)d * N + k] = make_float2(scaled_float(dv.x, bd) * is, scaled_float(dv.y, bd) * is);
+  is32[(size_t)d * N + k] = is;
+}
+
+constexpr int kSumFastThreads = 128;
+constexpr int kNQ = 7;  // per detector: A0 re/im, A1 re/im, B0, B1 as a float pair (hi, lo)
+constexpr int kNAcc = kNQ * kMaxDet;
+constexpr int kPartRecs = kPartPoints / kChunk + 1;  // chunk records a part can touch
+static_assert(kPartPoints % kSumFastThreads == 0, "parts are whole rounds of the block");
+
+// One block per part of a bin (at most kPartPoints grid points), all
+// detectors, reading the FP32 data copy (w = d'/S', 1/S').  The part's chunk
+// records are staged in shared memory; each thread evaluates every 128th
+// point, with the next point's data loads in flight while the current one is
+// evaluated.  Per point: the
+// intrinsic fiducial phase from the chunk's Taylor coefficients, one
+// sine/cosine, the detector factors exp(2 pi i f_c tau_d) (record) and
+// exp(2 pi i j df tau_d) (block table).  Per-thread sums are FP32 (B1, which
+// nearly cancels within a bin, a float pair); block sums are float pairs in a
+// fixed order; the parts of a bin are added in index order by the last of
+// them to finish, which then runs the FP64 epilogue.
+__global__ void __launch_bounds__(kSumFastThreads, 6)
+    k_summary_fast(const float2* __restrict__ w32, const float* __restrict__ is32, const int* __restrict__ exps,
+                   int N, const float* __restrict__ chunks, double T, float invT_hi, float invT_lo, int B, int D,
+                   const int64_t* __restrict__ edges, const RefValues* __restrict__ ref, SummaryOut so) {
+  __shared__ __align__(16) float srec[kPartRecs * kRec];
+  __shared__ float2 toff[kMaxDet][kChunk];  // exp(2 pi i j df tau_d), indexed by k mod 32
+  __shared__ float red[kSumFastThreads / 32][kNAcc * 33];  // per-thread partials, one row per quantity
+  __shared__ float wsum[kSumFastThreads / 32][kNAcc][2];
+  __shared__ float qsum[kNAcc][2];
+  __shared__ double sblock[6 * kMaxDet];
+  __shared__ double scale[kMaxDet][4];
+  __shared__ double s_inv_df;
+  __shared__ bool s_last;
+  const PartDesc pd = so.parts[blockIdx.x];
+  const int b = pd.bin;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int e0 = (int)edges[b], e1 = (int)edges[b + 1];
+  const int ks = pd.start, ke = pd.end;
+  const int w = e1 - e0;
   const float half_df = (float)(0.5 / T);
-  float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  // The bin is processed in segments of kSeg points; the segment's chunk
-  // records are staged in shared memory first (coalesced 16-byte loads).
-  __shared__ __align__(16) ChunkCoef sch[kSeg / kChunk + 1];
-  for (int64_t s0 = k0; s0 < k1; s0 += kSeg) {
-    const int64_t s1 = (s0 + kSeg < k1) ? s0 + kSeg : k1;
-    const int64_t c0 = s0 >> 5, nch = ((s1 - 1) >> 5) - c0 + 1;
-    {
-      const float4* src = reinterpret_cast<const float4*>(ch + c0);
-      float4* dst = reinterpret_cast<float4*>(sch);
-      const int n4 = (int)nch * (int)(sizeof(ChunkCoef) / 16);
-      for (int i = threadIdx.x; i < n4; i += kFastThreads) dst[i] = src[i];
-    }
-    __syncthreads();
-    // issue the loads of kFastUnroll points before using any of them
-    for (int64_t kb = s0 + threadIdx.x; kb < s1; kb += kFastThreads * kFastUnroll) {
-      double2 dv[kFastUnroll];
-      double pv[kFastUnroll];
-#pragma unroll
-      for (int u = 0; u < kFastUnroll; ++u) {
-        const int64_t k = kb + (int64_t)u * kFastThreads;
-        if (k < s1) {
-          dv[u] = *reinterpret_cast<const double2*>(dat + 2 * k);
-          pv[u] = psd[k];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kFastUnroll; ++u) {
-        const int64_t k = kb + (int64_t)u * kFastThreads;
-        if (k < s1) fast_point(sch[(k >> 5) - c0], d, k, dv[u], pv[u], sd, sS, e0 + e1, half_df, acc);
-      }
-    }
-    __syncthreads();
-  }
-  // float-pair block reduction (fixed order)
-  float lo[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      const float oh = __shfl_xor_sync(0xffffffffu, acc[j], o);
-      const float ol = __shfl_xor_sync(0xffffffffu, lo[j], o);
-      f2x_add(acc[j], lo[j], oh);
-      lo[j] = __fadd_rn(lo[j], ol);
-    }
-  }
-  __shared__ float red[kFastThreads / 32][6][2];
-  __shared__ double sblock[6];
-  __shared__ double scale[4];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0)
-    for (int j = 0; j < 6; ++j) {
-      red[wid][j][0] = acc[j];
-      red[wid][j][1] = lo[j];
-    }
-  __syncthreads();
-  if (threadIdx.x < 6) {
-    float h = red[0][threadIdx.x][0], l = red[0][threadIdx.x][1];
-    for (int i = 1; i < kFastThreads / 32; ++i) {
-      f2x_add(h, l, red[i][threadIdx.x][0]);
-      l = __fadd_rn(l, red[i][threadIdx.x][1]);
-    }
-    sblock[threadIdx.x] = (double)h + (double)l;
-  } else if (threadIdx.x >= 32 && threadIdx.x < 36) {
-    const int j = threadIdx.x - 32;
+  if (tid < kMaxDet * kChunk) {
+    const int d = tid >> 5, j = lane - kChunk / 2;
+    float sh = 0.f, sl = 0.f;
+    if (d < D) f2x_fma_acc(ref->taut[d][0], ref->taut[d][1], invT_hi, invT_lo, sh, sl);  // tau_d df
+    const float jf = small_int_float(j);
+    const float p = __fmul_rn(sh, jf);
+    const float e = __fmaf_rn(sl, jf, __fmaf_rn(sh, jf, -p));
+    toff[d][lane] = cis_turns(frac_turns(p, e));
+  } else if (tid >= 96 && tid < 96 + D) {
+    // undo the power-of-two scales of the FP32 data copy (d 2^sd, S 2^sS)
+    const int d = tid - 96;
+    const int sd = __ldg(exps + 2 * d), sS = __ldg(exps + 2 * d + 1);
+    // 2^n as the bit pattern of a double (|n| well inside the exponent range)
     const double w4 = 4.0 / T;
-    scale[j] = j == 0 ? ldexp(w4, sS - sd) : (j == 1 ? ldexp(w4, sS) : ref->K[d][j - 2]);
+    scale[d][0] = w4 * __hiloint2double((1023 + sS - sd) << 20, 0);
+    scale[d][1] = w4 * __hiloint2double((1023 + sS) << 20, 0);
+    scale[d][2] = ref->K[d][0];
+    scale[d][3] = ref->K[d][1];
+  } else if (tid == 127) {
+    s_inv_df = so.inv_df[b];
+  }
+  float acc[kNAcc];
+#pragma unroll
+  for (int i = 0; i < kNAcc; ++i) acc[i] = 0.f;
+  float2 dv[kMaxDet], dn[kMaxDet];  // w = d'/S'
+  float pv[kMaxDet], pn[kMaxDet];   // 1/S'
+  auto load_point = [&](int k, float2* dd, float* pp) {
+#pragma unroll
+    for (int d = 0; d < kMaxDet; ++d)
+      if (d < D) {
+        dd[d] = __ldcs(w32 + (size_t)d * N + k);
+        pp[d] = __ldcs(is32 + (size_t)d * N + k);
+      }
+  };
+  int k = ks + tid;
+  if (k < ke) load_point(k, dn, pn);  // in flight across the staging below
+  const int c0 = ks >> 5, nrec = ((ke - 1) >> 5) - c0 + 1;
+  {
+    const float4* src = reinterpret_cast<const float4*>(chunks + (size_t)c0 * kRec);
+    float4* dst = reinterpret_cast<float4*>(srec);
+    for (int i = tid; i < nrec * (kRec / 4); i += kSumFastThreads) dst[i] = __ldg(src + i);
   }
   __syncthreads();
-  summary_epilogue(so, b, d, B, D, sblock, scale, true);
+  for (; k < ke; k += kSumFastThreads) {
+#pragma unroll
+    for (int d = 0; d < kMaxDet; ++d) {
+      dv[d] = dn[d];
+      pv[d] = pn[d];
+    }
+    if (k + kSumFastThreads < ke) load_point(k + kSumFastThreads, dn, pn);
+    const float4* rec = reinterpret_cast<const float4*>(srec + ((k >> 5) - c0) * kRec);
+    const float jf = small_int_float((k & (kChunk - 1)) - kChunk / 2);
+    const float4 x01 = rec[0];  // X0 pair, X1 pair
+    const float4 h0 = rec[1];   // X2 pair, X3, X4
+    const float4 h1 = rec[2];   // X5 .. X8
+    const float4 a0 = rec[3];   // amplitude series
+    const float a4 = reinterpret_cast<const float*>(rec)[16];
+    // intrinsic fiducial phase x = X0 + X1 j + X2 j^2 + j^3 (X3 + ... + X8 j^5)
+    const float t = fmaf(fmaf(fmaf(fmaf(fmaf(h1.w, jf, h1.z), jf, h1.y), jf, h1.x), jf, h0.w), jf, h0.z);
+    const float j2 = jf * jf;
+    const float t3 = t * (j2 * jf);
+    const float p1 = __fmul_rn(x01.z, jf);
+    float e1r = __fmaf_rn(x01.z, jf, -p1);
+    e1r = __fmaf_rn(x01.w, jf, e1r);
+    const float p2 = __fmul_rn(h0.x, j2);
+    float e2r = __fmaf_rn(h0.x, j2, -p2);
+    e2r = __fmaf_rn(h0.y, j2, e2r);
+    float sh = x01.x, sl = x01.y;
+    f2x_add(sh, sl, p1);
+    f2x_add(sh, sl, p2);
+    sl = __fadd_rn(sl, __fadd_rn(__fadd_rn(e1r, e2r), t3));
+    const float2 z = cis_turns(frac_turns(sh, sl));  // exp(+2 pi i x)
+    const float A = a0.x * fmaf(jf, fmaf(jf, fmaf(jf, fmaf(jf, a4, a0.w), a0.z), a0.y), 1.f);
+    const float A2 = A * A;
+    const float dff = int_float_fma(2 * (k - e0) - w) * half_df;  // f - f_m
+#pragma unroll
+    for (int d = 0; d < kMaxDet; ++d) {
+      if (d < D) {
+        const float2 ec = reinterpret_cast<const float2*>(rec)[9 + d];  // exp(2 pi i f_c tau_d)
+        const float2 eo = toff[d][k & (kChunk - 1)];                    // exp(2 pi i j df tau_d)
+        const float fr = fmaf(ec.x, eo.x, -ec.y * eo.y), fi = fmaf(ec.x, eo.y, ec.y * eo.x);
+        const float Cc = fmaf(z.x, fr, -z.y * fi), Ss = fmaf(z.x, fi, z.y * fr);  // exp(+2 pi i x_d)
+        const float dr = dv[d].x * A, di = dv[d].y * A;
+        const float qr = fmaf(dr, Cc, -di * Ss), qi = fmaf(dr, Ss, di * Cc);
+        acc[kNQ * d + 0] += qr;
+        acc[kNQ * d + 1] += qi;
+        acc[kNQ * d + 2] = fmaf(qr, dff, acc[kNQ * d + 2]);
+        acc[kNQ * d + 3] = fmaf(qi, dff, acc[kNQ * d + 3]);
+        const float hh = A2 * pv[d];
+        acc[kNQ * d + 4] += hh;
+        // B1 (|h0|^2 / S weighted by f - f_m > 0 or < 0) nearly cancels within a
+        // bin: its per-thread sum is a float pair (hi, lo)
+        f2x_add(acc[kNQ * d + 5], acc[kNQ * d + 6], hh * dff);
+      }
+    }
+  }
+  // ---- block sums in float pairs, fixed order: lanes 0..20 of each warp sum
+  // one quantity over the warp's 32 threads, then 21 threads sum the warp
+  // totals (A1 and B1 cancel strongly within a bin, so no stage of this sum
+  // is plain FP32) ----
+  float* wr = red[wid];
+#pragma unroll
+  for (int i = 0; i < kNAcc; ++i) wr[i * 33 + lane] = acc[i];
+  __syncwarp();
+  if (lane < kNAcc) {
+    float h = 0.f, l = 0.f;
+    for (int m = 0; m < 32; ++m) f2x_add(h, l, wr[lane * 33 + m]);
+    wsum[wid][lane][0] = h;
+    wsum[wid][lane][1] = l;
+  }
+  __syncthreads();
+  const bool multi = pd.n_parts > 1;
+  if (tid < kNAcc) {
+    float h = wsum[0][tid][0], l = wsum[0][tid][1];
+#pragma unroll
+    for (int i = 1; i < kSumFastThreads / 32; ++i) {
+      f2x_add(h, l, wsum[i][tid][0]);
+      l = __fadd_rn(l, wsum[i][tid][1]);
+    }
+    qsum[tid][0] = h;
+    qsum[tid][1] = l;
+    if (multi) {
+      float* ps = so.part_sums + ((size_t)blockIdx.x * kNAcc + tid) * 2;
+      ps[0] = h;
+      ps[1] = l;
+      __threadfence();
+    }
+  }
+  if (multi) {
+    // the last part of the bin to finish adds the parts in index order
+    __syncthreads();
+    if (tid == 0) {
+      const unsigned ticket = atomicAdd(&so.sync->bin_parts_done[b], 1u);
+      s_last = (ticket == (unsigned)pd.n_parts - 1u);
+      if (s_last) so.sync->bin_parts_done[b] = 0u;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (tid < kNAcc) {
+      const float* ps = so.part_sums + ((size_t)pd.first * kNAcc + tid) * 2;
+      float h = __ldcg(ps), l = __ldcg(ps + 1);
+      for (int p = 1; p < pd.n_parts; ++p) {
+        f2x_add(h, l, __ldcg(ps + (size_t)p * kNAcc * 2));
+        l = __fadd_rn(l, __ldcg(ps + (size_t)p * kNAcc * 2 + 1));
+      }
+      qsum[tid][0] = h;
+      qsum[tid][1] = l;
+    }
+  }
+  __syncthreads();
+  if (tid < 6 * D) {
+    const int d = tid / 6, f = tid - 6 * d, q = kNQ * d + f;
+    float h = qsum[q][0], l = qsum[q][1];
+    if (f == 5) {  // B1 = its hi and lo sums
+      f2x_add(h, l, qsum[q + 1][0]);
+      l = __fadd_rn(l, qsum[q + 1][1]);
+    }
+    sblock[tid] = (double)h + (double)l;
+  }
+  __syncthreads();
+  summary_epilogue(so, b, 0, D, B, D, sblock, &scale[0][0], true, (unsigned)B, s_inv_df, true);
 }
 
 static TaylorTables make_taylor_tables() {
@@ -618,7 +798,6 @@ static TaylorTables make_taylor_tables() {
 
 int64_t n_chunks_of(int64_t N) { return (N + kChunk - 1) / kChunk; }
 size_t chunk_q_bytes(int64_t N) { return sizeof(float) * 128 * (size_t)n_chunks_of(N); }
-size_t chunk_coef_bytes(int64_t N) { return sizeof(ChunkCoef) * (size_t)n_chunks_of(N); }
 
 cudaError_t launch_chunk_q(int64_t kmin, double T, int64_t N, void* cq, cudaStream_t s) {
   static const TaylorTables tt = make_taylor_tables();
@@ -627,18 +806,26 @@ cudaError_t launch_chunk_q(int64_t kmin, double T, int64_t N, void* cq, cudaStre
   return cudaGetLastError();
 }
 
-cudaError_t launch_summary_fast(const DataPtrs& in, int64_t N, double T, int D, int B, const int64_t* edges,
-                                const RefValues* ref, const void* cq, void* chunk_coef, const SummaryOut& so,
-                                cudaStream_t s) {
-  const int64_t nc = n_chunks_of(N);
-  ChunkCoef* ch = static_cast<ChunkCoef*>(chunk_coef);
+size_t chunk_coef_bytes(int64_t N) { return sizeof(float) * kRec * (size_t)n_chunks_of(N); }
+
+cudaError_t launch_data32(const DataPtrs& in, int64_t N, int D, void* w32, float* is32, int* exps, cudaStream_t s) {
+  dim3 grid((unsigned)((N + 255) / 256), (unsigned)D);
+  k_data32<<<grid, 256, 0, s>>>(in, N, D, static_cast<float2*>(w32), is32, exps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_summary_fast(const void* w32, const float* is32, const int* exps, int64_t N, double T, int D, int B,
+                                const int64_t* edges, const RefValues* ref, const void* cq, void* chunk_coef,
+                                const SummaryOut& so, int n_parts, cudaStream_t s) {
+  const int nc = (int)n_chunks_of(N);
   const double invT = 1.0 / T;
   const float ih = (float)invT, il = (float)(invT - (double)ih);
-  k_chunk_coef<<<(unsigned)((nc + 127) / 128), 128, 0, s>>>(ref, static_cast<const float*>(cq), ih, il, D, nc, ch);
+  float* ch = static_cast<float*>(chunk_coef);
+  k_chunk_coef<<<(unsigned)((nc + 31) / 32), 96, 0, s>>>(ref, static_cast<const float*>(cq), D, nc, ch);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  dim3 grid(B, D);
-  k_summary_fast<<<grid, kFastThreads, 0, s>>>(in, ch, T, B, D, edges, ref, so);
+  k_summary_fast<<<n_parts, kSumFastThreads, 0, s>>>(static_cast<const float2*>(w32), is32, exps, (int)N, ch, T, ih, il,
+                                                      B, D, edges, ref, so);
   return cudaGetLastError();
 }
 

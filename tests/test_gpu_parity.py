@@ -296,11 +296,33 @@ def test_library_errors(rb, small):
 # ---------------------------------------------------------------------------
 # In-place rebuild (rb_event_rebuild): FP64 and fast (Taylor-chunk) summary
 # ---------------------------------------------------------------------------
-def _summary_close(g, ref, rel):
+def _summary_close(g, ref, rel, b1_cond=None):
+    """Every entry within rel of the largest entry of its detector.  With
+    b1_cond (the FP32 fast build), B1 = 4 df sum |h0|^2 / S (f - f_m), whose
+    terms change sign inside every bin, may instead be off by rel times the
+    sum of the absolute values of its terms (its condition number: rounding
+    of the terms, not of the sum, sets the error)."""
     for key in ("A0", "A1", "B0", "B1"):
         scale = np.max(np.abs(ref[key]), axis=1, keepdims=True)
+        if key == "B1" and b1_cond is not None:
+            scale = np.maximum(scale, b1_cond)
         err = np.max(np.abs(g[key] - ref[key]) / scale)
         assert err <= rel, (key, err)
+
+
+def _b1_condition(ev, theta_ref, edges):
+    """[D][B] sum over each bin of |4 df |h0|^2 / S (f - f_m)| (oracle waveform)."""
+    f, T = ev["f"], ev["T"]
+    D, B = ev["geom"].shape[0], len(edges) - 1
+    out = np.zeros((D, B))
+    for d in range(D):
+        h0 = oracle.strain(theta_ref, ev["geom"][d], ev["gmst"], f)
+        w = 4.0 / T * np.abs(h0) ** 2 / ev["psd"][d]
+        for b in range(B):
+            k0, k1 = edges[b], (edges[b + 1] + 1 if b == B - 1 else edges[b + 1])
+            fm = 0.5 * (f[edges[b]] + f[edges[b + 1]])
+            out[d, b] = np.sum(w[k0:k1] * np.abs(f[k0:k1] - fm))
+    return out
 
 
 def test_rebuild_fp64_is_bitwise_reproducible(rb, c2):
@@ -316,9 +338,10 @@ def test_fast_rebuild_summary_matches_oracle(rb, cfg):
     ev = inject(synth.make_event(cfg))
     B = ev["n_bins"]
     event = rb.Event.from_synth(ev, n_bins=B)
-    s = oracle.summary(ev, ev["theta_inj"], oracle.bin_edges(ev, B))
+    edges = oracle.bin_edges(ev, B)
+    s = oracle.summary(ev, ev["theta_inj"], edges)
     event.rebuild(mode="mixed")
-    _summary_close(event.summary(), s, 2e-6)
+    _summary_close(event.summary(), s, 2e-6, _b1_condition(ev, ev["theta_inj"], edges))
     th = synth.walkers(cfg, 512) if cfg != "C1" else synth.walkers("C1", 512)
     L = rb.loglike(event, torch.tensor(th, device="cuda"), mode="mixed").cpu().numpy()
     ref, dh, hh = _terms(ev, s, th)
@@ -348,5 +371,5 @@ def test_rebuild_new_reference_and_data(rb, c1):
     pp = [torch.tensor(ev["psd"][0], device="cuda")]
     event.rebuild(data=dd, psd=pp, mode="mixed")
     torch.cuda.synchronize()
-    _summary_close(event.summary(), s, 2e-6)
+    _summary_close(event.summary(), s, 2e-6, _b1_condition(ev2, new_ref, c1.edges))
     event.free()
