@@ -169,6 +169,12 @@ def main_kernel_flops(W: int, D: int, B: int, grad: bool) -> float:
     return float(W) * f
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the main kernel on this workload, from an ncu capture of this kernel version
+# (None once the kernel changes and until it is captured again).
+MAIN_KERNEL_TRAFFIC_BYTES = 2353920
+
+
 def fp32_peak_tflops() -> float:
     return N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
@@ -321,7 +327,7 @@ def run_gb300(args, dist: Dist):
                          "main_kernel_avg": main_avg_s * 1e3,
                          "batch_evals_per_s_main_kernel_only": W / main_avg_s},
         "roofline": {"bound": "alu", "kernel": "k_rb_mixed<grad> (fp32 pipe)", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": MAIN_KERNEL_TRAFFIC_BYTES,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"},
     }
     if not args.no_fp64 and args.mode != "fp64":
