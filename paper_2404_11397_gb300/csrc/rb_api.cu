@@ -39,6 +39,7 @@ cudaError_t launch_strain(const RefValues* src, int64_t kmin, int64_t N, double 
 cudaError_t launch_summary_fast(const void* w32, const float* is32, const int* exps, int64_t N, double T, int D, int B,
                                 const int64_t* edges, const RefValues* ref, const void* cq, void* chunk_coef,
                                 const SummaryOut& so, int n_parts, cudaStream_t s);
+cudaError_t launch_ref_dd(const double* theta_ref_dev, const EventConst& ec, RefValues* out, cudaStream_t s);
 cudaError_t launch_data32(const DataPtrs& in, int64_t N, int D, void* w32, float* is32, int* exps, cudaStream_t s);
 size_t chunk_coef_bytes(int64_t N);
 
@@ -79,6 +80,12 @@ static void arm_unit(double lat, double lon, double az, double a[3]) {
   for (int i = 0; i < 3; ++i) a[i] = std::cos(az) * n[i] + std::sin(az) * e[i];
 }
 
+// v = out[0] + out[1] with two floats (hi = v rounded, lo = the rest rounded).
+static void split_pair(double v, float* out) {
+  out[0] = (float)v;
+  out[1] = (float)(v - (double)out[0]);
+}
+
 DetGeom make_geom(double lat, double lon, double elev, double xaz, double yaz) {
   DetGeom g;
   double x[3], y[3];
@@ -93,6 +100,11 @@ DetGeom make_geom(double lat, double lon, double elev, double xaz, double yaz) {
   g.r[0] = (Nr + elev) * c * std::cos(lon);
   g.r[1] = (Nr + elev) * c * std::sin(lon);
   g.r[2] = (Nr * (1.0 - e2) + elev) * s;
+  for (int i = 0; i < 3; ++i) {
+    split_pair(x[i], g.xa[i]);
+    split_pair(y[i], g.ya[i]);
+    split_pair(g.r[i] / kClight, g.rc[i]);
+  }
   return g;
 }
 
@@ -190,6 +202,9 @@ int rb_event_free(rb_event_t ev) {
   cudaFree(e.d_chunks);
   cudaFree(e.d_invdf);
   cudaFree(e.d_share);
+  if (e.ev_fork) cudaEventDestroy(e.ev_fork);
+  if (e.ev_join) cudaEventDestroy(e.ev_join);
+  if (e.side) cudaStreamDestroy(e.side);
   cudaFree(e.d_sync);
   cudaFree(e.d_w32);
   cudaFree(e.d_is32);
@@ -235,6 +250,7 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
   e.ec.n_det = D;
   e.ec.pad = 0;
   e.ec.gmst = desc->gmst;
+  split_pair(desc->gmst, e.ec.gmst2);
   for (int d = 0; d < RB_MAX_DET; ++d) {
     if (d < D) {
       const rb_detector_desc& dd = desc->det[d];
@@ -292,6 +308,12 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
       e.device_bytes += a.n;
     }
     if (rc != RB_OK) break;
+    if ((err = cudaStreamCreateWithFlags(&e.side, cudaStreamNonBlocking)) != cudaSuccess ||
+        (err = cudaEventCreateWithFlags(&e.ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+        (err = cudaEventCreateWithFlags(&e.ev_join, cudaEventDisableTiming)) != cudaSuccess) {
+      rc = cuda_fail(err, "rebuild stream and events");
+      break;
+    }
     e.dev.n_det = D;
     e.dev.n_bins = B;
     e.dev.n_edges = E;
@@ -451,6 +473,7 @@ int rb_strain(const double* geom, double gmst, const double* theta_host, double 
   std::memset(&ec, 0, sizeof(ec));
   ec.n_det = 1;
   ec.gmst = gmst;
+  split_pair(gmst, ec.gmst2);
   ec.det[0] = make_geom(geom[0], geom[1], geom[2], geom[3], geom[4]);
   double* d_theta = nullptr;
   RefValues* d_src = nullptr;
@@ -484,9 +507,21 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
       in.psd[d] = e.d_psd + (size_t)d * e.N;
     }
   }
-  if ((err = launch_ref_values(e.d_theta_ref, e.ec, e.d_ref, s)) != cudaSuccess) return cuda_fail(err, "reference values kernel");
   const bool fast = mode != RB_FP64 && e.kmin >= 1024 && e.N <= (int64_t(1) << 30);
-  int launches = 2;
+  // Both sets of reference values are rebuilt: the float-float set (mixed
+  // path, fast summary) and the FP64 set (FP64 paths, FP64 summary).  The
+  // one this summary does not read runs on a forked stream, joined below.
+  if ((err = cudaEventRecord(e.ev_fork, s)) != cudaSuccess || (err = cudaStreamWaitEvent(e.side, e.ev_fork, 0)) != cudaSuccess)
+    return cuda_fail(err, "rebuild fork");
+  if (fast) {
+    if ((err = launch_ref_values(e.d_theta_ref, e.ec, e.d_ref, e.side)) != cudaSuccess) return cuda_fail(err, "reference values kernel");
+    if ((err = launch_ref_dd(e.d_theta_ref, e.ec, e.d_ref, s)) != cudaSuccess) return cuda_fail(err, "reference values kernel");
+  } else {
+    if ((err = launch_ref_dd(e.d_theta_ref, e.ec, e.d_ref, e.side)) != cudaSuccess) return cuda_fail(err, "reference values kernel");
+    if ((err = launch_ref_values(e.d_theta_ref, e.ec, e.d_ref, s)) != cudaSuccess) return cuda_fail(err, "reference values kernel");
+  }
+  if ((err = cudaEventRecord(e.ev_join, e.side)) != cudaSuccess) return cuda_fail(err, "rebuild join");
+  int launches = 3;
   if (fast) {
     // the FP32 working copy follows the data the sums are taken over: data
     // read in place are converted every time, the resident data only after
@@ -504,6 +539,7 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
     err = launch_summary(in, e.kmin, e.N, e.T, e.n_det, e.n_bins, e.d_edges, e.d_ref, e.out(), s);
   }
   if (err != cudaSuccess) return cuda_fail(err, "summary kernel");
+  if ((err = cudaStreamWaitEvent(s, e.ev_join, 0)) != cudaSuccess) return cuda_fail(err, "rebuild join");
   count_launches(launches);
   return RB_OK;
 }

@@ -36,6 +36,8 @@ struct EventEntry {
   float* d_is32 = nullptr;        // fast build: FP32 copy 1/S' [D][N]
   int* d_wexp = nullptr;          // fast build: power-of-two scales {sd, sS} per detector
   bool w32_resident = false;      // the FP32 copy holds the resident data
+  cudaStream_t side = nullptr;    // rebuild: branch for the reference values the summary does not use
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   PartDesc* d_parts = nullptr;    // fast build: parts of bins
   float* d_part_sums = nullptr;   // fast build: per-part float-pair sums
   int n_parts = 0;

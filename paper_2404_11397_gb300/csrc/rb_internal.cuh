@@ -39,6 +39,9 @@ constexpr double kMpcS = 3.085677581491367e22 / 299792458.0;  // 1 Mpc / c [s]
 struct DetGeom {
   double D[3][3];   // response tensor (x x^T - y y^T)/2
   double r[3];      // vertex [m], Earth-fixed
+  // float pairs (hi, lo) for the float-float set-up of the mixed path
+  float xa[3][2], ya[3][2];  // arm unit vectors
+  float rc[3][2];            // vertex / c [s]
 };
 
 // Constant event data needed by the per-walker set-up kernel.
@@ -46,6 +49,7 @@ struct EventConst {
   int n_det;
   int pad;
   double gmst;
+  float gmst2[2];  // gmst as a float pair
   DetGeom det[kMaxDet];
 };
 
@@ -70,8 +74,19 @@ struct DataPtrs {
 
 // Fiducial (theta_ref) values of an event, written by the reference kernel:
 // the FP64 values plus float-pair copies used by the FP32-pipe kernels.
+// Fiducial values of the mixed path, float pairs (hi, lo) from the
+// float-float set-up (the same instructions as a walker's set-up).
+struct RefDD {
+  float c[kNBasis][2];
+  float phi0[2];
+  float tau[kMaxDet][2];
+  float P[kMaxDet][2][2];
+  float amp[2];
+};
+
 struct RefValues {
-  Values v;
+  Values v;       // FP64 fiducial values (FP64 and FP64-phase paths)
+  RefDD dd;       // float-float fiducial values (mixed path)
   float chat[kNBasis][2];   // c_k / 2pi (turns), float pair
   float phi0t[2];           // Phi0 / 2pi (turns), float pair
   float taut[kMaxDet][2];   // tau_d [s], float pair

@@ -33,6 +33,7 @@
 #include <type_traits>
 
 #include "rb.h"
+#include "rb_dd.cuh"
 #include "rb_internal.cuh"
 
 namespace rb {
@@ -236,37 +237,40 @@ template <class T, int N> __device__ __forceinline__ void du_sincos(const Du<T, 
 // (Mc, q, chi1, chi2, Lambda1, Lambda2), and of the detector quantities with
 // respect to (iota, psi, ra, dec).  Same formulas as walker_values, carried in
 // precision T (FP32 suffices for the mixed paths: tangents need ~1e-6).
+// One warp computes the derivatives with respect to one pair of variables,
+// part 0: (Mc, q), part 1: (chi1, chi2), part 2: (Lambda1, Lambda2).
 template <class T>
-__device__ void tangents_intrinsic(const double* th, WalkerTan<T>& o) {
-  using D6 = Du<T, kNTanIntr>;
-  const D6 Mc = du_var<T, kNTanIntr>(T(th[0]), 0), q = du_var<T, kNTanIntr>(T(th[1]), 1);
-  const D6 chi1 = du_var<T, kNTanIntr>(T(th[2]), 2), chi2 = du_var<T, kNTanIntr>(T(th[3]), 3);
-  const D6 L1 = du_var<T, kNTanIntr>(T(th[4]), 4), L2 = du_var<T, kNTanIntr>(T(th[5]), 5);
-  const D6 one = du_const<T, kNTanIntr>(T(1));
-  const D6 opq = one + q;
-  const D6 eta = q / (opq * opq);
-  const D6 X1 = one / opq, X2 = q / opq;
-  const D6 X1_2 = X1 * X1, X2_2 = X2 * X2, X1_4 = X1_2 * X1_2, X2_4 = X2_2 * X2_2;
-  const D6 beta = T(1.0 / 12.0) * (chi1 * (T(113) * X1_2 + T(75) * eta) + chi2 * (T(113) * X2_2 + T(75) * eta));
-  const D6 sigma = T(474.0 / 48.0) * (eta * chi1 * chi2) + T(486.0 / 96.0) * (X1_2 * chi1 * chi1 + X2_2 * chi2 * chi2);
-  const D6 phi2 = T(3715.0 / 756.0) + T(55.0 / 9.0) * eta;
-  const D6 phi3 = T(-16.0 * kPi) + T(4) * beta;
-  const D6 phi4 = T(15293365.0 / 508032.0) + T(27145.0 / 504.0) * eta + T(3085.0 / 72.0) * (eta * eta) - T(10) * sigma;
-  const D6 phi5p = T(kPi * 38645.0 / 756.0) + T(-kPi * 65.0 / 9.0) * eta;
-  const D6 phi6c = T(11583231236531.0 / 4694215680.0 - (640.0 / 3.0) * kPi * kPi - (6848.0 / 21.0) * kEulerGamma) +
+__device__ void tangents_intrinsic(const double* th, int part, WalkerTan<T>& o) {
+  using DI = Du<T, 2>;
+  auto var = [&](int v) { return (v >> 1) == part ? du_var<T, 2>(T(th[v]), v & 1) : du_const<T, 2>(T(th[v])); };
+  const DI Mc = var(0), q = var(1);
+  const DI chi1 = var(2), chi2 = var(3);
+  const DI L1 = var(4), L2 = var(5);
+  const DI one = du_const<T, 2>(T(1));
+  const DI opq = one + q;
+  const DI eta = q / (opq * opq);
+  const DI X1 = one / opq, X2 = q / opq;
+  const DI X1_2 = X1 * X1, X2_2 = X2 * X2, X1_4 = X1_2 * X1_2, X2_4 = X2_2 * X2_2;
+  const DI beta = T(1.0 / 12.0) * (chi1 * (T(113) * X1_2 + T(75) * eta) + chi2 * (T(113) * X2_2 + T(75) * eta));
+  const DI sigma = T(474.0 / 48.0) * (eta * chi1 * chi2) + T(486.0 / 96.0) * (X1_2 * chi1 * chi1 + X2_2 * chi2 * chi2);
+  const DI phi2 = T(3715.0 / 756.0) + T(55.0 / 9.0) * eta;
+  const DI phi3 = T(-16.0 * kPi) + T(4) * beta;
+  const DI phi4 = T(15293365.0 / 508032.0) + T(27145.0 / 504.0) * eta + T(3085.0 / 72.0) * (eta * eta) - T(10) * sigma;
+  const DI phi5p = T(kPi * 38645.0 / 756.0) + T(-kPi * 65.0 / 9.0) * eta;
+  const DI phi6c = T(11583231236531.0 / 4694215680.0 - (640.0 / 3.0) * kPi * kPi - (6848.0 / 21.0) * kEulerGamma) +
                    T(-15737765635.0 / 3048192.0 + (2255.0 / 12.0) * kPi * kPi) * eta +
                    T(76055.0 / 1728.0) * (eta * eta) + T(-127825.0 / 1296.0) * (eta * eta * eta);
-  const D6 phi7 = T(kPi * 77096675.0 / 254016.0) + T(kPi * 378515.0 / 1512.0) * eta + T(-kPi * 74045.0 / 756.0) * (eta * eta);
-  const D6 phi10 = (T(-288) + T(264) * X1) * X1_4 * L1 + (T(-288) + T(264) * X2) * X2_4 * L2;
-  const D6 phi12 =
+  const DI phi7 = T(kPi * 77096675.0 / 254016.0) + T(kPi * 378515.0 / 1512.0) * eta + T(-kPi * 74045.0 / 756.0) * (eta * eta);
+  const DI phi10 = (T(-288) + T(264) * X1) * X1_4 * L1 + (T(-288) + T(264) * X2) * X2_4 * L2;
+  const DI phi12 =
       X1_4 * L1 * (T(-15895.0 / 28.0) + T(4595.0 / 28.0) * X1 + T(5715.0 / 14.0) * X1_2 + T(-325.0 / 7.0) * (X1_2 * X1)) +
       X2_4 * L2 * (T(-15895.0 / 28.0) + T(4595.0 / 28.0) * X2 + T(5715.0 / 14.0) * X2_2 + T(-325.0 / 7.0) * (X2_2 * X2));
-  const D6 lnMc = du_log(T(kPi * kMsunS) * Mc);
-  const D6 u = lnMc + T(-0.6) * du_log(eta);
-  const D6 a = du_exp(T(1.0 / 3.0) * u);
-  const D6 N0 = T(3.0 / 128.0) * du_exp(T(-5.0 / 3.0) * lnMc);
-  const D6 a2 = a * a, a3 = a2 * a, a4 = a2 * a2, a5 = a4 * a, a6 = a3 * a3, a7 = a6 * a, a10 = a5 * a5, a12 = a6 * a6;
-  D6 c[kNBasis];
+  const DI lnMc = du_log(T(kPi * kMsunS) * Mc);
+  const DI u = lnMc + T(-0.6) * du_log(eta);
+  const DI a = du_exp(T(1.0 / 3.0) * u);
+  const DI N0 = T(3.0 / 128.0) * du_exp(T(-5.0 / 3.0) * lnMc);
+  const DI a2 = a * a, a3 = a2 * a, a4 = a2 * a2, a5 = a4 * a, a6 = a3 * a3, a7 = a6 * a, a10 = a5 * a5, a12 = a6 * a6;
+  DI c[kNBasis];
   c[0] = N0;
   c[1] = N0 * a2 * phi2;
   c[2] = N0 * a3 * phi3;
@@ -277,17 +281,19 @@ __device__ void tangents_intrinsic(const double* th, WalkerTan<T>& o) {
   c[7] = N0 * a7 * phi7;
   c[8] = N0 * a10 * phi10;
   c[9] = N0 * a12 * phi12;
-  const D6 phi0v = N0 * a5 * phi5p * (T(1.0 + 1.5 * 1.791759469228055) + u);  // ln 6 = 1.7917594692
+  const DI phi0v = N0 * a5 * phi5p * (T(1.0 + 1.5 * 1.791759469228055) + u);  // ln 6 = 1.7917594692
   for (int k = 0; k < kNBasis; ++k)
-    for (int j = 0; j < kNTanIntr; ++j) o.dc[k][j] = c[k].d[j];
-  o.dphi0[0] = phi0v.d[0];
-  o.dphi0[1] = phi0v.d[1];
-  o.lnamp_Mc = T(5.0 / 6.0) / T(th[0]);
-  o.lnamp_dL = T(-1) / T(th[6]);
+    for (int j = 0; j < 2; ++j) o.dc[k][2 * part + j] = c[k].d[j];
+  if (part == 0) {
+    o.dphi0[0] = phi0v.d[0];
+    o.dphi0[1] = phi0v.d[1];
+    o.lnamp_Mc = T(5.0 / 6.0) / T(th[0]);
+    o.lnamp_dL = T(-1) / T(th[6]);
+  }
 }
 
 template <class T>
-__device__ void tangents_detector(const double* th, const EventConst& ec, WalkerTan<T>& o) {
+__device__ void tangents_detector(const double* th, const EventConst& ec, int d, WalkerTan<T>& o) {
   // detector tangents: variables (iota, psi, ra, dec)
   using D4 = Du<T, 4>;
   const D4 iota = du_var<T, 4>(T(th[9]), 0), psi = du_var<T, 4>(T(th[10]), 1);
@@ -302,11 +308,11 @@ __device__ void tangents_detector(const double* th, const EventConst& ec, Walker
   const D4 Y[3] = {sp * sg - cp * cg * sd, sp * cg + cp * sg * sd, cp * cd};
   // sky direction n(ra - gmst, dec) = (cd cos(-g), cd sin(-g), sd) = (cd cg, -cd sg, sd)
   const D4 n[3] = {cd * cg, T(-1) * (cd * sg), sd};
-  for (int d = 0; d < kMaxDet; ++d) {
+  {
     if (d >= ec.n_det) {
       for (int j = 0; j < 2; ++j) o.dtd[d][j] = T(0);
       for (int j = 0; j < 4; ++j) o.dlnP[d][j][0] = o.dlnP[d][j][1] = T(0);
-      continue;
+      return;
     }
     const DetGeom& G = ec.det[d];
     D4 fp = du_const<T, 4>(T(0)), fx = du_const<T, 4>(T(0));
@@ -403,12 +409,53 @@ __device__ void setup_absolute(const double* __restrict__ theta, int64_t w0, int
   roles_sync();
 }
 
-// Reference kernel: one block; lane 0's walker is theta_ref.
+// Tangent warps of the set-up kernels: which = 0..2 take the derivatives
+// with respect to one pair of intrinsic parameters, which = 3..5 those of
+// detector which - 3 (the work is split so that no warp's chain is long).
+constexpr int kTanWarps = 3 + kMaxDet;
+template <class TanT>
+__device__ void tangent_warp(const double* __restrict__ theta, int64_t W, int64_t w0, const EventConst& ec,
+                             void* __restrict__ tan_out, int which) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = w0 + lane;
+  const bool mine = w < W;
+  double th[kNPar];
+  const int64_t wc = mine ? w : W - 1;
+  for (int j = 0; j < kNPar; ++j) th[j] = theta[wc * kNPar + j];
+  WalkerTan<TanT>* tan = static_cast<WalkerTan<TanT>*>(tan_out) + wc;
+  WalkerTan<TanT> t;
+  if (which < 3) {
+    tangents_intrinsic<TanT>(th, which, t);
+    if (mine) {
+      for (int k = 0; k < kNBasis; ++k)
+        for (int j = 2 * which; j < 2 * which + 2; ++j) tan->dc[k][j] = t.dc[k][j];
+      if (which == 0) {
+        tan->dphi0[0] = t.dphi0[0];
+        tan->dphi0[1] = t.dphi0[1];
+        tan->lnamp_Mc = t.lnamp_Mc;
+        tan->lnamp_dL = t.lnamp_dL;
+      }
+    }
+  } else {
+    const int d = which - 3;
+    tangents_detector<TanT>(th, ec, d, t);
+    if (mine) {
+      tan->dtd[d][0] = t.dtd[d][0];
+      tan->dtd[d][1] = t.dtd[d][1];
+      for (int j = 0; j < 4; ++j) {
+        tan->dlnP[d][j][0] = t.dlnP[d][j][0];
+        tan->dlnP[d][j][1] = t.dlnP[d][j][1];
+      }
+    }
+  }
+}
+
+// FP64 reference kernel (FP64 and FP64-phase paths): one block; every lane
+// evaluates theta_ref.
 __global__ void __launch_bounds__(7 * 32) k_ref_values(const double* theta, EventConst ec, RefValues* out) {
   __shared__ SetupSmem S;
   setup_absolute(theta, 0, 1, ec, S);
-  const int j = threadIdx.x;
-  if (j == 0) {
+  if (threadIdx.x == 0) {
     Values v;
     for (int k = 0; k < kNBasis; ++k) v.c[k] = S.c[k][0];
     v.phi0 = S.phi0[0];
@@ -423,26 +470,6 @@ __global__ void __launch_bounds__(7 * 32) k_ref_values(const double* theta, Even
     v.valid = S.valid[0];
     v.pad = 0;
     out->v = v;
-  } else if (j >= 32 && j < 32 + kNBasis + 1 + 2 * kMaxDet) {
-    // float-pair copies, one quantity per lane (the FP64 instructions issue once)
-    const int i = j - 32;
-    // sqrt(5/24) pi^{-2/3} (G Msun/c^3)^{5/6} / (1 Mpc / c): amplitude of h0 per Msun^{5/6}/Mpc
-    const double a = 8.035028173395984e-06 / kMpcS * S.amp[0];
-    double x;
-    if (i < kNBasis) x = S.c[i][0] * (1.0 / kTwoPi);
-    else if (i == kNBasis) x = S.phi0[0] * (1.0 / kTwoPi);
-    else if (i < kNBasis + 1 + kMaxDet) x = (i - kNBasis - 1 < ec.n_det) ? S.tau[i - kNBasis - 1][0] : 0.0;
-    else x = 0.0;
-    const f2x p = f2x_from(x);
-    if (i < kNBasis) { out->chat[i][0] = p.hi; out->chat[i][1] = p.lo; }
-    else if (i == kNBasis) { out->phi0t[0] = p.hi; out->phi0t[1] = p.lo; }
-    else if (i < kNBasis + 1 + kMaxDet) { out->taut[i - kNBasis - 1][0] = p.hi; out->taut[i - kNBasis - 1][1] = p.lo; }
-    else {
-      const int d = i - kNBasis - 1 - kMaxDet;
-      const bool on = d < ec.n_det;
-      out->K[d][0] = on ? a * S.P[d][0][0] : 0.0;
-      out->K[d][1] = on ? a * S.P[d][1][0] : 0.0;
-    }
   }
 }
 
@@ -450,7 +477,7 @@ __global__ void __launch_bounds__(7 * 32) k_ref_values(const double* theta, Even
 // RB_FP64 writes WalkerF64 (+ double tangents); RB_MIXED_F64PHASE writes
 // WalkerF64 (+ float tangents).
 template <int MODE, bool GRAD>
-__global__ void __launch_bounds__(7 * 32) k_setup(const double* __restrict__ theta, int64_t W, EventConst ec,
+__global__ void __launch_bounds__((5 + kTanWarps) * 32) k_setup(const double* __restrict__ theta, int64_t W, EventConst ec,
                                                   const RefValues* __restrict__ ref, void* __restrict__ ws_out,
                                                   void* __restrict__ tan_out) {
   using TanT = typename std::conditional<MODE == RB_FP64, double, float>::type;
@@ -462,36 +489,7 @@ __global__ void __launch_bounds__(7 * 32) k_setup(const double* __restrict__ the
   if (warp >= 5) {
     // tangents (gradient only) do not depend on the FP64 phases: these warps
     // run them alongside and take no part in the role barriers
-    if (!GRAD) return;
-    double th[kNPar];
-    const int64_t wc = mine ? w : W - 1;
-    for (int j = 0; j < kNPar; ++j) th[j] = theta[wc * kNPar + j];
-    WalkerTan<TanT>* tan = static_cast<WalkerTan<TanT>*>(tan_out) + wc;
-    if (warp == 5) {
-      WalkerTan<TanT> t;
-      tangents_intrinsic<TanT>(th, t);
-      if (mine) {
-        for (int k = 0; k < kNBasis; ++k)
-          for (int j = 0; j < kNTanIntr; ++j) tan->dc[k][j] = t.dc[k][j];
-        tan->dphi0[0] = t.dphi0[0];
-        tan->dphi0[1] = t.dphi0[1];
-        tan->lnamp_Mc = t.lnamp_Mc;
-        tan->lnamp_dL = t.lnamp_dL;
-      }
-    } else {
-      WalkerTan<TanT> t;
-      tangents_detector<TanT>(th, ec, t);
-      if (mine) {
-        for (int d = 0; d < kMaxDet; ++d) {
-          tan->dtd[d][0] = t.dtd[d][0];
-          tan->dtd[d][1] = t.dtd[d][1];
-          for (int j = 0; j < 4; ++j) {
-            tan->dlnP[d][j][0] = t.dlnP[d][j][0];
-            tan->dlnP[d][j][1] = t.dlnP[d][j][1];
-          }
-        }
-      }
-    }
+    if (GRAD) tangent_warp<TanT>(theta, W, w0, ec, tan_out, warp - 5);
     return;
   }
   setup_absolute(theta, w0, W, ec, S);
@@ -581,6 +579,359 @@ __global__ void __launch_bounds__(7 * 32) k_setup(const double* __restrict__ the
   }
 }
 
+
+// ===========================================================================
+// Mixed path: the same set-up in float-float arithmetic on the FP32 pipe
+// (rb_dd.cuh).  Values are float pairs (hi, lo) with ~48 bits; the phase
+// coefficients need ~1e-12 relative and the delays ~1e-12 s, well inside.
+// Powers of the masses come from Newton roots instead of exp/log:
+//   x = pi Mc (G Msun/c^3),  a1 = x^1/3,  N0 = (3/128) a1^-5,
+//   Mc^5/6 = a1^5/2 / (pi G Msun/c^3)^5/6,  a = (pi M)^1/3 = a1 eta^-1/5,
+// and one logarithm ln a = ln(pi M) / 3 (2.5PN and 3PN logarithmic terms).
+// The antenna factor uses the arm unit vectors, F+ = ((x.X)^2 - (y.X)^2 -
+// (x.Y)^2 + (y.Y)^2) / 2, Fx = (x.X)(x.Y) - (y.X)(y.Y), the same as D:(XX-YY)
+// and D:(XY+YX) with D = (x x^T - y y^T)/2.
+// Float-float chains are latency-bound, so the work of a walker is split
+// into short roles on eight warps (phase 1: masses, eta, two halves of the PN
+// polynomials, the four sines/cosines; phase 2: the logarithmic and the power
+// parts of the coefficients, three antenna factors, the delays).  The whole
+// set-up is one noinline function, so a walker at theta_ref reproduces the
+// reference values bit for bit.
+// ===========================================================================
+namespace fx = rb::ffx;
+using fx::dd;
+
+constexpr int kDdRoleWarps = 8;
+constexpr int kDdRoleThreads = kDdRoleWarps * 32;
+__device__ __forceinline__ void ddroles_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kDdRoleThreads) : "memory"); }
+
+__device__ __forceinline__ dd ld2(const float2& v) { return {v.x, v.y}; }
+__device__ __forceinline__ float2 st2(dd v) { return make_float2(v.h, v.l); }
+__device__ __forceinline__ dd ldp(const float* p) { return {p[0], p[1]}; }
+__device__ __forceinline__ dd inv2pi() {
+  constexpr fx::cdd c(1.0 / kTwoPi);
+  return fx::K(c);
+}
+
+struct DdSmem {
+  double th[kNPar][kSetupWalkers];
+  float2 thd[kNPar][kSetupWalkers];  // theta as float pairs
+  float2 a1[kSetupWalkers], N0[kSetupWalkers], amp[kSetupWalkers], e15[kSetupWalkers];
+  float2 phi[8][kSetupWalkers];
+  float2 trig[8][kSetupWalkers];  // sin/cos of dec, (ra - gmst), psi, iota
+  float2 tau[kMaxDet][kSetupWalkers];
+  float2 c[kNBasis][kSetupWalkers], phi0[kSetupWalkers];
+  float2 P[kMaxDet][2][kSetupWalkers];
+  float2 E[2][kSetupWalkers];  // exp(-i dPhi0)
+  int valid[kSetupWalkers];
+};
+
+// PN polynomials phi2, phi3, phi4, phi5p (part 0) or phi6c, phi7, phi10,
+// phi12 (part 1) of the walker (see the FP64 role).
+__device__ __forceinline__ void ddpn(int part, dd qd, dd c1, dd c2, dd l1, dd l2, dd* phi) {
+  using fx::add;
+  using fx::mul;
+  using fx::K;
+  const dd opq = add(qd, 1.f);
+  const dd X1 = fx::div(1.f, opq), X2 = fx::div(qd, opq);
+  const dd eta = mul(X1, X2);
+  const dd eta2 = fx::sqr(eta);
+  const dd X1_2 = fx::sqr(X1), X2_2 = fx::sqr(X2);
+  if (part == 0) {
+    const dd e75 = mul(eta, 75.f);
+    // beta = (chi1 (113 X1^2 + 75 eta) + chi2 (113 X2^2 + 75 eta)) / 12
+    constexpr fx::cdd k12(1.0 / 12.0);
+    const dd beta = mul(add(mul(c1, add(mul(X1_2, 113.f), e75)), mul(c2, add(mul(X2_2, 113.f), e75))), K(k12));
+    // sigma = eta (474/48) chi1 chi2 + (486/96) (X1^2 chi1^2 + X2^2 chi2^2)
+    constexpr fx::cdd k474(474.0 / 48.0), k486(486.0 / 96.0);
+    const dd sigma = add(mul(mul(mul(eta, c1), c2), K(k474)),
+                         mul(add(mul(X1_2, fx::sqr(c1)), mul(X2_2, fx::sqr(c2))), K(k486)));
+    constexpr fx::cdd p2a(3715.0 / 756.0), p2b(55.0 / 9.0);
+    phi[0] = add(K(p2a), mul(eta, K(p2b)));
+    constexpr fx::cdd p3a(-16.0 * kPi);
+    phi[1] = add(K(p3a), mul(beta, 4.f));
+    constexpr fx::cdd p4a(15293365.0 / 508032.0), p4b(27145.0 / 504.0), p4c(3085.0 / 72.0);
+    phi[2] = add(add(add(K(p4a), mul(eta, K(p4b))), mul(eta2, K(p4c))), mul(sigma, -10.f));
+    constexpr fx::cdd p5a(kPi * 38645.0 / 756.0), p5b(-kPi * 65.0 / 9.0);
+    phi[3] = add(K(p5a), mul(eta, K(p5b)));
+  } else {
+    const dd eta3 = mul(eta2, eta);
+    const dd X1_4 = fx::sqr(X1_2), X2_4 = fx::sqr(X2_2);
+    constexpr fx::cdd p6a(11583231236531.0 / 4694215680.0 - (640.0 / 3.0) * kPi * kPi - (6848.0 / 21.0) * kEulerGamma);
+    constexpr fx::cdd p6b(-15737765635.0 / 3048192.0 + (2255.0 / 12.0) * kPi * kPi), p6c(76055.0 / 1728.0),
+        p6d(-127825.0 / 1296.0);
+    phi[4] = add(add(add(K(p6a), mul(eta, K(p6b))), mul(eta2, K(p6c))), mul(eta3, K(p6d)));
+    constexpr fx::cdd p7a(kPi * 77096675.0 / 254016.0), p7b(kPi * 378515.0 / 1512.0), p7c(-kPi * 74045.0 / 756.0);
+    phi[5] = add(add(K(p7a), mul(eta, K(p7b))), mul(eta2, K(p7c)));
+    // 5PN tidal: sum_i (-288 + 264 X_i) X_i^4 Lambda_i
+    phi[6] = add(mul(mul(add(mul(X1, 264.f), -288.f), X1_4), l1), mul(mul(add(mul(X2, 264.f), -288.f), X2_4), l2));
+    // 6PN tidal: sum_i X_i^4 Lambda_i (-15895/28 + 4595/28 X_i + 5715/14 X_i^2 - 325/7 X_i^3)
+    constexpr fx::cdd t0(-15895.0 / 28.0), t1(4595.0 / 28.0), t2(5715.0 / 14.0), t3(-325.0 / 7.0);
+    const dd q1 = add(add(add(K(t0), mul(X1, K(t1))), mul(X1_2, K(t2))), mul(mul(X1_2, X1), K(t3)));
+    const dd q2 = add(add(add(K(t0), mul(X2, K(t1))), mul(X2_2, K(t2))), mul(mul(X2_2, X2), K(t3)));
+    phi[7] = add(mul(mul(X1_4, l1), q1), mul(mul(X2_4, l2), q2));
+  }
+}
+
+// P_d = F+ (1 + cos^2 i)/2 - i Fx cos i from the arm unit vectors;
+// t = sin/cos of (dec, ra - gmst, psi, iota).
+__device__ __forceinline__ void ddantenna(const DetGeom& g, const dd* t, dd* P) {
+  using fx::add;
+  using fx::mul;
+  using fx::sub;
+  const dd sd = t[0], cd = t[1], sg = fx::neg(t[2]), cg = t[3];  // g = gmst - ra
+  const dd sp = t[4], cp = t[5], ci = t[7];
+  const dd sdcg = mul(sd, cg), sdsg = mul(sd, sg);
+  const dd X[3] = {fx::neg(add(mul(cp, sg), mul(sp, sdcg))), sub(mul(sp, sdsg), mul(cp, cg)), mul(sp, cd)};
+  const dd Y[3] = {sub(mul(sp, sg), mul(cp, sdcg)), add(mul(sp, cg), mul(cp, sdsg)), mul(cp, cd)};
+  auto dot = [&](const float (*v)[2], const dd* u) {
+    return add(add(mul(ldp(v[0]), u[0]), mul(ldp(v[1]), u[1])), mul(ldp(v[2]), u[2]));
+  };
+  const dd xX = dot(g.xa, X), xY = dot(g.xa, Y), yX = dot(g.ya, X), yY = dot(g.ya, Y);
+  const dd fp = mul(add(sub(fx::sqr(xX), fx::sqr(yX)), sub(fx::sqr(yY), fx::sqr(xY))), 0.5f);
+  const dd fc = sub(mul(xX, xY), mul(yX, yY));
+  P[0] = mul(mul(fp, add(fx::sqr(ci), 1.f)), 0.5f);
+  P[1] = fx::neg(mul(fc, ci));
+}
+
+// Phases 1 and 2 of the float-float set-up for the block's walkers (the
+// kDdRoleWarps role warps only), absolute values left in shared memory.
+__device__ __noinline__ void setup_absolute_dd(const double* __restrict__ theta, int64_t w0, int64_t W,
+                                               const EventConst& ec, DdSmem& S) {
+  using fx::add;
+  using fx::mul;
+  using fx::K;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kNPar * kSetupWalkers; i += kDdRoleThreads) {
+    const int l = i / kNPar, j = i % kNPar;
+    const int64_t w = (w0 + l < W) ? w0 + l : W - 1;  // pad with the last walker
+    const double v = theta[w * kNPar + j];
+    S.th[j][l] = v;
+    S.thd[j][l] = st2(fx::from_double(v));
+  }
+  ddroles_sync();
+  const int l = lane;
+  switch (warp) {
+    case 0: {  // masses and amplitude
+      double th[kNPar];
+      for (int j = 0; j < kNPar; ++j) th[j] = S.th[j][l];
+      S.valid[l] = theta_valid(th) ? 1 : 0;
+      constexpr fx::cdd kPiMsunDD(kPi * kMsunS);
+      constexpr fx::cdd kAmpInvDD(1.0 / 9.802409278970853e-05);  // (pi G Msun / c^3)^-5/6 [Msun^5/6]
+      constexpr fx::cdd k3over128(3.0 / 128.0);
+      const dd x = mul(K(kPiMsunDD), ld2(S.thd[0][l]));
+      const dd r = fx::cbrt(x);
+      const dd r2 = fx::sqr(r);
+      S.a1[l] = st2(r);
+      S.N0[l] = st2(fx::div(K(k3over128), mul(fx::sqr(r2), r)));
+      S.amp[l] = st2(fx::div(mul(mul(r2, fx::sqrt(r)), K(kAmpInvDD)), ld2(S.thd[6][l])));
+      break;
+    }
+    case 1: {  // eta^-1/5
+      const dd qd = ld2(S.thd[1][l]);
+      S.e15[l] = st2(fx::rroot5(fx::div(qd, fx::sqr(add(qd, 1.f)))));
+      break;
+    }
+    case 2:
+    case 3: {  // PN polynomials, two halves
+      dd phi[8];
+      const int part = warp - 2;
+      ddpn(part, ld2(S.thd[1][l]), ld2(S.thd[2][l]), ld2(S.thd[3][l]), ld2(S.thd[4][l]), ld2(S.thd[5][l]), phi);
+      for (int k = 4 * part; k < 4 * part + 4; ++k) S.phi[k][l] = st2(phi[k]);
+      break;
+    }
+    case 4:
+    case 5:
+    case 6:
+    case 7: {  // sin/cos of dec, ra - gmst, psi, iota
+      const int i = warp - 4;
+      const dd ang = (i == 0) ? ld2(S.thd[12][l])
+                   : (i == 1) ? fx::sub(ld2(S.thd[11][l]), ldp(ec.gmst2))
+                   : (i == 2) ? ld2(S.thd[10][l]) : ld2(S.thd[9][l]);
+      dd sn, cs;
+      fx::sincos(ang, &sn, &cs);
+      S.trig[2 * i][l] = st2(sn);
+      S.trig[2 * i + 1][l] = st2(cs);
+      break;
+    }
+  }
+  ddroles_sync();
+  switch (warp) {
+    case 0: {  // the two logarithmic coefficients and Phi0
+      const dd a = mul(ld2(S.a1[l]), ld2(S.e15[l]));
+      const dd la = fx::log(a);  // ln(pi M) / 3
+      const dd a2 = fx::sqr(a), a5 = mul(fx::sqr(a2), a), a6 = fx::sqr(mul(a2, a));
+      const dd N0 = ld2(S.N0[l]);
+      const dd N5 = mul(N0, a5), N6 = mul(N0, a6);
+      constexpr fx::cdd kLn4(1.3862943611198906), k6848(-6848.0 / 21.0);
+      S.c[5][l] = st2(mul(N6, add(ld2(S.phi[4][l]), mul(add(K(kLn4), la), K(k6848)))));  // f^1/3
+      // -phi_c - pi/4 + the v^0 part of the 2.5PN term, 1 + 1.5 ln 6 + ln(pi M)
+      constexpr fx::cdd kPi4(0.25 * kPi), kC(1.0 + 1.5 * 1.791759469228055);
+      const dd t = mul(N5, mul(ld2(S.phi[3][l]), add(K(kC), mul(la, 3.f))));
+      S.phi0[l] = st2(add(fx::sub(fx::neg(ld2(S.thd[8][l])), K(kPi4)), t));
+      break;
+    }
+    case 1: {  // the other coefficients
+      const dd a = mul(ld2(S.a1[l]), ld2(S.e15[l]));
+      const dd a2 = fx::sqr(a), a3 = mul(a2, a), a4 = fx::sqr(a2), a5 = mul(a4, a), a6 = fx::sqr(a3), a7 = mul(a6, a);
+      const dd a10 = fx::sqr(a5), a12 = fx::sqr(a6);
+      const dd N0 = ld2(S.N0[l]);
+      constexpr fx::cdd k6848_63(-6848.0 / 63.0);
+      S.c[0][l] = st2(N0);
+      S.c[1][l] = st2(mul(mul(N0, a2), ld2(S.phi[0][l])));
+      S.c[2][l] = st2(mul(mul(N0, a3), ld2(S.phi[1][l])));
+      S.c[3][l] = st2(mul(mul(N0, a4), ld2(S.phi[2][l])));
+      S.c[4][l] = st2(mul(mul(N0, a5), ld2(S.phi[3][l])));  // ln f
+      S.c[6][l] = st2(mul(mul(N0, a6), K(k6848_63)));       // f^1/3 ln f
+      S.c[7][l] = st2(mul(mul(N0, a7), ld2(S.phi[5][l])));
+      S.c[8][l] = st2(mul(mul(N0, a10), ld2(S.phi[6][l])));
+      S.c[9][l] = st2(mul(mul(N0, a12), ld2(S.phi[7][l])));
+      break;
+    }
+    case 2:
+    case 3:
+    case 4: {  // antenna factor of one detector
+      const int d = warp - 2;
+      if (d < ec.n_det) {
+        dd t[8], P[2];
+        for (int k = 0; k < 8; ++k) t[k] = ld2(S.trig[k][l]);
+        ddantenna(ec.det[d], t, P);
+        S.P[d][0][l] = st2(P[0]);
+        S.P[d][1][l] = st2(P[1]);
+      } else {
+        S.P[d][0][l] = S.P[d][1][l] = make_float2(0.f, 0.f);
+      }
+      break;
+    }
+    case 5: {  // tau_d = t_c - n.r_d / c, n = (cos dec cos(ra - gmst), cos dec sin(ra - gmst), sin dec)
+      const dd sd = ld2(S.trig[0][l]), cd = ld2(S.trig[1][l]);
+      const dd n0 = mul(cd, ld2(S.trig[3][l])), n1 = mul(cd, ld2(S.trig[2][l]));
+      const dd tc = ld2(S.thd[7][l]);
+      for (int d = 0; d < kMaxDet; ++d) {
+        const DetGeom& g = ec.det[d];
+        const dd nr = add(add(mul(n0, ldp(g.rc[0])), mul(n1, ldp(g.rc[1]))), mul(sd, ldp(g.rc[2])));
+        S.tau[d][l] = st2((d < ec.n_det) ? fx::sub(tc, nr) : dd{0.f, 0.f});
+      }
+      break;
+    }
+    default:
+      break;
+  }
+  ddroles_sync();
+}
+
+// Float-float reference kernel (mixed path and the fast summary build): one
+// block, every lane evaluates theta_ref; also writes the reference copies
+// used by the summary build (c/2pi, Phi0/2pi, tau as float pairs and the
+// complex h0 prefactor K_d = A_ref P_d in FP64).
+__global__ void __launch_bounds__(kDdRoleThreads) k_ref_dd(const double* theta, EventConst ec, RefValues* out) {
+  __shared__ DdSmem S;
+  setup_absolute_dd(theta, 0, 1, ec, S);
+  const int j = threadIdx.x;
+  RefDD& R = out->dd;
+  auto put = [](float* p, dd v) { p[0] = v.h; p[1] = v.l; };
+  if (j < kNBasis) {
+    const dd c = ld2(S.c[j][0]);
+    put(R.c[j], c);
+    put(out->chat[j], fx::mul(c, inv2pi()));
+  } else if (j == kNBasis) {
+    const dd p = ld2(S.phi0[0]);
+    put(R.phi0, p);
+    put(out->phi0t, fx::mul(p, inv2pi()));
+  } else if (j == kNBasis + 1) {
+    put(R.amp, ld2(S.amp[0]));
+  } else if (j >= 32 && j < 32 + kMaxDet) {
+    const int d = j - 32;
+    const bool on = d < ec.n_det;
+    const dd t = on ? ld2(S.tau[d][0]) : dd{0.f, 0.f};
+    put(R.tau[d], t);
+    put(out->taut[d], t);
+    const dd pr = on ? ld2(S.P[d][0][0]) : dd{0.f, 0.f}, pi = on ? ld2(S.P[d][1][0]) : dd{0.f, 0.f};
+    put(R.P[d][0], pr);
+    put(R.P[d][1], pi);
+    // sqrt(5/24) pi^{-2/3} (G Msun/c^3)^{5/6} / (1 Mpc / c): h0 amplitude per Msun^{5/6}/Mpc
+    constexpr fx::cdd kAmpH(8.035028173395984e-06 / kMpcS);
+    const dd a = fx::mul(fx::K(kAmpH), ld2(S.amp[0]));
+    out->K[d][0] = fx::to_double(fx::mul(a, pr));
+    out->K[d][1] = fx::to_double(fx::mul(a, pi));
+  }
+}
+
+// Mixed batch set-up: WalkerMixed (+ float tangents on the warps after the
+// role warps).
+template <bool GRAD>
+__global__ void __launch_bounds__(kDdRoleThreads + kTanWarps * 32) k_setup_dd(const double* __restrict__ theta, int64_t W,
+                                                                 EventConst ec, const RefValues* __restrict__ ref,
+                                                                 void* __restrict__ ws_out,
+                                                                 void* __restrict__ tan_out) {
+  __shared__ DdSmem S;
+  const int64_t w0 = (int64_t)blockIdx.x * kSetupWalkers;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t w = w0 + lane;
+  const bool mine = w < W;
+  if (warp >= kDdRoleWarps) {
+    if (GRAD) tangent_warp<float>(theta, W, w0, ec, tan_out, warp - kDdRoleWarps);
+    return;
+  }
+  setup_absolute_dd(theta, w0, W, ec, S);
+  const RefDD& r = ref->dd;
+  const int l = lane;
+  WalkerMixed* o = static_cast<WalkerMixed*>(ws_out) + w;
+  if (warp == 0) {
+    // exp(-i dPhi0): dPhi0 / 2pi = y in turns (float pair, whole turns
+    // dropped); exp(-2 pi i y) - 1 = -2 sin^2(pi y) - 2i sin(pi y) cos(pi y)
+    // from the high part, plus the first-order term of the low part
+    const dd y = fx::mul(fx::sub(ld2(S.phi0[l]), ldp(r.phi0)), inv2pi());
+    const float yh = __fadd_rn(y.h, -round_fma_pipe(y.h)), yl = y.l;
+    float sn, cs;
+    sincos_pi_half(yh, sn, cs);
+    const float er = -2.f * sn * sn, ei = -2.f * sn * cs;
+    const float t = 6.28318530717958648f * yl;
+    S.E[0][l] = st2(fx::add(fx::two_sum(1.f, er), ei * t));
+    S.E[1][l] = st2(fx::two_sum(ei, -(1.f + er) * t));
+  } else if (warp == 4 && mine) {
+    for (int d = 0; d < kMaxDet; ++d) {
+      const dd dt = (d < ec.n_det) ? fx::sub(ld2(S.tau[d][l]), ldp(r.tau[d])) : dd{0.f, 0.f};
+      o->tau_hi[d] = dt.h;
+      o->tau_lo[d] = dt.l;
+    }
+  } else if (warp == 5 && mine) {
+    for (int k = 0; k < kNBasis; ++k) {
+      const dd c = fx::sub(ld2(S.c[k][l]), ldp(r.c[k]));
+      o->dc_hi[k] = c.h;
+      o->dc_lo[k] = c.l;
+    }
+    o->valid = S.valid[l];
+    o->pad[0] = o->pad[1] = o->pad[2] = 0;
+  }
+  ddroles_sync();
+  if (warp >= 1 && warp <= kMaxDet && mine) {
+    const int d = warp - 1;
+    float rho_r = 0.f, rho_i = 0.f, sig_r = 0.f, sig_i = 0.f;
+    if (d < ec.n_det) {
+      using fx::add;
+      using fx::mul;
+      using fx::sub;
+      // Q = (amp / amp_ref) P exp(-i dPhi0);  rho = Q / P_ref;  sig = (Q - P_ref) / P_ref
+      const dd ampr = fx::div(ld2(S.amp[l]), ldp(r.amp));
+      const dd er = ld2(S.E[0][l]), ei = ld2(S.E[1][l]);
+      const dd pr = ld2(S.P[d][0][l]), pi = ld2(S.P[d][1][l]);
+      const dd qr = mul(ampr, sub(mul(pr, er), mul(pi, ei))), qi = mul(ampr, add(mul(pr, ei), mul(pi, er)));
+      const dd rr = ldp(r.P[d][0]), ri = ldp(r.P[d][1]);
+      const dd iden = fx::div(1.f, add(mul(rr, rr), mul(ri, ri)));
+      const dd xr = sub(qr, rr), xi = sub(qi, ri);
+      rho_r = mul(add(mul(qr, rr), mul(qi, ri)), iden).h;
+      rho_i = mul(sub(mul(qi, rr), mul(qr, ri)), iden).h;
+      sig_r = mul(add(mul(xr, rr), mul(xi, ri)), iden).h;
+      sig_i = mul(sub(mul(xi, rr), mul(xr, ri)), iden).h;
+    }
+    o->rho[d][0] = rho_r;
+    o->rho[d][1] = rho_i;
+    o->sig[d][0] = sig_r;
+    o->sig[d][1] = sig_i;
+  }
+}
+
 // Host-side launchers.
 cudaError_t launch_ref_values(const double* theta_ref_dev, const EventConst& ec, RefValues* out, cudaStream_t s) {
   k_ref_values<<<1, 5 * 32, 0, s>>>(theta_ref_dev, ec, out);
@@ -592,15 +943,27 @@ static cudaError_t launch_setup_t(const double* theta, int64_t W, const EventCon
                                   void* tan, bool grad, cudaStream_t s) {
   const unsigned grid = (unsigned)((W + kSetupWalkers - 1) / kSetupWalkers);
   if (grad)
-    k_setup<MODE, true><<<grid, 7 * 32, 0, s>>>(theta, W, ec, ref, ws, tan);
+    k_setup<MODE, true><<<grid, (5 + kTanWarps) * 32, 0, s>>>(theta, W, ec, ref, ws, tan);
   else
     k_setup<MODE, false><<<grid, 5 * 32, 0, s>>>(theta, W, ec, ref, ws, tan);
   return cudaGetLastError();
 }
 
+cudaError_t launch_ref_dd(const double* theta_ref_dev, const EventConst& ec, RefValues* out, cudaStream_t s) {
+  k_ref_dd<<<1, kDdRoleThreads, 0, s>>>(theta_ref_dev, ec, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_setup(int mode, const double* theta, int64_t W, const EventConst& ec, const RefValues* ref,
                          void* ws, void* tan, bool grad, cudaStream_t s) {
-  if (mode == RB_MIXED) return launch_setup_t<RB_MIXED>(theta, W, ec, ref, ws, tan, grad, s);
+  if (mode == RB_MIXED) {
+    const unsigned grid = (unsigned)((W + kSetupWalkers - 1) / kSetupWalkers);
+    if (grad)
+      k_setup_dd<true><<<grid, kDdRoleThreads + kTanWarps * 32, 0, s>>>(theta, W, ec, ref, ws, tan);
+    else
+      k_setup_dd<false><<<grid, kDdRoleThreads, 0, s>>>(theta, W, ec, ref, ws, tan);
+    return cudaGetLastError();
+  }
   if (mode == RB_FP64) return launch_setup_t<RB_FP64>(theta, W, ec, ref, ws, tan, grad, s);
   return launch_setup_t<RB_MIXED_F64PHASE>(theta, W, ec, ref, ws, tan, grad, s);
 }

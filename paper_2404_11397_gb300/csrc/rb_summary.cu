@@ -600,7 +600,7 @@ __global__ void __launch_bounds__(kSumFastThreads, 6)
   const int e0 = (int)edges[b], e1 = (int)edges[b + 1];
   const int ks = pd.start, ke = pd.end;
   const int w = e1 - e0;
-  const float half_df = (float)(0.5 / T);
+  const float half_df = 0.5f * invT_hi;  // (float)(0.5 / T): no FP64 divide per thread
   if (tid < kMaxDet * kChunk) {
     const int d = tid >> 5, j = lane - kChunk / 2;
     float sh = 0.f, sl = 0.f;
