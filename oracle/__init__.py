@@ -90,6 +90,10 @@ def _load():
     lib.orc_loglike_rb.argtypes = [c_int, dp, d, d, i64, i64, c_int, ip, dp, dp, dp, dp, dp, dp, dp, i64, dp,
                                    dp, c_int]
     lib.orc_loglike_rb.restype = c_int
+    lib.orc_z_to_theta.argtypes = [dp, i64, dp]
+    lib.orc_grad_theta_to_z.argtypes = [dp, dp, i64, dp]
+    lib.orc_mala_propose.argtypes = [dp, dp, dp, dp, dp, dp, i64, dp, ctypes.c_void_p]
+    lib.orc_mala_log_alpha.argtypes = [dp, dp, dp, dp, dp, dp, i64, c_int, dp]
     _lib = lib
     return lib
 
@@ -262,3 +266,69 @@ def loglike_rb(ev, summ, theta, grad: bool = False, with_b2: bool = False, nthre
     assert rc == 0
     return (logl, g) if grad else logl
 
+
+
+# ---------------------------------------------------------------------------
+# MALA local step (Sec. II.D), sampling coordinates of Table II:
+# z = (Mc, q, chi1, chi2, L1, L2, dL, tc, phic, cos iota, psi, ra, sin dec)
+# ---------------------------------------------------------------------------
+def z_to_theta(z):
+    lib = _load()
+    z = _f64(z).reshape(-1, NPAR)
+    th = np.zeros_like(z)
+    lib.orc_z_to_theta(_p(z), z.shape[0], _p(th))
+    return th
+
+
+def grad_theta_to_z(z, g_theta):
+    lib = _load()
+    z = _f64(z).reshape(-1, NPAR)
+    g = _f64(g_theta).reshape(-1, NPAR)
+    out = np.zeros_like(z)
+    lib.orc_grad_theta_to_z(_p(z), _p(g), z.shape[0], _p(out))
+    return out
+
+
+def mala_log_alpha(logp, logp_prop, g, g_prop, eps, xi):
+    """log alpha of the MALA acceptance for states of any dimension n."""
+    lib = _load()
+    g = _f64(g)
+    W, n = g.shape
+    out = np.zeros(W)
+    lib.orc_mala_log_alpha(_p(_f64(logp)), _p(_f64(logp_prop)), _p(g), _p(_f64(g_prop)), _p(_f64(eps)),
+                           _p(_f64(xi)), W, n, _p(out))
+    return out
+
+
+def mala_propose(z, g_z, eps, xi, lo, hi):
+    lib = _load()
+    z = _f64(z).reshape(-1, NPAR)
+    zp = np.zeros_like(z)
+    inside = np.zeros(z.shape[0], dtype=np.int32)
+    lib.orc_mala_propose(_p(z), _p(_f64(g_z)), _p(_f64(eps)), _p(_f64(xi)), _p(_f64(lo)), _p(_f64(hi)),
+                         z.shape[0], _p(zp), inside.ctypes.data_as(ctypes.c_void_p))
+    return zp, inside.astype(bool)
+
+
+def mala_logpost(ev, summ, z, lo, hi, nthreads=None):
+    """log pi(z) = log L(theta(z)) (uniform prior: constant inside the open box,
+    -inf outside) and d log pi / dz."""
+    z = _f64(z).reshape(-1, NPAR)
+    inside = np.all((z > np.asarray(lo)) & (z < np.asarray(hi)), axis=1)
+    zc = np.where(inside[:, None], z, np.clip(z, np.asarray(lo) + 1e-12, np.asarray(hi) - 1e-12))
+    th = z_to_theta(zc)
+    logl, g = loglike_rb(ev, summ, th, grad=True, nthreads=nthreads)
+    gz = grad_theta_to_z(zc, g)
+    return np.where(inside, logl, -np.inf), np.where(inside[:, None], gz, 0.0)
+
+
+def mala_step(ev, summ, z, logp, g_z, eps, xi, u, lo, hi, nthreads=None):
+    """One MALA step for every chain; returns (z, logp, g_z, accepted, log_alpha)."""
+    zp, inside = mala_propose(z, g_z, eps, xi, lo, hi)
+    logpp, gzp = mala_logpost(ev, summ, zp, lo, hi, nthreads)
+    la = mala_log_alpha(logp, logpp, g_z, gzp, eps, xi)
+    acc = inside & (np.log(_f64(u)) < la)
+    z = np.where(acc[:, None], zp, z)
+    logp = np.where(acc, logpp, logp)
+    g_z = np.where(acc[:, None], gzp, g_z)
+    return z, logp, g_z, acc, la

@@ -663,4 +663,71 @@ int orc_loglike_rb(int n_det, const double* geom, double gmst, double T, int64_t
   return 0;
 }
 
+// ----------------------------------------------------------------------------
+// MALA local step (Sec. II.D: flowMC's local sampler, the Metropolis-adjusted
+// Langevin algorithm), in the sampling coordinates of Table II,
+//   z = (Mc, q, chi1, chi2, Lambda1, Lambda2, d_L, t_c, phi_c, cos iota, psi, ra, sin dec),
+// with the uniform prior of Table II on a box [lo, hi] (log prior constant
+// inside, -inf outside).  With step sizes eps_j and standard normal draws xi_j:
+//   proposal   z' = z + eps^2/2 * grad log pi(z) + eps * xi
+//   log alpha  = log pi(z') - log pi(z) + log q(z | z') - log q(z' | z)
+//              = log pi(z') - log pi(z) - 1/2 sum_j [(xi_j + eps_j (g_j + g'_j) / 2)^2 - xi_j^2],
+// where q(b | a) is the Gaussian proposal density N(b; a + eps^2/2 g(a), eps^2)
+// (so z' - z - eps^2/2 g = eps xi and z - z' - eps^2/2 g' = -eps (xi + eps (g + g')/2));
+// accept when log u < log alpha for a uniform draw u.
+// ----------------------------------------------------------------------------
+
+// theta (likelihood parameters) from z: iota = acos(z_9), dec = asin(z_12).
+void orc_z_to_theta(const double* z, int64_t W, double* theta) {
+  for (int64_t w = 0; w < W; ++w) {
+    const double* a = z + kNPar * w;
+    double* t = theta + kNPar * w;
+    for (int j = 0; j < kNPar; ++j) t[j] = a[j];
+    t[9] = std::acos(a[9]);
+    t[12] = std::asin(a[12]);
+  }
+}
+
+// d log pi / dz from d log pi / dtheta: d iota / d cos iota = -1 / sin iota,
+// d dec / d sin dec = 1 / cos dec, with sin iota = sqrt(1 - z_9^2) and
+// cos dec = sqrt(1 - z_12^2) on the open box.
+void orc_grad_theta_to_z(const double* z, const double* g_theta, int64_t W, double* g_z) {
+  for (int64_t w = 0; w < W; ++w) {
+    const double* a = z + kNPar * w;
+    const double* g = g_theta + kNPar * w;
+    double* o = g_z + kNPar * w;
+    for (int j = 0; j < kNPar; ++j) o[j] = g[j];
+    o[9] = -g[9] / std::sqrt(1.0 - a[9] * a[9]);
+    o[12] = g[12] / std::sqrt(1.0 - a[12] * a[12]);
+  }
+}
+
+// Proposal z' and whether it lies inside the open box lo < z' < hi.
+void orc_mala_propose(const double* z, const double* g_z, const double* eps, const double* xi, const double* lo,
+                      const double* hi, int64_t W, double* zp, int* inside) {
+  for (int64_t w = 0; w < W; ++w) {
+    bool in = true;
+    for (int j = 0; j < kNPar; ++j) {
+      const int64_t i = kNPar * w + j;
+      zp[i] = z[i] + 0.5 * eps[j] * eps[j] * g_z[i] + eps[j] * xi[i];
+      in = in && zp[i] > lo[j] && zp[i] < hi[j];
+    }
+    inside[w] = in ? 1 : 0;
+  }
+}
+
+// log alpha of each chain (see above); log_pp = -inf gives -inf.
+void orc_mala_log_alpha(const double* logp, const double* logp_prop, const double* g_z, const double* g_z_prop,
+                        const double* eps, const double* xi, int64_t W, int n, double* log_alpha) {
+  for (int64_t w = 0; w < W; ++w) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) {
+      const int64_t i = (int64_t)n * w + j;
+      const double t = xi[i] + 0.5 * eps[j] * (g_z[i] + g_z_prop[i]);
+      s += t * t - xi[i] * xi[i];
+    }
+    log_alpha[w] = (logp_prop[w] == -INFINITY) ? -INFINITY : logp_prop[w] - logp[w] - 0.5 * s;
+  }
+}
+
 }  // extern "C"
