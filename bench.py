@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--no-mala", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--profile", action="store_true",
                    help="fixed short warm-up and no extra legs (for profiler launch lists)")
@@ -345,6 +346,8 @@ def run_gb300(args, dist: Dist):
         result["fp64_path"] = {"value": v64, "unit": UNIT, "ms_per_step": t64 * 1e3 / K64,
                                "main_kernel_ms": float(np.mean(m64)),
                                "speedup_of_mixed": value / v64}
+    if not args.no_mala:
+        result["mala_step"] = run_mala(rb, torch, event, ev, W, args, dist, device, flush)
     if not args.no_e2e:
         result["e2e"] = run_e2e(rb, torch, event, ev, data, psd, theta, W, args, dist, device)
     if not args.no_serving and dist.rank == 0:
@@ -354,6 +357,48 @@ def run_gb300(args, dist: Dist):
             result["serving"] = {"error": str(exc)[:200]}
     event.free()
     return result
+
+
+def run_mala(rb, torch, event, ev, W, args, dist, device, flush):
+    """The MALA local step of the sampler (Sec. II.D) for W chains on this
+    event: proposal, log L + gradient and the accept step fused into the
+    likelihood kernel.  Chains start in a posterior-scale box in the sampling
+    coordinates (cos iota, sin dec) with the GW170817 prior box (Mc extended to
+    contain the injection); draws are made before the timed region; L2
+    flushed before every step."""
+    import synth
+    th = synth.posterior_box(ev["theta_inj"], W, seed=41)
+    z = th.copy()
+    z[:, 9], z[:, 12] = np.cos(th[:, 9]), np.sin(th[:, 12])
+    lo = np.array([1.16, 0.125, -0.05, -0.05, 0.0, 0.0, 1.0, -0.1, 0.0, -1.0, 0.0, 0.0, -1.0])
+    hi = np.array([1.21, 1.0, 0.05, 0.05, 5000.0, 5000.0, 75.0, 0.1, 2 * np.pi, 1.0, np.pi, 2 * np.pi, 1.0])
+    # step sizes of the order of the posterior widths of this event
+    eps = np.array([1e-6, 1e-3, 5e-5, 5e-5, 5.0, 5.0, 0.1, 2e-6, 3e-3, 3e-3, 2e-3, 2e-4, 3e-4])
+    zt = torch.tensor(z, device=device)
+    logp, gz = rb.mala_init(event, zt, lo, hi, mode=args.mode)
+    K = max(3, min(args.steps, 20))
+    gen = torch.Generator(device=device).manual_seed(7)
+    xi = torch.randn(K + 3, W, 13, dtype=torch.float64, device=device, generator=gen)
+    u = torch.rand(K + 3, W, dtype=torch.float64, device=device, generator=gen)
+    for i in range(3):
+        rb.mala_step(event, zt, logp, gz, eps, lo, hi, xi[i], u[i], mode=args.mode)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    dist.barrier()
+    torch.cuda.synchronize()
+    accs = []
+    for k in range(K):
+        flush.zero_()
+        starts[k].record()
+        accs.append(rb.mala_step(event, zt, logp, gz, eps, lo, hi, xi[3 + k], u[3 + k], mode=args.mode))
+        ends[k].record()
+    torch.cuda.synchronize()
+    acc = float(torch.stack(accs).float().mean().item())
+    ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    t, v = whole_job_rate(dist, sum(ms) / 1e3, W * K, device)
+    return {"value": v, "unit": "chain-steps/s", "chains": W, "steps": K, "ms_per_step": t * 1e3 / K,
+            "acceptance": acc, "mode": args.mode,
+            "step": "rb_mala_step: proposal kernel, set-up, log L + adjoint with the accept step fused"}
 
 
 def run_e2e(rb, torch, event, ev, data, psd, theta, W, args, dist, device):
@@ -551,7 +596,7 @@ def run_reference(args, dist: Dist):
 def main():
     args = parse()
     if args.profile:
-        args.no_e2e = args.no_cpu = args.no_serving = args.no_fp64 = True
+        args.no_e2e = args.no_cpu = args.no_serving = args.no_fp64 = args.no_mala = True
     dist = Dist()
     if args.impl == "reference":
         dist.init("gloo")

@@ -181,6 +181,33 @@ RB_API int rb_loglike_grad_batch(rb_event_t ev, const double* theta_dev, int64_t
 RB_API int rb_loglike_grad_host(rb_event_t ev, const double* theta_host, int64_t W, double* logl_host, double* grad_host,
                          int mode, void* stream);
 
+/* MALA local step (Sec. II.D: the sampler's local proposal is the
+ * Metropolis-adjusted Langevin algorithm) for W chains, fused with the
+ * likelihood and its adjoint.  Chains live in the sampling coordinates of
+ * Table II, z = (Mc, q, chi1, chi2, Lambda1, Lambda2, d_L, t_c, phi_c,
+ * cos iota, psi, ra, sin dec), row-major [W][13] FP64 on the device, with the
+ * uniform prior of Table II on the open box lo < z < hi (host arrays of 13;
+ * the cos iota and sin dec bounds must lie in [-1, 1]): log pi(z) =
+ * log L(theta(z)) inside (the prior constant is dropped), -inf outside.
+ *
+ * rb_mala_init: logp_dev [W] = log pi(z), gz_dev [W][13] = d log pi / dz.
+ * rb_mala_step: with step sizes eps_host[13], standard normal draws xi_dev
+ *   [W][13] and uniform draws u_dev [W] in (0, 1] (both on the device, drawn by
+ *   the caller), proposes z' = z + eps^2/2 gz + eps xi, evaluates log pi(z')
+ *   and its gradient, and accepts when log u < log alpha with
+ *     log alpha = log pi(z') - log pi(z) - 1/2 sum_j [(xi_j + eps_j (gz_j + gz'_j)/2)^2 - xi_j^2];
+ *   z_dev, logp_dev and gz_dev are updated in place for accepted chains and
+ *   accepted_dev [W] (int, may be NULL) is set to 1/0.
+ * mode: RB_MIXED, RB_FP64 or RB_MIXED_F64PHASE (as rb_loglike_grad_batch).
+ * Asynchronous on `stream`; per call a workspace of ~240 B + the batch's per
+ * chain comes from the stream-ordered pool.  Errors: RB_EINVAL (NULL
+ * pointers, bad mode, empty box, negative step size), RB_ENOMEM, RB_ECUDA. */
+RB_API int rb_mala_init(rb_event_t ev, const double* z_dev, int64_t W, const double* lo_host, const double* hi_host,
+                        double* logp_dev, double* gz_dev, int mode, void* stream);
+RB_API int rb_mala_step(rb_event_t ev, double* z_dev, double* logp_dev, double* gz_dev, int64_t W,
+                        const double* eps_host, const double* lo_host, const double* hi_host, const double* xi_dev,
+                        const double* u_dev, int* accepted_dev, int mode, void* stream);
+
 /* Allocation-free form of rb_loglike_grad_batch (the paper has no
  * counterpart: it is an interface for callers that cannot allocate device
  * memory at call time -- e.g. inside a stream capture in global mode, or

@@ -697,8 +697,9 @@ void orc_grad_theta_to_z(const double* z, const double* g_theta, int64_t W, doub
     const double* g = g_theta + kNPar * w;
     double* o = g_z + kNPar * w;
     for (int j = 0; j < kNPar; ++j) o[j] = g[j];
-    o[9] = -g[9] / std::sqrt(1.0 - a[9] * a[9]);
-    o[12] = g[12] / std::sqrt(1.0 - a[12] * a[12]);
+    // 1 - z^2 as (1 - z)(1 + z): no cancellation next to the box edges z = +-1
+    o[9] = -g[9] / std::sqrt((1.0 - a[9]) * (1.0 + a[9]));
+    o[12] = g[12] / std::sqrt((1.0 - a[12]) * (1.0 + a[12]));
   }
 }
 

@@ -205,6 +205,43 @@ def strain(geom, gmst: float, theta, T: float, kmin: int, n_freq: int, device="c
     return torch.view_as_complex(out)
 
 
+def _host13(v) -> np.ndarray:
+    a = np.ascontiguousarray(v, dtype=np.float64).reshape(NPAR)
+    return a
+
+
+def mala_init(event: Event, z: torch.Tensor, lo, hi, mode="mixed", stream=None):
+    """log pi(z) [W] and d log pi / dz [W, 13] for chains in the sampling
+    coordinates (cos iota, sin dec) with the uniform prior on lo < z < hi."""
+    zz = _theta_dev(z)
+    W = zz.shape[0]
+    logp = torch.empty(W, dtype=torch.float64, device=zz.device)
+    gz = torch.empty(W, NPAR, dtype=torch.float64, device=zz.device)
+    lo_, hi_ = _host13(lo), _host13(hi)
+    check(load().rb_mala_init(event.handle, ctypes.c_void_p(zz.data_ptr()), W, ctypes.c_void_p(lo_.ctypes.data),
+                              ctypes.c_void_p(hi_.ctypes.data), ctypes.c_void_p(logp.data_ptr()),
+                              ctypes.c_void_p(gz.data_ptr()), _mode(mode), _stream_handle(stream)), "rb_mala_init")
+    return logp, gz
+
+
+def mala_step(event: Event, z: torch.Tensor, logp: torch.Tensor, gz: torch.Tensor, eps, lo, hi, xi: torch.Tensor,
+              u: torch.Tensor, mode="mixed", stream=None) -> torch.Tensor:
+    """One MALA step of every chain; z, logp, gz are updated in place (they
+    must be contiguous float64 device tensors).  Returns accepted [W] (int32)."""
+    for t in (z, logp, gz, xi, u):
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise ValueError("mala_step: z, logp, gz, xi, u must be contiguous float64 CUDA tensors")
+    W = z.shape[0]
+    acc = torch.empty(W, dtype=torch.int32, device=z.device)
+    eps_, lo_, hi_ = _host13(eps), _host13(lo), _host13(hi)
+    check(load().rb_mala_step(event.handle, ctypes.c_void_p(z.data_ptr()), ctypes.c_void_p(logp.data_ptr()),
+                              ctypes.c_void_p(gz.data_ptr()), W, ctypes.c_void_p(eps_.ctypes.data),
+                              ctypes.c_void_p(lo_.ctypes.data), ctypes.c_void_p(hi_.ctypes.data),
+                              ctypes.c_void_p(xi.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+                              ctypes.c_void_p(acc.data_ptr()), _mode(mode), _stream_handle(stream)), "rb_mala_step")
+    return acc
+
+
 def kernel_launch_count() -> int:
     return int(load().rb_kernel_launch_count())
 

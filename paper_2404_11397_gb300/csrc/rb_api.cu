@@ -24,9 +24,9 @@ cudaError_t launch_ref_values(const double* theta_ref_dev, const EventConst& ec,
 cudaError_t launch_setup(int mode, const double* theta, int64_t W, const EventConst& ec, const RefValues* ref,
                          void* ws, void* tan, bool grad, cudaStream_t s);
 cudaError_t launch_rb_mixed(const EventDev& ev, const void* ws, const void* tan, int64_t W, double* logl,
-                            double* grad, bool phase64, cudaStream_t s, int n_sm);
+                            double* grad, bool phase64, cudaStream_t s, int n_sm, const MalaArgs* mala);
 cudaError_t launch_rb_f64(const EventDev& ev, const void* ws, const void* tan, int64_t W, double* logl, double* grad,
-                          cudaStream_t s, int n_sm);
+                          cudaStream_t s, int n_sm, const MalaArgs* mala);
 cudaError_t launch_bin_edges(double f_low, double f_high, double T, int64_t kmin, int64_t N, int B, int64_t* edges,
                              cudaStream_t s);
 cudaError_t launch_summary(const DataPtrs& in, int64_t kmin, int64_t N, double T, int D, int B,
@@ -559,13 +559,13 @@ size_t walker_ws_bytes(int mode, bool grad) {
 // Set-up kernel + likelihood kernel for one batch.  If `scratch` is NULL the
 // per-walker workspace is taken from the stream-ordered pool of `s`.
 int run_batch(const EventEntry* e, const double* theta, int64_t W, double* logl, double* grad, int mode,
-              cudaStream_t s, void* scratch) {
+              cudaStream_t s, void* scratch, const MalaArgs* mala) {
   if (!e) return set_error(RB_EINVAL, "NULL event");
   if (W < 0) return set_error(RB_EINVAL, "W < 0");
   if (mode != RB_MIXED && mode != RB_FP64 && mode != RB_MIXED_F64PHASE) return set_error(RB_EINVAL, "bad mode %d", mode);
   if (W == 0) return RB_OK;
-  if (!theta || !logl) return set_error(RB_EINVAL, "NULL theta or logl");
-  const bool want_grad = grad != nullptr;
+  if (!theta || (!logl && !mala)) return set_error(RB_EINVAL, "NULL theta or logl");
+  const bool want_grad = grad != nullptr || mala != nullptr;
   const size_t ws_bytes = (mode == RB_MIXED) ? sizeof(WalkerMixed) * W : sizeof(WalkerF64) * W;
   const size_t tan_bytes = !want_grad ? 0 : (mode == RB_FP64 ? sizeof(WalkerTan<double>) : sizeof(WalkerTan<float>)) * W;
   void* buf = scratch;
@@ -584,9 +584,9 @@ int run_batch(const EventEntry* e, const double* theta, int64_t W, double* logl,
   if (err == cudaSuccess && tb) err = cudaEventRecord(tb, s);
   if (err == cudaSuccess) {
     if (mode == RB_FP64)
-      err = launch_rb_f64(e->dev, ws, tan, W, logl, grad, s, n_sm);
+      err = launch_rb_f64(e->dev, ws, tan, W, logl, grad, s, n_sm, mala);
     else
-      err = launch_rb_mixed(e->dev, ws, tan, W, logl, grad, mode == RB_MIXED_F64PHASE, s, n_sm);
+      err = launch_rb_mixed(e->dev, ws, tan, W, logl, grad, mode == RB_MIXED_F64PHASE, s, n_sm, mala);
   }
   if (err == cudaSuccess && ta) err = cudaEventRecord(ta, s);
   if (err != cudaSuccess) rc = cuda_fail(err, "likelihood kernels");

@@ -60,9 +60,10 @@ int sm_count();
 size_t walker_ws_bytes(int mode, bool grad);
 
 // Set-up + likelihood kernels for one batch; scratch = NULL takes the
-// workspace from the stream-ordered allocator.
+// workspace from the stream-ordered allocator.  With mala, the likelihood
+// kernel finishes each walker with the MALA accept step (logl, grad unused).
 int run_batch(const EventEntry* e, const double* theta, int64_t W, double* logl, double* grad, int mode,
-              cudaStream_t s, void* scratch);
+              cudaStream_t s, void* scratch, const MalaArgs* mala = nullptr);
 
 // Fiducial values, summary data, tables and base of an event from the given
 // device strain/PSD (NULL: the event's resident copy); no allocation, no

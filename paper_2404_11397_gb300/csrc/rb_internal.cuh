@@ -74,6 +74,22 @@ struct DataPtrs {
 
 // Fiducial (theta_ref) values of an event, written by the reference kernel:
 // the FP64 values plus float-pair copies used by the FP32-pipe kernels.
+// MALA local step state for the fused accept in the batch kernels (device
+// pointers, [W] or [W][13]; eps by value).  See rb_mala.cu.
+struct MalaArgs {
+  double* z;            // [W][13] chain state in sampling coordinates (updated on accept)
+  const double* zp;     // [W][13] proposal
+  double* logp;         // [W] log posterior of the state (updated on accept)
+  double* gz;           // [W][13] its gradient in sampling coordinates (updated on accept)
+  const double* xi;     // [W][13] standard normal draws of the proposal
+  const double* lu;     // [W] log of the uniform draws
+  const double* jac;    // [W][2] d iota / d cos iota, d dec / d sin dec at the proposal
+  const int* inside;    // [W] proposal inside the prior box
+  int* accepted;        // [W] output
+  double eps[kNPar];    // step sizes
+  int init;             // 1: adopt the proposal (= the state) unconditionally
+};
+
 // Fiducial values of the mixed path, float pairs (hi, lo) from the
 // float-float set-up (the same instructions as a walker's set-up).
 struct RefDD {

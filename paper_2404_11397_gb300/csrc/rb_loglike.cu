@@ -43,7 +43,48 @@ struct LaunchArgs {
   int64_t W;
   double* logl;
   double* grad;
+  MalaArgs mala;     // MALA kernels only
 };
+
+// MALA accept/reject for walker w after its log L and d log L / d theta
+// (lane j < 13 holds component j): gradient in sampling coordinates,
+//   log alpha = log pi(z') - log pi(z) - 1/2 sum_j [(xi_j + eps_j (g_j + g'_j)/2)^2 - xi_j^2]
+// (Sec. II.D, MALA; the sum over j is a warp reduction), accept when
+// log u < log alpha, and the chain state updated in place.  The whole warp
+// calls it (logl and inside are warp-uniform).
+__device__ __forceinline__ void mala_finish(const MalaArgs& m, int64_t w, int lane, double logl, double gth) {
+  const bool inside = m.inside[w] != 0;
+  const double logpp = inside ? logl : -INFINITY;
+  double gz = 0.0, term = 0.0;
+  if (lane < kNPar) {
+    gz = gth;
+    if (lane == 9) gz = gth * m.jac[2 * w];
+    else if (lane == 12) gz = gth * m.jac[2 * w + 1];
+    if (!inside) gz = 0.0;
+    const double xi = m.xi[w * kNPar + lane];
+    const double t = xi + 0.5 * m.eps[lane] * (m.gz[w * kNPar + lane] + gz);
+    term = t * t - xi * xi;
+  }
+  term = warp_sum_f64(term);
+  if (m.init) {
+    if (lane < kNPar) m.gz[w * kNPar + lane] = gz;
+    if (lane == 0) {
+      m.logp[w] = logpp;
+      m.accepted[w] = inside ? 1 : 0;
+    }
+    return;
+  }
+  const double la = (logpp == -INFINITY) ? -INFINITY : logpp - m.logp[w] - 0.5 * term;
+  const bool acc = m.lu[w] < la;
+  if (acc) {
+    if (lane < kNPar) {
+      m.z[w * kNPar + lane] = m.zp[w * kNPar + lane];
+      m.gz[w * kNPar + lane] = gz;
+    }
+    if (lane == 0) m.logp[w] = logpp;
+  }
+  if (lane == 0) m.accepted[w] = acc ? 1 : 0;
+}
 
 // Chain rule for one walker: lane j < 13 returns d log L / d theta_j from the
 // reduced adjoints (adj_c over the basis coefficients, adj_tau per detector
@@ -75,8 +116,9 @@ __device__ __forceinline__ double chain_rule(int j, int n_det, const T* adj_c, c
 // Mixed precision.  PHASE64 = false: phase as float pairs (FP32 pipe);
 // PHASE64 = true: phase accumulated in native FP64.
 // ---------------------------------------------------------------------------
-template <bool GRAD, bool PHASE64>
+template <bool GRAD, bool PHASE64, bool MALA = false>
 __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
+  static_assert(!MALA || GRAD, "the MALA step needs the gradient");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const EventDev& ev = a.ev;
   const int Ep = ev.e_pad, Bp = ev.b_pad, D = ev.n_det, B = ev.n_bins, E = ev.n_edges;
@@ -159,8 +201,12 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
       }
     }
     if (!valid) {
-      if (lane == 0) a.logl[w] = -INFINITY;
-      if (GRAD && lane < kNPar) a.grad[w * kNPar + lane] = 0.0;
+      if (MALA) {
+        mala_finish(a.mala, w, lane, -INFINITY, 0.0);
+      } else {
+        if (lane == 0) a.logl[w] = -INFINITY;
+        if (GRAD && lane < kNPar) a.grad[w * kNPar + lane] = 0.0;
+      }
       continue;
     }
 
@@ -270,7 +316,8 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
     }
 
     const double tot = warp_sum_f64((double)acc + (double)acc_lo);
-    if (lane == 0) a.logl[w] = *ev.base_logl + tot;
+    const double logl = *ev.base_logl + tot;
+    if (!MALA && lane == 0) a.logl[w] = logl;
     if (GRAD) {
       const float two_pi = 6.28318530717958648f;
 #pragma unroll
@@ -281,10 +328,13 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
         adj_rho[d][0] = warp_sum_f32(adj_rho[d][0]);
         adj_rho[d][1] = warp_sum_f32(adj_rho[d][1]);
       }
+      double g = 0.0;
       if (lane < kNPar) {
         const WalkerTan<float>& tn = reinterpret_cast<const WalkerTan<float>*>(a.tan)[w];
-        a.grad[w * kNPar + lane] = chain_rule<float>(lane, D, adj_c, adj_tau, adj_rho, rho, tn);
+        g = chain_rule<float>(lane, D, adj_c, adj_tau, adj_rho, rho, tn);
       }
+      if (MALA) mala_finish(a.mala, w, lane, logl, g);
+      else if (lane < kNPar) a.grad[w * kNPar + lane] = g;
     }
   }
 }
@@ -293,8 +343,9 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
 // Plain FP64 comparison path: same mapping, everything in FP64, tables read
 // through the cache from global memory.
 // ---------------------------------------------------------------------------
-template <bool GRAD>
+template <bool GRAD, bool MALA = false>
 __global__ void __launch_bounds__(256) k_rb_f64(LaunchArgs a) {
+  static_assert(!MALA || GRAD, "the MALA step needs the gradient");
   const EventDev& ev = a.ev;
   const int Ep = ev.e_pad, Bp = ev.b_pad, D = ev.n_det, B = ev.n_bins, E = ev.n_edges;
   const double* __restrict__ g64 = ev.tab64;
@@ -311,8 +362,12 @@ __global__ void __launch_bounds__(256) k_rb_f64(LaunchArgs a) {
   for (int64_t w = warp0; w < w_end; w += nwarps) {
     const WalkerF64* s = reinterpret_cast<const WalkerF64*>(a.ws) + w;
     if (!s->valid) {
-      if (lane == 0) a.logl[w] = -INFINITY;
-      if (GRAD && lane < kNPar) a.grad[w * kNPar + lane] = 0.0;
+      if (MALA) {
+        mala_finish(a.mala, w, lane, -INFINITY, 0.0);
+      } else {
+        if (lane == 0) a.logl[w] = -INFINITY;
+        if (GRAD && lane < kNPar) a.grad[w * kNPar + lane] = 0.0;
+      }
       continue;
     }
     double dc[kNBasis], tau[kMaxDet], rho[kMaxDet][2], sig[kMaxDet][2];
@@ -393,7 +448,8 @@ __global__ void __launch_bounds__(256) k_rb_f64(LaunchArgs a) {
       }
     }
     const double tot = warp_sum_f64(acc);
-    if (lane == 0) a.logl[w] = *ev.base_logl + tot;
+    const double logl = *ev.base_logl + tot;
+    if (!MALA && lane == 0) a.logl[w] = logl;
     if (GRAD) {
 #pragma unroll
       for (int k = 0; k < kNBasis; ++k) adj_c[k] = kTwoPi * warp_sum_f64(adj_c[k]);
@@ -403,10 +459,13 @@ __global__ void __launch_bounds__(256) k_rb_f64(LaunchArgs a) {
         adj_rho[d][0] = warp_sum_f64(adj_rho[d][0]);
         adj_rho[d][1] = warp_sum_f64(adj_rho[d][1]);
       }
+      double g = 0.0;
       if (lane < kNPar) {
         const WalkerTan<double>& tn = reinterpret_cast<const WalkerTan<double>*>(a.tan)[w];
-        a.grad[w * kNPar + lane] = chain_rule<double>(lane, D, adj_c, adj_tau, adj_rho, rho, tn);
+        g = chain_rule<double>(lane, D, adj_c, adj_tau, adj_rho, rho, tn);
       }
+      if (MALA) mala_finish(a.mala, w, lane, logl, g);
+      else if (lane < kNPar) a.grad[w * kNPar + lane] = g;
     }
   }
 }
@@ -461,39 +520,47 @@ static cudaError_t blocks_per_sm(const void* fn, int threads, size_t smem, int* 
   return cudaSuccess;
 }
 
-template <bool GRAD, bool PHASE64>
+template <bool GRAD, bool PHASE64, bool MALA = false>
 static cudaError_t launch_mixed_t(const LaunchArgs& a, cudaStream_t s, int n_sm) {
   const size_t smem = mixed_smem_bytes(a.ev, PHASE64);
-  const void* fn = reinterpret_cast<const void*>(k_rb_mixed<GRAD, PHASE64>);
+  const void* fn = reinterpret_cast<const void*>(k_rb_mixed<GRAD, PHASE64, MALA>);
   int per_sm = 0;
   cudaError_t err = blocks_per_sm(fn, kThreads, smem, &per_sm);
   if (err != cudaSuccess) return err;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int64_t blocks_needed = (a.W * 32 + kThreads - 1) / kThreads;
   const int64_t grid = std::min<int64_t>(blocks_needed, (int64_t)per_sm * n_sm);
-  k_rb_mixed<GRAD, PHASE64><<<(unsigned)grid, kThreads, smem, s>>>(a);
+  k_rb_mixed<GRAD, PHASE64, MALA><<<(unsigned)grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rb_mixed(const EventDev& ev, const void* ws, const void* tan, int64_t W, double* logl, double* grad,
-                            bool phase64, cudaStream_t s, int n_sm) {
-  LaunchArgs a{ev, ws, tan, W, logl, grad};
+                            bool phase64, cudaStream_t s, int n_sm, const MalaArgs* mala) {
+  LaunchArgs a{ev, ws, tan, W, logl, grad, {}};
+  if (mala) {
+    a.mala = *mala;
+    return phase64 ? launch_mixed_t<true, true, true>(a, s, n_sm) : launch_mixed_t<true, false, true>(a, s, n_sm);
+  }
   if (grad) return phase64 ? launch_mixed_t<true, true>(a, s, n_sm) : launch_mixed_t<true, false>(a, s, n_sm);
   return phase64 ? launch_mixed_t<false, true>(a, s, n_sm) : launch_mixed_t<false, false>(a, s, n_sm);
 }
 
 cudaError_t launch_rb_f64(const EventDev& ev, const void* ws, const void* tan, int64_t W, double* logl, double* grad,
-                          cudaStream_t s, int n_sm) {
-  LaunchArgs a{ev, ws, tan, W, logl, grad};
+                          cudaStream_t s, int n_sm, const MalaArgs* mala) {
+  LaunchArgs a{ev, ws, tan, W, logl, grad, {}};
+  if (mala) a.mala = *mala;
   const int bs = 256;
   int per_sm = 0;
-  const void* fn = grad ? reinterpret_cast<const void*>(k_rb_f64<true>) : reinterpret_cast<const void*>(k_rb_f64<false>);
+  const void* fn = mala ? reinterpret_cast<const void*>(k_rb_f64<true, true>)
+                 : grad ? reinterpret_cast<const void*>(k_rb_f64<true>) : reinterpret_cast<const void*>(k_rb_f64<false>);
   cudaError_t err = blocks_per_sm(fn, bs, 0, &per_sm);
   if (err != cudaSuccess) return err;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int64_t blocks_needed = (W * 32 + bs - 1) / bs;
   const int64_t grid = std::min<int64_t>(blocks_needed, (int64_t)per_sm * n_sm);
-  if (grad)
+  if (mala)
+    k_rb_f64<true, true><<<(unsigned)grid, bs, 0, s>>>(a);
+  else if (grad)
     k_rb_f64<true><<<(unsigned)grid, bs, 0, s>>>(a);
   else
     k_rb_f64<false><<<(unsigned)grid, bs, 0, s>>>(a);

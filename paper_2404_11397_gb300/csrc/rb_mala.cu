@@ -1,0 +1,132 @@
+// rb_mala.cu -- the MALA local step of the sampler (Sec. II.D: flowMC's local
+// sampler is the Metropolis-adjusted Langevin algorithm) for W chains, on the
+// device, fused with the likelihood and its adjoint.
+//
+// Sampling coordinates (Table II): z = (Mc, q, chi1, chi2, Lambda1, Lambda2,
+// d_L, t_c, phi_c, cos iota, psi, ra, sin dec) with the uniform prior of the
+// table on an open box lo < z < hi, so log pi(z) = log L(theta(z)) (+ const)
+// inside and -inf outside.  With step sizes eps_j and draws xi ~ N(0, 1), u ~ U(0, 1):
+//   z'        = z + eps^2/2 grad log pi(z) + eps xi                (k_mala_propose)
+//   log L(theta(z')) and d log L / d theta                         (set-up + batch kernel)
+//   log alpha = log pi(z') - log pi(z) - 1/2 sum_j [(xi_j + eps_j (g_j + g'_j)/2)^2 - xi_j^2]
+//   accept if log u < log alpha, state updated in place            (batch kernel epilogue)
+// The draws are inputs, so the step is reproducible.
+#include <cmath>
+#include <cstdint>
+
+#include "rb.h"
+#include "rb_api_internal.h"
+#include "rb_internal.cuh"
+
+namespace rb {
+
+struct MalaBox {
+  double eps[kNPar], lo[kNPar], hi[kNPar];
+};
+
+// One thread per chain: proposal, box test, likelihood parameters theta(z')
+// (theta(z) of the current state for a proposal outside the box: it is
+// evaluated but rejected), log u and the Jacobian factors of the two angle
+// coordinates at the proposal.
+__global__ void __launch_bounds__(128) k_mala_propose(const double* __restrict__ z, const double* __restrict__ gz,
+                                                     const double* __restrict__ xi, const double* __restrict__ u,
+                                                     MalaBox box, int64_t W, int init, double* __restrict__ zp,
+                                                     double* __restrict__ theta, double* __restrict__ lu,
+                                                     double* __restrict__ jac, int* __restrict__ inside) {
+  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= W) return;
+  double p[kNPar], c[kNPar];
+  bool in = true;
+  for (int j = 0; j < kNPar; ++j) {
+    const int64_t i = w * kNPar + j;
+    c[j] = z[i];
+    p[j] = init ? c[j] : c[j] + 0.5 * box.eps[j] * box.eps[j] * gz[i] + box.eps[j] * xi[i];
+    in = in && p[j] > box.lo[j] && p[j] < box.hi[j];
+    zp[i] = p[j];
+  }
+  const double* src = in ? p : c;
+  for (int j = 0; j < kNPar; ++j) theta[w * kNPar + j] = src[j];
+  theta[w * kNPar + 9] = acos(src[9]);
+  theta[w * kNPar + 12] = asin(src[12]);
+  // d iota / d cos iota = -1 / sin iota, d dec / d sin dec = 1 / cos dec
+  // (1 - z^2 as (1 - z)(1 + z): no cancellation next to the box edges)
+  jac[2 * w] = in ? -1.0 / sqrt((1.0 - p[9]) * (1.0 + p[9])) : 0.0;
+  jac[2 * w + 1] = in ? 1.0 / sqrt((1.0 - p[12]) * (1.0 + p[12])) : 0.0;
+  lu[w] = init ? 0.0 : log(u[w]);
+  inside[w] = in ? 1 : 0;
+}
+
+// Per-chain workspace of a MALA call (bytes per chain, without the batch's).
+static size_t mala_ws_bytes() { return sizeof(double) * (2 * kNPar + 1 + 2) + 2 * sizeof(int); }
+
+static int mala_run(rb_event_t ev, double* z, double* logp, double* gz, int64_t W, const double* eps_host,
+                    const double* lo_host, const double* hi_host, const double* xi, const double* u, int* accepted,
+                    int mode, void* stream, bool init, const char* who) {
+  if (!ev) return set_error(RB_EINVAL, "%s: NULL event", who);
+  if (W < 0) return set_error(RB_EINVAL, "%s: W < 0", who);
+  if (W == 0) return RB_OK;
+  if (!z || !logp || !gz || !lo_host || !hi_host) return set_error(RB_EINVAL, "%s: NULL argument", who);
+  if (!init && (!eps_host || !xi || !u)) return set_error(RB_EINVAL, "%s: NULL eps, xi or u", who);
+  if (mode != RB_MIXED && mode != RB_FP64 && mode != RB_MIXED_F64PHASE) return set_error(RB_EINVAL, "%s: bad mode %d", who, mode);
+  MalaBox box;
+  for (int j = 0; j < kNPar; ++j) {
+    box.eps[j] = init ? 0.0 : eps_host[j];
+    box.lo[j] = lo_host[j];
+    box.hi[j] = hi_host[j];
+    if (!(box.lo[j] < box.hi[j])) return set_error(RB_EINVAL, "%s: empty prior interval for parameter %d", who, j);
+    if (!init && !(box.eps[j] >= 0.0)) return set_error(RB_EINVAL, "%s: step size %d must be >= 0", who, j);
+  }
+  if (box.lo[9] < -1.0 || box.hi[9] > 1.0 || box.lo[12] < -1.0 || box.hi[12] > 1.0)
+    return set_error(RB_EINVAL, "%s: cos iota and sin dec bounds must lie in [-1, 1]", who);
+  const EventEntry* e = event_entry(ev);
+  cudaStream_t s = (cudaStream_t)stream;
+  char* buf = nullptr;
+  const size_t per = mala_ws_bytes();
+  cudaError_t err = cudaMallocAsync(reinterpret_cast<void**>(&buf), per * W, s);
+  if (err != cudaSuccess) return cuda_fail(err, "cudaMallocAsync MALA workspace");
+  double* zp = reinterpret_cast<double*>(buf);
+  double* theta = zp + kNPar * W;
+  double* lu = theta + kNPar * W;
+  double* jac = lu + W;
+  int* inside = reinterpret_cast<int*>(jac + 2 * W);
+  int* acc_scratch = inside + W;
+  k_mala_propose<<<(unsigned)((W + 127) / 128), 128, 0, s>>>(z, gz, xi, u, box, W, init ? 1 : 0, zp, theta, lu, jac,
+                                                               inside);
+  err = cudaGetLastError();
+  int rc = RB_OK;
+  if (err != cudaSuccess) {
+    rc = cuda_fail(err, "MALA proposal kernel");
+  } else {
+    count_launches(1);
+    MalaArgs m{};
+    m.z = z;
+    m.zp = zp;
+    m.logp = logp;
+    m.gz = gz;
+    m.xi = init ? zp : xi;  // unused terms when init (eps = 0)
+    m.lu = lu;
+    m.jac = jac;
+    m.inside = inside;
+    m.accepted = accepted ? accepted : acc_scratch;
+    for (int j = 0; j < kNPar; ++j) m.eps[j] = box.eps[j];
+    m.init = init ? 1 : 0;
+    rc = run_batch(e, theta, W, nullptr, nullptr, mode, s, nullptr, &m);
+  }
+  cudaFreeAsync(buf, s);
+  return rc;
+}
+
+}  // namespace rb
+
+extern "C" int rb_mala_init(rb_event_t ev, const double* z_dev, int64_t W, const double* lo_host,
+                            const double* hi_host, double* logp_dev, double* gz_dev, int mode, void* stream) {
+  return rb::mala_run(ev, const_cast<double*>(z_dev), logp_dev, gz_dev, W, nullptr, lo_host, hi_host, nullptr,
+                      nullptr, nullptr, mode, stream, true, "rb_mala_init");
+}
+
+extern "C" int rb_mala_step(rb_event_t ev, double* z_dev, double* logp_dev, double* gz_dev, int64_t W,
+                            const double* eps_host, const double* lo_host, const double* hi_host, const double* xi_dev,
+                            const double* u_dev, int* accepted_dev, int mode, void* stream) {
+  return rb::mala_run(ev, z_dev, logp_dev, gz_dev, W, eps_host, lo_host, hi_host, xi_dev, u_dev, accepted_dev, mode,
+                      stream, false, "rb_mala_step");
+}
