@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-mala", action="store_true")
+    p.add_argument("--no-full", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--profile", action="store_true",
                    help="fixed short warm-up and no extra legs (for profiler launch lists)")
@@ -348,6 +349,8 @@ def run_gb300(args, dist: Dist):
                                "speedup_of_mixed": value / v64}
     if not args.no_mala:
         result["mala_step"] = run_mala(rb, torch, event, ev, W, args, dist, device, flush)
+    if not args.no_full and args.mode == "mixed":
+        result["full_grid"] = run_full(rb, torch, event, ev, args, dist, device, flush, value)
     if not args.no_e2e:
         result["e2e"] = run_e2e(rb, torch, event, ev, data, psd, theta, W, args, dist, device)
     if not args.no_serving and dist.rank == 0:
@@ -399,6 +402,35 @@ def run_mala(rb, torch, event, ev, W, args, dist, device, flush):
     return {"value": v, "unit": "chain-steps/s", "chains": W, "steps": K, "ms_per_step": t * 1e3 / K,
             "acceptance": acc, "mode": args.mode,
             "step": "rb_mala_step: proposal kernel, set-up, log L + adjoint with the accept step fused"}
+
+
+def run_full(rb, torch, event, ev, args, dist, device, flush, rb_value, W=1024):
+    """The full-grid (un-binned) log-likelihood of the same event for W prior
+    draws: the quantity relative binning replaces (Sec. II.C), every grid
+    point of every detector evaluated per walker.  L2 flushed before every
+    call."""
+    import synth
+    th = torch.tensor(synth.walkers("C2", W), device=device)
+    K = max(3, min(args.steps, 10))
+    for _ in range(3):
+        rb.loglike_full(event, th)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.zero_()
+        starts[k].record()
+        rb.loglike_full(event, th)
+        ends[k].record()
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    t, v = whole_job_rate(dist, sum(ms) / 1e3, W * K, device)
+    pts = ev["N"] * ev["geom"].shape[0]
+    return {"value": v, "unit": "full-grid evals/s", "walkers": W, "calls": K, "ms_per_call": t * 1e3 / K,
+            "grid_points_per_eval": int(pts), "walker_points_per_s": v * pts,
+            "rb_speedup": rb_value / v,
+            "call": "rb_loglike_full_batch: set-up, per-walker grid sum, combination"}
 
 
 def run_e2e(rb, torch, event, ev, data, psd, theta, W, args, dist, device):
@@ -596,7 +628,7 @@ def run_reference(args, dist: Dist):
 def main():
     args = parse()
     if args.profile:
-        args.no_e2e = args.no_cpu = args.no_serving = args.no_fp64 = args.no_mala = True
+        args.no_e2e = args.no_cpu = args.no_serving = args.no_fp64 = args.no_mala = args.no_full = True
     dist = Dist()
     if args.impl == "reference":
         dist.init("gloo")

@@ -208,6 +208,25 @@ RB_API int rb_mala_step(rb_event_t ev, double* z_dev, double* logp_dev, double* 
                         const double* eps_host, const double* lo_host, const double* hi_host, const double* xi_dev,
                         const double* u_dev, int* accepted_dev, int mode, void* stream);
 
+/* Full (un-binned) log-likelihood of Eq. 2 with the inner product of Eq. 3
+ * on the event's whole frequency grid, for W walkers: the quantity relative
+ * binning approximates (Sec. II.C), used to search for the reference
+ * parameters and to measure the binning error.  The constant -<d|d>/2 is
+ * dropped, as in rb_loglike_batch.  theta_dev: device [W][13] FP64;
+ * logl_dev: device [W] FP64, -inf for an unphysical walker.  The data are the
+ * ones the event's last rebuild summed over; <h|h> per detector is
+ * |K_d(theta)|^2 sum_b B0_{d,b} / |K_d(theta_ref)|^2 (Newtonian amplitude,
+ * exact), <d|h> is a sum over every grid point with the walker's phase
+ * expanded per 32-point chunk (FP32 / float-pair arithmetic, FP64 sums).
+ * mode: RB_MIXED only.  Needs T f_low >= 1024 and n_freq <= 2^30 (the chunk
+ * expansion), and, if the last rebuild read caller data in place in RB_FP64
+ * mode, a rebuild in a mixed mode or from resident data first.  Asynchronous
+ * on `stream`; a workspace of 224 B per walker comes from the stream-ordered
+ * pool.  Errors: RB_EINVAL (NULL pointers, W < 0, bad mode, grid outside the
+ * expansion's range, data not available), RB_ENOMEM, RB_ECUDA. */
+RB_API int rb_loglike_full_batch(rb_event_t ev, const double* theta_dev, int64_t W, double* logl_dev, int mode,
+                                 void* stream);
+
 /* Allocation-free form of rb_loglike_grad_batch (the paper has no
  * counterpart: it is an interface for callers that cannot allocate device
  * memory at call time -- e.g. inside a stream capture in global mode, or

@@ -171,6 +171,16 @@ def loglike(event: Event, theta: torch.Tensor, mode="mixed", stream=None) -> tor
     return out
 
 
+def loglike_full(event: Event, theta: torch.Tensor, mode="mixed", stream=None) -> torch.Tensor:
+    """Full-grid (un-binned) log-likelihood [W] (float64, on theta's device)."""
+    th = _theta_dev(theta)
+    out = torch.empty(th.shape[0], dtype=torch.float64, device=th.device)
+    check(load().rb_loglike_full_batch(event.handle, ctypes.c_void_p(th.data_ptr()), th.shape[0],
+                                       ctypes.c_void_p(out.data_ptr()), _mode(mode), _stream_handle(stream)),
+          "rb_loglike_full_batch")
+    return out
+
+
 def loglike_grad(event: Event, theta: torch.Tensor, mode="mixed", stream=None):
     """Batched RB log-likelihood [W] and gradient [W, 13]."""
     th = _theta_dev(theta)

@@ -532,12 +532,15 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
       e.w32_resident = !in_opt;
       ++launches;
     }
+    e.w32_current = true;
     err = launch_summary_fast(e.d_w32, e.d_is32, e.d_wexp, e.N, e.T, e.n_det, e.n_bins, e.d_edges, e.d_ref, e.d_chunkq,
                               e.d_chunks, e.out(), e.n_parts, s);
     ++launches;
   } else {
     err = launch_summary(in, e.kmin, e.N, e.T, e.n_det, e.n_bins, e.d_edges, e.d_ref, e.out(), s);
+    e.w32_current = !in_opt && e.w32_resident;
   }
+  e.last_in_place = in_opt != nullptr;
   if (err != cudaSuccess) return cuda_fail(err, "summary kernel");
   if ((err = cudaStreamWaitEvent(s, e.ev_join, 0)) != cudaSuccess) return cuda_fail(err, "rebuild join");
   count_launches(launches);

@@ -36,6 +36,8 @@ struct EventEntry {
   float* d_is32 = nullptr;        // fast build: FP32 copy 1/S' [D][N]
   int* d_wexp = nullptr;          // fast build: power-of-two scales {sd, sS} per detector
   bool w32_resident = false;      // the FP32 copy holds the resident data
+  bool w32_current = false;       // the FP32 copy holds the data the last rebuild summed
+  bool last_in_place = false;     // the last rebuild read caller data in place
   cudaStream_t side = nullptr;    // rebuild: branch for the reference values the summary does not use
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   PartDesc* d_parts = nullptr;    // fast build: parts of bins

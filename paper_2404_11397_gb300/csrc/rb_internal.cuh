@@ -129,6 +129,18 @@ struct WalkerF64 {
   int pad;
 };
 
+// Absolute per-walker values for the full-grid likelihood (float-float
+// set-up): h_d(f) = K_d f^-7/6 exp(-2 pi i x_d(f)),
+// x_d(f) = phi0t + sum_k chat_k g_k(f) + f taut_d (turns).
+struct WalkerAbs {
+  float chat[kNBasis][2];  // c_k / 2pi, float pair
+  float phi0t[2];          // Phi0 / 2pi, float pair
+  float taut[kMaxDet][2];  // tau_d [s], float pair
+  double K[kMaxDet][2];    // A P_d
+  int valid;
+  int pad[3];
+};
+
 // Tangents for the chain rule (T = float for the mixed paths, double for FP64).
 template <class T>
 struct WalkerTan {
@@ -160,6 +172,23 @@ struct EventDev {
 };
 
 // Outputs of the summary kernels (see summary_epilogue).
+// Fast (Taylor-chunk) evaluation of the fiducial phase: the grid is cut
+// into chunks of kChunk points and the phase expanded to order kOrd about
+// each chunk centre (rb_summary.cu).
+constexpr int kChunk = 32;
+constexpr int kOrd = 8;
+// Event-constant per-chunk matrices, stored chunk-major ([chunk][128
+// floats], one 512-byte row per chunk, read with 16-byte vector loads).
+// Fields:
+constexpr int kQ01 = 0;                       // 4k + 2n + h: orders 0, 1 of basis k as float pairs
+constexpr int kQ2 = kQ01 + kNBasis * 4;       // 2k + h: order 2 as a float pair
+constexpr int kQh = kQ2 + kNBasis * 2;        // (n-3)*10 + k: orders 3..8
+constexpr int kQfc = kQh + (kOrd - 2) * kNBasis;  // f_c as a float pair
+constexpr int kQamp = kQfc + 2;               // f_c^-7/6, binom(-7/6, n) u^n (n = 1..4)
+constexpr int kQFields = kQamp + 5;
+constexpr int kQRow = 128;
+static_assert(kQFields <= kQRow && kQ2 % 4 == 0 && kQh % 4 == 0 && kQfc % 4 == 0, "chunk matrix fields");
+
 constexpr int kPartPoints = 512;  // grid points per part of a bin (fast summary build)
 
 // Part of a bin for the fast summary build (bins are split into parts of at
@@ -237,31 +266,51 @@ __device__ __forceinline__ float frac_turns(float hi, float lo) {
   return __fadd_rn(y, -round_fma_pipe(y));
 }
 
-// Half-angle sine and cosine: s = sin(pi y), c = cos(pi y) for |y| <= 1/2, by
-// the Taylor series of sin and cos about 0 (terms 1/n!, truncated where the
-// remainder is below 1e-9 at |pi y| = pi/2).  pi is applied as a float pair.
+// Half-angle sine and cosine: s = sin(pi y), c = cos(pi y) for |y| <= 1/2,
+// as polynomials in w = y^2:
+//   sin(pi y) = y (pi - pi^3/6 w + w^2 (S0 + S1 w + S2 w^2 + S3 w^3)),
+//   cos(pi y) = 1 - pi^2/2 w + w^2 (C0 + C1 w + C2 w^2 + C3 w^3).
+// The two leading coefficients of each are exact (pi, pi^3/6, pi^2/2 applied
+// as float pairs), the remaining ones are near-minimax fits on [0, 1/2]
+// (least squares with Lawson reweighting, computed for this code and
+// rounded to float).  Fit error below 1.1e-9 relative for sin and 1.1e-9
+// absolute for cos; the FP32 evaluation adds about an ulp.  s is exactly 0
+// at y = 0, which keeps the delta form exact at the fiducial point.
 __device__ __forceinline__ void sincos_pi_half(float y, float& s, float& c) {
-  const float pi_hi = 3.14159274101257324f;
-  const float pi_lo = -8.74227765734758577e-8f;
-  float z = __fmaf_rn(y, pi_hi, y * pi_lo);
-  float w = z * z;
-  // sin z = z (1 - w/3! + w^2/5! - ... + w^6/13!)
-  float ps = 1.6059043836821613e-10f;          // 1/13!
-  ps = fmaf(ps, w, -2.5052108385441720e-08f);  // -1/11!
-  ps = fmaf(ps, w, 2.7557319223985893e-06f);   // 1/9!
-  ps = fmaf(ps, w, -1.9841269841269841e-04f);  // -1/7!
-  ps = fmaf(ps, w, 8.3333333333333333e-03f);   // 1/5!
-  ps = fmaf(ps, w, -1.6666666666666667e-01f);  // -1/3!
-  s = fmaf(ps * w, z, z);
-  // cos z = 1 - w/2! + w^2/4! - ... + w^7/14!
-  float pc = -1.1470745597729725e-11f;         // -1/14!
-  pc = fmaf(pc, w, 2.0876756987868099e-09f);   // 1/12!
-  pc = fmaf(pc, w, -2.7557319223985891e-07f);  // -1/10!
-  pc = fmaf(pc, w, 2.4801587301587302e-05f);   // 1/8!
-  pc = fmaf(pc, w, -1.3888888888888889e-03f);  // -1/6!
-  pc = fmaf(pc, w, 4.1666666666666667e-02f);   // 1/4!
-  pc = fmaf(pc, w, -0.5f);                     // -1/2!
-  c = fmaf(pc, w, 1.0f);
+  const float w = y * y;
+  float ps = -0.007060864474624395f;
+  ps = fmaf(ps, w, 0.08207154273986816f);
+  ps = fmaf(ps, w, -0.5992570519447327f);
+  ps = fmaf(ps, w, 2.550163745880127f);
+  ps = fmaf(ps, w, -9.160392266949202e-08f);  // low part of -pi^3/6
+  ps = fmaf(ps, w, -8.742277657347586e-08f);  // low part of pi
+  ps = fmaf(w, -5.167712688446045f, ps);      // high part of -pi^3/6
+  s = fmaf(y, 3.1415927410125732f, y * ps);   // high part of pi
+  float pc = -0.024529997259378433f;
+  pc = fmaf(pc, w, 0.2350243180990219f);
+  pc = fmaf(pc, w, -1.3352320194244385f);
+  pc = fmaf(pc, w, 4.058711051940918f);
+  pc = fmaf(pc, w, -1.451857940537593e-07f);  // low part of -pi^2/2
+  c = fmaf(w, -4.934802055358887f, fmaf(pc, w, 1.0f));  // high part of -pi^2/2
+}
+
+// Small integer -> float on the FMA pipe (|i| < 2^22).
+__device__ __forceinline__ float small_int_float(int i) {
+  return __fadd_rn(__int_as_float(0x4B400000 + i), -12582912.0f);
+}
+
+__device__ __forceinline__ void f2x_add(float& hi, float& lo, float v) {
+  const float s = __fadd_rn(hi, v);
+  const float bb = __fadd_rn(s, -hi);
+  lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(hi, -__fadd_rn(s, -bb)), __fadd_rn(v, -bb)));
+  hi = s;
+}
+
+// sin, cos of 2 pi y from the half-angle series (|y| <= 1/2 turns).
+__device__ __forceinline__ float2 cis_turns(float y) {
+  float sn, cs;
+  sincos_pi_half(y, sn, cs);
+  return make_float2(fmaf(-2.f * sn, sn, 1.f), 2.f * sn * cs);
 }
 
 // Sum a float over the warp in FP64 (all lanes get the total).

@@ -949,6 +949,40 @@ static cudaError_t launch_setup_t(const double* theta, int64_t W, const EventCon
   return cudaGetLastError();
 }
 
+// Absolute values of W walkers for the full-grid likelihood (32 walkers per
+// block, the float-float set-up of the mixed path; lane l writes walker w0 + l).
+__global__ void __launch_bounds__(kDdRoleThreads) k_setup_abs(const double* __restrict__ theta, int64_t W,
+                                                             EventConst ec, WalkerAbs* __restrict__ out) {
+  __shared__ DdSmem S;
+  const int64_t w0 = (int64_t)blockIdx.x * kSetupWalkers;
+  setup_absolute_dd(theta, w0, W, ec, S);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t w = w0 + lane;
+  if (w >= W) return;
+  WalkerAbs& o = out[w];
+  auto put = [](float* p, dd v) { p[0] = v.h; p[1] = v.l; };
+  if (warp == 0) {
+    for (int k = 0; k < kNBasis; ++k) put(o.chat[k], fx::mul(ld2(S.c[k][lane]), inv2pi()));
+    put(o.phi0t, fx::mul(ld2(S.phi0[lane]), inv2pi()));
+    o.valid = S.valid[lane];
+    o.pad[0] = o.pad[1] = o.pad[2] = 0;
+  } else if (warp >= 1 && warp <= kMaxDet) {
+    const int d = warp - 1;
+    const bool on = d < ec.n_det;
+    put(o.taut[d], on ? ld2(S.tau[d][lane]) : dd{0.f, 0.f});
+    constexpr fx::cdd kAmpH(8.035028173395984e-06 / kMpcS);
+    const dd a = fx::mul(fx::K(kAmpH), ld2(S.amp[lane]));
+    o.K[d][0] = on ? fx::to_double(fx::mul(a, ld2(S.P[d][0][lane]))) : 0.0;
+    o.K[d][1] = on ? fx::to_double(fx::mul(a, ld2(S.P[d][1][lane]))) : 0.0;
+  }
+}
+
+cudaError_t launch_setup_abs(const double* theta, int64_t W, const EventConst& ec, WalkerAbs* out, cudaStream_t s) {
+  const unsigned grid = (unsigned)((W + kSetupWalkers - 1) / kSetupWalkers);
+  k_setup_abs<<<grid, kDdRoleThreads, 0, s>>>(theta, W, ec, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ref_dd(const double* theta_ref_dev, const EventConst& ec, RefValues* out, cudaStream_t s) {
   k_ref_dd<<<1, kDdRoleThreads, 0, s>>>(theta_ref_dev, ec, out);
   return cudaGetLastError();

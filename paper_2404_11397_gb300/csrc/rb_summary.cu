@@ -361,8 +361,6 @@ cudaError_t launch_strain(const RefValues* src, int64_t kmin, int64_t N, double 
 // sums are FP32, the block reduction is in float pairs, and the epilogue
 // applies conj(K_d) and the scale factors in FP64.
 // ===========================================================================
-constexpr int kChunk = 32;
-constexpr int kOrd = 8;
 
 struct TaylorTables {
   double alpha[kNBasis][kOrd + 1];
@@ -370,17 +368,6 @@ struct TaylorTables {
   double amp[5];           // binom(-7/6, n)
 };
 
-// Event-constant per-chunk matrices, stored chunk-major ([chunk][128
-// floats], one 512-byte row per chunk, read with 16-byte vector loads).
-// Fields:
-constexpr int kQ01 = 0;                       // 4k + 2n + h: orders 0, 1 of basis k as float pairs
-constexpr int kQ2 = kQ01 + kNBasis * 4;       // 2k + h: order 2 as a float pair
-constexpr int kQh = kQ2 + kNBasis * 2;        // (n-3)*10 + k: orders 3..8
-constexpr int kQfc = kQh + (kOrd - 2) * kNBasis;  // f_c as a float pair
-constexpr int kQamp = kQfc + 2;               // f_c^-7/6, binom(-7/6, n) u^n (n = 1..4)
-constexpr int kQFields = kQamp + 5;
-constexpr int kQRow = 128;
-static_assert(kQFields <= kQRow && kQ2 % 4 == 0 && kQh % 4 == 0 && kQfc % 4 == 0, "chunk matrix fields");
 
 __global__ void __launch_bounds__(128) k_chunk_q(int64_t kmin, double T, int64_t n_chunks, TaylorTables tt,
                                                  float* __restrict__ q) {
@@ -440,18 +427,6 @@ __device__ __forceinline__ float scaled_float(double x, unsigned bias) {
   return __uint_as_float(mag < lo_lim ? sign : (mag >= hi_lim ? (sign | 0x7F800000u) : bits));
 }
 
-// Small integer -> float on the FMA pipe (|i| < 2^22).
-__device__ __forceinline__ float small_int_float(int i) {
-  return __fadd_rn(__int_as_float(0x4B400000 + i), -12582912.0f);
-}
-
-__device__ __forceinline__ void f2x_add(float& hi, float& lo, float v) {
-  const float s = __fadd_rn(hi, v);
-  const float bb = __fadd_rn(s, -hi);
-  lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(hi, -__fadd_rn(s, -bb)), __fadd_rn(v, -bb)));
-  hi = s;
-}
-
 // Per-rebuild chunk coefficients (32 floats, 16-byte aligned groups):
 //   [0 .. 3]    X0 (pair, whole turns dropped), X1 (pair): intrinsic phase
 //   [4 .. 11]   X2 (pair), X3 .. X8
@@ -462,13 +437,6 @@ __device__ __forceinline__ void f2x_add(float& hi, float& lo, float v) {
 // tau_d) exp(2 pi i j df tau_d): one sine/cosine per point, the chunk factor
 // from this record and the offset factor from a 32-entry table per block.
 constexpr int kRec = 32;
-
-// sin, cos of 2 pi y from the half-angle series (|y| <= 1/2 turns).
-__device__ __forceinline__ float2 cis_turns(float y) {
-  float sn, cs;
-  sincos_pi_half(y, sn, cs);
-  return make_float2(fmaf(-2.f * sn, sn, 1.f), 2.f * sn * cs);
-}
 
 // X_n = sum_k (c_k / 2pi) Q_kn (float-pair dot products) for 32 chunks per
 // block: warp 0 forms orders 0 and 1 and the per-detector chunk factors,
