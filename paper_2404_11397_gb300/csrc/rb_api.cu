@@ -261,7 +261,7 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
   }
   const int E = B + 1;
   const int Ep = round_up(E, 4), Bp = round_up(B, 4);
-  const size_t edge32 = (size_t)(2 * kNBasis + 2) * Ep;
+  const size_t edge32 = (size_t)4 * kEdgeQuads * Ep;
   const size_t tab32 = edge32 + (size_t)D * 6 * Bp;
   const size_t tab64 = (size_t)(kNBasis + 1) * Ep + (size_t)D * 6 * Bp;
   {

@@ -26,6 +26,8 @@ namespace rb {
 constexpr int kNPar = 13;
 constexpr int kMaxDet = 3;
 constexpr int kNBasis = 10;
+constexpr int kEdgeQuads = kNBasis / 2 + 1;  // float4 groups per edge in the float tables
+static_assert(kNBasis % 2 == 0, "basis pairs per float4 of the edge tables");
 constexpr int kNTanIntr = 6;  // Mc, q, chi1, chi2, Lambda1, Lambda2
 
 constexpr double kPi = 3.141592653589793238462643383279502884;
@@ -157,15 +159,17 @@ struct EventDev {
   int64_t kmin, n_freq;
   double T;
   const double* base_logl;  // device: sum_d (Re sum_b A0 - sum_b B0 / 2) = log L(theta_ref)
-  // float image copied to shared memory by the mixed kernels:
-  //   [0 .. 10*Ep)       g_hi[k][e]  (g_k(f_e)/2pi, high part)
-  //   [10*Ep .. 20*Ep)   g_lo[k][e]
-  //   [20*Ep .. 21*Ep)   f_hi[e], [21*Ep .. 22*Ep) f_lo[e]
-  //   then per detector 6 rows of Bp: a0r, a0i, a1r, a1i, b0, b1
+  // float image copied to shared memory by the mixed kernels, laid out for
+  // 16-byte loads (lane l reads edge / bin c0 + l: consecutive 16 B, no bank
+  // conflicts):
+  //   edge part, float4 [kEdgeQuads][Ep]: quad q < 5 holds
+  //     {g_hi[2q], g_lo[2q], g_hi[2q+1], g_lo[2q+1]}  (g_k(f_e)/2pi as float pairs),
+  //     quad 5 holds {f_hi, f_lo, 0, 0};
+  //   bin part, float4 [D][Bp] {a0r, a0i, a1r, a1i}, then float2 [D][Bp] {b0, b1}
   //   (alpha0 = A0/2, alpha1 = A1/df_b, beta0 = B0/2, beta1 = B1/df_b)
   const float* tab32;
   size_t tab32_floats;   // multiple of 4
-  size_t edge32_floats;  // length of the edge part (22*Ep)
+  size_t edge32_floats;  // length of the edge part (4*kEdgeQuads*Ep)
   // FP64 tables: g[k][e] (10*Ep), f[e] (Ep), then per detector 6 rows of Bp
   const double* tab64;
   const RefValues* ref;

@@ -125,10 +125,7 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
 
   // Stage the tables (16-byte vector copies).
   const float* sbin;
-  const float* ghi = nullptr;
-  const float* glo = nullptr;
-  const float* fhi = nullptr;
-  const float* flo = nullptr;
+  const float4* g4 = nullptr;  // [kEdgeQuads][Ep] basis pairs and f_e (float pairs)
   const double* g64 = nullptr;
   const double* f64 = nullptr;
   {
@@ -139,10 +136,7 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
       const size_t n4 = ev.tab32_floats / 4;
       for (size_t i = tid; i < n4; i += blockDim.x) dst[i] = src[i];
       const float* s = reinterpret_cast<const float*>(smem_raw);
-      ghi = s;
-      glo = s + (size_t)kNBasis * Ep;
-      fhi = s + (size_t)2 * kNBasis * Ep;
-      flo = fhi + Ep;
+      g4 = reinterpret_cast<const float4*>(s);
       sbin = s + ev.edge32_floats;
     } else {
       const size_t n_e64 = (size_t)(kNBasis + 1) * Ep;  // g[10][Ep], f[Ep]
@@ -161,6 +155,8 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
   __syncthreads();
 
   const int lane = threadIdx.x & 31;
+  const float4* binA = reinterpret_cast<const float4*>(sbin);             // [D][Bp] a0r a0i a1r a1i
+  const float2* binB = reinterpret_cast<const float2*>(sbin + 4 * D * Bp);  // [D][Bp] b0 b1
   // each block takes a contiguous, equal share of the walkers (so every SM
   // gets W / grid of them, +-1), its warps take them in turn
   const int64_t per_blk = a.W / gridDim.x, rem_blk = a.W % gridDim.x;
@@ -231,15 +227,22 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
       // detector-independent phase sum_k dc_k g_k(f_e) / 2pi  [turns]
       float xh = 0.f, xl = 0.f;
       double x64 = 0.0;
+      float fe, fe_lo = 0.f;
       if (!PHASE64) {
 #pragma unroll
-        for (int k = 0; k < kNBasis; ++k) f2x_fma_acc(dch[k], dcl[k], ghi[k * Ep + ee], glo[k * Ep + ee], xh, xl);
+        for (int q = 0; q < kNBasis / 2; ++q) {
+          const float4 g = g4[q * Ep + ee];
+          f2x_fma_acc(dch[2 * q], dcl[2 * q], g.x, g.y, xh, xl);
+          f2x_fma_acc(dch[2 * q + 1], dcl[2 * q + 1], g.z, g.w, xh, xl);
+        }
+        const float2 f2 = *reinterpret_cast<const float2*>(g4 + (kEdgeQuads - 1) * Ep + ee);
+        fe = f2.x;
+        fe_lo = f2.y;
       } else {
 #pragma unroll
         for (int k = 0; k < kNBasis; ++k) x64 = fma(dc64[k], g64[k * Ep + ee], x64);
+        fe = (float)f64[ee];
       }
-      float fe;
-      if (!PHASE64) fe = fhi[ee]; else fe = (float)f64[ee];
       float adj_x = 0.f;
 
 #pragma unroll
@@ -248,7 +251,7 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
           float y;
           if (!PHASE64) {
             float yh = xh, yl = xl;
-            f2x_fma_acc(tauh[d], taul[d], fe, flo[ee], yh, yl);
+            f2x_fma_acc(tauh[d], taul[d], fe, fe_lo, yh, yl);
             y = frac_turns(yh, yl);
           } else {
             const double xd = fma(f64[ee], tau64[d], x64);
@@ -263,9 +266,9 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
           const float ni = __shfl_down_sync(kFull, di, 1);
           float Ur = 0.f, Ui = 0.f, Vr = 0.f, Vi = 0.f;
           if (has_bin) {
-            const float* bt = sbin + (size_t)d * 6 * Bp;
-            const float a0r = bt[e], a0i = bt[Bp + e], a1r = bt[2 * Bp + e], a1i = bt[3 * Bp + e];
-            const float b0 = bt[4 * Bp + e], b1 = bt[5 * Bp + e];
+            const float4 ta = binA[d * Bp + e];
+            const float2 tb = binB[d * Bp + e];
+            const float a0r = ta.x, a0i = ta.y, a1r = ta.z, a1i = ta.w, b0 = tb.x, b1 = tb.y;
             const float sr = dr + nr, si = di + ni, tr = nr - dr, ti = ni - di;
             float v = a0r * sr;
             v = fmaf(a0i, si, v);
@@ -307,7 +310,11 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
       if (GRAD && has_edge) {
         if (!PHASE64) {
 #pragma unroll
-          for (int k = 0; k < kNBasis; ++k) adj_c[k] = fmaf(adj_x, ghi[k * Ep + ee], adj_c[k]);
+          for (int q = 0; q < kNBasis / 2; ++q) {
+            const float4 g = g4[q * Ep + ee];
+            adj_c[2 * q] = fmaf(adj_x, g.x, adj_c[2 * q]);
+            adj_c[2 * q + 1] = fmaf(adj_x, g.z, adj_c[2 * q + 1]);
+          }
         } else {
 #pragma unroll
           for (int k = 0; k < kNBasis; ++k) adj_c[k] = fmaf(adj_x, (float)g64[k * Ep + ee], adj_c[k]);

@@ -145,7 +145,9 @@ __device__ void summary_epilogue(const SummaryOut& so, int b, int d0, int nd, in
       so.summ[((size_t)d * B + b) * 6 + f] = o;
       const double t = (f == 2 || f == 3 || f == 5) ? o * inv_df_b : 0.5 * o;
       so.bin64[((size_t)d * 6 + f) * so.Bp + b] = t;
-      so.bin32[((size_t)d * 6 + f) * so.Bp + b] = (float)t;
+      // float image: {a0r, a0i, a1r, a1i} quads, then {b0, b1} pairs
+      const size_t db = (size_t)d * so.Bp + b;
+      so.bin32[f < 4 ? db * 4 + f : (size_t)4 * D * so.Bp + db * 2 + (f - 4)] = (float)t;
     }
     const double b0 = __shfl_sync(0xffffffffu, o, (6 * g + 4) & 31);
     const double sh = (mine && f == 0) ? o - 0.5 * b0 : 0.0;
@@ -272,16 +274,16 @@ __global__ void k_edge_tables(int64_t kmin, double T, int D, int B, int Ep, int 
     } else {
       for (int k = 0; k < kNBasis; ++k) g[k] = 0.0;
     }
-    for (int k = 0; k < kNBasis; ++k) {
-      tab64[(size_t)k * Ep + e] = g[k];
-      const f2x p = f2x_from(g[k]);
-      tab32[(size_t)k * Ep + e] = p.hi;
-      tab32[(size_t)(kNBasis + k) * Ep + e] = p.lo;
+    float4* t4 = reinterpret_cast<float4*>(tab32);  // [kEdgeQuads][Ep]
+    for (int q = 0; q < kNBasis / 2; ++q) {
+      tab64[(size_t)(2 * q) * Ep + e] = g[2 * q];
+      tab64[(size_t)(2 * q + 1) * Ep + e] = g[2 * q + 1];
+      const f2x p0 = f2x_from(g[2 * q]), p1 = f2x_from(g[2 * q + 1]);
+      t4[(size_t)q * Ep + e] = make_float4(p0.hi, p0.lo, p1.hi, p1.lo);
     }
     tab64[(size_t)kNBasis * Ep + e] = f;
     const f2x fp = f2x_from(f);
-    tab32[(size_t)2 * kNBasis * Ep + e] = fp.hi;
-    tab32[(size_t)(2 * kNBasis + 1) * Ep + e] = fp.lo;
+    t4[(size_t)(kEdgeQuads - 1) * Ep + e] = make_float4(fp.hi, fp.lo, 0.f, 0.f);
   }
   for (int b = tid; b < B; b += nth) inv_df[b] = T / (double)(edges[b + 1] - edges[b]);
   // bin tables: zero the padding once (the summary kernels write b < B)
