@@ -161,12 +161,18 @@ struct EventDev {
   const double* base_logl;  // device: sum_d (Re sum_b A0 - sum_b B0 / 2) = log L(theta_ref)
   // float image copied to shared memory by the mixed kernels, laid out for
   // 16-byte loads (lane l reads edge / bin c0 + l: consecutive 16 B, no bank
-  // conflicts):
+  // conflicts) whose halves are ready operands of the paired FP32
+  // instructions:
   //   edge part, float4 [kEdgeQuads][Ep]: quad q < 5 holds
-  //     {g_hi[2q], g_lo[2q], g_hi[2q+1], g_lo[2q+1]}  (g_k(f_e)/2pi as float pairs),
+  //     {g_hi[2q], g_hi[2q+1], g_lo[2q], g_lo[2q+1]}  (g_k(f_e)/2pi as float pairs),
   //     quad 5 holds {f_hi, f_lo, 0, 0};
-  //   bin part, float4 [D][Bp] {a0r, a0i, a1r, a1i}, then float2 [D][Bp] {b0, b1}
-  //   (alpha0 = A0/2, alpha1 = A1/df_b, beta0 = B0/2, beta1 = B1/df_b)
+  //   bin part, with alpha0 = A0/2, alpha1 = A1/df_b, beta0 = B0/2,
+  //   beta1 = B1/df_b, the betas stored negated:
+  //     if D >= 2, detectors 0 and 1 side by side, float4 [3][Bp]:
+  //       {a0r_0, a0r_1, a0i_0, a0i_1}, {a1r_0, a1r_1, a1i_0, a1i_1},
+  //       {-b0_0, -b0_1, -b1_0, -b1_1};
+  //     if D is odd, detector D - 1 after that: float4 [Bp] {a0r, a0i, a1r, a1i},
+  //       then float2 [Bp] {-b0, -b1}
   const float* tab32;
   size_t tab32_floats;   // multiple of 4
   size_t edge32_floats;  // length of the edge part (4*kEdgeQuads*Ep)

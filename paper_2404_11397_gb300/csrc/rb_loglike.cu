@@ -113,15 +113,167 @@ __device__ __forceinline__ double chain_rule(int j, int n_det, const T* adj_c, c
 }
 
 // ---------------------------------------------------------------------------
-// Mixed precision.  PHASE64 = false: phase as float pairs (FP32 pipe);
-// PHASE64 = true: phase accumulated in native FP64.
+// Paired FP32 arithmetic.  V = float evaluates one detector; V = float2
+// evaluates detectors 0 and 1 side by side with the sm_100+ paired
+// instructions (FFMA2 / FADD2 / FMUL2: one issue slot for two lanes of work,
+// each component rounded exactly as the scalar instruction).  The hot loop is
+// bound by instruction issue, so pairing cuts its time where the FMA pipe
+// has room.
 // ---------------------------------------------------------------------------
-template <bool GRAD, bool PHASE64, bool MALA = false>
+namespace pv {
+__device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float neg(float a) { return -a; }
+__device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub(float2 a, float2 b) {
+  float2 r;
+  asm("{.reg .b64 x, y, z;\n\tmov.b64 x, {%2, %3};\n\tmov.b64 y, {%4, %5};\n\tsub.rn.f32x2 z, x, y;\n\tmov.b64 {%0, %1}, z;}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }  // folded into the consumer
+template <class V> __device__ __forceinline__ V splat(float x);
+template <> __device__ __forceinline__ float splat<float>(float x) { return x; }
+template <> __device__ __forceinline__ float2 splat<float2>(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float shfl_down(float v) { return __shfl_down_sync(kFull, v, 1); }
+__device__ __forceinline__ float2 shfl_down(float2 v) {
+  return make_float2(__shfl_down_sync(kFull, v.x, 1), __shfl_down_sync(kFull, v.y, 1));
+}
+__device__ __forceinline__ float shfl_up(float v) { return __shfl_up_sync(kFull, v, 1); }
+__device__ __forceinline__ float2 shfl_up(float2 v) {
+  return make_float2(__shfl_up_sync(kFull, v.x, 1), __shfl_up_sync(kFull, v.y, 1));
+}
+
+// s_hi + s_lo += (a_hi + a_lo)(b_hi + b_lo): Dekker product, Knuth sum
+// (the same steps as f2x_fma_acc).
+template <class V>
+__device__ __forceinline__ void fma_acc(V a_hi, V a_lo, V b_hi, V b_lo, V& s_hi, V& s_lo) {
+  const V p = mul(a_hi, b_hi);
+  V e = fma(a_hi, b_hi, neg(p));
+  e = fma(a_hi, b_lo, e);
+  e = fma(a_lo, b_hi, e);
+  const V s = add(s_hi, p);
+  const V bb = sub(s, s_hi);
+  const V err = add(sub(s_hi, sub(s, bb)), sub(p, bb));
+  s_hi = s;
+  s_lo = add(s_lo, add(err, e));
+}
+
+// Fractional part of hi + lo in turns (as frac_turns).
+template <class V>
+__device__ __forceinline__ V frac(V hi, V lo) {
+  const V m = splat<V>(12582912.0f);  // 1.5 * 2^23: round to nearest on the FMA pipe
+  const V r = sub(hi, sub(add(hi, m), m));
+  const V y = add(r, lo);
+  return sub(y, sub(add(y, m), m));
+}
+
+// sin(pi y), cos(pi y) for |y| <= 1/2 (the polynomials of sincos_pi_half).
+template <class V>
+__device__ __forceinline__ void sincos_half(V y, V& s, V& c) {
+  const V w = mul(y, y);
+  V ps = splat<V>(-0.007060864474624395f);
+  ps = fma(ps, w, splat<V>(0.08207154273986816f));
+  ps = fma(ps, w, splat<V>(-0.5992570519447327f));
+  ps = fma(ps, w, splat<V>(2.550163745880127f));
+  ps = fma(ps, w, splat<V>(-9.160392266949202e-08f));  // low part of -pi^3/6
+  ps = fma(ps, w, splat<V>(-8.742277657347586e-08f));  // low part of pi
+  ps = fma(w, splat<V>(-5.167712688446045f), ps);      // high part of -pi^3/6
+  s = fma(y, splat<V>(3.1415927410125732f), mul(y, ps));  // high part of pi
+  V pc = splat<V>(-0.024529997259378433f);
+  pc = fma(pc, w, splat<V>(0.2350243180990219f));
+  pc = fma(pc, w, splat<V>(-1.3352320194244385f));
+  pc = fma(pc, w, splat<V>(4.058711051940918f));
+  pc = fma(pc, w, splat<V>(-1.451857940537593e-07f));  // low part of -pi^2/2
+  c = fma(w, splat<V>(-4.934802055358887f), fma(pc, w, splat<V>(1.0f)));  // high part of -pi^2/2
+}
+
+// Per-walker detector constants and adjoint accumulators of one detector
+// (V = float) or of the detector pair 0, 1 (V = float2).
+template <class V>
+struct DetState {
+  V tau_h, tau_l;          // delta tau [s] as a float pair
+  V rho_r, rho_i, sig_r, sig_i;
+  V acc, acc_lo;           // log L terms, float-pair accumulator
+  V adj_tau, adj_rr, adj_ri;
+};
+
+// One bin edge (and the bin on its right) for one detector or a detector
+// pair: half-angle sin/cos, delta = rho (e^{-2 pi i y} - 1) + sigma, the
+// neighbour edge by a shuffle, the bin's contraction with the tables (bins
+// of lanes 0..30) and, with GRAD, the edge cotangent.  Returns d log L / dy
+// per detector (times 1/2pi) for the basis adjoint.  The whole warp calls it.
+template <bool GRAD, class V>
+__device__ __forceinline__ V det_edge(V y, DetState<V>& st, const V* bt, bool has_bin, bool has_edge, int lane, V fe) {
+  V sn, cs;
+  sincos_half(y, sn, cs);
+  const V t2 = mul(splat<V>(-2.f), sn);
+  const V em_r = mul(t2, sn), em_i = mul(t2, cs);  // e^{-2 pi i y} - 1
+  const V dr = fma(st.rho_r, em_r, fma(neg(st.rho_i), em_i, st.sig_r));
+  const V di = fma(st.rho_r, em_i, fma(st.rho_i, em_r, st.sig_i));
+  const V nr = shfl_down(dr), ni = shfl_down(di);
+  V Ur = splat<V>(0.f), Ui = Ur, Vr = Ur, Vi = Ur;
+  if (has_bin) {
+    // bt: alpha0 (re, im), alpha1 (re, im), -beta0, -beta1
+    const V sr = add(dr, nr), si = add(di, ni), tr = sub(nr, dr), ti = sub(ni, di);
+    V v = mul(bt[0], sr);
+    v = fma(bt[1], si, v);
+    v = fma(bt[2], tr, v);
+    v = fma(bt[3], ti, v);
+    v = fma(bt[4], fma(splat<V>(0.25f), fma(sr, sr, mul(si, si)), sr), v);
+    v = fma(bt[5], fma(splat<V>(0.5f), fma(sr, tr, mul(si, ti)), tr), v);
+    const V s = add(st.acc, v);  // two-sum into (acc, acc_lo)
+    const V bb = sub(s, st.acc);
+    st.acc_lo = add(st.acc_lo, add(sub(st.acc, sub(s, bb)), sub(v, bb)));
+    st.acc = s;
+    if (GRAD) {
+      const V hs_r = fma(splat<V>(0.5f), sr, splat<V>(1.f)), hs_i = mul(splat<V>(0.5f), si);  // 1 + s/2
+      const V hb1 = mul(splat<V>(0.5f), bt[5]);
+      Ur = fma(bt[4], hs_r, fma(hb1, tr, bt[0]));
+      Ui = fma(bt[4], hs_i, fma(hb1, ti, bt[1]));
+      Vr = fma(bt[5], hs_r, bt[2]);
+      Vi = fma(bt[5], hs_i, bt[3]);
+    }
+  }
+  V dldx = splat<V>(0.f);
+  if (GRAD) {
+    V gr = sub(Ur, Vr), gi = sub(Ui, Vi);  // own bin (edge on its left)
+    const V lr = shfl_up(add(Ur, Vr)), li = shfl_up(add(Ui, Vi));
+    if (lane > 0) {
+      gr = add(gr, lr);
+      gi = add(gi, li);
+    }
+    if (has_edge) {
+      const V rr = add(splat<V>(1.f), dr);
+      dldx = fma(gr, di, mul(neg(gi), rr));  // Im(conj(gbar) r); times 2 pi later
+      st.adj_tau = fma(dldx, fe, st.adj_tau);
+      const V Er = add(splat<V>(1.f), em_r);  // gbar_rho += gbar conj(E)
+      st.adj_rr = fma(gr, Er, fma(gi, em_i, st.adj_rr));
+      st.adj_ri = fma(gi, Er, fma(neg(gr), em_i, st.adj_ri));
+    }
+  }
+  return dldx;
+}
+}  // namespace pv
+
+// ---------------------------------------------------------------------------
+// Mixed precision.  PHASE64 = false: phase as float pairs (FP32 pipe);
+// PHASE64 = true: phase accumulated in native FP64.  ND = number of
+// detectors, a compile-time constant so that the independent chains of the
+// detector pair and the single detector interleave in one instruction stream.
+// ---------------------------------------------------------------------------
+template <int ND, bool GRAD, bool PHASE64, bool MALA = false>
 __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
   static_assert(!MALA || GRAD, "the MALA step needs the gradient");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const EventDev& ev = a.ev;
-  const int Ep = ev.e_pad, Bp = ev.b_pad, D = ev.n_det, B = ev.n_bins, E = ev.n_edges;
+  constexpr int D = ND;
+  const int Ep = ev.e_pad, Bp = ev.b_pad, B = ev.n_bins, E = ev.n_edges;
 
   // Stage the tables (16-byte vector copies).
   const float* sbin;
@@ -155,8 +307,13 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
   __syncthreads();
 
   const int lane = threadIdx.x & 31;
-  const float4* binA = reinterpret_cast<const float4*>(sbin);             // [D][Bp] a0r a0i a1r a1i
-  const float2* binB = reinterpret_cast<const float2*>(sbin + 4 * D * Bp);  // [D][Bp] b0 b1
+  // detectors 0 and 1 form a pair when D >= 2; an odd detector count leaves
+  // detector D - 1 single (bin table layout in EventDev)
+  constexpr bool paired = D >= 2;
+  constexpr int ds = (D & 1) ? D - 1 : -1;
+  const float4* binP = reinterpret_cast<const float4*>(sbin);                                // [3][Bp]
+  const float4* binS4 = reinterpret_cast<const float4*>(sbin + (paired ? 12 * Bp : 0));      // [Bp]
+  const float2* binS2 = reinterpret_cast<const float2*>(sbin + (paired ? 12 * Bp : 0) + 4 * Bp);  // [Bp]
   // each block takes a contiguous, equal share of the walkers (so every SM
   // gets W / grid of them, +-1), its warps take them in turn
   const int64_t per_blk = a.W / gridDim.x, rem_blk = a.W % gridDim.x;
@@ -167,34 +324,49 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
 
   for (int64_t w = warp0; w < w_end; w += nwarps) {
     // ---- per-walker constants (uniform across the warp) ----
-    float dch[kNBasis], dcl[kNBasis];
+    float2 dch[kNBasis / 2], dcl[kNBasis / 2];  // basis coefficients 2q, 2q+1
     double dc64[kNBasis];
-    float tauh[kMaxDet], taul[kMaxDet];
     double tau64[kMaxDet];
-    float rho[kMaxDet][2], sig[kMaxDet][2];
+    float rho[kMaxDet][2];
+    pv::DetState<float2> P;  // detectors 0, 1
+    pv::DetState<float> S;   // detector ds
     int valid;
-    if (!PHASE64) {
-      const WalkerMixed* s = reinterpret_cast<const WalkerMixed*>(a.ws) + w;
-      valid = s->valid;
+    {
+      float th[kMaxDet], tl[kMaxDet], sg[kMaxDet][2];
+      if (!PHASE64) {
+        const WalkerMixed* s = reinterpret_cast<const WalkerMixed*>(a.ws) + w;
+        valid = s->valid;
 #pragma unroll
-      for (int k = 0; k < kNBasis; ++k) { dch[k] = s->dc_hi[k]; dcl[k] = s->dc_lo[k]; }
+        for (int q = 0; q < kNBasis / 2; ++q) {
+          dch[q] = make_float2(s->dc_hi[2 * q], s->dc_hi[2 * q + 1]);
+          dcl[q] = make_float2(s->dc_lo[2 * q], s->dc_lo[2 * q + 1]);
+        }
 #pragma unroll
-      for (int d = 0; d < kMaxDet; ++d) {
-        tauh[d] = s->tau_hi[d]; taul[d] = s->tau_lo[d];
-        rho[d][0] = s->rho[d][0]; rho[d][1] = s->rho[d][1];
-        sig[d][0] = s->sig[d][0]; sig[d][1] = s->sig[d][1];
+        for (int d = 0; d < kMaxDet; ++d) {
+          th[d] = s->tau_hi[d]; tl[d] = s->tau_lo[d];
+          rho[d][0] = s->rho[d][0]; rho[d][1] = s->rho[d][1];
+          sg[d][0] = s->sig[d][0]; sg[d][1] = s->sig[d][1];
+        }
+      } else {
+        const WalkerF64* s = reinterpret_cast<const WalkerF64*>(a.ws) + w;
+        valid = s->valid;
+#pragma unroll
+        for (int k = 0; k < kNBasis; ++k) dc64[k] = s->dc[k];
+#pragma unroll
+        for (int d = 0; d < kMaxDet; ++d) {
+          tau64[d] = s->tau[d];
+          th[d] = tl[d] = 0.f;
+          rho[d][0] = (float)s->rho[d][0]; rho[d][1] = (float)s->rho[d][1];
+          sg[d][0] = (float)s->sig[d][0]; sg[d][1] = (float)s->sig[d][1];
+        }
       }
-    } else {
-      const WalkerF64* s = reinterpret_cast<const WalkerF64*>(a.ws) + w;
-      valid = s->valid;
-#pragma unroll
-      for (int k = 0; k < kNBasis; ++k) dc64[k] = s->dc[k];
-#pragma unroll
-      for (int d = 0; d < kMaxDet; ++d) {
-        tau64[d] = s->tau[d];
-        rho[d][0] = (float)s->rho[d][0]; rho[d][1] = (float)s->rho[d][1];
-        sig[d][0] = (float)s->sig[d][0]; sig[d][1] = (float)s->sig[d][1];
-      }
+      P.tau_h = make_float2(th[0], th[1]); P.tau_l = make_float2(tl[0], tl[1]);
+      P.rho_r = make_float2(rho[0][0], rho[1][0]); P.rho_i = make_float2(rho[0][1], rho[1][1]);
+      P.sig_r = make_float2(sg[0][0], sg[1][0]); P.sig_i = make_float2(sg[0][1], sg[1][1]);
+      constexpr int dss = ds < 0 ? 0 : ds;
+      S.tau_h = th[dss]; S.tau_l = tl[dss];
+      S.rho_r = rho[dss][0]; S.rho_i = rho[dss][1];
+      S.sig_r = sg[dss][0]; S.sig_i = sg[dss][1];
     }
     if (!valid) {
       if (MALA) {
@@ -206,139 +378,128 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
       continue;
     }
 
-    // float-pair accumulator: for walkers far from the fiducial point the
+    // float-pair accumulators: for walkers far from the fiducial point the
     // per-bin terms add up to about -log L(theta_ref), so a single float would
     // lose ~1e-3 of absolute precision
-    float acc = 0.f, acc_lo = 0.f;
-    float adj_c[kNBasis], adj_tau[kMaxDet], adj_rho[kMaxDet][2];
-    if (GRAD) {
+    P.acc = P.acc_lo = P.adj_tau = P.adj_rr = P.adj_ri = make_float2(0.f, 0.f);
+    S.acc = S.acc_lo = S.adj_tau = S.adj_rr = S.adj_ri = 0.f;
+    float2 adj_c[kNBasis / 2];
 #pragma unroll
-      for (int k = 0; k < kNBasis; ++k) adj_c[k] = 0.f;
-#pragma unroll
-      for (int d = 0; d < kMaxDet; ++d) { adj_tau[d] = 0.f; adj_rho[d][0] = adj_rho[d][1] = 0.f; }
-    }
+    for (int q = 0; q < kNBasis / 2; ++q) adj_c[q] = make_float2(0.f, 0.f);
 
     for (int c0 = 0; c0 < B; c0 += 31) {
       const int e = c0 + lane;
       const bool has_edge = e < E;
       const bool has_bin = (lane < 31) && (e < B);
       const int ee = has_edge ? e : E - 1;
+      const int eb = has_bin ? e : 0;
 
-      // detector-independent phase sum_k dc_k g_k(f_e) / 2pi  [turns]
-      float xh = 0.f, xl = 0.f;
+      // detector-independent phase sum_k dc_k g_k(f_e) / 2pi [turns]: two
+      // float-pair accumulators (even k, odd k) side by side, then merged
+      float xh, xl, fe, fe_lo = 0.f;
       double x64 = 0.0;
-      float fe, fe_lo = 0.f;
       if (!PHASE64) {
+        float2 sh = make_float2(0.f, 0.f), sl = sh;
 #pragma unroll
         for (int q = 0; q < kNBasis / 2; ++q) {
-          const float4 g = g4[q * Ep + ee];
-          f2x_fma_acc(dch[2 * q], dcl[2 * q], g.x, g.y, xh, xl);
-          f2x_fma_acc(dch[2 * q + 1], dcl[2 * q + 1], g.z, g.w, xh, xl);
+          const float4 g = g4[q * Ep + ee];  // {g_hi[2q], g_hi[2q+1], g_lo[2q], g_lo[2q+1]}
+          pv::fma_acc(dch[q], dcl[q], make_float2(g.x, g.y), make_float2(g.z, g.w), sh, sl);
         }
+        xh = __fadd_rn(sh.x, sh.y);  // two-sum of the high parts
+        const float bb = __fsub_rn(xh, sh.x);
+        const float err = __fadd_rn(__fsub_rn(sh.x, __fsub_rn(xh, bb)), __fsub_rn(sh.y, bb));
+        xl = __fadd_rn(err, __fadd_rn(sl.x, sl.y));
         const float2 f2 = *reinterpret_cast<const float2*>(g4 + (kEdgeQuads - 1) * Ep + ee);
         fe = f2.x;
         fe_lo = f2.y;
       } else {
 #pragma unroll
-        for (int k = 0; k < kNBasis; ++k) x64 = fma(dc64[k], g64[k * Ep + ee], x64);
+        for (int k = 0; k < kNBasis; ++k) x64 = ::fma(dc64[k], g64[k * Ep + ee], x64);
         fe = (float)f64[ee];
+        xh = xl = 0.f;
       }
-      float adj_x = 0.f;
 
-#pragma unroll
-      for (int d = 0; d < kMaxDet; ++d) {
-        if (d < D) {
-          float y;
-          if (!PHASE64) {
-            float yh = xh, yl = xl;
-            f2x_fma_acc(tauh[d], taul[d], fe, fe_lo, yh, yl);
-            y = frac_turns(yh, yl);
-          } else {
-            const double xd = fma(f64[ee], tau64[d], x64);
-            y = (float)(xd - rint(xd));
-          }
-          float sn, cs;
-          sincos_pi_half(y, sn, cs);
-          const float em_r = -2.f * sn * sn, em_i = -2.f * sn * cs;
-          const float dr = fmaf(rho[d][0], em_r, fmaf(-rho[d][1], em_i, sig[d][0]));
-          const float di = fmaf(rho[d][0], em_i, fmaf(rho[d][1], em_r, sig[d][1]));
-          const float nr = __shfl_down_sync(kFull, dr, 1);
-          const float ni = __shfl_down_sync(kFull, di, 1);
-          float Ur = 0.f, Ui = 0.f, Vr = 0.f, Vi = 0.f;
-          if (has_bin) {
-            const float4 ta = binA[d * Bp + e];
-            const float2 tb = binB[d * Bp + e];
-            const float a0r = ta.x, a0i = ta.y, a1r = ta.z, a1i = ta.w, b0 = tb.x, b1 = tb.y;
-            const float sr = dr + nr, si = di + ni, tr = nr - dr, ti = ni - di;
-            float v = a0r * sr;
-            v = fmaf(a0i, si, v);
-            v = fmaf(a1r, tr, v);
-            v = fmaf(a1i, ti, v);
-            v = fmaf(-b0, fmaf(0.25f, fmaf(sr, sr, si * si), sr), v);
-            v = fmaf(-b1, fmaf(0.5f, fmaf(sr, tr, si * ti), tr), v);
-            {  // two-sum into (acc, acc_lo)
-              const float sum = __fadd_rn(acc, v);
-              const float bb = __fadd_rn(sum, -acc);
-              acc_lo = __fadd_rn(acc_lo, __fadd_rn(__fadd_rn(acc, -__fadd_rn(sum, -bb)), __fadd_rn(v, -bb)));
-              acc = sum;
-            }
-            if (GRAD) {
-              const float hs_r = fmaf(0.5f, sr, 1.f), hs_i = 0.5f * si;  // 1 + s/2
-              Ur = fmaf(-b0, hs_r, fmaf(-0.5f * b1, tr, a0r));
-              Ui = fmaf(-b0, hs_i, fmaf(-0.5f * b1, ti, a0i));
-              Vr = fmaf(-b1, hs_r, a1r);
-              Vi = fmaf(-b1, hs_i, a1i);
-            }
-          }
-          if (GRAD) {
-            float gr = Ur - Vr, gi = Ui - Vi;  // own bin (edge on its left)
-            const float lr = __shfl_up_sync(kFull, Ur + Vr, 1);
-            const float li = __shfl_up_sync(kFull, Ui + Vi, 1);
-            if (lane > 0) { gr += lr; gi += li; }
-            if (has_edge) {
-              const float rr = 1.f + dr, ri = di;
-              const float dldx = gr * ri - gi * rr;  // Im(conj(gbar) r); times 2 pi later
-              adj_x += dldx;
-              adj_tau[d] = fmaf(dldx, fe, adj_tau[d]);
-              const float Er = 1.f + em_r, Ei = em_i;  // gbar_rho += gbar conj(E)
-              adj_rho[d][0] += gr * Er + gi * Ei;
-              adj_rho[d][1] += gi * Er - gr * Ei;
-            }
-          }
+      float adj_x = 0.f;
+      if constexpr (paired) {
+        float2 y;
+        if (!PHASE64) {
+          float2 yh = make_float2(xh, xh), yl = make_float2(xl, xl);
+          pv::fma_acc(P.tau_h, P.tau_l, make_float2(fe, fe), make_float2(fe_lo, fe_lo), yh, yl);
+          y = pv::frac(yh, yl);
+        } else {
+          const double x0 = ::fma(f64[ee], tau64[0], x64), x1 = ::fma(f64[ee], tau64[1], x64);
+          y = make_float2((float)(x0 - rint(x0)), (float)(x1 - rint(x1)));
         }
+        const float4 q0 = binP[eb], q1 = binP[Bp + eb], q2 = binP[2 * Bp + eb];
+        const float2 bt[6] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y),
+                              make_float2(q1.z, q1.w), make_float2(q2.x, q2.y), make_float2(q2.z, q2.w)};
+        const float2 g = pv::det_edge<GRAD>(y, P, bt, has_bin, has_edge, lane, make_float2(fe, fe));
+        adj_x = __fadd_rn(g.x, g.y);
+      }
+      if constexpr (ds >= 0) {
+        float y;
+        if (!PHASE64) {
+          float yh = xh, yl = xl;
+          pv::fma_acc(S.tau_h, S.tau_l, fe, fe_lo, yh, yl);
+          y = pv::frac(yh, yl);
+        } else {
+          const double xd = ::fma(f64[ee], tau64[ds], x64);
+          y = (float)(xd - rint(xd));
+        }
+        const float4 q0 = binS4[eb];
+        const float2 q1 = binS2[eb];
+        const float bt[6] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y};
+        adj_x = __fadd_rn(adj_x, pv::det_edge<GRAD>(y, S, bt, has_bin, has_edge, lane, fe));
       }
       if (GRAD && has_edge) {
+        const float2 ax = make_float2(adj_x, adj_x);
         if (!PHASE64) {
 #pragma unroll
           for (int q = 0; q < kNBasis / 2; ++q) {
             const float4 g = g4[q * Ep + ee];
-            adj_c[2 * q] = fmaf(adj_x, g.x, adj_c[2 * q]);
-            adj_c[2 * q + 1] = fmaf(adj_x, g.z, adj_c[2 * q + 1]);
+            adj_c[q] = pv::fma(ax, make_float2(g.x, g.y), adj_c[q]);
           }
         } else {
 #pragma unroll
-          for (int k = 0; k < kNBasis; ++k) adj_c[k] = fmaf(adj_x, (float)g64[k * Ep + ee], adj_c[k]);
+          for (int q = 0; q < kNBasis / 2; ++q)
+            adj_c[q] = pv::fma(ax, make_float2((float)g64[2 * q * Ep + ee], (float)g64[(2 * q + 1) * Ep + ee]),
+                               adj_c[q]);
         }
       }
     }
 
-    const double tot = warp_sum_f64((double)acc + (double)acc_lo);
+    double part = (double)S.acc + (double)S.acc_lo;
+    if constexpr (paired) part += ((double)P.acc.x + (double)P.acc_lo.x) + ((double)P.acc.y + (double)P.acc_lo.y);
+    const double tot = warp_sum_f64(part);
     const double logl = *ev.base_logl + tot;
     if (!MALA && lane == 0) a.logl[w] = logl;
     if (GRAD) {
       const float two_pi = 6.28318530717958648f;
+      float ac[kNBasis], at[kMaxDet], ar[kMaxDet][2];
 #pragma unroll
-      for (int k = 0; k < kNBasis; ++k) adj_c[k] = two_pi * warp_sum_f32(adj_c[k]);
+      for (int q = 0; q < kNBasis / 2; ++q) {
+        ac[2 * q] = two_pi * warp_sum_f32(adj_c[q].x);
+        ac[2 * q + 1] = two_pi * warp_sum_f32(adj_c[q].y);
+      }
 #pragma unroll
-      for (int d = 0; d < kMaxDet; ++d) {
-        adj_tau[d] = two_pi * warp_sum_f32(adj_tau[d]);
-        adj_rho[d][0] = warp_sum_f32(adj_rho[d][0]);
-        adj_rho[d][1] = warp_sum_f32(adj_rho[d][1]);
+      for (int d = 0; d < kMaxDet; ++d) at[d] = ar[d][0] = ar[d][1] = 0.f;
+      if constexpr (paired) {
+        at[0] = two_pi * warp_sum_f32(P.adj_tau.x);
+        at[1] = two_pi * warp_sum_f32(P.adj_tau.y);
+        ar[0][0] = warp_sum_f32(P.adj_rr.x);
+        ar[1][0] = warp_sum_f32(P.adj_rr.y);
+        ar[0][1] = warp_sum_f32(P.adj_ri.x);
+        ar[1][1] = warp_sum_f32(P.adj_ri.y);
+      }
+      if constexpr (ds >= 0) {
+        at[ds] = two_pi * warp_sum_f32(S.adj_tau);
+        ar[ds][0] = warp_sum_f32(S.adj_rr);
+        ar[ds][1] = warp_sum_f32(S.adj_ri);
       }
       double g = 0.0;
       if (lane < kNPar) {
         const WalkerTan<float>& tn = reinterpret_cast<const WalkerTan<float>*>(a.tan)[w];
-        g = chain_rule<float>(lane, D, adj_c, adj_tau, adj_rho, rho, tn);
+        g = chain_rule<float>(lane, D, ac, at, ar, rho, tn);
       }
       if (MALA) mala_finish(a.mala, w, lane, logl, g);
       else if (lane < kNPar) a.grad[w * kNPar + lane] = g;
@@ -527,18 +688,28 @@ static cudaError_t blocks_per_sm(const void* fn, int threads, size_t smem, int* 
   return cudaSuccess;
 }
 
-template <bool GRAD, bool PHASE64, bool MALA = false>
-static cudaError_t launch_mixed_t(const LaunchArgs& a, cudaStream_t s, int n_sm) {
+template <int ND, bool GRAD, bool PHASE64, bool MALA>
+static cudaError_t launch_mixed_nd(const LaunchArgs& a, cudaStream_t s, int n_sm) {
   const size_t smem = mixed_smem_bytes(a.ev, PHASE64);
-  const void* fn = reinterpret_cast<const void*>(k_rb_mixed<GRAD, PHASE64, MALA>);
+  const void* fn = reinterpret_cast<const void*>(k_rb_mixed<ND, GRAD, PHASE64, MALA>);
   int per_sm = 0;
   cudaError_t err = blocks_per_sm(fn, kThreads, smem, &per_sm);
   if (err != cudaSuccess) return err;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int64_t blocks_needed = (a.W * 32 + kThreads - 1) / kThreads;
   const int64_t grid = std::min<int64_t>(blocks_needed, (int64_t)per_sm * n_sm);
-  k_rb_mixed<GRAD, PHASE64, MALA><<<(unsigned)grid, kThreads, smem, s>>>(a);
+  k_rb_mixed<ND, GRAD, PHASE64, MALA><<<(unsigned)grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <bool GRAD, bool PHASE64, bool MALA = false>
+static cudaError_t launch_mixed_t(const LaunchArgs& a, cudaStream_t s, int n_sm) {
+  switch (a.ev.n_det) {
+    case 1: return launch_mixed_nd<1, GRAD, PHASE64, MALA>(a, s, n_sm);
+    case 2: return launch_mixed_nd<2, GRAD, PHASE64, MALA>(a, s, n_sm);
+    case 3: return launch_mixed_nd<3, GRAD, PHASE64, MALA>(a, s, n_sm);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_rb_mixed(const EventDev& ev, const void* ws, const void* tan, int64_t W, double* logl, double* grad,

@@ -145,9 +145,15 @@ __device__ void summary_epilogue(const SummaryOut& so, int b, int d0, int nd, in
       so.summ[((size_t)d * B + b) * 6 + f] = o;
       const double t = (f == 2 || f == 3 || f == 5) ? o * inv_df_b : 0.5 * o;
       so.bin64[((size_t)d * 6 + f) * so.Bp + b] = t;
-      // float image: {a0r, a0i, a1r, a1i} quads, then {b0, b1} pairs
-      const size_t db = (size_t)d * so.Bp + b;
-      so.bin32[f < 4 ? db * 4 + f : (size_t)4 * D * so.Bp + db * 2 + (f - 4)] = (float)t;
+      // float image (layout in EventDev), with beta0 and beta1 negated
+      const float t32 = (float)(f >= 4 ? -t : t);
+      const size_t Bp = so.Bp;
+      if (D >= 2 && d < 2)  // detector pair: quad f/2 holds {x_0, x_1, y_0, y_1} of fields (f&~1, f|1)
+        so.bin32[((size_t)(f >> 1) * Bp + b) * 4 + (f & 1) * 2 + d] = t32;
+      else {                // the single detector D - 1
+        const size_t base = (D >= 2) ? 12 * Bp : 0;
+        so.bin32[f < 4 ? base + (size_t)b * 4 + f : base + 4 * Bp + (size_t)b * 2 + (f - 4)] = t32;
+      }
     }
     const double b0 = __shfl_sync(0xffffffffu, o, (6 * g + 4) & 31);
     const double sh = (mine && f == 0) ? o - 0.5 * b0 : 0.0;
@@ -279,7 +285,7 @@ __global__ void k_edge_tables(int64_t kmin, double T, int D, int B, int Ep, int 
       tab64[(size_t)(2 * q) * Ep + e] = g[2 * q];
       tab64[(size_t)(2 * q + 1) * Ep + e] = g[2 * q + 1];
       const f2x p0 = f2x_from(g[2 * q]), p1 = f2x_from(g[2 * q + 1]);
-      t4[(size_t)q * Ep + e] = make_float4(p0.hi, p0.lo, p1.hi, p1.lo);
+      t4[(size_t)q * Ep + e] = make_float4(p0.hi, p1.hi, p0.lo, p1.lo);
     }
     tab64[(size_t)kNBasis * Ep + e] = f;
     const f2x fp = f2x_from(f);

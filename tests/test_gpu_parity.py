@@ -76,6 +76,22 @@ def small(rb):
     return Case(rb, "C2", n_bins=45, T=8.0, f_low=20.0, f_high=512.0)
 
 
+@pytest.fixture(scope="module")
+def two(rb):
+    # two detectors: the pair-only layout of the mixed kernel's bin tables
+    return Case(rb, "C2", n_bins=150, T=32.0, sites=("H1", "L1"))
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_two_detectors(rb, two, mode):
+    th = synth.draw_box(two.ev["theta_inj"], 300, seed=23, rel=0.01, abs_width=1e-2 * synth.PRIOR_WIDTH)
+    L, G = rb.loglike_grad(two.event, torch.tensor(th, device="cuda"), mode=mode)
+    ref, dh, hh = _terms(two.ev, two.s, th)
+    assert np.all(np.abs(L.cpu().numpy() - ref) <= _tol(mode, dh, hh))
+    _, ref_G = oracle.loglike_rb(two.ev, two.s, th[:24], grad=True)
+    assert np.all(np.abs(G.cpu().numpy()[:24] - ref_G) <= _gtol(mode, ref_G))
+
+
 def test_grid_and_info(rb, c1, c2):
     for c in (c1, c2):
         inf = c.event.info()
