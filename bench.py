@@ -182,7 +182,13 @@ def main_kernel_flops(W: int, D: int, B: int, grad: bool) -> float:
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the main kernel on this workload, from an ncu capture of this kernel version
 # (None once the kernel changes and until it is captured again).
-MAIN_KERNEL_TRAFFIC_BYTES = 2353920
+MAIN_KERNEL_TRAFFIC_BYTES = 2349312
+
+
+# Algorithmic FP32 flops of the full-grid sum per (walker, grid point) with 3
+# detectors: the phase polynomial (30), one sin/cos (20), and per detector the
+# delay rotation, the product with the data and the accumulation (14 each).
+FULL_FLOPS_PER_WALKER_POINT = 92
 
 
 def fp32_peak_tflops() -> float:
@@ -426,10 +432,16 @@ def run_full(rb, torch, event, ev, args, dist, device, flush, rb_value, W=1024):
     torch.cuda.synchronize()
     ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     t, v = whole_job_rate(dist, sum(ms) / 1e3, W * K, device)
-    pts = ev["N"] * ev["geom"].shape[0]
+    N = ev["N"]
+    achieved = FULL_FLOPS_PER_WALKER_POINT * v * N / 1e12
+    peak = fp32_peak_tflops()
     return {"value": v, "unit": "full-grid evals/s", "walkers": W, "calls": K, "ms_per_call": t * 1e3 / K,
-            "grid_points_per_eval": int(pts), "walker_points_per_s": v * pts,
+            "grid_points_per_eval": int(N * ev["geom"].shape[0]), "walker_points_per_s": v * N,
             "rb_speedup": rb_value / v,
+            "roofline": {"bound": "alu", "kernel": "k_full_z (fp32 pipe)", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak,
+                         "flops_per_walker_point": FULL_FLOPS_PER_WALKER_POINT,
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"},
             "call": "rb_loglike_full_batch: set-up, per-walker grid sum, combination"}
 
 
