@@ -22,9 +22,12 @@
 // memory (read once for the 8 walkers; the event's data stay in L2); lane l
 // of a warp forms its walker's coefficients for chunk l, then evaluates the
 // points l, l + 32, ... of the segment, which all have the in-chunk offset
-// j = l - 16, so its delay factor exp(2 pi i j df tau_d) is a constant.
-// Per-lane sums are FP32 per segment, accumulated in float pairs; the warp
-// sum and the final combination are FP64.
+// j = l - 16, so its delay factor exp(2 pi i j df tau_d) is a constant that
+// is applied once to the lane's sum, after the loop.  Per point: the chunk
+// record (five 16-byte broadcast loads), the phase polynomial, one sin/cos,
+// and per detector exp(2 pi i f_c tau_d) times the point's phasor times the
+// data.  Per-lane sums are FP32 per segment, accumulated in float pairs; the
+// warp sum and the final combination are FP64.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -44,10 +47,11 @@ constexpr size_t kFullSmem = sizeof(float) * kSegC * kQRow + sizeof(float2) * kM
                              sizeof(float) * kFullWarps * kSegC * kFRec;
 
 // Per slice and walker: the slice's part of Z_d (complex, 3 detectors) as
-// FP64 in zout[slice][w][6].
+// FP64 in zout[slice][w][6].  ND = number of detectors.
+template <int ND>
 __global__ void __launch_bounds__(kFullThreads) k_full_z(const float2* __restrict__ w32, int N,
                                                         const float* __restrict__ q, int n_chunks,
-                                                        const WalkerAbs* __restrict__ wabs, int64_t W, int D,
+                                                        const WalkerAbs* __restrict__ wabs, int64_t W,
                                                         float invT_hi, float invT_lo, int seg_per_slice,
                                                         double* __restrict__ zout) {
   // dynamic shared memory: chunk matrices of the segment, (d'/S') f^-7/6,
@@ -56,6 +60,7 @@ __global__ void __launch_bounds__(kFullThreads) k_full_z(const float2* __restric
   float* qs = reinterpret_cast<float*>(smem_full);
   float2 (*wa)[kSegP] = reinterpret_cast<float2 (*)[kSegP]>(qs + kSegC * kQRow);
   float (*rec)[kSegC][kFRec] = reinterpret_cast<float (*)[kSegC][kFRec]>(wa + kMaxDet);
+  constexpr int D = ND;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t w = (int64_t)blockIdx.x * kFullWarps + warp;
   const bool live = w < W;
@@ -152,32 +157,32 @@ __global__ void __launch_bounds__(kFullThreads) k_full_z(const float2* __restric
     for (int d = 0; d < kMaxDet; ++d) acc[d][0] = acc[d][1] = 0.f;
     for (int c = 0; c < nc; ++c) {
       const int p = c * kChunk + lane;
-      const float* r = rec[warp][c];
+      const float4* r4 = reinterpret_cast<const float4*>(rec[warp][c]);
+      const float4 qa = r4[0], qb = r4[1], qc = r4[2];  // X0 hi/lo, X1 hi/lo | X2 hi/lo, X3, X4 | X5..X8
       // x = X0 + X1 j + X2 j^2 + j^3 (X3 + ... + X8 j^5)
-      const float t = fmaf(fmaf(fmaf(fmaf(fmaf(r[11], jf, r[10]), jf, r[9]), jf, r[8]), jf, r[7]), jf, r[6]);
+      const float t = fmaf(fmaf(fmaf(fmaf(fmaf(qc.w, jf, qc.z), jf, qc.y), jf, qc.x), jf, qb.w), jf, qb.z);
       const float j2 = jf * jf;
       const float t3 = t * (j2 * jf);
-      const float p1 = __fmul_rn(r[2], jf);
-      float e1 = __fmaf_rn(r[2], jf, -p1);
-      e1 = __fmaf_rn(r[3], jf, e1);
-      const float p2 = __fmul_rn(r[4], j2);
-      float e2 = __fmaf_rn(r[4], j2, -p2);
-      e2 = __fmaf_rn(r[5], j2, e2);
-      float sh = r[0], sl = r[1];
+      const float p1 = __fmul_rn(qa.z, jf);
+      float e1 = __fmaf_rn(qa.z, jf, -p1);
+      e1 = __fmaf_rn(qa.w, jf, e1);
+      const float p2 = __fmul_rn(qb.x, j2);
+      float e2 = __fmaf_rn(qb.x, j2, -p2);
+      e2 = __fmaf_rn(qb.y, j2, e2);
+      float sh = qa.x, sl = qa.y;
       f2x_add(sh, sl, p1);
       f2x_add(sh, sl, p2);
       sl = __fadd_rn(sl, __fadd_rn(__fadd_rn(e1, e2), t3));
       const float2 z = cis_turns(frac_turns(sh, sl));  // exp(+2 pi i x)
+      const float4 ea = r4[3];  // exp(2 pi i f_c tau_d): d = 0, 1
+      const float2 eb = *reinterpret_cast<const float2*>(r4 + 4);  // d = 2
+      const float er[kMaxDet] = {ea.x, ea.z, eb.x}, ei[kMaxDet] = {ea.y, ea.w, eb.y};
 #pragma unroll
-      for (int d = 0; d < kMaxDet; ++d) {
-        if (d < D) {
-          const float er = r[12 + 2 * d], ei = r[13 + 2 * d];
-          const float fr = fmaf(er, toff[d].x, -ei * toff[d].y), fi = fmaf(er, toff[d].y, ei * toff[d].x);
-          const float cr = fmaf(z.x, fr, -z.y * fi), ci = fmaf(z.x, fi, z.y * fr);  // exp(+2 pi i x_d)
-          const float2 v = wa[d][p];
-          acc[d][0] = fmaf(v.x, cr, fmaf(-v.y, ci, acc[d][0]));
-          acc[d][1] = fmaf(v.x, ci, fmaf(v.y, cr, acc[d][1]));
-        }
+      for (int d = 0; d < D; ++d) {
+        const float ur = fmaf(z.x, er[d], -z.y * ei[d]), ui = fmaf(z.x, ei[d], z.y * er[d]);
+        const float2 v = wa[d][p];
+        acc[d][0] = fmaf(v.x, ur, fmaf(-v.y, ui, acc[d][0]));
+        acc[d][1] = fmaf(v.x, ui, fmaf(v.y, ur, acc[d][1]));
       }
     }
 #pragma unroll
@@ -188,11 +193,14 @@ __global__ void __launch_bounds__(kFullThreads) k_full_z(const float2* __restric
   }
   if (!live) return;
   double* zo = zout + ((size_t)blockIdx.y * W + w) * 6;
-  // warp sums in FP64 (lane order fixed by the butterfly)
+  // the lane's delay factor exp(2 pi i j df tau_d), then warp sums in FP64
+  // (lane order fixed by the butterfly)
 #pragma unroll
   for (int d = 0; d < kMaxDet; ++d) {
-    const double re = warp_sum_f64((double)zh[d][0] + (double)zl[d][0]);
-    const double im = warp_sum_f64((double)zh[d][1] + (double)zl[d][1]);
+    const double sr = (double)zh[d][0] + (double)zl[d][0], si = (double)zh[d][1] + (double)zl[d][1];
+    const double tr = toff[d].x, ti = toff[d].y;
+    const double re = warp_sum_f64(sr * tr - si * ti);
+    const double im = warp_sum_f64(sr * ti + si * tr);
     if (lane == 0) {
       zo[2 * d] = valid ? re : 0.0;
       zo[2 * d + 1] = valid ? im : 0.0;
@@ -281,11 +289,13 @@ extern "C" int rb_loglike_full_batch(rb_event_t ev, const double* theta_dev, int
     e.w32_resident = e.w32_current = true;
     count_launches(1);
   }
-  static bool smem_raised = false;  // idempotent attribute; races only repeat it
-  if (!smem_raised) {
-    if ((err = cudaFuncSetAttribute(k_full_z, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFullSmem)) != cudaSuccess)
+  void (*const kz)(const float2*, int, const float*, int, const WalkerAbs*, int64_t, float, float, int, double*) =
+      e.n_det == 1 ? k_full_z<1> : e.n_det == 2 ? k_full_z<2> : k_full_z<3>;
+  static bool smem_raised[kMaxDet] = {false, false, false};  // idempotent attribute; races only repeat it
+  if (!smem_raised[e.n_det - 1]) {
+    if ((err = cudaFuncSetAttribute(kz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFullSmem)) != cudaSuccess)
       return cuda_fail(err, "rb_loglike_full_batch: shared memory attribute");
-    smem_raised = true;
+    smem_raised[e.n_det - 1] = true;
   }
   // slices of the grid per group of 8 walkers: at least two waves of blocks
   // (2 per SM), then the count in the next few that wastes the least of the last wave
@@ -320,9 +330,9 @@ extern "C" int rb_loglike_full_batch(rb_event_t ev, const double* theta_dev, int
   if ((err = launch_setup_abs(theta_dev, W, e.ec, wabs, s)) != cudaSuccess) {
     rc = cuda_fail(err, "rb_loglike_full_batch: set-up kernel");
   } else {
-    k_full_z<<<dim3((unsigned)wblocks, (unsigned)n_slices), kFullThreads, kFullSmem, s>>>(
-        static_cast<const float2*>(e.d_w32), (int)e.N, static_cast<const float*>(e.d_chunkq), nc, wabs, W, e.n_det, ih,
-        il, seg_per_slice, zout);
+    kz<<<dim3((unsigned)wblocks, (unsigned)n_slices), kFullThreads, kFullSmem, s>>>(
+        static_cast<const float2*>(e.d_w32), (int)e.N, static_cast<const float*>(e.d_chunkq), nc, wabs, W, ih, il,
+        seg_per_slice, zout);
     k_full_finish<<<(unsigned)((W + 127) / 128), 128, 0, s>>>(zout, n_slices, wabs, W, e.n_det, e.n_bins, e.T, e.d_wexp,
                                                               e.d_summ, e.d_ref, logl_dev);
     if ((err = cudaGetLastError()) != cudaSuccess) rc = cuda_fail(err, "rb_loglike_full_batch: kernels");
