@@ -231,42 +231,46 @@ def run_gb300(args, dist: Dist):
     lib = rb.load()
     import ctypes
 
-    def launch(mode, stream_handle, rebuild=True):
+    def launch(mode, stream_handle, combined=True):
         """One step through the C ABI: rebuild the summary data from the
-        event's HBM-resident strain and PSD, then log L + gradient for the batch."""
+        event's HBM-resident strain and PSD, then log L + gradient for the
+        batch -- in one call (the walkers' set-up overlapped with the summary
+        sums) or as the two calls in sequence."""
         m = rb.MODES[mode]
-        rc = lib.rb_event_rebuild(event.handle, None, None, None, 0, m, stream_handle) if rebuild else 0
-        if rc == 0:
-            rc = lib.rb_loglike_grad_batch(event.handle, ctypes.c_void_p(theta.data_ptr()), W,
-                                           ctypes.c_void_p(logl.data_ptr()), ctypes.c_void_p(grad.data_ptr()), m,
-                                           stream_handle)
+        th, lo, gr = (ctypes.c_void_p(t.data_ptr()) for t in (theta, logl, grad))
+        if combined:
+            rc = lib.rb_rebuild_loglike_grad(event.handle, th, W, lo, gr, m, stream_handle)
+        else:
+            rc = lib.rb_event_rebuild(event.handle, None, None, None, 0, m, stream_handle)
+            if rc == 0:
+                rc = lib.rb_loglike_grad_batch(event.handle, th, W, lo, gr, m, stream_handle)
         if rc != 0:
             raise RuntimeError(lib.rb_last_error().decode())
 
-    def step(mode):
-        launch(mode, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    def step(mode, combined=True):
+        launch(mode, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), combined)
 
     graphs = {}
 
-    def graph_for(mode):
+    def graph_for(mode, combined=True):
         """The step captured once as a CUDA graph (removes per-launch host cost)."""
-        if mode not in graphs:
+        if (mode, combined) not in graphs:
             side = torch.cuda.Stream()
             side.wait_stream(torch.cuda.current_stream())
             with torch.cuda.stream(side):
                 for _ in range(3):
-                    step(mode)
+                    step(mode, combined)
             torch.cuda.current_stream().wait_stream(side)
             torch.cuda.synchronize()
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, capture_error_mode="relaxed"):
-                step(mode)
+                step(mode, combined)
             torch.cuda.synchronize()
-            graphs[mode] = g
-        return graphs[mode]
+            graphs[(mode, combined)] = g
+        return graphs[(mode, combined)]
 
-    def timed(mode, K, Wm):
-        g = graph_for(mode)
+    def timed(mode, K, Wm, combined=True):
+        g = graph_for(mode, combined)
         for _ in range(Wm):
             g.replay()
         torch.cuda.synchronize()
@@ -284,7 +288,7 @@ def run_gb300(args, dist: Dist):
         dist.barrier()
         # kernels per step, counted from one plain (non-graph) launch of the same step
         n0 = rb.kernel_launch_count()
-        step(mode)
+        step(mode, combined)
         torch.cuda.synchronize()
         per_step = rb.kernel_launch_count() - n0
         step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
@@ -320,6 +324,7 @@ def run_gb300(args, dist: Dist):
     step_ms, launches = timed(args.mode, args.steps, 0)
     clocks = sampler.stop()
     main_ms = main_kernel_ms(args.mode, max(5, min(args.steps, 50)))
+    two_ms, _ = timed(args.mode, max(3, min(args.steps, 20)), 3, combined=False)
     total_s = sum(step_ms) / 1e3
     max_total_s, value = whole_job_rate(dist, total_s, W * args.steps, device)
     main_avg_s = float(np.mean(main_ms)) / 1e3
@@ -333,12 +338,14 @@ def run_gb300(args, dist: Dist):
         "data": "synthetic: seeded noise (analytic aLIGO-like PSD) + TaylorF2-tidal injection; prior-box walkers",
         "config": {"workload": WORKLOAD, "detectors": D, "T_s": ev["T"], "f_low": ev["f_low"], "f_high": ev["f_high"],
                    "n_freq": ev["N"], "n_bins": B, "walkers": W, "mode": args.mode,
-                   "step": "rb_event_rebuild (summary data from HBM-resident strain) + rb_loglike_grad_batch, "
-                           "replayed as one captured CUDA graph",
+                   "step": "rb_rebuild_loglike_grad: summary rebuild from the HBM-resident strain + log L and "
+                           "gradient of the batch (walker set-up overlapped with the summary sums), replayed as "
+                           "one captured CUDA graph",
                    "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas{dist.world}"},
         "gpu_launches": int(launches),
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
         "breakdown_ms": {"step_median": float(np.median(step_ms)), "step_p99": float(np.percentile(step_ms, 99)),
+                         "two_call_step_median": float(np.median(two_ms)),
                          "main_kernel_avg": main_avg_s * 1e3,
                          "batch_evals_per_s_main_kernel_only": W / main_avg_s},
         "roofline": {"bound": "alu", "kernel": "k_rb_mixed<grad> (fp32 pipe)", "achieved": achieved, "peak": peak,

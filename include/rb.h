@@ -174,6 +174,19 @@ RB_API int rb_loglike_batch(rb_event_t ev, const double* theta_dev, int64_t W, d
 RB_API int rb_loglike_grad_batch(rb_event_t ev, const double* theta_dev, int64_t W, double* logl_dev, double* grad_dev,
                           int mode, void* stream);
 
+/* rb_event_rebuild from the event's resident data and current theta_ref
+ * followed by rb_loglike_grad_batch, in one call (grad_dev may be NULL for
+ * log L only): the results are those of the two calls in sequence on
+ * `stream`.  With RB_MIXED and the chunk-expanded summary (T f_low >= 1024,
+ * n_freq <= 2^30) the walkers' set-up, which needs only the reference values
+ * and theta, runs on the event's forked stream concurrently with the summary
+ * sums and is joined before the likelihood kernel; otherwise the two calls
+ * run in sequence.  theta_dev must be ready on `stream` when the call is
+ * made.  Asynchronous; the workspace comes from the stream-ordered pool.
+ * Errors: those of the two calls. */
+RB_API int rb_rebuild_loglike_grad(rb_event_t ev, const double* theta_dev, int64_t W, double* logl_dev,
+                                   double* grad_dev, int mode, void* stream);
+
 /* End-to-end convenience form of rb_loglike_grad_batch for host buffers:
  * copies theta_host [W][13] to the device, evaluates, copies logl_host [W]
  * (and grad_host [W][13] unless NULL) back, and synchronises the stream.

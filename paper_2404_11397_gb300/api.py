@@ -171,6 +171,21 @@ def loglike(event: Event, theta: torch.Tensor, mode="mixed", stream=None) -> tor
     return out
 
 
+def rebuild_loglike_grad(event: Event, theta: torch.Tensor, mode="mixed", stream=None, grad: bool = True):
+    """Rebuild the summary data from the event's resident data, then log L [W]
+    (and the gradient [W, 13] unless grad=False) in one call, with the walkers'
+    set-up overlapped with the summary sums."""
+    th = _theta_dev(theta)
+    W = th.shape[0]
+    out = torch.empty(W, dtype=torch.float64, device=th.device)
+    g = torch.empty(W, NPAR, dtype=torch.float64, device=th.device) if grad else None
+    check(load().rb_rebuild_loglike_grad(event.handle, ctypes.c_void_p(th.data_ptr()), W,
+                                         ctypes.c_void_p(out.data_ptr()),
+                                         ctypes.c_void_p(g.data_ptr()) if g is not None else None, _mode(mode),
+                                         _stream_handle(stream)), "rb_rebuild_loglike_grad")
+    return (out, g) if grad else out
+
+
 def loglike_full(event: Event, theta: torch.Tensor, mode="mixed", stream=None) -> torch.Tensor:
     """Full-grid (un-binned) log-likelihood [W] (float64, on theta's device)."""
     th = _theta_dev(theta)

@@ -204,6 +204,7 @@ int rb_event_free(rb_event_t ev) {
   cudaFree(e.d_share);
   if (e.ev_fork) cudaEventDestroy(e.ev_fork);
   if (e.ev_join) cudaEventDestroy(e.ev_join);
+  if (e.ev_ref) cudaEventDestroy(e.ev_ref);
   if (e.side) cudaStreamDestroy(e.side);
   cudaFree(e.d_sync);
   cudaFree(e.d_w32);
@@ -310,7 +311,8 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
     if (rc != RB_OK) break;
     if ((err = cudaStreamCreateWithFlags(&e.side, cudaStreamNonBlocking)) != cudaSuccess ||
         (err = cudaEventCreateWithFlags(&e.ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
-        (err = cudaEventCreateWithFlags(&e.ev_join, cudaEventDisableTiming)) != cudaSuccess) {
+        (err = cudaEventCreateWithFlags(&e.ev_join, cudaEventDisableTiming)) != cudaSuccess ||
+        (err = cudaEventCreateWithFlags(&e.ev_ref, cudaEventDisableTiming)) != cudaSuccess) {
       rc = cuda_fail(err, "rebuild stream and events");
       break;
     }
@@ -432,6 +434,40 @@ int rb_loglike_grad_batch(rb_event_t ev, const double* theta_dev, int64_t W, dou
   return rb::run_batch(event_entry(ev), theta_dev, W, logl_dev, grad_dev, mode, (cudaStream_t)stream, nullptr);
 }
 
+int rb_rebuild_loglike_grad(rb_event_t ev, const double* theta_dev, int64_t W, double* logl_dev, double* grad_dev,
+                            int mode, void* stream) {
+  using namespace rb;
+  if (!ev) return set_error(RB_EINVAL, "rb_rebuild_loglike_grad: NULL event");
+  if (W < 0) return set_error(RB_EINVAL, "rb_rebuild_loglike_grad: W < 0");
+  if (mode != RB_MIXED && mode != RB_FP64 && mode != RB_MIXED_F64PHASE)
+    return set_error(RB_EINVAL, "rb_rebuild_loglike_grad: bad mode %d", mode);
+  if (W > 0 && (!theta_dev || !logl_dev)) return set_error(RB_EINVAL, "rb_rebuild_loglike_grad: NULL theta or logl");
+  EventEntry& e = ev->e;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool overlap = W > 0 && mode == RB_MIXED && e.kmin >= 1024 && e.N <= (int64_t(1) << 30);
+  if (!overlap) {  // the two calls in sequence
+    int rc = rebuild_event(e, nullptr, mode, s);
+    if (rc != RB_OK || W == 0) return rc;
+    return run_batch(&e, theta_dev, W, logl_dev, grad_dev, mode, s, nullptr);
+  }
+  const bool want_grad = grad_dev != nullptr;
+  const size_t ws_bytes = sizeof(WalkerMixed) * W, tan_bytes = want_grad ? sizeof(WalkerTan<float>) * W : 0;
+  void* buf = nullptr;
+  cudaError_t err = cudaMallocAsync(&buf, ws_bytes + tan_bytes, s);
+  if (err != cudaSuccess) return cuda_fail(err, "cudaMallocAsync workspace");
+  void* tan = want_grad ? static_cast<void*>(static_cast<char*>(buf) + ws_bytes) : nullptr;
+  const SideSetup ss{theta_dev, W, buf, tan, want_grad};
+  int rc = rebuild_event(e, nullptr, mode, s, &ss);
+  if (rc == RB_OK) {
+    if ((err = launch_batch_main(&e, buf, tan, W, logl_dev, grad_dev, mode, s, nullptr)) != cudaSuccess)
+      rc = cuda_fail(err, "likelihood kernel");
+    else
+      count_launches(1);
+  }
+  cudaFreeAsync(buf, s);
+  return rc;
+}
+
 int rb_loglike_batch(rb_event_t ev, const double* theta_dev, int64_t W, double* logl_dev, int mode, void* stream) {
   return rb::run_batch(event_entry(ev), theta_dev, W, logl_dev, nullptr, mode, (cudaStream_t)stream, nullptr);
 }
@@ -496,7 +532,7 @@ int rb_strain(const double* geom, double gmst, const double* theta_host, double 
 
 namespace rb {
 
-int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t s) {
+int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t s, const SideSetup* ss) {
   cudaError_t err;
   DataPtrs in{};
   if (in_opt) {
@@ -508,20 +544,31 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
     }
   }
   const bool fast = mode != RB_FP64 && e.kmin >= 1024 && e.N <= (int64_t(1) << 30);
+  if (ss && !(fast && mode == RB_MIXED)) return set_error(RB_EINVAL, "overlapped set-up needs the mixed fast rebuild");
   // Both sets of reference values are rebuilt: the float-float set (mixed
   // path, fast summary) and the FP64 set (FP64 paths, FP64 summary).  The
   // one this summary does not read runs on a forked stream, joined below.
   if ((err = cudaEventRecord(e.ev_fork, s)) != cudaSuccess || (err = cudaStreamWaitEvent(e.side, e.ev_fork, 0)) != cudaSuccess)
     return cuda_fail(err, "rebuild fork");
+  int launches = 3;
   if (fast) {
     if ((err = launch_ref_values(e.d_theta_ref, e.ec, e.d_ref, e.side)) != cudaSuccess) return cuda_fail(err, "reference values kernel");
     if ((err = launch_ref_dd(e.d_theta_ref, e.ec, e.d_ref, s)) != cudaSuccess) return cuda_fail(err, "reference values kernel");
+    if (ss) {
+      // the walkers' set-up reads the float-float reference values and theta
+      // only: on the forked stream, after the FP64 set, concurrent with the
+      // chunk coefficients and the summary sums
+      if ((err = cudaEventRecord(e.ev_ref, s)) != cudaSuccess || (err = cudaStreamWaitEvent(e.side, e.ev_ref, 0)) != cudaSuccess)
+        return cuda_fail(err, "rebuild fork");
+      if ((err = launch_setup(RB_MIXED, ss->theta, ss->W, e.ec, e.d_ref, ss->ws, ss->tan, ss->grad, e.side)) != cudaSuccess)
+        return cuda_fail(err, "set-up kernel");
+      ++launches;
+    }
   } else {
     if ((err = launch_ref_dd(e.d_theta_ref, e.ec, e.d_ref, e.side)) != cudaSuccess) return cuda_fail(err, "reference values kernel");
     if ((err = launch_ref_values(e.d_theta_ref, e.ec, e.d_ref, s)) != cudaSuccess) return cuda_fail(err, "reference values kernel");
   }
   if ((err = cudaEventRecord(e.ev_join, e.side)) != cudaSuccess) return cuda_fail(err, "rebuild join");
-  int launches = 3;
   if (fast) {
     // the FP32 working copy follows the data the sums are taken over: data
     // read in place are converted every time, the resident data only after
@@ -580,11 +627,20 @@ int run_batch(const EventEntry* e, const double* theta, int64_t W, double* logl,
   void* ws = buf;
   void* tan = want_grad ? static_cast<void*>(static_cast<char*>(buf) + ws_bytes) : nullptr;
   int rc = RB_OK;
+  err = launch_setup(mode, theta, W, e->ec, e->d_ref, ws, tan, want_grad, s);
+  if (err == cudaSuccess) err = launch_batch_main(e, ws, tan, W, logl, grad, mode, s, mala);
+  if (err != cudaSuccess) rc = cuda_fail(err, "likelihood kernels");
+  else count_launches(2);
+  if (!scratch) cudaFreeAsync(buf, s);
+  return rc;
+}
+
+cudaError_t launch_batch_main(const EventEntry* e, void* ws, void* tan, int64_t W, double* logl, double* grad, int mode,
+                              cudaStream_t s, const MalaArgs* mala) {
   const int n_sm = sm_count();
   cudaEvent_t tb = static_cast<cudaEvent_t>(g_trace_before.load());
   cudaEvent_t ta = static_cast<cudaEvent_t>(g_trace_after.load());
-  err = launch_setup(mode, theta, W, e->ec, e->d_ref, ws, tan, want_grad, s);
-  if (err == cudaSuccess && tb) err = cudaEventRecord(tb, s);
+  cudaError_t err = tb ? cudaEventRecord(tb, s) : cudaSuccess;
   if (err == cudaSuccess) {
     if (mode == RB_FP64)
       err = launch_rb_f64(e->dev, ws, tan, W, logl, grad, s, n_sm, mala);
@@ -592,10 +648,7 @@ int run_batch(const EventEntry* e, const double* theta, int64_t W, double* logl,
       err = launch_rb_mixed(e->dev, ws, tan, W, logl, grad, mode == RB_MIXED_F64PHASE, s, n_sm, mala);
   }
   if (err == cudaSuccess && ta) err = cudaEventRecord(ta, s);
-  if (err != cudaSuccess) rc = cuda_fail(err, "likelihood kernels");
-  else count_launches(2);
-  if (!scratch) cudaFreeAsync(buf, s);
-  return rc;
+  return err;
 }
 
 }  // namespace rb

@@ -40,6 +40,7 @@ struct EventEntry {
   bool last_in_place = false;     // the last rebuild read caller data in place
   cudaStream_t side = nullptr;    // rebuild: branch for the reference values the summary does not use
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_ref = nullptr;   // rebuild + batch: float-float reference values ready
   PartDesc* d_parts = nullptr;    // fast build: parts of bins
   float* d_part_sums = nullptr;   // fast build: per-part float-pair sums
   int n_parts = 0;
@@ -72,7 +73,20 @@ int run_batch(const EventEntry* e, const double* theta, int64_t W, double* logl,
 // synchronisation.
 // mode RB_FP64 uses the FP64 summary kernel; the mixed modes use the fast
 // Taylor-chunk kernel when T f_low >= 1024 and N <= 2^30 (FP64 kernel otherwise).
-int rebuild_event(EventEntry& e, const DataPtrs* in, int mode, cudaStream_t s);
+// The walkers' set-up of a batch that follows a rebuild on the same stream
+// (rb_rebuild_loglike_grad): it needs only the reference values and theta, so
+// the rebuild runs it on its forked stream, overlapped with the summary sums.
+struct SideSetup {
+  const double* theta;
+  int64_t W;
+  void* ws;
+  void* tan;
+  bool grad;
+};
+int rebuild_event(EventEntry& e, const DataPtrs* in, int mode, cudaStream_t s, const SideSetup* side_setup = nullptr);
+// The likelihood kernel of a batch whose set-up has been done (trace events around it).
+cudaError_t launch_batch_main(const EventEntry* e, void* ws, void* tan, int64_t W, double* logl, double* grad, int mode,
+                              cudaStream_t s, const MalaArgs* mala);
 
 // Events recorded on the launch stream right before / after the main
 // likelihood kernel of every batch (NULL disables).

@@ -389,3 +389,40 @@ def test_rebuild_new_reference_and_data(rb, c1):
     torch.cuda.synchronize()
     _summary_close(event.summary(), s, 2e-6, _b1_condition(ev2, new_ref, c1.edges))
     event.free()
+
+
+# ---------------------------------------------------------------------------
+# Rebuild + batch in one call (rb_rebuild_loglike_grad): the walkers' set-up
+# overlapped with the summary sums gives the results of the two calls
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", MODES)
+def test_rebuild_and_batch_equals_two_calls(rb, c2, small, mode):
+    for c in (c2, small):  # the chunk-expanded rebuild, and one that falls back to the FP64 sums
+        th = torch.tensor(synth.posterior_box(c.ev["theta_inj"], 333, seed=91), device="cuda")
+        c.event.rebuild(mode=mode)
+        L1, G1 = rb.loglike_grad(c.event, th, mode=mode)
+        L2, G2 = rb.rebuild_loglike_grad(c.event, th, mode=mode)
+        torch.testing.assert_close(L2, L1, rtol=0, atol=0)
+        torch.testing.assert_close(G2, G1, rtol=0, atol=0)
+        L3 = rb.rebuild_loglike_grad(c.event, th, mode=mode, grad=False)
+        torch.testing.assert_close(L3, rb.loglike(c.event, th, mode=mode), rtol=0, atol=0)
+
+
+def test_rebuild_and_batch_in_a_cuda_graph(rb, c2):
+    th = torch.tensor(synth.walkers("C2", 1000), device="cuda")
+    L_ref, G_ref = rb.rebuild_loglike_grad(c2.event, th)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        out = rb.rebuild_loglike_grad(c2.event, th)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="relaxed"):
+        L, G = rb.rebuild_loglike_grad(c2.event, th)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    torch.testing.assert_close(L, L_ref, rtol=0, atol=0)
+    torch.testing.assert_close(G, G_ref, rtol=0, atol=0)
+    # empty batch: only the rebuild
+    assert rb.rebuild_loglike_grad(c2.event, th[:0])[0].numel() == 0
