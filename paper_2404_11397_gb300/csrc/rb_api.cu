@@ -552,16 +552,20 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
     return cuda_fail(err, "rebuild fork");
   int launches = 3;
   if (fast) {
-    if ((err = launch_ref_values(e.d_theta_ref, e.ec, e.d_ref, e.side)) != cudaSuccess) return cuda_fail(err, "reference values kernel");
+    if (!ss && (err = launch_ref_values(e.d_theta_ref, e.ec, e.d_ref, e.side)) != cudaSuccess)
+      return cuda_fail(err, "reference values kernel");
     if ((err = launch_ref_dd(e.d_theta_ref, e.ec, e.d_ref, s)) != cudaSuccess) return cuda_fail(err, "reference values kernel");
     if (ss) {
       // the walkers' set-up reads the float-float reference values and theta
-      // only: on the forked stream, after the FP64 set, concurrent with the
-      // chunk coefficients and the summary sums
+      // only: on the forked stream, launched as soon as they exist so that its
+      // blocks are resident before the summary sums fill the GPU; the FP64
+      // set (off the critical path) follows it
       if ((err = cudaEventRecord(e.ev_ref, s)) != cudaSuccess || (err = cudaStreamWaitEvent(e.side, e.ev_ref, 0)) != cudaSuccess)
         return cuda_fail(err, "rebuild fork");
       if ((err = launch_setup(RB_MIXED, ss->theta, ss->W, e.ec, e.d_ref, ss->ws, ss->tan, ss->grad, e.side)) != cudaSuccess)
         return cuda_fail(err, "set-up kernel");
+      if ((err = launch_ref_values(e.d_theta_ref, e.ec, e.d_ref, e.side)) != cudaSuccess)
+        return cuda_fail(err, "reference values kernel");
       ++launches;
     }
   } else {
