@@ -453,8 +453,9 @@ def run_full(rb, torch, event, ev, args, dist, device, flush, rb_value, W=1024):
 
 
 def run_e2e(rb, torch, event, ev, data, psd, theta, W, args, dist, device):
-    """Same metric through the public API on pinned host buffers: strain/PSD
-    and walkers copied in every step, log L and gradient copied out."""
+    """Same metric through the public API on pinned host buffers
+    (rb_rebuild_loglike_grad_host): strain/PSD and walkers copied in every
+    step, log L and gradient copied out, the stream synchronised."""
     import ctypes
     D, N = ev["geom"].shape[0], ev["N"]
     h_data = [data[d].cpu().pin_memory() for d in range(D)]
@@ -468,11 +469,9 @@ def run_e2e(rb, torch, event, ev, data, psd, theta, W, args, dist, device):
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
     def step():
-        rc = lib.rb_event_rebuild(event.handle, None, dp, pp, 0, rb.MODES[args.mode], stream)
-        if rc == 0:
-            rc = lib.rb_loglike_grad_host(event.handle, ctypes.c_void_p(h_theta.data_ptr()), W,
-                                          ctypes.c_void_p(h_logl.data_ptr()), ctypes.c_void_p(h_grad.data_ptr()),
-                                          rb.MODES[args.mode], stream)
+        rc = lib.rb_rebuild_loglike_grad_host(event.handle, dp, pp, ctypes.c_void_p(h_theta.data_ptr()), W,
+                                              ctypes.c_void_p(h_logl.data_ptr()), ctypes.c_void_p(h_grad.data_ptr()),
+                                              rb.MODES[args.mode], stream)
         if rc != 0:
             raise RuntimeError(lib.rb_last_error().decode())
 

@@ -186,6 +186,29 @@ def rebuild_loglike_grad(event: Event, theta: torch.Tensor, mode="mixed", stream
     return (out, g) if grad else out
 
 
+def rebuild_loglike_grad_host(event: Event, data, psd, theta: np.ndarray, logl_out: np.ndarray,
+                              grad_out: Optional[np.ndarray], mode="mixed", stream=None) -> None:
+    """End-to-end step on host buffers: new strain/PSD (per detector, [N][2]
+    and [N] float64, ideally pinned) and walkers in, summary rebuilt, log L
+    (and gradient) out; synchronises the stream."""
+    D = event.n_det
+    keep = [np.ascontiguousarray(a, dtype=np.float64) if not isinstance(a, torch.Tensor) else a
+            for a in list(data) + list(psd)]
+    ptrs = [a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data for a in keep]
+    dp = (ctypes.c_void_p * D)(*ptrs[:D])
+    pp = (ctypes.c_void_p * D)(*ptrs[D:])
+    th = theta if isinstance(theta, torch.Tensor) else np.ascontiguousarray(theta, dtype=np.float64)
+    th_ptr = th.data_ptr() if isinstance(th, torch.Tensor) else th.ctypes.data
+    lo_ptr = logl_out.data_ptr() if isinstance(logl_out, torch.Tensor) else logl_out.ctypes.data
+    gr_ptr = None
+    if grad_out is not None:
+        gr_ptr = grad_out.data_ptr() if isinstance(grad_out, torch.Tensor) else grad_out.ctypes.data
+    W = th.shape[0]
+    check(load().rb_rebuild_loglike_grad_host(event.handle, dp, pp, ctypes.c_void_p(th_ptr), W, ctypes.c_void_p(lo_ptr),
+                                              ctypes.c_void_p(gr_ptr) if gr_ptr else None, _mode(mode),
+                                              _stream_handle(stream)), "rb_rebuild_loglike_grad_host")
+
+
 def loglike_full(event: Event, theta: torch.Tensor, mode="mixed", stream=None) -> torch.Tensor:
     """Full-grid (un-binned) log-likelihood [W] (float64, on theta's device)."""
     th = _theta_dev(theta)

@@ -62,6 +62,43 @@ int cuda_fail(cudaError_t e, const char* what) {
   return set_error(RB_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// Stream-ordered workspace allocations come from a memory pool owned by the
+// library (one per device) that keeps up to 1 GiB of freed memory reserved.
+// The device's default pool returns freed memory at every synchronisation,
+// after which the next allocation maps it again: with a synchronising caller
+// (the host-buffer entry points) that costs more than the kernels.
+static cudaMemPool_t library_pool(int dev) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  static bool tried[64] = {};
+  if (dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!tried[dev]) {
+    tried[dev] = true;
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
+      uint64_t keep = 1ull << 30;
+      if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) == cudaSuccess) pools[dev] = pool;
+      else cudaMemPoolDestroy(pool);
+    } else {
+      cudaGetLastError();  // fall back to the default pool
+    }
+  }
+  return pools[dev];
+}
+
+cudaError_t ws_alloc(void** p, size_t bytes, cudaStream_t s) {
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  cudaMemPool_t pool = library_pool(dev);
+  return pool ? cudaMallocFromPoolAsync(p, bytes, pool, s) : cudaMallocAsync(p, bytes, s);
+}
+
 int sm_count() {
   static std::once_flag once;
   static int n = 0;
@@ -205,6 +242,8 @@ int rb_event_free(rb_event_t ev) {
   if (e.ev_fork) cudaEventDestroy(e.ev_fork);
   if (e.ev_join) cudaEventDestroy(e.ev_join);
   if (e.ev_ref) cudaEventDestroy(e.ev_ref);
+  if (e.ev_data) cudaEventDestroy(e.ev_data);
+  if (e.copy) cudaStreamDestroy(e.copy);
   if (e.side) cudaStreamDestroy(e.side);
   cudaFree(e.d_sync);
   cudaFree(e.d_w32);
@@ -312,7 +351,9 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
     if ((err = cudaStreamCreateWithFlags(&e.side, cudaStreamNonBlocking)) != cudaSuccess ||
         (err = cudaEventCreateWithFlags(&e.ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
         (err = cudaEventCreateWithFlags(&e.ev_join, cudaEventDisableTiming)) != cudaSuccess ||
-        (err = cudaEventCreateWithFlags(&e.ev_ref, cudaEventDisableTiming)) != cudaSuccess) {
+        (err = cudaEventCreateWithFlags(&e.ev_ref, cudaEventDisableTiming)) != cudaSuccess ||
+        (err = cudaStreamCreateWithFlags(&e.copy, cudaStreamNonBlocking)) != cudaSuccess ||
+        (err = cudaEventCreateWithFlags(&e.ev_data, cudaEventDisableTiming)) != cudaSuccess) {
       rc = cuda_fail(err, "rebuild stream and events");
       break;
     }
@@ -442,30 +483,7 @@ int rb_rebuild_loglike_grad(rb_event_t ev, const double* theta_dev, int64_t W, d
   if (mode != RB_MIXED && mode != RB_FP64 && mode != RB_MIXED_F64PHASE)
     return set_error(RB_EINVAL, "rb_rebuild_loglike_grad: bad mode %d", mode);
   if (W > 0 && (!theta_dev || !logl_dev)) return set_error(RB_EINVAL, "rb_rebuild_loglike_grad: NULL theta or logl");
-  EventEntry& e = ev->e;
-  cudaStream_t s = (cudaStream_t)stream;
-  const bool overlap = W > 0 && mode == RB_MIXED && e.kmin >= 1024 && e.N <= (int64_t(1) << 30);
-  if (!overlap) {  // the two calls in sequence
-    int rc = rebuild_event(e, nullptr, mode, s);
-    if (rc != RB_OK || W == 0) return rc;
-    return run_batch(&e, theta_dev, W, logl_dev, grad_dev, mode, s, nullptr);
-  }
-  const bool want_grad = grad_dev != nullptr;
-  const size_t ws_bytes = sizeof(WalkerMixed) * W, tan_bytes = want_grad ? sizeof(WalkerTan<float>) * W : 0;
-  void* buf = nullptr;
-  cudaError_t err = cudaMallocAsync(&buf, ws_bytes + tan_bytes, s);
-  if (err != cudaSuccess) return cuda_fail(err, "cudaMallocAsync workspace");
-  void* tan = want_grad ? static_cast<void*>(static_cast<char*>(buf) + ws_bytes) : nullptr;
-  const SideSetup ss{theta_dev, W, buf, tan, want_grad};
-  int rc = rebuild_event(e, nullptr, mode, s, &ss);
-  if (rc == RB_OK) {
-    if ((err = launch_batch_main(&e, buf, tan, W, logl_dev, grad_dev, mode, s, nullptr)) != cudaSuccess)
-      rc = cuda_fail(err, "likelihood kernel");
-    else
-      count_launches(1);
-  }
-  cudaFreeAsync(buf, s);
-  return rc;
+  return rebuild_and_batch(ev->e, theta_dev, W, logl_dev, grad_dev, mode, (cudaStream_t)stream, nullptr);
 }
 
 int rb_loglike_batch(rb_event_t ev, const double* theta_dev, int64_t W, double* logl_dev, int mode, void* stream) {
@@ -483,15 +501,64 @@ int rb_loglike_grad_host(rb_event_t ev, const double* theta_host, int64_t W, dou
   int rc = RB_OK;
   cudaError_t err;
   do {
-    if ((err = cudaMallocAsync(&d_theta, sizeof(double) * kNPar * W, s)) != cudaSuccess) { rc = cuda_fail(err, "cudaMallocAsync theta"); break; }
-    if ((err = cudaMallocAsync(&d_logl, sizeof(double) * W, s)) != cudaSuccess) { rc = cuda_fail(err, "cudaMallocAsync logl"); break; }
-    if (grad_host && (err = cudaMallocAsync(&d_grad, sizeof(double) * kNPar * W, s)) != cudaSuccess) { rc = cuda_fail(err, "cudaMallocAsync grad"); break; }
+    if ((err = ws_alloc(reinterpret_cast<void**>(&d_theta), sizeof(double) * kNPar * W, s)) != cudaSuccess) { rc = cuda_fail(err, "workspace allocation (theta)"); break; }
+    if ((err = ws_alloc(reinterpret_cast<void**>(&d_logl), sizeof(double) * W, s)) != cudaSuccess) { rc = cuda_fail(err, "workspace allocation (logl)"); break; }
+    if (grad_host && (err = ws_alloc(reinterpret_cast<void**>(&d_grad), sizeof(double) * kNPar * W, s)) != cudaSuccess) { rc = cuda_fail(err, "workspace allocation (grad)"); break; }
     if ((err = cudaMemcpyAsync(d_theta, theta_host, sizeof(double) * kNPar * W, cudaMemcpyHostToDevice, s)) != cudaSuccess) { rc = cuda_fail(err, "copy theta"); break; }
     rc = rb::run_batch(&ev->e, d_theta, W, d_logl, d_grad, mode, s, nullptr);
     if (rc != RB_OK) break;
     if ((err = cudaMemcpyAsync(logl_host, d_logl, sizeof(double) * W, cudaMemcpyDeviceToHost, s)) != cudaSuccess) { rc = cuda_fail(err, "copy logl"); break; }
     if (grad_host && (err = cudaMemcpyAsync(grad_host, d_grad, sizeof(double) * kNPar * W, cudaMemcpyDeviceToHost, s)) != cudaSuccess) { rc = cuda_fail(err, "copy grad"); break; }
   } while (false);
+  if (d_theta) cudaFreeAsync(d_theta, s);
+  if (d_logl) cudaFreeAsync(d_logl, s);
+  if (d_grad) cudaFreeAsync(d_grad, s);
+  err = cudaStreamSynchronize(s);
+  if (rc == RB_OK && err != cudaSuccess) rc = cuda_fail(err, "synchronise");
+  return rc;
+}
+
+int rb_rebuild_loglike_grad_host(rb_event_t ev, const double* const* data_host, const double* const* psd_host,
+                                 const double* theta_host, int64_t W, double* logl_host, double* grad_host, int mode,
+                                 void* stream) {
+  using namespace rb;
+  if (!ev) return set_error(RB_EINVAL, "rb_rebuild_loglike_grad_host: NULL event");
+  if (W < 0) return set_error(RB_EINVAL, "rb_rebuild_loglike_grad_host: W < 0");
+  if (mode != RB_MIXED && mode != RB_FP64 && mode != RB_MIXED_F64PHASE)
+    return set_error(RB_EINVAL, "rb_rebuild_loglike_grad_host: bad mode %d", mode);
+  if (!data_host || !psd_host) return set_error(RB_EINVAL, "rb_rebuild_loglike_grad_host: NULL data or psd");
+  EventEntry& e = ev->e;
+  for (int d = 0; d < e.n_det; ++d)
+    if (!data_host[d] || !psd_host[d]) return set_error(RB_EINVAL, "rb_rebuild_loglike_grad_host: detector %d has NULL data/psd", d);
+  if (W > 0 && (!theta_host || !logl_host)) return set_error(RB_EINVAL, "rb_rebuild_loglike_grad_host: NULL buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  double *d_theta = nullptr, *d_logl = nullptr, *d_grad = nullptr;
+  int rc = RB_OK;
+  cudaError_t err;
+  do {
+    // strain and PSD into the event's resident copy on the copy stream, in
+    // parallel with the data-independent kernels of the rebuild and batch
+    if ((err = cudaEventRecord(e.ev_fork, s)) != cudaSuccess || (err = cudaStreamWaitEvent(e.copy, e.ev_fork, 0)) != cudaSuccess) { rc = cuda_fail(err, "copy fork"); break; }
+    e.w32_resident = false;
+    for (int d = 0; d < e.n_det && err == cudaSuccess; ++d) {
+      err = cudaMemcpyAsync(e.d_data + 2 * (size_t)d * e.N, data_host[d], sizeof(double) * 2 * e.N, cudaMemcpyHostToDevice, e.copy);
+      if (err == cudaSuccess)
+        err = cudaMemcpyAsync(e.d_psd + (size_t)d * e.N, psd_host[d], sizeof(double) * e.N, cudaMemcpyHostToDevice, e.copy);
+    }
+    if (err != cudaSuccess || (err = cudaEventRecord(e.ev_data, e.copy)) != cudaSuccess) { rc = cuda_fail(err, "copy strain"); break; }
+    if (W > 0) {
+      if ((err = ws_alloc(reinterpret_cast<void**>(&d_theta), sizeof(double) * kNPar * W, s)) != cudaSuccess) { rc = cuda_fail(err, "workspace allocation (theta)"); break; }
+      if ((err = ws_alloc(reinterpret_cast<void**>(&d_logl), sizeof(double) * W, s)) != cudaSuccess) { rc = cuda_fail(err, "workspace allocation (logl)"); break; }
+      if (grad_host && (err = ws_alloc(reinterpret_cast<void**>(&d_grad), sizeof(double) * kNPar * W, s)) != cudaSuccess) { rc = cuda_fail(err, "workspace allocation (grad)"); break; }
+      if ((err = cudaMemcpyAsync(d_theta, theta_host, sizeof(double) * kNPar * W, cudaMemcpyHostToDevice, s)) != cudaSuccess) { rc = cuda_fail(err, "copy theta"); break; }
+    }
+    rc = rebuild_and_batch(e, d_theta, W, d_logl, d_grad, mode, s, e.ev_data);
+    if (rc != RB_OK || W == 0) break;
+    if ((err = cudaMemcpyAsync(logl_host, d_logl, sizeof(double) * W, cudaMemcpyDeviceToHost, s)) != cudaSuccess) { rc = cuda_fail(err, "copy logl"); break; }
+    if (grad_host && (err = cudaMemcpyAsync(grad_host, d_grad, sizeof(double) * kNPar * W, cudaMemcpyDeviceToHost, s)) != cudaSuccess) { rc = cuda_fail(err, "copy grad"); break; }
+  } while (false);
+  // the copy stream is joined into `stream` (also when the rebuild failed early)
+  cudaStreamWaitEvent(s, e.ev_data, 0);
   if (d_theta) cudaFreeAsync(d_theta, s);
   if (d_logl) cudaFreeAsync(d_logl, s);
   if (d_grad) cudaFreeAsync(d_grad, s);
@@ -516,8 +583,8 @@ int rb_strain(const double* geom, double gmst, const double* theta_host, double 
   int rc = RB_OK;
   cudaError_t err;
   do {
-    if ((err = cudaMallocAsync(&d_theta, sizeof(double) * kNPar, s)) != cudaSuccess) { rc = cuda_fail(err, "cudaMallocAsync theta"); break; }
-    if ((err = cudaMallocAsync(&d_src, sizeof(RefValues), s)) != cudaSuccess) { rc = cuda_fail(err, "cudaMallocAsync values"); break; }
+    if ((err = ws_alloc(reinterpret_cast<void**>(&d_theta), sizeof(double) * kNPar, s)) != cudaSuccess) { rc = cuda_fail(err, "workspace allocation (theta)"); break; }
+    if ((err = ws_alloc(reinterpret_cast<void**>(&d_src), sizeof(RefValues), s)) != cudaSuccess) { rc = cuda_fail(err, "workspace allocation (values)"); break; }
     if ((err = cudaMemcpyAsync(d_theta, theta_host, sizeof(double) * kNPar, cudaMemcpyHostToDevice, s)) != cudaSuccess) { rc = cuda_fail(err, "copy theta"); break; }
     if ((err = launch_ref_values(d_theta, ec, d_src, s)) != cudaSuccess) { rc = cuda_fail(err, "values kernel"); break; }
     if ((err = launch_strain(d_src, kmin, n_freq, T, h_dev, s)) != cudaSuccess) { rc = cuda_fail(err, "strain kernel"); break; }
@@ -577,6 +644,8 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
     // the FP32 working copy follows the data the sums are taken over: data
     // read in place are converted every time, the resident data only after
     // they change
+    if (ss && ss->data_ready && (err = cudaStreamWaitEvent(s, ss->data_ready, 0)) != cudaSuccess)
+      return cuda_fail(err, "rebuild: wait for the data copies");
     if (in_opt || !e.w32_resident) {
       if ((err = launch_data32(in, e.N, e.n_det, e.d_w32, e.d_is32, e.d_wexp, s)) != cudaSuccess)
         return cuda_fail(err, "data conversion kernel");
@@ -625,8 +694,8 @@ int run_batch(const EventEntry* e, const double* theta, int64_t W, double* logl,
   void* buf = scratch;
   cudaError_t err;
   if (!buf) {
-    err = cudaMallocAsync(&buf, ws_bytes + tan_bytes, s);
-    if (err != cudaSuccess) return cuda_fail(err, "cudaMallocAsync workspace");
+    err = ws_alloc(reinterpret_cast<void**>(&buf), ws_bytes + tan_bytes, s);
+    if (err != cudaSuccess) return cuda_fail(err, "workspace allocation");
   }
   void* ws = buf;
   void* tan = want_grad ? static_cast<void*>(static_cast<char*>(buf) + ws_bytes) : nullptr;
@@ -636,6 +705,38 @@ int run_batch(const EventEntry* e, const double* theta, int64_t W, double* logl,
   if (err != cudaSuccess) rc = cuda_fail(err, "likelihood kernels");
   else count_launches(2);
   if (!scratch) cudaFreeAsync(buf, s);
+  return rc;
+}
+
+// Rebuild from the resident data + batch, the walkers' set-up overlapped with
+// the summary sums when the mixed chunk-expanded rebuild applies.  If
+// data_ready is not NULL the resident data are complete only after it (the
+// data-independent kernels run meanwhile).
+int rebuild_and_batch(EventEntry& e, const double* theta, int64_t W, double* logl, double* grad, int mode,
+                      cudaStream_t s, cudaEvent_t data_ready) {
+  cudaError_t err;
+  const bool overlap = W > 0 && mode == RB_MIXED && e.kmin >= 1024 && e.N <= (int64_t(1) << 30);
+  if (!overlap) {  // the two calls in sequence
+    if (data_ready && (err = cudaStreamWaitEvent(s, data_ready, 0)) != cudaSuccess)
+      return cuda_fail(err, "wait for the data copies");
+    int rc = rebuild_event(e, nullptr, mode, s);
+    if (rc != RB_OK || W == 0) return rc;
+    return run_batch(&e, theta, W, logl, grad, mode, s, nullptr);
+  }
+  const bool want_grad = grad != nullptr;
+  const size_t ws_bytes = sizeof(WalkerMixed) * W, tan_bytes = want_grad ? sizeof(WalkerTan<float>) * W : 0;
+  void* buf = nullptr;
+  if ((err = ws_alloc(reinterpret_cast<void**>(&buf), ws_bytes + tan_bytes, s)) != cudaSuccess) return cuda_fail(err, "workspace allocation");
+  void* tan = want_grad ? static_cast<void*>(static_cast<char*>(buf) + ws_bytes) : nullptr;
+  const SideSetup ss{theta, W, buf, tan, want_grad, data_ready};
+  int rc = rebuild_event(e, nullptr, mode, s, &ss);
+  if (rc == RB_OK) {
+    if ((err = launch_batch_main(&e, buf, tan, W, logl, grad, mode, s, nullptr)) != cudaSuccess)
+      rc = cuda_fail(err, "likelihood kernel");
+    else
+      count_launches(1);
+  }
+  cudaFreeAsync(buf, s);
   return rc;
 }
 

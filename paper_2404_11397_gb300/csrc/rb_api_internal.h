@@ -41,6 +41,8 @@ struct EventEntry {
   cudaStream_t side = nullptr;    // rebuild: branch for the reference values the summary does not use
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_ref = nullptr;   // rebuild + batch: float-float reference values ready
+  cudaStream_t copy = nullptr;    // host-buffer rebuild + batch: strain/PSD copies in
+  cudaEvent_t ev_data = nullptr;  // ... and their completion
   PartDesc* d_parts = nullptr;    // fast build: parts of bins
   float* d_part_sums = nullptr;   // fast build: per-part float-pair sums
   int n_parts = 0;
@@ -82,8 +84,13 @@ struct SideSetup {
   void* ws;
   void* tan;
   bool grad;
+  cudaEvent_t data_ready;  // if not NULL: the resident data are complete only after this event
 };
 int rebuild_event(EventEntry& e, const DataPtrs* in, int mode, cudaStream_t s, const SideSetup* side_setup = nullptr);
+// Stream-ordered allocation from the library's memory pool (see rb_api.cu).
+cudaError_t ws_alloc(void** p, size_t bytes, cudaStream_t s);
+int rebuild_and_batch(EventEntry& e, const double* theta, int64_t W, double* logl, double* grad, int mode,
+                      cudaStream_t s, cudaEvent_t data_ready);
 // The likelihood kernel of a batch whose set-up has been done (trace events around it).
 cudaError_t launch_batch_main(const EventEntry* e, void* ws, void* tan, int64_t W, double* logl, double* grad, int mode,
                               cudaStream_t s, const MalaArgs* mala);

@@ -320,8 +320,8 @@ extern "C" int rb_loglike_full_batch(rb_event_t ev, const double* theta_dev, int
   const int seg_per_slice = (n_seg + n_slices - 1) / n_slices;
   char* buf = nullptr;
   const size_t abs_bytes = sizeof(WalkerAbs) * W, z_bytes = sizeof(double) * 6 * W * n_slices;
-  err = cudaMallocAsync(reinterpret_cast<void**>(&buf), abs_bytes + z_bytes, s);
-  if (err != cudaSuccess) return cuda_fail(err, "rb_loglike_full_batch: cudaMallocAsync");
+  err = ws_alloc(reinterpret_cast<void**>(&buf), abs_bytes + z_bytes, s);
+  if (err != cudaSuccess) return cuda_fail(err, "rb_loglike_full_batch: workspace allocation");
   WalkerAbs* wabs = reinterpret_cast<WalkerAbs*>(buf);
   double* zout = reinterpret_cast<double*>(buf + abs_bytes);
   const double invT = 1.0 / e.T;

@@ -82,8 +82,8 @@ static int mala_run(rb_event_t ev, double* z, double* logp, double* gz, int64_t 
   cudaStream_t s = (cudaStream_t)stream;
   char* buf = nullptr;
   const size_t per = mala_ws_bytes();
-  cudaError_t err = cudaMallocAsync(reinterpret_cast<void**>(&buf), per * W, s);
-  if (err != cudaSuccess) return cuda_fail(err, "cudaMallocAsync MALA workspace");
+  cudaError_t err = ws_alloc(reinterpret_cast<void**>(&buf), per * W, s);
+  if (err != cudaSuccess) return cuda_fail(err, "MALA workspace allocation");
   double* zp = reinterpret_cast<double*>(buf);
   double* theta = zp + kNPar * W;
   double* lu = theta + kNPar * W;

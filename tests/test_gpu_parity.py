@@ -426,3 +426,28 @@ def test_rebuild_and_batch_in_a_cuda_graph(rb, c2):
     torch.testing.assert_close(G, G_ref, rtol=0, atol=0)
     # empty batch: only the rebuild
     assert rb.rebuild_loglike_grad(c2.event, th[:0])[0].numel() == 0
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_rebuild_and_batch_host_equals_two_calls(rb, c2, mode):
+    """Host-buffer step (data copied on the copy stream while the data-free
+    kernels run) against rb_event_rebuild(host data) + rb_loglike_grad_host."""
+    ev = c2.ev
+    D = ev["geom"].shape[0]
+    new = ev["noise"] * 0.5 + ev["signal"]
+    data = [torch.tensor(np.stack([new[d].real, new[d].imag], -1)).pin_memory() for d in range(D)]
+    psd = [torch.tensor(ev["psd"][d]).pin_memory() for d in range(D)]
+    th = synth.posterior_box(ev["theta_inj"], 257, seed=97)
+    L1, G1 = np.zeros(257), np.zeros((257, 13))
+    c2.event.rebuild(data=[d.numpy() for d in data], psd=[p.numpy() for p in psd], mode=mode)
+    rb.loglike_grad_host(c2.event, th, L1, G1, mode=mode)
+    L2, G2 = np.zeros(257), np.zeros((257, 13))
+    rb.rebuild_loglike_grad_host(c2.event, data, psd, th, L2, G2, mode=mode)
+    np.testing.assert_array_equal(L2, L1)
+    np.testing.assert_array_equal(G2, G1)
+    # log L only, then back to the original data (the module's other tests use it)
+    L3 = np.zeros(257)
+    rb.rebuild_loglike_grad_host(c2.event, data, psd, th, L3, None, mode=mode)
+    np.testing.assert_array_equal(L3, L1)
+    orig = [np.ascontiguousarray(np.stack([ev["data"][d].real, ev["data"][d].imag], -1)) for d in range(D)]
+    c2.event.rebuild(data=orig, psd=[ev["psd"][d] for d in range(D)], mode="fp64")
