@@ -40,6 +40,7 @@ cudaError_t launch_summary_fast(const void* w32, const float* is32, const int* e
                                 const int64_t* edges, const RefValues* ref, const void* cq, void* chunk_coef,
                                 const SummaryOut& so, int n_parts, cudaStream_t s);
 cudaError_t launch_ref_dd(const double* theta_ref_dev, const EventConst& ec, RefValues* out, cudaStream_t s);
+cudaError_t launch_tangents(const double* theta, int64_t W, const EventConst& ec, void* tan, cudaStream_t s);
 cudaError_t launch_data32(const DataPtrs& in, int64_t N, int D, void* w32, float* is32, int* exps, cudaStream_t s);
 size_t chunk_coef_bytes(int64_t N);
 
@@ -243,6 +244,8 @@ int rb_event_free(rb_event_t ev) {
   if (e.ev_join) cudaEventDestroy(e.ev_join);
   if (e.ev_ref) cudaEventDestroy(e.ev_ref);
   if (e.ev_data) cudaEventDestroy(e.ev_data);
+  if (e.ev_tan) cudaEventDestroy(e.ev_tan);
+  if (e.tanst) cudaStreamDestroy(e.tanst);
   if (e.copy) cudaStreamDestroy(e.copy);
   if (e.side) cudaStreamDestroy(e.side);
   cudaFree(e.d_sync);
@@ -353,7 +356,9 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
         (err = cudaEventCreateWithFlags(&e.ev_join, cudaEventDisableTiming)) != cudaSuccess ||
         (err = cudaEventCreateWithFlags(&e.ev_ref, cudaEventDisableTiming)) != cudaSuccess ||
         (err = cudaStreamCreateWithFlags(&e.copy, cudaStreamNonBlocking)) != cudaSuccess ||
-        (err = cudaEventCreateWithFlags(&e.ev_data, cudaEventDisableTiming)) != cudaSuccess) {
+        (err = cudaEventCreateWithFlags(&e.ev_data, cudaEventDisableTiming)) != cudaSuccess ||
+        (err = cudaStreamCreateWithFlags(&e.tanst, cudaStreamNonBlocking)) != cudaSuccess ||
+        (err = cudaEventCreateWithFlags(&e.ev_tan, cudaEventDisableTiming)) != cudaSuccess) {
       rc = cuda_fail(err, "rebuild stream and events");
       break;
     }
@@ -618,6 +623,13 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
   if ((err = cudaEventRecord(e.ev_fork, s)) != cudaSuccess || (err = cudaStreamWaitEvent(e.side, e.ev_fork, 0)) != cudaSuccess)
     return cuda_fail(err, "rebuild fork");
   int launches = 3;
+  if (ss && ss->grad) {
+    // the tangents depend on theta only: on their own stream from the start
+    if ((err = cudaStreamWaitEvent(e.tanst, e.ev_fork, 0)) != cudaSuccess) return cuda_fail(err, "rebuild fork");
+    if ((err = launch_tangents(ss->theta, ss->W, e.ec, ss->tan, e.tanst)) != cudaSuccess) return cuda_fail(err, "tangent kernel");
+    if ((err = cudaEventRecord(e.ev_tan, e.tanst)) != cudaSuccess) return cuda_fail(err, "rebuild join");
+    ++launches;
+  }
   if (fast) {
     if (!ss && (err = launch_ref_values(e.d_theta_ref, e.ec, e.d_ref, e.side)) != cudaSuccess)
       return cuda_fail(err, "reference values kernel");
@@ -629,7 +641,7 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
       // set (off the critical path) follows it
       if ((err = cudaEventRecord(e.ev_ref, s)) != cudaSuccess || (err = cudaStreamWaitEvent(e.side, e.ev_ref, 0)) != cudaSuccess)
         return cuda_fail(err, "rebuild fork");
-      if ((err = launch_setup(RB_MIXED, ss->theta, ss->W, e.ec, e.d_ref, ss->ws, ss->tan, ss->grad, e.side)) != cudaSuccess)
+      if ((err = launch_setup(RB_MIXED, ss->theta, ss->W, e.ec, e.d_ref, ss->ws, nullptr, false, e.side)) != cudaSuccess)
         return cuda_fail(err, "set-up kernel");
       if ((err = launch_ref_values(e.d_theta_ref, e.ec, e.d_ref, e.side)) != cudaSuccess)
         return cuda_fail(err, "reference values kernel");
@@ -663,6 +675,7 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
   e.last_in_place = in_opt != nullptr;
   if (err != cudaSuccess) return cuda_fail(err, "summary kernel");
   if ((err = cudaStreamWaitEvent(s, e.ev_join, 0)) != cudaSuccess) return cuda_fail(err, "rebuild join");
+  if (ss && ss->grad && (err = cudaStreamWaitEvent(s, e.ev_tan, 0)) != cudaSuccess) return cuda_fail(err, "rebuild join");
   count_launches(launches);
   return RB_OK;
 }

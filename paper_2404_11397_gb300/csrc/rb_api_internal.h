@@ -41,6 +41,8 @@ struct EventEntry {
   cudaStream_t side = nullptr;    // rebuild: branch for the reference values the summary does not use
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_ref = nullptr;   // rebuild + batch: float-float reference values ready
+  cudaStream_t tanst = nullptr;   // rebuild + batch: the walkers' tangents
+  cudaEvent_t ev_tan = nullptr;
   cudaStream_t copy = nullptr;    // host-buffer rebuild + batch: strain/PSD copies in
   cudaEvent_t ev_data = nullptr;  // ... and their completion
   PartDesc* d_parts = nullptr;    // fast build: parts of bins

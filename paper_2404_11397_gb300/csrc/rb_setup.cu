@@ -983,6 +983,20 @@ cudaError_t launch_setup_abs(const double* theta, int64_t W, const EventConst& e
   return cudaGetLastError();
 }
 
+// The FP32 tangents alone, one warp per tangent group and 32 walkers per
+// block: they depend on theta only, so the combined rebuild + batch runs them
+// on a stream of their own from the start of the call.
+__global__ void __launch_bounds__(kTanWarps * 32) k_tangents(const double* __restrict__ theta, int64_t W, EventConst ec,
+                                                             void* __restrict__ tan_out) {
+  tangent_warp<float>(theta, W, (int64_t)blockIdx.x * kSetupWalkers, ec, tan_out, threadIdx.x >> 5);
+}
+
+cudaError_t launch_tangents(const double* theta, int64_t W, const EventConst& ec, void* tan, cudaStream_t s) {
+  const unsigned grid = (unsigned)((W + kSetupWalkers - 1) / kSetupWalkers);
+  k_tangents<<<grid, kTanWarps * 32, 0, s>>>(theta, W, ec, tan);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ref_dd(const double* theta_ref_dev, const EventConst& ec, RefValues* out, cudaStream_t s) {
   k_ref_dd<<<1, kDdRoleThreads, 0, s>>>(theta_ref_dev, ec, out);
   return cudaGetLastError();
