@@ -182,7 +182,12 @@ RB_API int rb_loglike_grad_batch(rb_event_t ev, const double* theta_dev, int64_t
  * and theta, runs on the event's forked stream concurrently with the summary
  * sums and is joined before the likelihood kernel; otherwise the two calls
  * run in sequence.  theta_dev must be ready on `stream` when the call is
- * made.  Asynchronous; the workspace comes from the stream-ordered pool.
+ * made.  Asynchronous.  The per-walker workspace is kept by the event between
+ * calls: it is allocated (cudaMalloc) when a call needs more than the event
+ * holds and the stream is not being captured; a call captured in a graph
+ * with a larger batch than any before it takes its workspace from the
+ * stream-ordered pool instead.  Outgrown workspaces are released with the
+ * event, so graphs that captured them stay valid while the event lives.
  * Errors: those of the two calls. */
 RB_API int rb_rebuild_loglike_grad(rb_event_t ev, const double* theta_dev, int64_t W, double* logl_dev,
                                    double* grad_dev, int mode, void* stream);

@@ -240,6 +240,8 @@ int rb_event_free(rb_event_t ev) {
   cudaFree(e.d_chunks);
   cudaFree(e.d_invdf);
   cudaFree(e.d_share);
+  cudaFree(e.step_ws);
+  for (int i = 0; i < e.n_step_ws_old; ++i) cudaFree(e.step_ws_old[i]);
   if (e.ev_fork) cudaEventDestroy(e.ev_fork);
   if (e.ev_join) cudaEventDestroy(e.ev_join);
   if (e.ev_ref) cudaEventDestroy(e.ev_ref);
@@ -738,8 +740,24 @@ int rebuild_and_batch(EventEntry& e, const double* theta, int64_t W, double* log
   }
   const bool want_grad = grad != nullptr;
   const size_t ws_bytes = sizeof(WalkerMixed) * W, tan_bytes = want_grad ? sizeof(WalkerTan<float>) * W : 0;
-  void* buf = nullptr;
-  if ((err = ws_alloc(reinterpret_cast<void**>(&buf), ws_bytes + tan_bytes, s)) != cudaSuccess) return cuda_fail(err, "workspace allocation");
+  const size_t need = ws_bytes + tan_bytes;
+  // the event's persistent workspace, grown when the stream is not being
+  // captured; otherwise (or if too many buffers were outgrown) a per-call one
+  if (e.step_ws_bytes < need) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if ((err = cudaStreamIsCapturing(s, &cs)) != cudaSuccess) return cuda_fail(err, "capture query");
+    if (cs == cudaStreamCaptureStatusNone && e.n_step_ws_old < 16) {
+      void* nb = nullptr;
+      if ((err = cudaMalloc(&nb, need)) != cudaSuccess) return cuda_fail(err, "workspace allocation");
+      if (e.step_ws) e.step_ws_old[e.n_step_ws_old++] = e.step_ws;
+      e.step_ws = nb;
+      e.step_ws_bytes = need;
+    }
+  }
+  const bool own = e.step_ws_bytes >= need;
+  void* buf = own ? e.step_ws : nullptr;
+  if (!own && (err = ws_alloc(reinterpret_cast<void**>(&buf), need, s)) != cudaSuccess)
+    return cuda_fail(err, "workspace allocation");
   void* tan = want_grad ? static_cast<void*>(static_cast<char*>(buf) + ws_bytes) : nullptr;
   const SideSetup ss{theta, W, buf, tan, want_grad, data_ready};
   int rc = rebuild_event(e, nullptr, mode, s, &ss);
@@ -749,7 +767,7 @@ int rebuild_and_batch(EventEntry& e, const double* theta, int64_t W, double* log
     else
       count_launches(1);
   }
-  cudaFreeAsync(buf, s);
+  if (!own) cudaFreeAsync(buf, s);
   return rc;
 }
 

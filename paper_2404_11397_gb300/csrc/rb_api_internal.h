@@ -41,6 +41,13 @@ struct EventEntry {
   cudaStream_t side = nullptr;    // rebuild: branch for the reference values the summary does not use
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_ref = nullptr;   // rebuild + batch: float-float reference values ready
+  // rebuild + batch: the walkers' workspace, kept between calls (grown outside
+  // stream capture only; outgrown buffers stay allocated until the event is
+  // freed, so a captured graph never refers to freed memory)
+  void* step_ws = nullptr;
+  size_t step_ws_bytes = 0;
+  void* step_ws_old[16] = {};
+  int n_step_ws_old = 0;
   cudaStream_t tanst = nullptr;   // rebuild + batch: the walkers' tangents
   cudaEvent_t ev_tan = nullptr;
   cudaStream_t copy = nullptr;    // host-buffer rebuild + batch: strain/PSD copies in
