@@ -323,6 +323,95 @@ __device__ __forceinline__ float2 cis_turns(float y) {
   return make_float2(fmaf(-2.f * sn, sn, 1.f), 2.f * sn * cs);
 }
 
+// ---------------------------------------------------------------------------
+// Paired FP32 arithmetic.  V = float evaluates one detector; V = float2
+// evaluates detectors 0 and 1 side by side with the sm_100+ paired
+// instructions (FFMA2 / FADD2 / FMUL2: one issue slot for two lanes of work,
+// each component rounded exactly as the scalar instruction).
+// ---------------------------------------------------------------------------
+namespace pv {
+__device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float neg(float a) { return -a; }
+__device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub(float2 a, float2 b) {
+  float2 r;
+  asm("{.reg .b64 x, y, z;\n\tmov.b64 x, {%2, %3};\n\tmov.b64 y, {%4, %5};\n\tsub.rn.f32x2 z, x, y;\n\tmov.b64 {%0, %1}, z;}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }  // folded into the consumer
+template <class V> __device__ __forceinline__ V splat(float x);
+template <> __device__ __forceinline__ float splat<float>(float x) { return x; }
+template <> __device__ __forceinline__ float2 splat<float2>(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float shfl_down(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ float2 shfl_down(float2 v) {
+  return make_float2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
+}
+__device__ __forceinline__ float shfl_up(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ float2 shfl_up(float2 v) {
+  return make_float2(__shfl_up_sync(0xffffffffu, v.x, 1), __shfl_up_sync(0xffffffffu, v.y, 1));
+}
+
+// s_hi + s_lo += (a_hi + a_lo)(b_hi + b_lo): Dekker product, Knuth sum
+// (the same steps as f2x_fma_acc).
+template <class V>
+__device__ __forceinline__ void fma_acc(V a_hi, V a_lo, V b_hi, V b_lo, V& s_hi, V& s_lo) {
+  const V p = mul(a_hi, b_hi);
+  V e = fma(a_hi, b_hi, neg(p));
+  e = fma(a_hi, b_lo, e);
+  e = fma(a_lo, b_hi, e);
+  const V s = add(s_hi, p);
+  const V bb = sub(s, s_hi);
+  const V err = add(sub(s_hi, sub(s, bb)), sub(p, bb));
+  s_hi = s;
+  s_lo = add(s_lo, add(err, e));
+}
+
+// Fractional part of hi + lo in turns (as frac_turns).
+template <class V>
+__device__ __forceinline__ V frac(V hi, V lo) {
+  const V m = splat<V>(12582912.0f);  // 1.5 * 2^23: round to nearest on the FMA pipe
+  const V r = sub(hi, sub(add(hi, m), m));
+  const V y = add(r, lo);
+  return sub(y, sub(add(y, m), m));
+}
+
+// sin(pi y), cos(pi y) for |y| <= 1/2 (the polynomials of sincos_pi_half).
+template <class V>
+__device__ __forceinline__ void sincos_half(V y, V& s, V& c) {
+  const V w = mul(y, y);
+  V ps = splat<V>(-0.007060864474624395f);
+  ps = fma(ps, w, splat<V>(0.08207154273986816f));
+  ps = fma(ps, w, splat<V>(-0.5992570519447327f));
+  ps = fma(ps, w, splat<V>(2.550163745880127f));
+  ps = fma(ps, w, splat<V>(-9.160392266949202e-08f));  // low part of -pi^3/6
+  ps = fma(ps, w, splat<V>(-8.742277657347586e-08f));  // low part of pi
+  ps = fma(w, splat<V>(-5.167712688446045f), ps);      // high part of -pi^3/6
+  s = fma(y, splat<V>(3.1415927410125732f), mul(y, ps));  // high part of pi
+  V pc = splat<V>(-0.024529997259378433f);
+  pc = fma(pc, w, splat<V>(0.2350243180990219f));
+  pc = fma(pc, w, splat<V>(-1.3352320194244385f));
+  pc = fma(pc, w, splat<V>(4.058711051940918f));
+  pc = fma(pc, w, splat<V>(-1.451857940537593e-07f));  // low part of -pi^2/2
+  c = fma(w, splat<V>(-4.934802055358887f), fma(pc, w, splat<V>(1.0f)));  // high part of -pi^2/2
+}
+
+// hi + lo += v (Knuth two-sum, as f2x_add).
+template <class V>
+__device__ __forceinline__ void add_acc(V& hi, V& lo, V v) {
+  const V s = add(hi, v);
+  const V bb = sub(s, hi);
+  lo = add(lo, add(sub(hi, sub(s, bb)), sub(v, bb)));
+  hi = s;
+}
+}  // namespace pv
+
 // Sum a float over the warp in FP64 (all lanes get the total).
 __device__ __forceinline__ double warp_sum_f64(double v) {
 #pragma unroll

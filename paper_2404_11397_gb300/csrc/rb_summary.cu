@@ -439,7 +439,8 @@ __device__ __forceinline__ float scaled_float(double x, unsigned bias) {
 //   [0 .. 3]    X0 (pair, whole turns dropped), X1 (pair): intrinsic phase
 //   [4 .. 11]   X2 (pair), X3 .. X8
 //   [12 .. 16]  f_c^-7/6, binom(-7/6, n) u^n (n = 1..4)
-//   [18 .. 23]  exp(+2 pi i f_c tau_d) per detector (cos, sin)
+//   [18 .. 19]  exp(+2 pi i f_c tau_d) of the single detector D-1 (D odd)
+//   [20 .. 23]  the same for detectors 0 and 1 (D >= 2): {re_0, re_1, im_0, im_1}
 // The detector delay enters the fiducial phase linearly, x_d(f) = x(f) +
 // f tau_d, so per grid point exp(2 pi i x_d) = exp(2 pi i x) exp(2 pi i f_c
 // tau_d) exp(2 pi i j df tau_d): one sine/cosine per point, the chunk factor
@@ -470,12 +471,15 @@ __global__ void __launch_bounds__(96) k_chunk_coef(const RefValues* __restrict__
       f2x_fma_acc(ch, cl, m[k].z, m[k].w, x1h, x1l);
     }
     reinterpret_cast<float4*>(rec)[0] = make_float4(__fadd_rn(x0h, -round_fma_pipe(x0h)), x0l, x1h, x1l);
+    float2 e[kMaxDet];
 #pragma unroll
     for (int d = 0; d < kMaxDet; ++d) {
       float ah = 0.f, al = 0.f;
       if (d < D) f2x_fma_acc(ref->taut[d][0], ref->taut[d][1], fc.x, fc.y, ah, al);
-      reinterpret_cast<float2*>(rec)[9 + d] = cis_turns(frac_turns(ah, al));
+      e[d] = cis_turns(frac_turns(ah, al));
     }
+    if (D >= 2) reinterpret_cast<float4*>(rec)[5] = make_float4(e[0].x, e[1].x, e[0].y, e[1].y);
+    if (D & 1) reinterpret_cast<float2*>(rec)[9] = e[D - 1];
   } else if (task == 1) {
     float4 m[kNBasis / 2];
 #pragma unroll
@@ -557,12 +561,16 @@ static_assert(kPartPoints % kSumFastThreads == 0, "parts are whole rounds of the
 // nearly cancels within a bin, a float pair); block sums are float pairs in a
 // fixed order; the parts of a bin are added in index order by the last of
 // them to finish, which then runs the FP64 epilogue.
+template <int ND>
 __global__ void __launch_bounds__(kSumFastThreads, 6)
     k_summary_fast(const float2* __restrict__ w32, const float* __restrict__ is32, const int* __restrict__ exps,
                    int N, const float* __restrict__ chunks, double T, float invT_hi, float invT_lo, int B, int D,
                    const int64_t* __restrict__ edges, const RefValues* __restrict__ ref, SummaryOut so) {
   __shared__ __align__(16) float srec[kPartRecs * kRec];
-  __shared__ float2 toff[kMaxDet][kChunk];  // exp(2 pi i j df tau_d), indexed by k mod 32
+  // exp(2 pi i j df tau_d), indexed by k mod 32: detectors 0 and 1 as
+  // {re_0, re_1, im_0, im_1}, the single detector D-1 as {re, im}
+  __shared__ float4 toffP[kChunk];
+  __shared__ float2 toffS[kChunk];
   __shared__ float red[kSumFastThreads / 32][kNAcc * 33];  // per-thread partials, one row per quantity
   __shared__ float wsum[kSumFastThreads / 32][kNAcc][2];
   __shared__ float qsum[kNAcc][2];
@@ -584,7 +592,13 @@ __global__ void __launch_bounds__(kSumFastThreads, 6)
     const float jf = small_int_float(j);
     const float p = __fmul_rn(sh, jf);
     const float e = __fmaf_rn(sl, jf, __fmaf_rn(sh, jf, -p));
-    toff[d][lane] = cis_turns(frac_turns(p, e));
+    const float2 t = cis_turns(frac_turns(p, e));
+    if (ND >= 2 && d < 2) {
+      float* tp = reinterpret_cast<float*>(&toffP[lane]);
+      tp[d] = t.x;
+      tp[2 + d] = t.y;
+    }
+    if ((ND & 1) && d == ND - 1) toffS[lane] = t;
   } else if (tid >= 96 && tid < 96 + D) {
     // undo the power-of-two scales of the FP32 data copy (d 2^sd, S 2^sS)
     const int d = tid - 96;
@@ -598,11 +612,16 @@ __global__ void __launch_bounds__(kSumFastThreads, 6)
   } else if (tid == 127) {
     s_inv_df = so.inv_df[b];
   }
-  float acc[kNAcc];
+  // per-thread sums, kNQ per detector: detectors 0 and 1 paired, D-1 single
+  float2 accP[kNQ];
+  float accS[kNQ];
 #pragma unroll
-  for (int i = 0; i < kNAcc; ++i) acc[i] = 0.f;
+  for (int i = 0; i < kNQ; ++i) {
+    accP[i] = make_float2(0.f, 0.f);
+    accS[i] = 0.f;
+  }
   float2 dv[kMaxDet], dn[kMaxDet];  // w = d'/S'
-  float pv[kMaxDet], pn[kMaxDet];   // 1/S'
+  float isv[kMaxDet], pn[kMaxDet];  // 1/S'
   auto load_point = [&](int k, float2* dd, float* pp) {
 #pragma unroll
     for (int d = 0; d < kMaxDet; ++d)
@@ -624,7 +643,7 @@ __global__ void __launch_bounds__(kSumFastThreads, 6)
 #pragma unroll
     for (int d = 0; d < kMaxDet; ++d) {
       dv[d] = dn[d];
-      pv[d] = pn[d];
+      isv[d] = pn[d];
     }
     if (k + kSumFastThreads < ke) load_point(k + kSumFastThreads, dn, pn);
     const float4* rec = reinterpret_cast<const float4*>(srec + ((k >> 5) - c0) * kRec);
@@ -652,31 +671,60 @@ __global__ void __launch_bounds__(kSumFastThreads, 6)
     const float A = a0.x * fmaf(jf, fmaf(jf, fmaf(jf, fmaf(jf, a4, a0.w), a0.z), a0.y), 1.f);
     const float A2 = A * A;
     const float dff = int_float_fma(2 * (k - e0) - w) * half_df;  // f - f_m
-#pragma unroll
-    for (int d = 0; d < kMaxDet; ++d) {
-      if (d < D) {
-        const float2 ec = reinterpret_cast<const float2*>(rec)[9 + d];  // exp(2 pi i f_c tau_d)
-        const float2 eo = toff[d][k & (kChunk - 1)];                    // exp(2 pi i j df tau_d)
-        const float fr = fmaf(ec.x, eo.x, -ec.y * eo.y), fi = fmaf(ec.x, eo.y, ec.y * eo.x);
-        const float Cc = fmaf(z.x, fr, -z.y * fi), Ss = fmaf(z.x, fi, z.y * fr);  // exp(+2 pi i x_d)
-        const float dr = dv[d].x * A, di = dv[d].y * A;
-        const float qr = fmaf(dr, Cc, -di * Ss), qi = fmaf(dr, Ss, di * Cc);
-        acc[kNQ * d + 0] += qr;
-        acc[kNQ * d + 1] += qi;
-        acc[kNQ * d + 2] = fmaf(qr, dff, acc[kNQ * d + 2]);
-        acc[kNQ * d + 3] = fmaf(qi, dff, acc[kNQ * d + 3]);
-        const float hh = A2 * pv[d];
-        acc[kNQ * d + 4] += hh;
-        // B1 (|h0|^2 / S weighted by f - f_m > 0 or < 0) nearly cancels within a
-        // bin: its per-thread sum is a float pair (hi, lo)
-        f2x_add(acc[kNQ * d + 5], acc[kNQ * d + 6], hh * dff);
-      }
+    if constexpr (ND >= 2) {  // detectors 0 and 1, paired
+      const float4 ep = rec[5];                 // exp(2 pi i f_c tau_d)
+      const float4 tp = toffP[k & (kChunk - 1)];  // exp(2 pi i j df tau_d)
+      const float2 er = make_float2(ep.x, ep.y), ei = make_float2(ep.z, ep.w);
+      const float2 tr = make_float2(tp.x, tp.y), ti = make_float2(tp.z, tp.w);
+      const float2 fr = pv::fma(er, tr, pv::mul(pv::neg(ei), ti)), fi = pv::fma(er, ti, pv::mul(ei, tr));
+      const float2 zx = make_float2(z.x, z.x), zy = make_float2(z.y, z.y);
+      const float2 Cc = pv::fma(zx, fr, pv::mul(pv::neg(zy), fi)), Ss = pv::fma(zx, fi, pv::mul(zy, fr));
+      const float2 AA = make_float2(A, A);
+      const float2 dr = pv::mul(make_float2(dv[0].x, dv[1].x), AA), di = pv::mul(make_float2(dv[0].y, dv[1].y), AA);
+      const float2 qr = pv::fma(dr, Cc, pv::mul(pv::neg(di), Ss)), qi = pv::fma(dr, Ss, pv::mul(di, Cc));
+      const float2 D2 = make_float2(dff, dff);
+      accP[0] = pv::add(accP[0], qr);
+      accP[1] = pv::add(accP[1], qi);
+      accP[2] = pv::fma(qr, D2, accP[2]);
+      accP[3] = pv::fma(qi, D2, accP[3]);
+      const float2 hh = pv::mul(make_float2(A2, A2), make_float2(isv[0], isv[1]));
+      accP[4] = pv::add(accP[4], hh);
+      // B1 (|h0|^2 / S weighted by f - f_m > 0 or < 0) nearly cancels within a
+      // bin: its per-thread sum is a float pair (hi, lo)
+      pv::add_acc(accP[5], accP[6], pv::mul(hh, D2));
+    }
+    if constexpr ((ND & 1) != 0) {  // the single detector D-1
+      constexpr int d = ND - 1;
+      const float2 ec = reinterpret_cast<const float2*>(rec)[9];  // exp(2 pi i f_c tau_d)
+      const float2 eo = toffS[k & (kChunk - 1)];                  // exp(2 pi i j df tau_d)
+      const float fr = fmaf(ec.x, eo.x, -ec.y * eo.y), fi = fmaf(ec.x, eo.y, ec.y * eo.x);
+      const float Cc = fmaf(z.x, fr, -z.y * fi), Ss = fmaf(z.x, fi, z.y * fr);  // exp(+2 pi i x_d)
+      const float dr = dv[d].x * A, di = dv[d].y * A;
+      const float qr = fmaf(dr, Cc, -di * Ss), qi = fmaf(dr, Ss, di * Cc);
+      accS[0] += qr;
+      accS[1] += qi;
+      accS[2] = fmaf(qr, dff, accS[2]);
+      accS[3] = fmaf(qi, dff, accS[3]);
+      const float hh = A2 * isv[d];
+      accS[4] += hh;
+      f2x_add(accS[5], accS[6], hh * dff);
     }
   }
   // ---- block sums in float pairs, fixed order: lanes 0..20 of each warp sum
   // one quantity over the warp's 32 threads, then 21 threads sum the warp
   // totals (A1 and B1 cancel strongly within a bin, so no stage of this sum
   // is plain FP32) ----
+  float acc[kNAcc];
+#pragma unroll
+  for (int q = 0; q < kNQ; ++q) {
+#pragma unroll
+    for (int d = 0; d < kMaxDet; ++d) acc[kNQ * d + q] = 0.f;
+    if (ND >= 2) {
+      acc[q] = accP[q].x;
+      acc[kNQ + q] = accP[q].y;
+    }
+    if (ND & 1) acc[kNQ * (ND - 1) + q] = accS[q];
+  }
   float* wr = red[wid];
 #pragma unroll
   for (int i = 0; i < kNAcc; ++i) wr[i * 33 + lane] = acc[i];
@@ -800,8 +848,9 @@ cudaError_t launch_summary_fast(const void* w32, const float* is32, const int* e
   k_chunk_coef<<<(unsigned)((nc + 31) / 32), 96, 0, s>>>(ref, static_cast<const float*>(cq), D, nc, ch);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  k_summary_fast<<<n_parts, kSumFastThreads, 0, s>>>(static_cast<const float2*>(w32), is32, exps, (int)N, ch, T, ih, il,
-                                                      B, D, edges, ref, so);
+  auto kf = D == 1 ? k_summary_fast<1> : D == 2 ? k_summary_fast<2> : k_summary_fast<3>;
+  kf<<<n_parts, kSumFastThreads, 0, s>>>(static_cast<const float2*>(w32), is32, exps, (int)N, ch, T, ih, il, B, D, edges,
+                                         ref, so);
   return cudaGetLastError();
 }
 
