@@ -17,16 +17,17 @@
 //
 // Mapping: a block of 8 warps owns 8 walkers (one per warp) and one slice of
 // the grid (blockIdx.y), which it walks in segments of 32 chunks (1024
-// points); the number of slices is picked so the grid fills whole waves.  Per segment the block
-// stages the chunk matrices and the FP32 data copy times f^-7/6 in shared
-// memory (read once for the 8 walkers; the event's data stay in L2); lane l
-// of a warp forms its walker's coefficients for chunk l, then evaluates the
-// points l, l + 32, ... of the segment, which all have the in-chunk offset
-// j = l - 16, so its delay factor exp(2 pi i j df tau_d) is a constant that
-// is applied once to the lane's sum, after the loop.  Per point: the chunk
-// record (five 16-byte broadcast loads), the phase polynomial, one sin/cos,
-// and per detector exp(2 pi i f_c tau_d) times the point's phasor times the
-// data.  Per-lane sums are FP32 per segment, accumulated in float pairs; the
+// points); the number of slices is picked so the grid fills whole waves.  Per
+// segment the block stages the chunk matrices and the FP32 data copy times
+// f^-7/6 in shared memory, the data transposed (read once for the 8 walkers;
+// the event's data stay in L2).  Lane c of a warp forms its walker's Taylor
+// coefficients and chunk factors exp(2 pi i f_c tau_d) for chunk c, keeps them
+// in registers and walks the chunk's 32 points; the offset factors
+// exp(2 pi i (j - 16) df tau_d), the same for all lanes at a given offset j,
+// come from a per-warp table (broadcast loads), and the chunk factor is
+// applied once to the chunk's sum.  Per point: the phase polynomial, one
+// sin/cos, and per detector the offset factor times the phasor times the
+// data.  Per-lane sums are FP32 per chunk, accumulated in float pairs; the
 // warp sum and the final combination are FP64.
 #include <algorithm>
 #include <cmath>
@@ -42,9 +43,10 @@ constexpr int kFullWarps = 8;
 constexpr int kFullThreads = kFullWarps * 32;
 constexpr int kSegC = 32;                 // chunks per segment
 constexpr int kSegP = kSegC * kChunk;     // points per segment
-constexpr int kFRec = 20;                 // floats per walker-chunk record
-constexpr size_t kFullSmem = sizeof(float) * kSegC * kQRow + sizeof(float2) * kMaxDet * kSegP +
-                             sizeof(float) * kFullWarps * kSegC * kFRec;
+constexpr int kWtRow = kSegC + 1;       // transposed data row (padded: conflict-free stores)
+constexpr int kQPad = kQRow + 1;        // staged chunk-matrix row (padded: lane c reads row c without conflicts)
+constexpr size_t kFullSmem = sizeof(float) * (kSegC * kQPad + 1) + sizeof(float2) * kMaxDet * kChunk * kWtRow +
+                             sizeof(float2) * kFullWarps * kChunk * kMaxDet;
 
 // Per slice and walker: the slice's part of Z_d (complex, 3 detectors) as
 // FP64 in zout[slice][w][6].  ND = number of detectors.
@@ -54,12 +56,13 @@ __global__ void __launch_bounds__(kFullThreads) k_full_z(const float2* __restric
                                                         const WalkerAbs* __restrict__ wabs, int64_t W,
                                                         float invT_hi, float invT_lo, int seg_per_slice,
                                                         double* __restrict__ zout) {
-  // dynamic shared memory: chunk matrices of the segment, (d'/S') f^-7/6,
-  // per-walker chunk coefficients
+  // dynamic shared memory: the segment's chunk matrices; its data times
+  // f^-7/6 transposed, wt[d][j][c] for point c * 32 + j of the segment; and per
+  // warp the walker's offset factors exp(2 pi i (j - 16) df tau_d), tw[j][d]
   extern __shared__ __align__(16) unsigned char smem_full[];
   float* qs = reinterpret_cast<float*>(smem_full);
-  float2 (*wa)[kSegP] = reinterpret_cast<float2 (*)[kSegP]>(qs + kSegC * kQRow);
-  float (*rec)[kSegC][kFRec] = reinterpret_cast<float (*)[kSegC][kFRec]>(wa + kMaxDet);
+  float2 (*wt)[kChunk][kWtRow] = reinterpret_cast<float2 (*)[kChunk][kWtRow]>(qs + kSegC * kQPad + (kSegC * kQPad) % 2);
+  float2 (*tw)[kChunk][kMaxDet] = reinterpret_cast<float2 (*)[kChunk][kMaxDet]>(wt + kMaxDet);
   constexpr int D = ND;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t w = (int64_t)blockIdx.x * kFullWarps + warp;
@@ -79,15 +82,17 @@ __global__ void __launch_bounds__(kFullThreads) k_full_z(const float2* __restric
     p0[0] = p0[1] = 0.f;
     for (int d = 0; d < kMaxDet; ++d) tt[d][0] = tt[d][1] = 0.f;
   }
-  // this lane's in-chunk offset j = lane - 16 and delay factors exp(2 pi i j df tau_d)
-  const float jf = small_int_float(lane - kChunk / 2);
-  float2 toff[kMaxDet];
-  for (int d = 0; d < kMaxDet; ++d) {
-    float sh = 0.f, sl = 0.f;
-    f2x_fma_acc(tt[d][0], tt[d][1], invT_hi, invT_lo, sh, sl);  // tau_d df
-    const float p = __fmul_rn(sh, jf);
-    const float e = __fmaf_rn(sl, jf, __fmaf_rn(sh, jf, -p));
-    toff[d] = cis_turns(frac_turns(p, e));
+  // offset factors of the walker: lane j forms exp(2 pi i (j - 16) df tau_d)
+  {
+    const float jf = small_int_float(lane - kChunk / 2);
+#pragma unroll
+    for (int d = 0; d < kMaxDet; ++d) {
+      float sh = 0.f, sl = 0.f;
+      f2x_fma_acc(tt[d][0], tt[d][1], invT_hi, invT_lo, sh, sl);  // tau_d df
+      const float p = __fmul_rn(sh, jf);
+      const float e = __fmaf_rn(sl, jf, __fmaf_rn(sh, jf, -p));
+      tw[warp][lane][d] = cis_turns(frac_turns(p, e));
+    }
   }
   float zh[kMaxDet][2], zl[kMaxDet][2];  // Z_d as float pairs (re, im)
   for (int d = 0; d < kMaxDet; ++d) zh[d][0] = zh[d][1] = zl[d][0] = zl[d][1] = 0.f;
@@ -95,112 +100,110 @@ __global__ void __launch_bounds__(kFullThreads) k_full_z(const float2* __restric
   const int sg0 = blockIdx.y * seg_per_slice, sg1 = min(n_seg, sg0 + seg_per_slice);
   for (int sg = sg0; sg < sg1; ++sg) {
     const int c0 = sg * kSegC, nc = min(kSegC, n_chunks - c0);
-    __syncthreads();  // the previous segment is no longer read
+    __syncthreads();  // the previous segment is no longer read (and tw is written)
     {
-      const float4* src = reinterpret_cast<const float4*>(q + (size_t)c0 * kQRow);
-      float4* dst = reinterpret_cast<float4*>(qs);
-      for (int i = tid; i < nc * (kQRow / 4); i += kFullThreads) dst[i] = __ldg(src + i);
-    }
-    for (int i = tid; i < D * kSegP; i += kFullThreads) {
-      const int d = i / kSegP, p = i - d * kSegP;
-      const int k = c0 * kChunk + p;
-      wa[d][p] = (k < N) ? __ldg(w32 + (size_t)d * N + k) : make_float2(0.f, 0.f);
+      const float* src = q + (size_t)c0 * kQRow;
+      for (int i = tid; i < nc * kQRow; i += kFullThreads) {
+        const int c = i / kQRow;
+        qs[c * kQPad + (i - c * kQRow)] = __ldg(src + i);
+      }
     }
     __syncthreads();
-    // amplitude f^-7/6 = f_c^-7/6 (1 + j u)^-7/6 from the chunk's series
+    // data times f^-7/6 = f_c^-7/6 (1 + j u)^-7/6 (chunk series), transposed;
+    // points past the grid are zero
     for (int i = tid; i < D * kSegP; i += kFullThreads) {
       const int d = i / kSegP, p = i - d * kSegP;
-      const float* qa = qs + (p >> 5) * kQRow + kQamp;
-      const float j = small_int_float((p & (kChunk - 1)) - kChunk / 2);
-      const float A = qa[0] * fmaf(j, fmaf(j, fmaf(j, fmaf(j, qa[4], qa[3]), qa[2]), qa[1]), 1.f);
-      const float2 v = wa[d][p];
-      wa[d][p] = make_float2(v.x * A, v.y * A);
+      const int c = p >> 5, jj = p & (kChunk - 1);
+      const int k = c0 * kChunk + p;
+      float2 v = make_float2(0.f, 0.f);
+      if (c < nc && k < N) {
+        const float* qa = qs + c * kQPad + kQamp;
+        const float j = small_int_float(jj - kChunk / 2);
+        const float A = qa[0] * fmaf(j, fmaf(j, fmaf(j, fmaf(j, qa[4], qa[3]), qa[2]), qa[1]), 1.f);
+        v = __ldg(w32 + (size_t)d * N + k);
+        v = make_float2(v.x * A, v.y * A);
+      }
+      wt[d][jj][c] = v;
     }
-    // this walker's coefficients of chunk `lane` (X0 with Phi0, whole turns dropped)
-    if (lane < nc) {
-      const float* row = qs + lane * kQRow;
-      float x0h = p0[0], x0l = p0[1], x1h = 0.f, x1l = 0.f, x2h = 0.f, x2l = 0.f, xn[kOrd - 2];
+    // lane c: the walker's coefficients of chunk c (X0 with Phi0, whole turns
+    // dropped) and the chunk factors exp(2 pi i f_c tau_d), in registers
+    float X0h = 0.f, X0l = 0.f, X1h = 0.f, X1l = 0.f, X2h = 0.f, X2l = 0.f, xn[kOrd - 2];
+    float2 E[kMaxDet];
 #pragma unroll
-      for (int n = 0; n < kOrd - 2; ++n) xn[n] = 0.f;
+    for (int n = 0; n < kOrd - 2; ++n) xn[n] = 0.f;
+#pragma unroll
+    for (int d = 0; d < kMaxDet; ++d) E[d] = make_float2(1.f, 0.f);
+    const bool act = live && valid && lane < nc;
+    if (act) {
+      const float* row = qs + lane * kQPad;
+      X0h = p0[0];
+      X0l = p0[1];
 #pragma unroll
       for (int k = 0; k < kNBasis; ++k) {
         const float a = ch[k][0], b = ch[k][1];
-        f2x_fma_acc(a, b, row[kQ01 + 4 * k], row[kQ01 + 4 * k + 1], x0h, x0l);
-        f2x_fma_acc(a, b, row[kQ01 + 4 * k + 2], row[kQ01 + 4 * k + 3], x1h, x1l);
-        f2x_fma_acc(a, b, row[kQ2 + 2 * k], row[kQ2 + 2 * k + 1], x2h, x2l);
+        f2x_fma_acc(a, b, row[kQ01 + 4 * k], row[kQ01 + 4 * k + 1], X0h, X0l);
+        f2x_fma_acc(a, b, row[kQ01 + 4 * k + 2], row[kQ01 + 4 * k + 3], X1h, X1l);
+        f2x_fma_acc(a, b, row[kQ2 + 2 * k], row[kQ2 + 2 * k + 1], X2h, X2l);
 #pragma unroll
         for (int n = 0; n < kOrd - 2; ++n) xn[n] = fmaf(a, row[kQh + n * kNBasis + k], xn[n]);
       }
-      float* r = rec[warp][lane];
-      r[0] = __fadd_rn(x0h, -round_fma_pipe(x0h));
-      r[1] = x0l;
-      r[2] = x1h;
-      r[3] = x1l;
-      r[4] = x2h;
-      r[5] = x2l;
-#pragma unroll
-      for (int n = 0; n < kOrd - 2; ++n) r[6 + n] = xn[n];
+      X0h = __fadd_rn(X0h, -round_fma_pipe(X0h));
       const float fch = row[kQfc], fcl = row[kQfc + 1];
 #pragma unroll
-      for (int d = 0; d < kMaxDet; ++d) {
+      for (int d = 0; d < D; ++d) {
         float ah = 0.f, al = 0.f;
         f2x_fma_acc(tt[d][0], tt[d][1], fch, fcl, ah, al);  // f_c tau_d
-        const float2 e = cis_turns(frac_turns(ah, al));
-        r[12 + 2 * d] = e.x;
-        r[13 + 2 * d] = e.y;
+        E[d] = cis_turns(frac_turns(ah, al));
       }
     }
-    __syncthreads();
-    if (!live || !valid) continue;
+    __syncthreads();  // wt complete
+    if (!act) continue;
     float acc[kMaxDet][2];
 #pragma unroll
     for (int d = 0; d < kMaxDet; ++d) acc[d][0] = acc[d][1] = 0.f;
-    for (int c = 0; c < nc; ++c) {
-      const int p = c * kChunk + lane;
-      const float4* r4 = reinterpret_cast<const float4*>(rec[warp][c]);
-      const float4 qa = r4[0], qb = r4[1], qc = r4[2];  // X0 hi/lo, X1 hi/lo | X2 hi/lo, X3, X4 | X5..X8
+#pragma unroll 2
+    for (int jj = 0; jj < kChunk; ++jj) {
+      const float jf = small_int_float(jj - kChunk / 2);
       // x = X0 + X1 j + X2 j^2 + j^3 (X3 + ... + X8 j^5)
-      const float t = fmaf(fmaf(fmaf(fmaf(fmaf(qc.w, jf, qc.z), jf, qc.y), jf, qc.x), jf, qb.w), jf, qb.z);
+      const float t = fmaf(fmaf(fmaf(fmaf(fmaf(xn[5], jf, xn[4]), jf, xn[3]), jf, xn[2]), jf, xn[1]), jf, xn[0]);
       const float j2 = jf * jf;
       const float t3 = t * (j2 * jf);
-      const float p1 = __fmul_rn(qa.z, jf);
-      float e1 = __fmaf_rn(qa.z, jf, -p1);
-      e1 = __fmaf_rn(qa.w, jf, e1);
-      const float p2 = __fmul_rn(qb.x, j2);
-      float e2 = __fmaf_rn(qb.x, j2, -p2);
-      e2 = __fmaf_rn(qb.y, j2, e2);
-      float sh = qa.x, sl = qa.y;
+      const float p1 = __fmul_rn(X1h, jf);
+      float e1 = __fmaf_rn(X1h, jf, -p1);
+      e1 = __fmaf_rn(X1l, jf, e1);
+      const float p2 = __fmul_rn(X2h, j2);
+      float e2 = __fmaf_rn(X2h, j2, -p2);
+      e2 = __fmaf_rn(X2l, j2, e2);
+      float sh = X0h, sl = X0l;
       f2x_add(sh, sl, p1);
       f2x_add(sh, sl, p2);
       sl = __fadd_rn(sl, __fadd_rn(__fadd_rn(e1, e2), t3));
       const float2 z = cis_turns(frac_turns(sh, sl));  // exp(+2 pi i x)
-      const float4 ea = r4[3];  // exp(2 pi i f_c tau_d): d = 0, 1
-      const float2 eb = *reinterpret_cast<const float2*>(r4 + 4);  // d = 2
-      const float er[kMaxDet] = {ea.x, ea.z, eb.x}, ei[kMaxDet] = {ea.y, ea.w, eb.y};
 #pragma unroll
       for (int d = 0; d < D; ++d) {
-        const float ur = fmaf(z.x, er[d], -z.y * ei[d]), ui = fmaf(z.x, ei[d], z.y * er[d]);
-        const float2 v = wa[d][p];
+        const float2 T = tw[warp][jj][d];  // exp(2 pi i (j - 16) df tau_d), same for all lanes
+        const float ur = fmaf(z.x, T.x, -z.y * T.y), ui = fmaf(z.x, T.y, z.y * T.x);
+        const float2 v = wt[d][jj][lane];
         acc[d][0] = fmaf(v.x, ur, fmaf(-v.y, ui, acc[d][0]));
         acc[d][1] = fmaf(v.x, ui, fmaf(v.y, ur, acc[d][1]));
       }
     }
+    // the chunk factor, once per chunk, then into the lane's float pairs
 #pragma unroll
-    for (int d = 0; d < kMaxDet; ++d) {
-      f2x_add(zh[d][0], zl[d][0], acc[d][0]);
-      f2x_add(zh[d][1], zl[d][1], acc[d][1]);
+    for (int d = 0; d < D; ++d) {
+      const float gr = fmaf(E[d].x, acc[d][0], -E[d].y * acc[d][1]);
+      const float gi = fmaf(E[d].x, acc[d][1], E[d].y * acc[d][0]);
+      f2x_add(zh[d][0], zl[d][0], gr);
+      f2x_add(zh[d][1], zl[d][1], gi);
     }
   }
   if (!live) return;
   double* zo = zout + ((size_t)blockIdx.y * W + w) * 6;
-  // the lane's delay factor exp(2 pi i j df tau_d), then warp sums in FP64
-  // (lane order fixed by the butterfly)
+  // warp sums in FP64 (lane order fixed by the butterfly)
 #pragma unroll
   for (int d = 0; d < kMaxDet; ++d) {
-    const double sr = (double)zh[d][0] + (double)zl[d][0], si = (double)zh[d][1] + (double)zl[d][1];
-    const double tr = toff[d].x, ti = toff[d].y;
-    const double re = warp_sum_f64(sr * tr - si * ti);
-    const double im = warp_sum_f64(sr * ti + si * tr);
+    const double re = warp_sum_f64((double)zh[d][0] + (double)zl[d][0]);
+    const double im = warp_sum_f64((double)zh[d][1] + (double)zl[d][1]);
     if (lane == 0) {
       zo[2 * d] = valid ? re : 0.0;
       zo[2 * d + 1] = valid ? im : 0.0;
