@@ -45,8 +45,8 @@ constexpr int kSegC = 32;                 // chunks per segment
 constexpr int kSegP = kSegC * kChunk;     // points per segment
 constexpr int kWtRow = kSegC + 1;       // transposed data row (padded: conflict-free stores)
 constexpr int kQPad = kQRow + 1;        // staged chunk-matrix row (padded: lane c reads row c without conflicts)
-constexpr size_t kFullSmem = sizeof(float) * (kSegC * kQPad + 1) + sizeof(float2) * kMaxDet * kChunk * kWtRow +
-                             sizeof(float2) * kFullWarps * kChunk * kMaxDet;
+constexpr size_t kFullSmem = sizeof(float) * (kSegC * kQPad + 4) + (sizeof(float4) + sizeof(float2)) * kChunk * kWtRow +
+                             (sizeof(float4) + sizeof(float2)) * kFullWarps * kChunk;
 
 // Per slice and walker: the slice's part of Z_d (complex, 3 detectors) as
 // FP64 in zout[slice][w][6].  ND = number of detectors.
@@ -57,12 +57,18 @@ __global__ void __launch_bounds__(kFullThreads) k_full_z(const float2* __restric
                                                         float invT_hi, float invT_lo, int seg_per_slice,
                                                         double* __restrict__ zout) {
   // dynamic shared memory: the segment's chunk matrices; its data times
-  // f^-7/6 transposed, wt[d][j][c] for point c * 32 + j of the segment; and per
-  // warp the walker's offset factors exp(2 pi i (j - 16) df tau_d), tw[j][d]
+  // f^-7/6 transposed, for point c * 32 + j of the segment at [j][c] --
+  // detectors 0 and 1 as {re_0, re_1, im_0, im_1} (wp), the single detector
+  // D-1 as {re, im} (ws); and per warp the walker's offset factors
+  // exp(2 pi i (j - 16) df tau_d) in the same two forms (tp, ts)
   extern __shared__ __align__(16) unsigned char smem_full[];
   float* qs = reinterpret_cast<float*>(smem_full);
-  float2 (*wt)[kChunk][kWtRow] = reinterpret_cast<float2 (*)[kChunk][kWtRow]>(qs + kSegC * kQPad + (kSegC * kQPad) % 2);
-  float2 (*tw)[kChunk][kMaxDet] = reinterpret_cast<float2 (*)[kChunk][kMaxDet]>(wt + kMaxDet);
+  float4 (*wp)[kWtRow] = reinterpret_cast<float4 (*)[kWtRow]>(qs + kSegC * kQPad + 4 - (kSegC * kQPad) % 4);
+  float2 (*ws)[kWtRow] = reinterpret_cast<float2 (*)[kWtRow]>(wp + kChunk);
+  float4 (*tp)[kChunk] = reinterpret_cast<float4 (*)[kChunk]>(ws + kChunk);
+  float2 (*ts)[kChunk] = reinterpret_cast<float2 (*)[kChunk]>(tp + kFullWarps);
+  constexpr bool kPair = ND >= 2;
+  constexpr int kSingle = (ND & 1) ? ND - 1 : -1;
   constexpr int D = ND;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t w = (int64_t)blockIdx.x * kFullWarps + warp;
@@ -85,14 +91,17 @@ __global__ void __launch_bounds__(kFullThreads) k_full_z(const float2* __restric
   // offset factors of the walker: lane j forms exp(2 pi i (j - 16) df tau_d)
   {
     const float jf = small_int_float(lane - kChunk / 2);
+    float2 t[kMaxDet];
 #pragma unroll
     for (int d = 0; d < kMaxDet; ++d) {
       float sh = 0.f, sl = 0.f;
       f2x_fma_acc(tt[d][0], tt[d][1], invT_hi, invT_lo, sh, sl);  // tau_d df
       const float p = __fmul_rn(sh, jf);
       const float e = __fmaf_rn(sl, jf, __fmaf_rn(sh, jf, -p));
-      tw[warp][lane][d] = cis_turns(frac_turns(p, e));
+      t[d] = cis_turns(frac_turns(p, e));
     }
+    tp[warp][lane] = make_float4(t[0].x, t[1].x, t[0].y, t[1].y);
+    ts[warp][lane] = t[kSingle < 0 ? 0 : kSingle];
   }
   float zh[kMaxDet][2], zl[kMaxDet][2];  // Z_d as float pairs (re, im)
   for (int d = 0; d < kMaxDet; ++d) zh[d][0] = zh[d][1] = zl[d][0] = zl[d][1] = 0.f;
@@ -111,19 +120,22 @@ __global__ void __launch_bounds__(kFullThreads) k_full_z(const float2* __restric
     __syncthreads();
     // data times f^-7/6 = f_c^-7/6 (1 + j u)^-7/6 (chunk series), transposed;
     // points past the grid are zero
-    for (int i = tid; i < D * kSegP; i += kFullThreads) {
-      const int d = i / kSegP, p = i - d * kSegP;
+    for (int p = tid; p < kSegP; p += kFullThreads) {
       const int c = p >> 5, jj = p & (kChunk - 1);
       const int k = c0 * kChunk + p;
-      float2 v = make_float2(0.f, 0.f);
+      float2 v[kMaxDet] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
       if (c < nc && k < N) {
         const float* qa = qs + c * kQPad + kQamp;
         const float j = small_int_float(jj - kChunk / 2);
         const float A = qa[0] * fmaf(j, fmaf(j, fmaf(j, fmaf(j, qa[4], qa[3]), qa[2]), qa[1]), 1.f);
-        v = __ldg(w32 + (size_t)d * N + k);
-        v = make_float2(v.x * A, v.y * A);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          const float2 x = __ldg(w32 + (size_t)d * N + k);
+          v[d] = make_float2(x.x * A, x.y * A);
+        }
       }
-      wt[d][jj][c] = v;
+      if (kPair) wp[jj][c] = make_float4(v[0].x, v[1].x, v[0].y, v[1].y);
+      if (kSingle >= 0) ws[jj][c] = v[kSingle < 0 ? 0 : kSingle];
     }
     // lane c: the walker's coefficients of chunk c (X0 with Phi0, whole turns
     // dropped) and the chunk factors exp(2 pi i f_c tau_d), in registers
@@ -158,9 +170,8 @@ __global__ void __launch_bounds__(kFullThreads) k_full_z(const float2* __restric
     }
     __syncthreads();  // wt complete
     if (!act) continue;
-    float acc[kMaxDet][2];
-#pragma unroll
-    for (int d = 0; d < kMaxDet; ++d) acc[d][0] = acc[d][1] = 0.f;
+    float2 apr = make_float2(0.f, 0.f), api = apr;  // detectors 0, 1
+    float asr = 0.f, asi = 0.f;                     // detector D-1
 #pragma unroll 2
     for (int jj = 0; jj < kChunk; ++jj) {
       const float jf = small_int_float(jj - kChunk / 2);
@@ -179,16 +190,32 @@ __global__ void __launch_bounds__(kFullThreads) k_full_z(const float2* __restric
       f2x_add(sh, sl, p2);
       sl = __fadd_rn(sl, __fadd_rn(__fadd_rn(e1, e2), t3));
       const float2 z = cis_turns(frac_turns(sh, sl));  // exp(+2 pi i x)
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        const float2 T = tw[warp][jj][d];  // exp(2 pi i (j - 16) df tau_d), same for all lanes
+      // offset factor exp(2 pi i (j - 16) df tau_d) (the same for all lanes)
+      // times the phasor, times the data
+      if constexpr (kPair) {
+        const float4 T = tp[warp][jj];
+        const float4 v = wp[jj][lane];
+        const float2 Tr = make_float2(T.x, T.y), Ti = make_float2(T.z, T.w);
+        const float2 zx = make_float2(z.x, z.x), zy = make_float2(z.y, z.y);
+        const float2 ur = pv::fma(zx, Tr, pv::mul(pv::neg(zy), Ti)), ui = pv::fma(zx, Ti, pv::mul(zy, Tr));
+        const float2 vr = make_float2(v.x, v.y), vi = make_float2(v.z, v.w);
+        apr = pv::fma(vr, ur, pv::fma(pv::neg(vi), ui, apr));
+        api = pv::fma(vr, ui, pv::fma(vi, ur, api));
+      }
+      if constexpr (kSingle >= 0) {
+        const float2 T = ts[warp][jj];
         const float ur = fmaf(z.x, T.x, -z.y * T.y), ui = fmaf(z.x, T.y, z.y * T.x);
-        const float2 v = wt[d][jj][lane];
-        acc[d][0] = fmaf(v.x, ur, fmaf(-v.y, ui, acc[d][0]));
-        acc[d][1] = fmaf(v.x, ui, fmaf(v.y, ur, acc[d][1]));
+        const float2 v = ws[jj][lane];
+        asr = fmaf(v.x, ur, fmaf(-v.y, ui, asr));
+        asi = fmaf(v.x, ui, fmaf(v.y, ur, asi));
       }
     }
     // the chunk factor, once per chunk, then into the lane's float pairs
+    float acc[kMaxDet][2] = {{apr.x, api.x}, {apr.y, api.y}, {0.f, 0.f}};
+    if (kSingle >= 0) {
+      acc[kSingle < 0 ? 0 : kSingle][0] = asr;
+      acc[kSingle < 0 ? 0 : kSingle][1] = asi;
+    }
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       const float gr = fmaf(E[d].x, acc[d][0], -E[d].y * acc[d][1]);
