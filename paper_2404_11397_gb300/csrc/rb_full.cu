@@ -30,6 +30,7 @@
 // data.  Per-lane sums are FP32 per chunk, accumulated in float pairs; the
 // warp sum and the final combination are FP64.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 
@@ -321,11 +322,11 @@ extern "C" int rb_loglike_full_batch(rb_event_t ev, const double* theta_dev, int
   }
   void (*const kz)(const float2*, int, const float*, int, const WalkerAbs*, int64_t, float, float, int, double*) =
       e.n_det == 1 ? k_full_z<1> : e.n_det == 2 ? k_full_z<2> : k_full_z<3>;
-  static bool smem_raised[kMaxDet] = {false, false, false};  // idempotent attribute; races only repeat it
-  if (!smem_raised[e.n_det - 1]) {
+  static std::atomic<bool> smem_raised[kMaxDet];  // the attribute is idempotent: concurrent first calls only repeat it
+  if (!smem_raised[e.n_det - 1].load(std::memory_order_acquire)) {
     if ((err = cudaFuncSetAttribute(kz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFullSmem)) != cudaSuccess)
       return cuda_fail(err, "rb_loglike_full_batch: shared memory attribute");
-    smem_raised[e.n_det - 1] = true;
+    smem_raised[e.n_det - 1].store(true, std::memory_order_release);
   }
   // slices of the grid per group of 8 walkers: at least two waves of blocks
   // (2 per SM), then the count in the next few that wastes the least of the last wave

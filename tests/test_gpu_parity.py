@@ -8,6 +8,8 @@ Tolerances (stated in the library's design notes):
 * gradient: |dg_j| <= 1e-4 max(|g_j|, 1e-2 max_j |g_j|)  (mixed), 1e-8 (FP64);
 * at the fiducial point every mode returns the FP64 constant exactly.
 """
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -451,3 +453,44 @@ def test_rebuild_and_batch_host_equals_two_calls(rb, c2, mode):
     np.testing.assert_array_equal(L3, L1)
     orig = [np.ascontiguousarray(np.stack([ev["data"][d].real, ev["data"][d].imag], -1)) for d in range(D)]
     c2.event.rebuild(data=orig, psd=[ev["psd"][d] for d in range(D)], mode="fp64")
+
+
+def test_rebuild_and_batch_graph_survives_workspace_growth(rb, c2):
+    """A graph captured with the event's workspace stays valid after a larger
+    eager call grows it (outgrown workspaces live as long as the event)."""
+    ev = inject(synth.make_event("C2", T=32.0))
+    event = rb.Event.from_synth(ev, n_bins=150)
+    small = torch.tensor(synth.posterior_box(ev["theta_inj"], 300, seed=5), device="cuda")
+    big = torch.tensor(synth.posterior_box(ev["theta_inj"], 2000, seed=6), device="cuda")
+    L0, G0 = rb.rebuild_loglike_grad(event, small)  # eager: allocates the event's workspace
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        rb.rebuild_loglike_grad(event, small)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="relaxed"):
+        L, G = rb.rebuild_loglike_grad(event, small)
+    Lb, Gb = rb.rebuild_loglike_grad(event, big)  # grows the workspace
+    Lb2, Gb2 = rb.loglike_grad(event, big)
+    torch.testing.assert_close(Lb, Lb2, rtol=0, atol=0)
+    g.replay()
+    torch.cuda.synchronize()
+    torch.testing.assert_close(L, L0, rtol=0, atol=0)
+    torch.testing.assert_close(G, G0, rtol=0, atol=0)
+    del g
+    event.free()
+
+
+def test_rebuild_and_batch_errors(rb, c2):
+    th = torch.tensor(np.array(c2.ev["theta_inj"])[None], device="cuda")
+    with pytest.raises(rb.RBError) as e:
+        rb.rebuild_loglike_grad(c2.event, th, mode=9)
+    assert e.value.status == rb.RB_EINVAL
+    lib = rb.load()
+    D = c2.ev["geom"].shape[0]
+    null = (ctypes.c_void_p * D)()
+    L = np.zeros(1)
+    rc = lib.rb_rebuild_loglike_grad_host(c2.event.handle, null, null, ctypes.c_void_p(th.cpu().numpy().ctypes.data), 1,
+                                          ctypes.c_void_p(L.ctypes.data), None, rb.RB_MIXED, None)
+    assert rc == rb.RB_EINVAL and b"NULL data/psd" in lib.rb_last_error()
