@@ -245,6 +245,7 @@ int rb_event_free(rb_event_t ev) {
   if (e.ev_fork) cudaEventDestroy(e.ev_fork);
   if (e.ev_join) cudaEventDestroy(e.ev_join);
   if (e.ev_ref) cudaEventDestroy(e.ev_ref);
+  if (e.ev_setup) cudaEventDestroy(e.ev_setup);
   if (e.ev_data) cudaEventDestroy(e.ev_data);
   if (e.ev_tan) cudaEventDestroy(e.ev_tan);
   if (e.tanst) cudaStreamDestroy(e.tanst);
@@ -357,6 +358,7 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
         (err = cudaEventCreateWithFlags(&e.ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
         (err = cudaEventCreateWithFlags(&e.ev_join, cudaEventDisableTiming)) != cudaSuccess ||
         (err = cudaEventCreateWithFlags(&e.ev_ref, cudaEventDisableTiming)) != cudaSuccess ||
+        (err = cudaEventCreateWithFlags(&e.ev_setup, cudaEventDisableTiming)) != cudaSuccess ||
         (err = cudaStreamCreateWithFlags(&e.copy, cudaStreamNonBlocking)) != cudaSuccess ||
         (err = cudaEventCreateWithFlags(&e.ev_data, cudaEventDisableTiming)) != cudaSuccess ||
         (err = cudaStreamCreateWithFlags(&e.tanst, cudaStreamNonBlocking)) != cudaSuccess ||
@@ -645,6 +647,7 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
         return cuda_fail(err, "rebuild fork");
       if ((err = launch_setup(RB_MIXED, ss->theta, ss->W, e.ec, e.d_ref, ss->ws, nullptr, false, e.side)) != cudaSuccess)
         return cuda_fail(err, "set-up kernel");
+      if ((err = cudaEventRecord(e.ev_setup, e.side)) != cudaSuccess) return cuda_fail(err, "rebuild join");
       if ((err = launch_ref_values(e.d_theta_ref, e.ec, e.d_ref, e.side)) != cudaSuccess)
         return cuda_fail(err, "reference values kernel");
       ++launches;
@@ -676,7 +679,10 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
   }
   e.last_in_place = in_opt != nullptr;
   if (err != cudaSuccess) return cuda_fail(err, "summary kernel");
-  if ((err = cudaStreamWaitEvent(s, e.ev_join, 0)) != cudaSuccess) return cuda_fail(err, "rebuild join");
+  // with the overlapped set-up the caller's likelihood kernel waits for the
+  // set-up (and tangents) only; it joins the FP64 reference set after that
+  // kernel (finish_rebuild_join)
+  if ((err = cudaStreamWaitEvent(s, ss ? e.ev_setup : e.ev_join, 0)) != cudaSuccess) return cuda_fail(err, "rebuild join");
   if (ss && ss->grad && (err = cudaStreamWaitEvent(s, e.ev_tan, 0)) != cudaSuccess) return cuda_fail(err, "rebuild join");
   count_launches(launches);
   return RB_OK;
@@ -766,6 +772,9 @@ int rebuild_and_batch(EventEntry& e, const double* theta, int64_t W, double* log
       rc = cuda_fail(err, "likelihood kernel");
     else
       count_launches(1);
+    // the FP64 reference set (forked stream) is complete before anything
+    // that follows this call on `s`
+    if ((err = cudaStreamWaitEvent(s, e.ev_join, 0)) != cudaSuccess && rc == RB_OK) rc = cuda_fail(err, "rebuild join");
   }
   if (!own) cudaFreeAsync(buf, s);
   return rc;

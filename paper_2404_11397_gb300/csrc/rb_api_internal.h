@@ -41,6 +41,7 @@ struct EventEntry {
   cudaStream_t side = nullptr;    // rebuild: branch for the reference values the summary does not use
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_ref = nullptr;   // rebuild + batch: float-float reference values ready
+  cudaEvent_t ev_setup = nullptr; // rebuild + batch: the walkers' set-up done (forked stream)
   // rebuild + batch: the walkers' workspace, kept between calls (grown outside
   // stream capture only; outgrown buffers stay allocated until the event is
   // freed, so a captured graph never refers to freed memory)
