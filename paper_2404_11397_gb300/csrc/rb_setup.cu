@@ -473,13 +473,14 @@ __global__ void __launch_bounds__(7 * 32) k_ref_values(const double* theta, Even
   }
 }
 
-// Batch set-up.  MODE RB_MIXED writes WalkerMixed (+ float tangents);
-// RB_FP64 writes WalkerF64 (+ double tangents); RB_MIXED_F64PHASE writes
-// WalkerF64 (+ float tangents).
+// Batch set-up in FP64 for the FP64 paths: RB_FP64 writes WalkerF64 (+
+// double tangents), RB_MIXED_F64PHASE writes WalkerF64 (+ float tangents).
+// (RB_MIXED uses the float-float set-up, k_setup_dd.)
 template <int MODE, bool GRAD>
 __global__ void __launch_bounds__((5 + kTanWarps) * 32) k_setup(const double* __restrict__ theta, int64_t W, EventConst ec,
                                                   const RefValues* __restrict__ ref, void* __restrict__ ws_out,
                                                   void* __restrict__ tan_out) {
+  static_assert(MODE == RB_FP64 || MODE == RB_MIXED_F64PHASE, "RB_MIXED uses the float-float set-up");
   using TanT = typename std::conditional<MODE == RB_FP64, double, float>::type;
   __shared__ SetupSmem S;
   const int64_t w0 = (int64_t)blockIdx.x * kSetupWalkers;
@@ -496,7 +497,7 @@ __global__ void __launch_bounds__((5 + kTanWarps) * 32) k_setup(const double* __
   const Values& r = ref->v;
   const int l = lane;
   if (warp == 0) {
-    // constant-phase factor exp(-i dPhi0) (FP64 from the half angle in mixed modes)
+    // constant-phase factor exp(-i dPhi0) (FP64; from the half angle for the FP64-phase mode)
     const double dphi0 = wrap_pi(S.phi0[l] - r.phi0);
     if (MODE == RB_FP64) {
       double sp, cp;
@@ -518,34 +519,16 @@ __global__ void __launch_bounds__((5 + kTanWarps) * 32) k_setup(const double* __
   } else if (warp == 4 && mine) {
     for (int d = 0; d < kMaxDet; ++d) {
       const double dt = (d < ec.n_det) ? S.tau[d][l] - r.tau[d] : 0.0;
-      if (MODE == RB_MIXED) {
-        const f2x t = f2x_from(dt);
-        WalkerMixed* o = static_cast<WalkerMixed*>(ws_out) + w;
-        o->tau_hi[d] = t.hi;
-        o->tau_lo[d] = t.lo;
-      } else {
-        static_cast<WalkerF64*>(ws_out)[w].tau[d] = dt;
-      }
+      static_cast<WalkerF64*>(ws_out)[w].tau[d] = dt;
     }
   }
   roles_sync();
   // phase 3: coefficient differences (warp 0) and prefactor ratios per detector (warps 1-3), FP64
   if (warp == 0 && mine) {
-    if (MODE == RB_MIXED) {
-      WalkerMixed* o = static_cast<WalkerMixed*>(ws_out) + w;
-      for (int k = 0; k < kNBasis; ++k) {
-        const f2x c = f2x_from(S.c[k][l] - r.c[k]);
-        o->dc_hi[k] = c.hi;
-        o->dc_lo[k] = c.lo;
-      }
-      o->valid = S.valid[l];
-      o->pad[0] = o->pad[1] = o->pad[2] = 0;
-    } else {
-      WalkerF64* o = static_cast<WalkerF64*>(ws_out) + w;
-      for (int k = 0; k < kNBasis; ++k) o->dc[k] = S.c[k][l] - r.c[k];
-      o->valid = S.valid[l];
-      o->pad = 0;
-    }
+    WalkerF64* o = static_cast<WalkerF64*>(ws_out) + w;
+    for (int k = 0; k < kNBasis; ++k) o->dc[k] = S.c[k][l] - r.c[k];
+    o->valid = S.valid[l];
+    o->pad = 0;
   } else if (warp >= 1 && warp <= kMaxDet && mine) {
     const int d = warp - 1;
     double rho_r = 0.0, rho_i = 0.0, sig_r = 0.0, sig_i = 0.0;
@@ -563,19 +546,11 @@ __global__ void __launch_bounds__((5 + kTanWarps) * 32) k_setup(const double* __
       sig_r = (xr * rr + xi * ri) / den;
       sig_i = (xi * rr - xr * ri) / den;
     }
-    if (MODE == RB_MIXED) {
-      WalkerMixed* o = static_cast<WalkerMixed*>(ws_out) + w;
-      o->rho[d][0] = (float)rho_r;
-      o->rho[d][1] = (float)rho_i;
-      o->sig[d][0] = (float)sig_r;
-      o->sig[d][1] = (float)sig_i;
-    } else {
-      WalkerF64* o = static_cast<WalkerF64*>(ws_out) + w;
-      o->rho[d][0] = rho_r;
-      o->rho[d][1] = rho_i;
-      o->sig[d][0] = sig_r;
-      o->sig[d][1] = sig_i;
-    }
+    WalkerF64* o = static_cast<WalkerF64*>(ws_out) + w;
+    o->rho[d][0] = rho_r;
+    o->rho[d][1] = rho_i;
+    o->sig[d][0] = sig_r;
+    o->sig[d][1] = sig_i;
   }
 }
 
