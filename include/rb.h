@@ -187,7 +187,9 @@ RB_API int rb_loglike_grad_batch(rb_event_t ev, const double* theta_dev, int64_t
  * holds and the stream is not being captured; a call captured in a graph
  * with a larger batch than any before it takes its workspace from the
  * stream-ordered pool instead.  Outgrown workspaces are released with the
- * event, so graphs that captured them stay valid while the event lives.
+ * event, so graphs that captured them stay valid while the event lives.  The
+ * event's auxiliary stream for the tangents is created by its first combined
+ * call, which should therefore not be inside a global-mode stream capture.
  * Errors: those of the two calls. */
 RB_API int rb_rebuild_loglike_grad(rb_event_t ev, const double* theta_dev, int64_t W, double* logl_dev,
                                    double* grad_dev, int mode, void* stream);

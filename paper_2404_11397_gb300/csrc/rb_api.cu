@@ -358,11 +358,7 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
         (err = cudaEventCreateWithFlags(&e.ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
         (err = cudaEventCreateWithFlags(&e.ev_join, cudaEventDisableTiming)) != cudaSuccess ||
         (err = cudaEventCreateWithFlags(&e.ev_ref, cudaEventDisableTiming)) != cudaSuccess ||
-        (err = cudaEventCreateWithFlags(&e.ev_setup, cudaEventDisableTiming)) != cudaSuccess ||
-        (err = cudaStreamCreateWithFlags(&e.copy, cudaStreamNonBlocking)) != cudaSuccess ||
-        (err = cudaEventCreateWithFlags(&e.ev_data, cudaEventDisableTiming)) != cudaSuccess ||
-        (err = cudaStreamCreateWithFlags(&e.tanst, cudaStreamNonBlocking)) != cudaSuccess ||
-        (err = cudaEventCreateWithFlags(&e.ev_tan, cudaEventDisableTiming)) != cudaSuccess) {
+        (err = cudaEventCreateWithFlags(&e.ev_setup, cudaEventDisableTiming)) != cudaSuccess) {
       rc = cuda_fail(err, "rebuild stream and events");
       break;
     }
@@ -484,6 +480,17 @@ int rb_loglike_grad_batch(rb_event_t ev, const double* theta_dev, int64_t W, dou
   return rb::run_batch(event_entry(ev), theta_dev, W, logl_dev, grad_dev, mode, (cudaStream_t)stream, nullptr);
 }
 
+namespace rb {
+// The tangent and copy streams of the combined calls, created on an event's
+// first combined call (most resident events never need them).
+static cudaError_t ensure_stream(cudaStream_t& st, cudaEvent_t& ev) {
+  cudaError_t err = cudaSuccess;
+  if (!st && (err = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) return err;
+  if (!ev && (err = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return err;
+  return err;
+}
+}  // namespace rb
+
 int rb_rebuild_loglike_grad(rb_event_t ev, const double* theta_dev, int64_t W, double* logl_dev, double* grad_dev,
                             int mode, void* stream) {
   using namespace rb;
@@ -544,6 +551,7 @@ int rb_rebuild_loglike_grad_host(rb_event_t ev, const double* const* data_host, 
   double *d_theta = nullptr, *d_logl = nullptr, *d_grad = nullptr;
   int rc = RB_OK;
   cudaError_t err;
+  if ((err = ensure_stream(e.copy, e.ev_data)) != cudaSuccess) return cuda_fail(err, "copy stream");
   do {
     // strain and PSD into the event's resident copy on the copy stream, in
     // parallel with the data-independent kernels of the rebuild and batch
@@ -745,6 +753,7 @@ int rebuild_and_batch(EventEntry& e, const double* theta, int64_t W, double* log
     return run_batch(&e, theta, W, logl, grad, mode, s, nullptr);
   }
   const bool want_grad = grad != nullptr;
+  if (want_grad && (err = ensure_stream(e.tanst, e.ev_tan)) != cudaSuccess) return cuda_fail(err, "tangent stream");
   const size_t ws_bytes = sizeof(WalkerMixed) * W, tan_bytes = want_grad ? sizeof(WalkerTan<float>) * W : 0;
   const size_t need = ws_bytes + tan_bytes;
   // the event's persistent workspace, grown when the stream is not being
