@@ -84,7 +84,7 @@ def _tol(mode, lp):
     return np.maximum(1e-3, 2e-6 * np.abs(lp) * 4)
 
 
-@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "mixed_f64phase"])
 def test_mala_init_matches_oracle(rb, setup, mode):
     S = setup
     z = torch.tensor(S["z0"], device="cuda")
@@ -102,7 +102,7 @@ def test_mala_init_matches_oracle(rb, setup, mode):
     assert r[i, j] <= 1.0, (i, j, gz[i, j], gzo[i, j], S["z0"][i, j])
 
 
-@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "mixed_f64phase"])
 def test_mala_step_matches_oracle(rb, setup, mode):
     S = setup
     lpo, gzo = oracle.mala_logpost(S["ev"], S["s"], S["z0"], S["lo"], S["hi"])
