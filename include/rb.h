@@ -194,16 +194,20 @@ RB_API int rb_loglike_grad_batch(rb_event_t ev, const double* theta_dev, int64_t
 RB_API int rb_rebuild_loglike_grad(rb_event_t ev, const double* theta_dev, int64_t W, double* logl_dev,
                                    double* grad_dev, int mode, void* stream);
 
-/* End-to-end form of rb_rebuild_loglike_grad for host buffers: copies the
+/* End-to-end form of rb_rebuild_loglike_grad for host buffers: brings the
  * new strain data_host[d] ([n_freq][2]) and PSD psd_host[d] ([n_freq]) of
  * every detector into the event's resident copy and theta_host [W][13] to
  * the device, rebuilds the summary data (current theta_ref), evaluates log L
  * (and the gradient unless grad_host is NULL), copies logl_host [W] (and
  * grad_host [W][13]) back and synchronises `stream`.  The strain and PSD
- * copies run on the event's copy stream while the kernels that do not read
- * them (reference values, walker set-up) run; host buffers should be pinned
- * for full copy bandwidth.  Results equal rb_event_rebuild with the same
- * host data followed by rb_loglike_grad_host.  Errors: those of the two calls. */
+ * move on the event's copy stream while the kernels that do not read them
+ * (reference values, walker set-up) run.  Pinned (page-locked, mapped)
+ * buffers whose data_host[d] start on a 16-byte and psd_host[d] on an 8-byte
+ * boundary are read by one kernel over the host link, which writes the
+ * resident FP64 copy and the FP32 working copy in the same pass; other
+ * buffers are copied by the copy engine and then converted.  Both give the
+ * same bits.  Results equal rb_event_rebuild with the same host data followed
+ * by rb_loglike_grad_host.  Errors: those of the two calls. */
 RB_API int rb_rebuild_loglike_grad_host(rb_event_t ev, const double* const* data_host, const double* const* psd_host,
                                         const double* theta_host, int64_t W, double* logl_host, double* grad_host,
                                         int mode, void* stream);

@@ -36,12 +36,15 @@ cudaError_t launch_edge_tables(int64_t kmin, double T, int D, int B, int Ep, int
 cudaError_t launch_chunk_q(int64_t kmin, double T, int64_t N, void* cq, cudaStream_t s);
 size_t chunk_q_bytes(int64_t N);
 cudaError_t launch_strain(const RefValues* src, int64_t kmin, int64_t N, double T, double* h, cudaStream_t s);
-cudaError_t launch_summary_fast(const void* w32, const float* is32, const int* exps, int64_t N, double T, int D, int B,
-                                const int64_t* edges, const RefValues* ref, const void* cq, void* chunk_coef,
-                                const SummaryOut& so, int n_parts, cudaStream_t s);
+cudaError_t launch_chunk_coef(int64_t N, int D, const RefValues* ref, const void* cq, void* chunk_coef, cudaStream_t s);
+cudaError_t launch_summary_parts(const void* w32, const float* is32, const int* exps, int64_t N, double T, int D, int B,
+                                 const int64_t* edges, const RefValues* ref, const void* chunk_coef,
+                                 const SummaryOut& so, int p0, int p1, cudaStream_t s);
 cudaError_t launch_ref_dd(const double* theta_ref_dev, const EventConst& ec, RefValues* out, cudaStream_t s);
 cudaError_t launch_tangents(const double* theta, int64_t W, const EventConst& ec, void* tan, cudaStream_t s);
 cudaError_t launch_data32(const DataPtrs& in, int64_t N, int D, void* w32, float* is32, int* exps, cudaStream_t s);
+cudaError_t launch_pull32(const DataPtrs& src, int64_t N, int D, double* data, double* psd, void* w32, float* is32,
+                          int* exps, int n_sm, cudaStream_t s);
 size_t chunk_coef_bytes(int64_t N);
 
 // ---- diagnostics ----
@@ -534,6 +537,22 @@ int rb_loglike_grad_host(rb_event_t ev, const double* theta_host, int64_t W, dou
   return rc;
 }
 
+namespace rb {
+// Device address of a pinned, mapped host buffer that starts on an `align`
+// boundary, or NULL (pageable memory, or unaligned).
+static const double* mapped_host(const double* p, size_t align) {
+  if (!p || reinterpret_cast<uintptr_t>(p) % align != 0) return nullptr;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  if (reinterpret_cast<uintptr_t>(a.devicePointer) % align != 0) return nullptr;
+  return static_cast<const double*>(a.devicePointer);
+}
+}  // namespace rb
+
 int rb_rebuild_loglike_grad_host(rb_event_t ev, const double* const* data_host, const double* const* psd_host,
                                  const double* theta_host, int64_t W, double* logl_host, double* grad_host, int mode,
                                  void* stream) {
@@ -551,16 +570,32 @@ int rb_rebuild_loglike_grad_host(rb_event_t ev, const double* const* data_host, 
   double *d_theta = nullptr, *d_logl = nullptr, *d_grad = nullptr;
   int rc = RB_OK;
   cudaError_t err;
+  // pinned (mapped) buffers are read by one kernel over the host link, which
+  // writes the resident FP64 copies and the FP32 working copy together;
+  // others are copied in by the copy engine (and converted by the rebuild)
+  DataPtrs src{};
+  bool mapped = true;
+  for (int d = 0; d < e.n_det && mapped; ++d) {
+    src.data[d] = mapped_host(data_host[d], 16);
+    src.psd[d] = mapped_host(psd_host[d], 8);
+    mapped = src.data[d] && src.psd[d];
+  }
   if ((err = ensure_stream(e.copy, e.ev_data)) != cudaSuccess) return cuda_fail(err, "copy stream");
   do {
     // strain and PSD into the event's resident copy on the copy stream, in
     // parallel with the data-independent kernels of the rebuild and batch
     if ((err = cudaEventRecord(e.ev_fork, s)) != cudaSuccess || (err = cudaStreamWaitEvent(e.copy, e.ev_fork, 0)) != cudaSuccess) { rc = cuda_fail(err, "copy fork"); break; }
-    e.w32_resident = false;
-    for (int d = 0; d < e.n_det && err == cudaSuccess; ++d) {
-      err = cudaMemcpyAsync(e.d_data + 2 * (size_t)d * e.N, data_host[d], sizeof(double) * 2 * e.N, cudaMemcpyHostToDevice, e.copy);
-      if (err == cudaSuccess)
-        err = cudaMemcpyAsync(e.d_psd + (size_t)d * e.N, psd_host[d], sizeof(double) * e.N, cudaMemcpyHostToDevice, e.copy);
+    if (mapped) {
+      err = launch_pull32(src, e.N, e.n_det, e.d_data, e.d_psd, e.d_w32, e.d_is32, e.d_wexp, sm_count(), e.copy);
+      if (err == cudaSuccess) count_launches(1);
+      e.w32_resident = true;  // once ev_data completes
+    } else {
+      e.w32_resident = false;
+      for (int d = 0; d < e.n_det && err == cudaSuccess; ++d) {
+        err = cudaMemcpyAsync(e.d_data + 2 * (size_t)d * e.N, data_host[d], sizeof(double) * 2 * e.N, cudaMemcpyHostToDevice, e.copy);
+        if (err == cudaSuccess)
+          err = cudaMemcpyAsync(e.d_psd + (size_t)d * e.N, psd_host[d], sizeof(double) * e.N, cudaMemcpyHostToDevice, e.copy);
+      }
     }
     if (err != cudaSuccess || (err = cudaEventRecord(e.ev_data, e.copy)) != cudaSuccess) { rc = cuda_fail(err, "copy strain"); break; }
     if (W > 0) {
@@ -669,6 +704,10 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
     // the FP32 working copy follows the data the sums are taken over: data
     // read in place are converted every time, the resident data only after
     // they change
+    // the chunk coefficients need the reference values only: ahead of any
+    // wait for the data
+    if ((err = launch_chunk_coef(e.N, e.n_det, e.d_ref, e.d_chunkq, e.d_chunks, s)) != cudaSuccess)
+      return cuda_fail(err, "chunk coefficient kernel");
     if (ss && ss->data_ready && (err = cudaStreamWaitEvent(s, ss->data_ready, 0)) != cudaSuccess)
       return cuda_fail(err, "rebuild: wait for the data copies");
     if (in_opt || !e.w32_resident) {
@@ -678,8 +717,8 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
       ++launches;
     }
     e.w32_current = true;
-    err = launch_summary_fast(e.d_w32, e.d_is32, e.d_wexp, e.N, e.T, e.n_det, e.n_bins, e.d_edges, e.d_ref, e.d_chunkq,
-                              e.d_chunks, e.out(), e.n_parts, s);
+    err = launch_summary_parts(e.d_w32, e.d_is32, e.d_wexp, e.N, e.T, e.n_det, e.n_bins, e.d_edges, e.d_ref,
+                               e.d_chunks, e.out(), 0, e.n_parts, s);
     ++launches;
   } else {
     err = launch_summary(in, e.kmin, e.N, e.T, e.n_det, e.n_bins, e.d_edges, e.d_ref, e.out(), s);
@@ -741,6 +780,7 @@ int run_batch(const EventEntry* e, const double* theta, int64_t W, double* logl,
 // the summary sums when the mixed chunk-expanded rebuild applies.  If
 // data_ready is not NULL the resident data are complete only after it (the
 // data-independent kernels run meanwhile).
+
 int rebuild_and_batch(EventEntry& e, const double* theta, int64_t W, double* logl, double* grad, int mode,
                       cudaStream_t s, cudaEvent_t data_ready) {
   cudaError_t err;

@@ -544,6 +544,53 @@ __global__ void __launch_bounds__(256) k_data32(DataPtrs in, int64_t N, int D, f
   is32[(size_t)d * N + k] = is;
 }
 
+// Host-buffer step: the strain and PSD read straight from pinned host memory
+// mapped into the device address space (one pass over the host link), stored
+// as the event's resident FP64 copies and converted to the FP32 working copy
+// with the k_data32 arithmetic.  Block row d = detector; the blocks of a row
+// stride over the points with two points in flight per thread.
+__global__ void __launch_bounds__(256) k_pull32(DataPtrs src, int64_t N, double* __restrict__ data,
+                                                double* __restrict__ psd, float2* __restrict__ w32,
+                                                float* __restrict__ is32, int* __restrict__ exps) {
+  const int d = blockIdx.y;
+  const double2* __restrict__ sd2 = reinterpret_cast<const double2*>(src.data[d]);
+  const double* __restrict__ sp = src.psd[d];
+  const int ex = ((__double2hiint(__ldcs(sp)) >> 20) & 0x7FF) - 1023;
+  const int sS = -ex, sdx = -(ex / 2);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    exps[2 * d] = sdx;
+    exps[2 * d + 1] = sS;
+  }
+  const unsigned bS = (unsigned)(896 - sS) << 20, bd = (unsigned)(896 - sdx) << 20;
+  double2* __restrict__ od = reinterpret_cast<double2*>(data) + (size_t)d * N;
+  double* __restrict__ op = psd + (size_t)d * N;
+  float2* __restrict__ ow = w32 + (size_t)d * N;
+  float* __restrict__ oi = is32 + (size_t)d * N;
+  auto put = [&](int64_t k, double2 dv, double pv) {
+    const float is = __frcp_rn(scaled_float(pv, bS));
+    __stcs(od + k, dv);
+    __stcs(op + k, pv);
+    ow[k] = make_float2(scaled_float(dv.x, bd) * is, scaled_float(dv.y, bd) * is);
+    oi[k] = is;
+  };
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; k + stride < N; k += 2 * stride) {
+    const double2 a = __ldcs(sd2 + k), b = __ldcs(sd2 + k + stride);
+    const double pa = __ldcs(sp + k), pb = __ldcs(sp + k + stride);
+    put(k, a, pa);
+    put(k + stride, b, pb);
+  }
+  if (k < N) put(k, __ldcs(sd2 + k), __ldcs(sp + k));
+}
+
+cudaError_t launch_pull32(const DataPtrs& src, int64_t N, int D, double* data, double* psd, void* w32, float* is32,
+                          int* exps, int n_sm, cudaStream_t s) {
+  dim3 grid((unsigned)std::max(1, (2 * n_sm + D - 1) / D), (unsigned)D);
+  k_pull32<<<grid, 256, 0, s>>>(src, N, data, psd, static_cast<float2*>(w32), is32, exps);
+  return cudaGetLastError();
+}
+
 constexpr int kSumFastThreads = 128;
 constexpr int kNQ = 7;  // per detector: A0 re/im, A1 re/im, B0, B1 as a float pair (hi, lo)
 constexpr int kNAcc = kNQ * kMaxDet;
@@ -565,7 +612,7 @@ template <int ND>
 __global__ void __launch_bounds__(kSumFastThreads, 6)
     k_summary_fast(const float2* __restrict__ w32, const float* __restrict__ is32, const int* __restrict__ exps,
                    int N, const float* __restrict__ chunks, double T, float invT_hi, float invT_lo, int B, int D,
-                   const int64_t* __restrict__ edges, const RefValues* __restrict__ ref, SummaryOut so) {
+                   const int64_t* __restrict__ edges, const RefValues* __restrict__ ref, SummaryOut so, int p_off) {
   __shared__ __align__(16) float srec[kPartRecs * kRec];
   // exp(2 pi i j df tau_d), indexed by k mod 32: detectors 0 and 1 as
   // {re_0, re_1, im_0, im_1}, the single detector D-1 as {re, im}
@@ -578,7 +625,8 @@ __global__ void __launch_bounds__(kSumFastThreads, 6)
   __shared__ double scale[kMaxDet][4];
   __shared__ double s_inv_df;
   __shared__ bool s_last;
-  const PartDesc pd = so.parts[blockIdx.x];
+  const int pid = (int)blockIdx.x + p_off;  // this block's part
+  const PartDesc pd = so.parts[pid];
   const int b = pd.bin;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int e0 = (int)edges[b], e1 = (int)edges[b + 1];
@@ -747,7 +795,7 @@ __global__ void __launch_bounds__(kSumFastThreads, 6)
     qsum[tid][0] = h;
     qsum[tid][1] = l;
     if (multi) {
-      float* ps = so.part_sums + ((size_t)blockIdx.x * kNAcc + tid) * 2;
+      float* ps = so.part_sums + ((size_t)pid * kNAcc + tid) * 2;
       ps[0] = h;
       ps[1] = l;
       __threadfence();
@@ -838,19 +886,23 @@ cudaError_t launch_data32(const DataPtrs& in, int64_t N, int D, void* w32, float
   return cudaGetLastError();
 }
 
-cudaError_t launch_summary_fast(const void* w32, const float* is32, const int* exps, int64_t N, double T, int D, int B,
-                                const int64_t* edges, const RefValues* ref, const void* cq, void* chunk_coef,
-                                const SummaryOut& so, int n_parts, cudaStream_t s) {
+cudaError_t launch_chunk_coef(int64_t N, int D, const RefValues* ref, const void* cq, void* chunk_coef, cudaStream_t s) {
   const int nc = (int)n_chunks_of(N);
+  k_chunk_coef<<<(unsigned)((nc + 31) / 32), 96, 0, s>>>(ref, static_cast<const float*>(cq), D, nc,
+                                                        static_cast<float*>(chunk_coef));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_summary_parts(const void* w32, const float* is32, const int* exps, int64_t N, double T, int D, int B,
+                                 const int64_t* edges, const RefValues* ref, const void* chunk_coef,
+                                 const SummaryOut& so, int p0, int p1, cudaStream_t s) {
+  if (p0 < 0 || p1 <= p0) return cudaErrorInvalidValue;
   const double invT = 1.0 / T;
   const float ih = (float)invT, il = (float)(invT - (double)ih);
-  float* ch = static_cast<float*>(chunk_coef);
-  k_chunk_coef<<<(unsigned)((nc + 31) / 32), 96, 0, s>>>(ref, static_cast<const float*>(cq), D, nc, ch);
-  cudaError_t err = cudaGetLastError();
-  if (err != cudaSuccess) return err;
   auto kf = D == 1 ? k_summary_fast<1> : D == 2 ? k_summary_fast<2> : k_summary_fast<3>;
-  kf<<<n_parts, kSumFastThreads, 0, s>>>(static_cast<const float2*>(w32), is32, exps, (int)N, ch, T, ih, il, B, D, edges,
-                                         ref, so);
+  kf<<<(unsigned)(p1 - p0), kSumFastThreads, 0, s>>>(static_cast<const float2*>(w32), is32, exps, (int)N,
+                                                      static_cast<const float*>(chunk_coef), T, ih, il, B, D, edges,
+                                                      ref, so, p0);
   return cudaGetLastError();
 }
 

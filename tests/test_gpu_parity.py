@@ -455,6 +455,58 @@ def test_rebuild_and_batch_host_equals_two_calls(rb, c2, mode):
     c2.event.rebuild(data=orig, psd=[ev["psd"][d] for d in range(D)], mode="fp64")
 
 
+def _pinned(a, offset):
+    """Pinned float64 copy of `a` that starts `offset` elements into its allocation."""
+    flat = np.ascontiguousarray(a, dtype=np.float64).ravel()
+    t = torch.empty(flat.size + 2, dtype=torch.float64).pin_memory()
+    v = t[offset:offset + flat.size]
+    v.copy_(torch.from_numpy(flat))
+    return v
+
+
+@pytest.fixture(scope="module")
+def two64(rb):
+    # two detectors on a grid long enough (T f_low >= 1024) for the chunk-expanded summary
+    return Case(rb, "C2", n_bins=150, T=64.0, sites=("L1", "V1"))
+
+
+@pytest.mark.parametrize("case", ["c2", "two64"])
+def test_host_step_mapped_equals_copied(rb, case, request):
+    """The host-buffer step reads 16-byte-aligned pinned buffers in the summary
+    kernel itself (conversion, resident copies and sums in one pass over the
+    host link); other buffers are copied in first.  Both give the same bits,
+    and leave the same resident data behind."""
+    c = request.getfixturevalue(case)
+    ev = c.ev
+    D = ev["geom"].shape[0]
+    new = ev["noise"] * 0.7 + ev["signal"]
+    arrs = [np.stack([new[d].real, new[d].imag], -1) for d in range(D)]
+    th = synth.posterior_box(ev["theta_inj"], 300, seed=41)
+    outs = {}
+    for name, (data, psd) in {
+        "mapped": ([_pinned(a, 0) for a in arrs], [_pinned(ev["psd"][d], 0) for d in range(D)]),
+        "pinned, 8-byte offset": ([_pinned(a, 1) for a in arrs], [_pinned(ev["psd"][d], 1) for d in range(D)]),
+        "pageable": (arrs, [ev["psd"][d] for d in range(D)]),
+    }.items():
+        L, G = np.zeros(300), np.zeros((300, 13))
+        rb.rebuild_loglike_grad_host(c.event, data, psd, th, L, G, mode="mixed")
+        # what the step left resident: the batch on the resident copy, the
+        # FP64 summary and the full-grid sum (FP32 copy)
+        Ld, Gd = rb.rebuild_loglike_grad(c.event, torch.tensor(th, device="cuda"))
+        Lf = rb.loglike_full(c.event, torch.tensor(th[:8], device="cuda"))
+        outs[name] = (L, G, Ld.cpu().numpy(), Gd.cpu().numpy(), c.event.summary(), Lf.cpu().numpy())
+    ref = outs["pageable"]
+    np.testing.assert_array_equal(ref[2], ref[0])
+    np.testing.assert_array_equal(ref[3], ref[1])
+    for name, o in outs.items():
+        for i in (0, 1, 2, 3, 5):
+            np.testing.assert_array_equal(o[i], ref[i], err_msg=name)
+        for k in ("A0", "A1", "B0", "B1"):
+            np.testing.assert_array_equal(o[4][k], ref[4][k], err_msg=f"{name} {k}")
+    orig = [np.ascontiguousarray(np.stack([ev["data"][d].real, ev["data"][d].imag], -1)) for d in range(D)]
+    c.event.rebuild(data=orig, psd=[ev["psd"][d] for d in range(D)], mode="fp64")
+
+
 def test_rebuild_and_batch_graph_survives_workspace_growth(rb, c2):
     """A graph captured with the event's workspace stays valid after a larger
     eager call grows it (outgrown workspaces live as long as the event)."""
