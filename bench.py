@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--no-mala", action="store_true")
     p.add_argument("--no-full", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-summary-build", action="store_true")
     p.add_argument("--profile", action="store_true",
                    help="fixed short warm-up and no extra legs (for profiler launch lists)")
     return p.parse_args()
@@ -371,8 +372,66 @@ def run_gb300(args, dist: Dist):
             result["serving"] = run_serving(rb, torch, device)
         except Exception as exc:  # report, do not hide
             result["serving"] = {"error": str(exc)[:200]}
+    if not args.no_summary_build:
+        result["summary_build"] = run_summary_build(rb, torch, event, ev, flush)
     event.free()
     return result
+
+
+def hbm_peak_gbs():
+    """Measured copy bandwidth of this machine's GPUs, if recorded beside the repository."""
+    try:
+        with open(ROOT / "MEASURED_PEAKS.json") as f:
+            v = json.load(f).get("hbm_gbs")
+        return float(v) if v else None
+    except (OSError, ValueError):
+        return None
+
+
+def run_summary_build(rb, torch, event, ev, flush, reps=10):
+    """The summary-data build (Sec. II.C) from the event's HBM-resident strain
+    and PSD, three ways, each timed as a whole rb_event_rebuild call after an L2
+    flush (median of `reps`):
+    * mixed: fiducial waveform from per-chunk Taylor coefficients in FP32,
+      reading the FP32 working copy (12 B per point and detector);
+    * FP64 inline: fiducial waveform generated in FP64 at every point (24 B
+      read, and the waveform stored: 16 B written);
+    * FP64 stored: strain, PSD and the stored waveform streamed (40 B read).
+    Runs last: it leaves the FP64 sums in place."""
+    import ctypes
+    lib = rb.load()
+    D, N = ev["geom"].shape[0], ev["N"]
+    sh = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    th = np.ascontiguousarray(event.theta_ref, dtype=np.float64)
+    thp = th.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+    def timed(theta_ptr, mode):
+        ts = []
+        for i in range(reps + 2):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            rc = lib.rb_event_rebuild(event.handle, theta_ptr, None, None, 0, rb.MODES[mode], sh)
+            b.record()
+            torch.cuda.synchronize()
+            if rc != 0:
+                raise RuntimeError(lib.rb_last_error().decode())
+            if i >= 2:
+                ts.append(a.elapsed_time(b) / 1e3)
+        return float(np.median(ts))
+
+    t_mixed = timed(None, "mixed")
+    t_inline = timed(thp, "fp64")  # a theta_ref argument discards the stored waveform
+    t_stored = timed(None, "fp64")
+    peak = hbm_peak_gbs()
+    out = {"n_freq": N, "detectors": D, "timed": "whole rb_event_rebuild call, CUDA events, L2 flushed, median"}
+    for name, t, nbytes in (("mixed", t_mixed, 12 * D * N), ("fp64_inline", t_inline, 40 * D * N),
+                            ("fp64_stored", t_stored, 40 * D * N)):
+        gbs = nbytes / t / 1e9
+        out[name] = {"ms": t * 1e3, "bytes": nbytes, "GB_s": gbs,
+                     "frac_of_measured_hbm": gbs / peak if peak else None}
+    return out
 
 
 def run_mala(rb, torch, event, ev, W, args, dist, device, flush):
@@ -647,6 +706,7 @@ def main():
     args = parse()
     if args.profile:
         args.no_e2e = args.no_cpu = args.no_serving = args.no_fp64 = args.no_mala = args.no_full = True
+        args.no_summary_build = True
     dist = Dist()
     if args.impl == "reference":
         dist.init("gloo")

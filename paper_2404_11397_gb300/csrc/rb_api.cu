@@ -30,7 +30,10 @@ cudaError_t launch_rb_f64(const EventDev& ev, const void* ws, const void* tan, i
 cudaError_t launch_bin_edges(double f_low, double f_high, double T, int64_t kmin, int64_t N, int B, int64_t* edges,
                              cudaStream_t s);
 cudaError_t launch_summary(const DataPtrs& in, int64_t kmin, int64_t N, double T, int D, int B,
-                           const int64_t* edges, const RefValues* ref, const SummaryOut& so, cudaStream_t s);
+                           const int64_t* edges, const RefValues* ref, const SummaryOut& so, double* h0_out,
+                           cudaStream_t s);
+cudaError_t launch_summary_stored(const DataPtrs& in, const double* h0, int64_t kmin, int64_t N, double T, int D, int B,
+                                  const int64_t* edges, const SummaryOut& so, int n_parts, cudaStream_t s);
 cudaError_t launch_edge_tables(int64_t kmin, double T, int D, int B, int Ep, int Bp, const int64_t* edges,
                                float* tab32, size_t edge32_floats, double* tab64, double* inv_df, cudaStream_t s);
 cudaError_t launch_chunk_q(int64_t kmin, double T, int64_t N, void* cq, cudaStream_t s);
@@ -260,6 +263,7 @@ int rb_event_free(rb_event_t ev) {
   cudaFree(e.d_wexp);
   cudaFree(e.d_parts);
   cudaFree(e.d_part_sums);
+  cudaFree(e.d_h0);
   delete ev;
   return RB_OK;
 }
@@ -343,6 +347,7 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
         {(void**)&e.d_base, sizeof(double), "base"},
         {(void**)&e.d_data, sizeof(double) * 2 * D * N, "strain"},
         {(void**)&e.d_psd, sizeof(double) * D * N, "psd"},
+        {(void**)&e.d_h0, sizeof(double) * 2 * D * N, "stored fiducial waveform"},
         {(void**)&e.d_theta_ref, sizeof(double) * kNPar, "theta_ref"},
         {(void**)&e.d_chunkq, chunk_q_bytes(N), "chunk matrices"},
         {(void**)&e.d_chunks, chunk_coef_bytes(N), "chunk coefficients"},
@@ -414,6 +419,7 @@ int rb_event_rebuild(rb_event_t ev, const double* theta_ref_host, const double* 
   if (theta_ref_host) {
     if (!theta_ok(theta_ref_host)) return set_error(RB_EINVAL, "rb_event_rebuild: unphysical theta_ref");
     std::memcpy(e.theta_ref, theta_ref_host, sizeof(e.theta_ref));
+    e.h0_valid = false;  // the stored fiducial waveform belongs to the old theta_ref
     if ((err = cudaMemcpyAsync(e.d_theta_ref, theta_ref_host, sizeof(double) * kNPar, cudaMemcpyHostToDevice, s)) != cudaSuccess)
       return cuda_fail(err, "rb_event_rebuild: copy theta_ref");
   }
@@ -697,7 +703,10 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
     }
   } else {
     if ((err = launch_ref_dd(e.d_theta_ref, e.ec, e.d_ref, e.side)) != cudaSuccess) return cuda_fail(err, "reference values kernel");
-    if ((err = launch_ref_values(e.d_theta_ref, e.ec, e.d_ref, s)) != cudaSuccess) return cuda_fail(err, "reference values kernel");
+    // the streamed FP64 build (stored h0) does not read the reference values:
+    // they are then rebuilt on the forked stream too
+    if ((err = launch_ref_values(e.d_theta_ref, e.ec, e.d_ref, e.h0_valid ? e.side : s)) != cudaSuccess)
+      return cuda_fail(err, "reference values kernel");
   }
   if ((err = cudaEventRecord(e.ev_join, e.side)) != cudaSuccess) return cuda_fail(err, "rebuild join");
   if (fast) {
@@ -720,8 +729,15 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
     err = launch_summary_parts(e.d_w32, e.d_is32, e.d_wexp, e.N, e.T, e.n_det, e.n_bins, e.d_edges, e.d_ref,
                                e.d_chunks, e.out(), 0, e.n_parts, s);
     ++launches;
+  } else if (e.h0_valid) {
+    // FP64 sums from the fiducial waveform stored by the last inline build
+    // for this theta_ref: strain, PSD and h0 streamed, no waveform arithmetic
+    err = launch_summary_stored(in, e.d_h0, e.kmin, e.N, e.T, e.n_det, e.n_bins, e.d_edges, e.out(), e.n_parts, s);
+    e.w32_current = !in_opt && e.w32_resident;
   } else {
-    err = launch_summary(in, e.kmin, e.N, e.T, e.n_det, e.n_bins, e.d_edges, e.d_ref, e.out(), s);
+    // FP64 waveform generated inline, and stored for the next builds
+    err = launch_summary(in, e.kmin, e.N, e.T, e.n_det, e.n_bins, e.d_edges, e.d_ref, e.out(), e.d_h0, s);
+    e.h0_valid = err == cudaSuccess;
     e.w32_current = !in_opt && e.w32_resident;
   }
   e.last_in_place = in_opt != nullptr;

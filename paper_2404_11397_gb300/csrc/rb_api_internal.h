@@ -26,6 +26,8 @@ struct EventEntry {
   double* d_base = nullptr;
   double* d_data = nullptr;   // resident strain [D][N][2]
   double* d_psd = nullptr;    // resident PSD [D][N]
+  double* d_h0 = nullptr;     // stored fiducial waveform h0_d(f) [D][N][2] (FP64 builds)
+  bool h0_valid = false;      // d_h0 holds h0 for the current theta_ref
   double* d_theta_ref = nullptr;
   void* d_chunkq = nullptr;   // event-constant per-chunk Taylor matrices (fast summary build)
   void* d_chunks = nullptr;   // per-rebuild chunk coefficients (fast summary build)

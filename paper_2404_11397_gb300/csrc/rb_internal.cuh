@@ -228,8 +228,12 @@ struct SummaryOut {
   double* base;          // log L(theta_ref)
   int Bp;
   const PartDesc* parts;  // fast build: [n_parts]
-  float* part_sums;       // fast build: [n_parts][7 kMaxDet][2] float pairs
+  float* part_sums;       // fast builds: [n_parts][kPartSlots] doubles, or float pairs [n_parts][7 kMaxDet][2]
 };
+// per-part sums of the builds that split bins into parts: 7 kMaxDet float
+// pairs (fast build) or 6 kMaxDet doubles (stored-waveform FP64 build)
+constexpr int kPartSlots = 7 * kMaxDet;
+static_assert(6 * kMaxDet <= kPartSlots, "the FP64 part sums fit the part slots");
 
 // ---------------------------------------------------------------------------
 // Float-float helpers (all operations rounded explicitly: no contraction or

@@ -218,7 +218,8 @@ __device__ void summary_epilogue(const SummaryOut& so, int b, int d0, int nd, in
 constexpr int kSumThreads = 128;
 __global__ void __launch_bounds__(kSumThreads) k_summary(DataPtrs in, int64_t kmin, int64_t N, double T, int B, int D,
                                                          const int64_t* __restrict__ edges,
-                                                         const RefValues* __restrict__ ref, SummaryOut so) {
+                                                         const RefValues* __restrict__ ref, SummaryOut so,
+                                                         double* __restrict__ h0_out) {
   const int b = blockIdx.x, d = blockIdx.y;
   const Values& v = ref->v;
   const int64_t k0 = edges[b];
@@ -230,6 +231,7 @@ __global__ void __launch_bounds__(kSumThreads) k_summary(DataPtrs in, int64_t km
     const double f = grid_f(kmin, k, T);
     double hr, hi;
     strain_f64(v, d, f, hr, hi);
+    if (h0_out) __stcs(reinterpret_cast<double2*>(h0_out) + (size_t)d * N + k, make_double2(hr, hi));
     const double dr = in.data[d][2 * k], di = in.data[d][2 * k + 1];
     const double w = w0 / in.psd[d][k];
     const double xr = dr * hr + di * hi, xi = di * hr - dr * hi, hh = hr * hr + hi * hi;
@@ -329,9 +331,91 @@ cudaError_t launch_bin_edges(double f_low, double f_high, double T, int64_t kmin
 }
 
 cudaError_t launch_summary(const DataPtrs& in, int64_t kmin, int64_t N, double T, int D, int B,
-                           const int64_t* edges, const RefValues* ref, const SummaryOut& so, cudaStream_t s) {
+                           const int64_t* edges, const RefValues* ref, const SummaryOut& so, double* h0_out,
+                           cudaStream_t s) {
   dim3 grid(B, D);
-  k_summary<<<grid, kSumThreads, 0, s>>>(in, kmin, N, T, B, D, edges, ref, so);
+  k_summary<<<grid, kSumThreads, 0, s>>>(in, kmin, N, T, B, D, edges, ref, so, h0_out);
+  return cudaGetLastError();
+}
+
+// FP64 summary sums from the stored fiducial waveform h0_d(f) (written by
+// k_summary for the current theta_ref): the build then streams the strain,
+// the PSD and h0, 40 B per (point, detector), with no waveform arithmetic.
+// One warp per part of a bin (the fast build's parts), all detectors; the
+// per-point terms are k_summary's expressions; warp sums in a fixed order,
+// the parts of a bin added in index order by the last of them to finish,
+// which runs the FP64 epilogue (base log L by the fixed-point sum).
+template <int ND>
+__global__ void __launch_bounds__(32) k_summary_stored(DataPtrs in, const double* __restrict__ h0, int64_t kmin,
+                                                       int64_t N, double T, int B, const int64_t* __restrict__ edges,
+                                                       SummaryOut so) {
+  __shared__ double sblock[6 * kMaxDet];
+  __shared__ bool s_last;
+  const int pid = blockIdx.x, lane = threadIdx.x;
+  const PartDesc pd = so.parts[pid];
+  const int b = pd.bin;
+  const double fm = 0.5 * (grid_f(kmin, edges[b], T) + grid_f(kmin, edges[b + 1], T));
+  const double w0 = 4.0 / T;
+  double acc[ND][6];
+#pragma unroll
+  for (int d = 0; d < ND; ++d)
+#pragma unroll
+    for (int j = 0; j < 6; ++j) acc[d][j] = 0.0;
+  for (int64_t k = pd.start + lane; k < pd.end; k += 32) {
+    const double f = grid_f(kmin, k, T);
+    const double df = f - fm;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      const double2 dv = __ldcs(reinterpret_cast<const double2*>(in.data[d]) + k);
+      const double2 hv = __ldcs(reinterpret_cast<const double2*>(h0) + (size_t)d * N + k);
+      const double w = w0 / __ldcs(in.psd[d] + k);
+      const double hr = hv.x, hi = hv.y, dr = dv.x, di = dv.y;
+      const double xr = dr * hr + di * hi, xi = di * hr - dr * hi, hh = hr * hr + hi * hi;
+      acc[d][0] += w * xr;
+      acc[d][1] += w * xi;
+      acc[d][2] += w * xr * df;
+      acc[d][3] += w * xi * df;
+      acc[d][4] += w * hh;
+      acc[d][5] += w * hh * df;
+    }
+  }
+  double mine = 0.0;  // lane 6 d + j holds sum (d, j)
+#pragma unroll
+  for (int d = 0; d < ND; ++d)
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const double t = warp_sum_f64(acc[d][j]);
+      if (lane == 6 * d + j) mine = t;
+    }
+  if (pd.n_parts > 1) {
+    double* ps = reinterpret_cast<double*>(so.part_sums);  // [n_parts][kPartSlots] doubles
+    if (lane < 6 * ND) ps[(size_t)pid * kPartSlots + lane] = mine;
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) {
+      const unsigned ticket = atomicAdd(&so.sync->bin_parts_done[b], 1u);
+      s_last = (ticket == (unsigned)pd.n_parts - 1u);
+      if (s_last) so.sync->bin_parts_done[b] = 0u;
+    }
+    __syncwarp();
+    if (!s_last) return;
+    __threadfence();
+    if (lane < 6 * ND) {
+      const double* p0 = ps + (size_t)pd.first * kPartSlots + lane;
+      double t = __ldcg(p0);
+      for (int p = 1; p < pd.n_parts; ++p) t += __ldcg(p0 + (size_t)p * kPartSlots);
+      mine = t;
+    }
+  }
+  if (lane < 6 * ND) sblock[lane] = mine;
+  __syncwarp();
+  summary_epilogue(so, b, 0, ND, B, ND, sblock, nullptr, false, (unsigned)B, so.inv_df[b], true);
+}
+
+cudaError_t launch_summary_stored(const DataPtrs& in, const double* h0, int64_t kmin, int64_t N, double T, int D, int B,
+                                  const int64_t* edges, const SummaryOut& so, int n_parts, cudaStream_t s) {
+  auto kf = D == 1 ? k_summary_stored<1> : D == 2 ? k_summary_stored<2> : k_summary_stored<3>;
+  kf<<<(unsigned)n_parts, 32, 0, s>>>(in, h0, kmin, N, T, B, edges, so);
   return cudaGetLastError();
 }
 

@@ -344,11 +344,17 @@ def _b1_condition(ev, theta_ref, edges):
 
 
 def test_rebuild_fp64_is_bitwise_reproducible(rb, c2):
-    before = c2.event.summary()
-    c2.event.rebuild(mode="fp64")
-    after = c2.event.summary()
-    for key in ("A0", "A1", "B0", "B1"):
-        np.testing.assert_array_equal(before[key], after[key])
+    def twice(**kw):
+        c2.event.rebuild(mode="fp64", **kw)
+        first = c2.event.summary()
+        c2.event.rebuild(mode="fp64", **kw)
+        return first, c2.event.summary()
+
+    # streamed from the stored waveform, then generated inline (a theta_ref
+    # argument discards the stored waveform)
+    for before, after in (twice(), twice(theta_ref=c2.event.theta_ref)):
+        for key in ("A0", "A1", "B0", "B1"):
+            np.testing.assert_array_equal(before[key], after[key])
 
 
 @pytest.mark.parametrize("cfg", ["C1", "C2", "C4"])
@@ -368,6 +374,51 @@ def test_fast_rebuild_summary_matches_oracle(rb, cfg):
     L = rb.loglike(event, torch.tensor(thp, device="cuda"), mode="mixed").cpu().numpy()
     ref, dh, hh = _terms(ev, s, thp)
     assert np.all(np.abs(L - ref) <= _tol("mixed", dh, hh))
+    event.free()
+
+
+def test_fp64_build_from_stored_waveform(rb):
+    """An FP64 build that generates h0 inline stores it for its theta_ref; the
+    next FP64 builds with the same theta_ref stream strain, PSD and h0 instead.
+    Both match the oracle, agree to rounding, and a new theta_ref (or new data
+    read in place) is handled."""
+    ev = inject(synth.make_event("C2", T=16.0, f_high=1024.0))
+    B = 120
+    edges = oracle.bin_edges(ev, B)
+    event = rb.Event.from_synth(ev, n_bins=B)  # inline FP64 build
+    inline = event.summary()
+    base_inline = event.info()["base_logl"]
+    s = oracle.summary(ev, ev["theta_inj"], edges)
+    _summary_close(inline, s, 1e-9)
+    event.rebuild(mode="fp64")  # stored waveform
+    stored = event.summary()
+    _summary_close(stored, s, 1e-9)
+    _summary_close(stored, inline, 1e-11)
+    # the streamed build adds the bins' shares of log L(theta_ref) in fixed
+    # point (2^-32 per bin), the inline one in FP64
+    assert abs(event.info()["base_logl"] - base_inline) <= 1e-9 * abs(base_inline)
+    th = synth.posterior_box(ev["theta_inj"], 64, seed=131)
+    L = rb.loglike(event, torch.tensor(th, device="cuda"), mode="fp64").cpu().numpy()
+    ref, dh, hh = _terms(ev, s, th)
+    assert np.all(np.abs(L - ref) <= _tol("fp64", dh, hh))
+    # a new reference point: generated inline again (and stored), then streamed
+    new_ref = synth.posterior_box(ev["theta_inj"], 1, seed=133)[0]
+    s2 = oracle.summary(ev, new_ref, edges)
+    event.rebuild(theta_ref=new_ref, mode="fp64")
+    _summary_close(event.summary(), s2, 1e-9)
+    event.rebuild(mode="fp64")
+    _summary_close(event.summary(), s2, 1e-9)
+    assert abs(event.info()["base_logl"] - oracle.loglike_full(ev, new_ref)[0]) <= 1e-9 * abs(event.info()["base_logl"])
+    # new data read in place by the streamed build
+    D = ev["geom"].shape[0]
+    new = ev["noise"] * 0.5 + ev["signal"]
+    ev3 = dict(ev)
+    ev3["data"] = new
+    dd = [torch.tensor(np.stack([new[d].real, new[d].imag], -1), device="cuda") for d in range(D)]
+    pp = [torch.tensor(ev["psd"][d], device="cuda") for d in range(D)]
+    event.rebuild(data=dd, psd=pp, mode="fp64")
+    torch.cuda.synchronize()
+    _summary_close(event.summary(), oracle.summary(ev3, new_ref, edges), 1e-9)
     event.free()
 
 
