@@ -140,7 +140,11 @@ RB_API int rb_event_free(rb_event_t ev);
  * with data_on_device = 1 they are device pointers read in place (no copy,
  * they must stay valid until the stream reaches the rebuild), otherwise host
  * pointers copied into the event.  mode RB_FP64: the summary sums are formed
- * in FP64 (as rb_build_summary does); RB_MIXED / RB_MIXED_F64PHASE: the
+ * in FP64 (as rb_build_summary does).  The FP64 build that generates h0 keeps
+ * it (16 B per point and detector, counted in device_bytes); later FP64 builds
+ * with the same theta_ref stream the strain, the PSD and that stored h0
+ * instead of regenerating it (the same sums in another order, within FP64
+ * rounding), and a theta_ref argument discards it.  RB_MIXED / RB_MIXED_F64PHASE: the
  * fiducial phase is expanded in a Taylor series per 32-point chunk of the
  * grid (coefficients in FP64) and every grid point is evaluated in FP32 and
  * float-pair arithmetic, which keeps the build bound by memory bandwidth
