@@ -147,7 +147,7 @@ RB_API int rb_event_free(rb_event_t ev);
  * rounding), and a theta_ref argument discards it.  RB_MIXED / RB_MIXED_F64PHASE: the
  * fiducial phase is expanded in a Taylor series per 32-point chunk of the
  * grid (coefficients in FP64) and every grid point is evaluated in FP32 and
- * float-pair arithmetic, which keeps the build bound by memory bandwidth
+ * float-pair arithmetic, which keeps the per-point work off the FP64 pipe
  * (used when T f_low >= 1024 and N <= 2^30, otherwise the FP64 sums are used).
  * Asynchronous on `stream`, allocates nothing; batch calls ordered after it
  * on the same stream see the new tables, and the caller must not run batches
