@@ -341,34 +341,62 @@ cudaError_t launch_summary(const DataPtrs& in, int64_t kmin, int64_t N, double T
 // FP64 summary sums from the stored fiducial waveform h0_d(f) (written by
 // k_summary for the current theta_ref): the build then streams the strain,
 // the PSD and h0, 40 B per (point, detector), with no waveform arithmetic.
-// One warp per part of a bin (the fast build's parts), all detectors; the
-// per-point terms are k_summary's expressions; warp sums in a fixed order,
-// the parts of a bin added in index order by the last of them to finish,
-// which runs the FP64 epilogue (base log L by the fixed-point sum).
+// One block of kStoredThreads per part of a bin (the fast build's parts), all
+// detectors; the per-point terms are k_summary's, with f = (kmin + k) (1/T)
+// and 1/S from rcp_newton in place of the two FP64 divisions (the FP64 pipe
+// is the bound); block sums in a fixed order, the parts of a bin added in index order by the
+// last of them to finish, which runs the FP64 epilogue (base log L by the
+// fixed-point sum).  Several warps per part keep enough FP64 work in flight
+// to cover the FP64 pipe's latency.
+constexpr int kStoredThreads = 128;
+
+// 1/S for a positive normal double by Newton-Raphson iteration for the
+// reciprocal, r <- r + r (1 - S r), which doubles the correct bits per step:
+// the seed is the FP32 reciprocal of S scaled to [1, 2) (built and moved back
+// to FP64 with integer operations, ~23 correct bits), two steps give FP64
+// accuracy (within 1 ulp).  Four FP64 FMAs in all; other inputs take the
+// division.
+__device__ __forceinline__ double rcp_newton(double S) {
+  const unsigned hi = (unsigned)__double2hiint(S), lo = (unsigned)__double2loint(S);
+  const int ef = (int)((hi >> 20) & 0x7FFu);
+  if (ef == 0 || ef == 0x7FF || (hi >> 31)) return 1.0 / S;
+  const float s1 = __uint_as_float(0x3F800000u | ((hi & 0xFFFFFu) << 3) | (lo >> 29));  // S 2^-e, truncated
+  const unsigned rb = __float_as_uint(__frcp_rn(s1));  // in (0.5, 1]
+  const int er = (int)((rb >> 23) & 0xFFu) - 127;
+  const unsigned m = rb & 0x7FFFFFu;
+  double r = __hiloint2double((int)(((unsigned)(er + 1023 - (ef - 1023)) << 20) | (m >> 3)), (int)((m & 7u) << 29));
+  r = fma(r, fma(-S, r, 1.0), r);
+  r = fma(r, fma(-S, r, 1.0), r);
+  return r;
+}
+
 template <int ND>
-__global__ void __launch_bounds__(32) k_summary_stored(DataPtrs in, const double* __restrict__ h0, int64_t kmin,
-                                                       int64_t N, double T, int B, const int64_t* __restrict__ edges,
-                                                       SummaryOut so) {
+__global__ void __launch_bounds__(kStoredThreads) k_summary_stored(DataPtrs in, const double* __restrict__ h0,
+                                                                   int64_t kmin, int64_t N, double T, int B,
+                                                                   const int64_t* __restrict__ edges, SummaryOut so) {
+  __shared__ double red[6 * ND][kStoredThreads];  // per-thread sums, one row per quantity
+  __shared__ double qsum[6 * kMaxDet];
   __shared__ double sblock[6 * kMaxDet];
   __shared__ bool s_last;
-  const int pid = blockIdx.x, lane = threadIdx.x;
+  const int pid = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const PartDesc pd = so.parts[pid];
   const int b = pd.bin;
   const double fm = 0.5 * (grid_f(kmin, edges[b], T) + grid_f(kmin, edges[b + 1], T));
-  const double w0 = 4.0 / T;
+  const double inv_T = 1.0 / T;
   double acc[ND][6];
 #pragma unroll
   for (int d = 0; d < ND; ++d)
 #pragma unroll
     for (int j = 0; j < 6; ++j) acc[d][j] = 0.0;
-  for (int64_t k = pd.start + lane; k < pd.end; k += 32) {
-    const double f = grid_f(kmin, k, T);
+  // sums of the terms over S; the factor 4 df = 4 / T is applied to the sums
+  for (int64_t k = pd.start + tid; k < pd.end; k += kStoredThreads) {
+    const double f = (double)(kmin + k) * inv_T;
     const double df = f - fm;
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
       const double2 dv = __ldcs(reinterpret_cast<const double2*>(in.data[d]) + k);
       const double2 hv = __ldcs(reinterpret_cast<const double2*>(h0) + (size_t)d * N + k);
-      const double w = w0 / __ldcs(in.psd[d] + k);
+      const double w = rcp_newton(__ldcs(in.psd[d] + k));
       const double hr = hv.x, hi = hv.y, dr = dv.x, di = dv.y;
       const double xr = dr * hr + di * hi, xi = di * hr - dr * hi, hh = hr * hr + hi * hi;
       acc[d][0] += w * xr;
@@ -379,43 +407,51 @@ __global__ void __launch_bounds__(32) k_summary_stored(DataPtrs in, const double
       acc[d][5] += w * hh * df;
     }
   }
-  double mine = 0.0;  // lane 6 d + j holds sum (d, j)
+  // block sums in a fixed order: warp w takes quantities w, w + 4, ...; each
+  // lane adds the 4 threads l, l + 32, l + 64, l + 96, then a shuffle tree
 #pragma unroll
   for (int d = 0; d < ND; ++d)
 #pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      const double t = warp_sum_f64(acc[d][j]);
-      if (lane == 6 * d + j) mine = t;
-    }
+    for (int j = 0; j < 6; ++j) red[6 * d + j][tid] = acc[d][j];
+  __syncthreads();
+  for (int q = wid; q < 6 * ND; q += kStoredThreads / 32) {
+    double v = red[q][lane];
+#pragma unroll
+    for (int i = 1; i < kStoredThreads / 32; ++i) v += red[q][lane + 32 * i];
+    v = warp_sum_f64(v);
+    if (lane == 0) qsum[q] = 4.0 * inv_T * v;
+  }
+  __syncthreads();
+  double mine = tid < 6 * ND ? qsum[tid] : 0.0;
   if (pd.n_parts > 1) {
     double* ps = reinterpret_cast<double*>(so.part_sums);  // [n_parts][kPartSlots] doubles
-    if (lane < 6 * ND) ps[(size_t)pid * kPartSlots + lane] = mine;
+    if (tid < 6 * ND) ps[(size_t)pid * kPartSlots + tid] = mine;
     __threadfence();
-    __syncwarp();
-    if (lane == 0) {
+    __syncthreads();
+    if (tid == 0) {
       const unsigned ticket = atomicAdd(&so.sync->bin_parts_done[b], 1u);
       s_last = (ticket == (unsigned)pd.n_parts - 1u);
       if (s_last) so.sync->bin_parts_done[b] = 0u;
     }
-    __syncwarp();
+    __syncthreads();
     if (!s_last) return;
     __threadfence();
-    if (lane < 6 * ND) {
-      const double* p0 = ps + (size_t)pd.first * kPartSlots + lane;
+    if (tid < 6 * ND) {
+      const double* p0 = ps + (size_t)pd.first * kPartSlots + tid;
       double t = __ldcg(p0);
       for (int p = 1; p < pd.n_parts; ++p) t += __ldcg(p0 + (size_t)p * kPartSlots);
       mine = t;
     }
   }
-  if (lane < 6 * ND) sblock[lane] = mine;
-  __syncwarp();
+  if (tid < 6 * ND) sblock[tid] = mine;
+  __syncthreads();
   summary_epilogue(so, b, 0, ND, B, ND, sblock, nullptr, false, (unsigned)B, so.inv_df[b], true);
 }
 
 cudaError_t launch_summary_stored(const DataPtrs& in, const double* h0, int64_t kmin, int64_t N, double T, int D, int B,
                                   const int64_t* edges, const SummaryOut& so, int n_parts, cudaStream_t s) {
   auto kf = D == 1 ? k_summary_stored<1> : D == 2 ? k_summary_stored<2> : k_summary_stored<3>;
-  kf<<<(unsigned)n_parts, 32, 0, s>>>(in, h0, kmin, N, T, B, edges, so);
+  kf<<<(unsigned)n_parts, kStoredThreads, 0, s>>>(in, h0, kmin, N, T, B, edges, so);
   return cudaGetLastError();
 }
 
