@@ -513,8 +513,10 @@ def run_full(rb, torch, event, ev, args, dist, device, flush, rb_value, W=1024):
 
 def run_e2e(rb, torch, event, ev, data, psd, theta, W, args, dist, device):
     """Same metric through the public API on pinned host buffers
-    (rb_rebuild_loglike_grad_host): strain/PSD and walkers copied in every
-    step, log L and gradient copied out, the stream synchronised."""
+    (rb_rebuild_loglike_grad_host): strain/PSD and walkers brought in every
+    step (strain/PSD read by a kernel over the host link, walkers copied), log
+    L and gradient written back to the pinned outputs, the stream
+    synchronised."""
     import ctypes
     D, N = ev["geom"].shape[0], ev["N"]
     h_data = [data[d].cpu().pin_memory() for d in range(D)]

@@ -210,8 +210,11 @@ RB_API int rb_rebuild_loglike_grad(rb_event_t ev, const double* theta_dev, int64
  * boundary are read by one kernel over the host link, which writes the
  * resident FP64 copy and the FP32 working copy in the same pass; other
  * buffers are copied by the copy engine and then converted.  Both give the
- * same bits.  Results equal rb_event_rebuild with the same host data followed
- * by rb_loglike_grad_host.  Errors: those of the two calls. */
+ * same bits.  When logl_host (and grad_host, if not NULL) are pinned, mapped
+ * buffers starting on 8-byte boundaries, the likelihood kernel writes them
+ * directly and no copy back is made.  Results equal rb_event_rebuild with the
+ * same host data followed by rb_loglike_grad_host.  Errors: those of the two
+ * calls. */
 RB_API int rb_rebuild_loglike_grad_host(rb_event_t ev, const double* const* data_host, const double* const* psd_host,
                                         const double* theta_host, int64_t W, double* logl_host, double* grad_host,
                                         int mode, void* stream);
@@ -219,7 +222,9 @@ RB_API int rb_rebuild_loglike_grad_host(rb_event_t ev, const double* const* data
 /* End-to-end convenience form of rb_loglike_grad_batch for host buffers:
  * copies theta_host [W][13] to the device, evaluates, copies logl_host [W]
  * (and grad_host [W][13] unless NULL) back, and synchronises the stream.
- * theta_host/logl_host/grad_host should be pinned for full copy bandwidth. */
+ * theta_host/logl_host/grad_host should be pinned for full copy bandwidth;
+ * pinned, mapped, 8-byte-aligned logl_host/grad_host are written by the
+ * likelihood kernel directly (no copy back). */
 RB_API int rb_loglike_grad_host(rb_event_t ev, const double* theta_host, int64_t W, double* logl_host, double* grad_host,
                          int mode, void* stream);
 

@@ -231,14 +231,19 @@ def loglike_grad(event: Event, theta: torch.Tensor, mode="mixed", stream=None):
     return out, grad
 
 
-def loglike_grad_host(event: Event, theta: np.ndarray, logl_out: np.ndarray, grad_out: Optional[np.ndarray],
-                      mode="mixed", stream=None) -> None:
-    """End-to-end call on host buffers (copies in, evaluates, copies out, syncs)."""
+def _host_ptr(a) -> int:
+    return a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data
+
+
+def loglike_grad_host(event: Event, theta: np.ndarray, logl_out, grad_out=None, mode="mixed", stream=None) -> None:
+    """End-to-end call on host buffers (numpy arrays or CPU tensors, ideally
+    pinned): copies in, evaluates, copies out (pinned outputs are written by
+    the kernel directly), synchronises."""
     th = np.ascontiguousarray(theta, dtype=np.float64)
     W = th.shape[0]
     check(load().rb_loglike_grad_host(event.handle, ctypes.c_void_p(th.ctypes.data), W,
-                                      ctypes.c_void_p(logl_out.ctypes.data),
-                                      ctypes.c_void_p(grad_out.ctypes.data) if grad_out is not None else None,
+                                      ctypes.c_void_p(_host_ptr(logl_out)),
+                                      ctypes.c_void_p(_host_ptr(grad_out)) if grad_out is not None else None,
                                       _mode(mode), _stream_handle(stream)), "rb_loglike_grad_host")
 
 

@@ -515,34 +515,6 @@ int rb_loglike_batch(rb_event_t ev, const double* theta_dev, int64_t W, double* 
   return rb::run_batch(event_entry(ev), theta_dev, W, logl_dev, nullptr, mode, (cudaStream_t)stream, nullptr);
 }
 
-int rb_loglike_grad_host(rb_event_t ev, const double* theta_host, int64_t W, double* logl_host, double* grad_host,
-                         int mode, void* stream) {
-  if (!ev) return set_error(RB_EINVAL, "rb_loglike_grad_host: NULL event");
-  if (W < 0) return set_error(RB_EINVAL, "rb_loglike_grad_host: W < 0");
-  if (W == 0) return RB_OK;
-  if (!theta_host || !logl_host) return set_error(RB_EINVAL, "rb_loglike_grad_host: NULL buffer");
-  cudaStream_t s = (cudaStream_t)stream;
-  double *d_theta = nullptr, *d_logl = nullptr, *d_grad = nullptr;
-  int rc = RB_OK;
-  cudaError_t err;
-  do {
-    if ((err = ws_alloc(reinterpret_cast<void**>(&d_theta), sizeof(double) * kNPar * W, s)) != cudaSuccess) { rc = cuda_fail(err, "workspace allocation (theta)"); break; }
-    if ((err = ws_alloc(reinterpret_cast<void**>(&d_logl), sizeof(double) * W, s)) != cudaSuccess) { rc = cuda_fail(err, "workspace allocation (logl)"); break; }
-    if (grad_host && (err = ws_alloc(reinterpret_cast<void**>(&d_grad), sizeof(double) * kNPar * W, s)) != cudaSuccess) { rc = cuda_fail(err, "workspace allocation (grad)"); break; }
-    if ((err = cudaMemcpyAsync(d_theta, theta_host, sizeof(double) * kNPar * W, cudaMemcpyHostToDevice, s)) != cudaSuccess) { rc = cuda_fail(err, "copy theta"); break; }
-    rc = rb::run_batch(&ev->e, d_theta, W, d_logl, d_grad, mode, s, nullptr);
-    if (rc != RB_OK) break;
-    if ((err = cudaMemcpyAsync(logl_host, d_logl, sizeof(double) * W, cudaMemcpyDeviceToHost, s)) != cudaSuccess) { rc = cuda_fail(err, "copy logl"); break; }
-    if (grad_host && (err = cudaMemcpyAsync(grad_host, d_grad, sizeof(double) * kNPar * W, cudaMemcpyDeviceToHost, s)) != cudaSuccess) { rc = cuda_fail(err, "copy grad"); break; }
-  } while (false);
-  if (d_theta) cudaFreeAsync(d_theta, s);
-  if (d_logl) cudaFreeAsync(d_logl, s);
-  if (d_grad) cudaFreeAsync(d_grad, s);
-  err = cudaStreamSynchronize(s);
-  if (rc == RB_OK && err != cudaSuccess) rc = cuda_fail(err, "synchronise");
-  return rc;
-}
-
 namespace rb {
 // Device address of a pinned, mapped host buffer that starts on an `align`
 // boundary, or NULL (pageable memory, or unaligned).
@@ -557,7 +529,54 @@ static const double* mapped_host(const double* p, size_t align) {
   if (reinterpret_cast<uintptr_t>(a.devicePointer) % align != 0) return nullptr;
   return static_cast<const double*>(a.devicePointer);
 }
+
+// Output buffers of the host-buffer calls: when log L (and the gradient, if
+// asked for) are pinned, mapped host buffers, the likelihood kernel writes
+// them directly over the host link and no copy back is needed.
+struct HostOut {
+  double* logl = nullptr;
+  double* grad = nullptr;
+  bool direct = false;
+};
+static HostOut mapped_outputs(double* logl_host, double* grad_host) {
+  HostOut o;
+  o.logl = const_cast<double*>(mapped_host(logl_host, 8));
+  o.grad = grad_host ? const_cast<double*>(mapped_host(grad_host, 8)) : nullptr;
+  o.direct = o.logl && (!grad_host || o.grad);
+  return o;
+}
 }  // namespace rb
+
+int rb_loglike_grad_host(rb_event_t ev, const double* theta_host, int64_t W, double* logl_host, double* grad_host,
+                         int mode, void* stream) {
+  if (!ev) return set_error(RB_EINVAL, "rb_loglike_grad_host: NULL event");
+  if (W < 0) return set_error(RB_EINVAL, "rb_loglike_grad_host: W < 0");
+  if (W == 0) return RB_OK;
+  if (!theta_host || !logl_host) return set_error(RB_EINVAL, "rb_loglike_grad_host: NULL buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  double *d_theta = nullptr, *d_logl = nullptr, *d_grad = nullptr;
+  const rb::HostOut out = rb::mapped_outputs(logl_host, grad_host);
+  int rc = RB_OK;
+  cudaError_t err;
+  do {
+    if ((err = ws_alloc(reinterpret_cast<void**>(&d_theta), sizeof(double) * kNPar * W, s)) != cudaSuccess) { rc = cuda_fail(err, "workspace allocation (theta)"); break; }
+    if (!out.direct) {
+      if ((err = ws_alloc(reinterpret_cast<void**>(&d_logl), sizeof(double) * W, s)) != cudaSuccess) { rc = cuda_fail(err, "workspace allocation (logl)"); break; }
+      if (grad_host && (err = ws_alloc(reinterpret_cast<void**>(&d_grad), sizeof(double) * kNPar * W, s)) != cudaSuccess) { rc = cuda_fail(err, "workspace allocation (grad)"); break; }
+    }
+    if ((err = cudaMemcpyAsync(d_theta, theta_host, sizeof(double) * kNPar * W, cudaMemcpyHostToDevice, s)) != cudaSuccess) { rc = cuda_fail(err, "copy theta"); break; }
+    rc = rb::run_batch(&ev->e, d_theta, W, out.direct ? out.logl : d_logl, out.direct ? out.grad : d_grad, mode, s, nullptr);
+    if (rc != RB_OK || out.direct) break;
+    if ((err = cudaMemcpyAsync(logl_host, d_logl, sizeof(double) * W, cudaMemcpyDeviceToHost, s)) != cudaSuccess) { rc = cuda_fail(err, "copy logl"); break; }
+    if (grad_host && (err = cudaMemcpyAsync(grad_host, d_grad, sizeof(double) * kNPar * W, cudaMemcpyDeviceToHost, s)) != cudaSuccess) { rc = cuda_fail(err, "copy grad"); break; }
+  } while (false);
+  if (d_theta) cudaFreeAsync(d_theta, s);
+  if (d_logl) cudaFreeAsync(d_logl, s);
+  if (d_grad) cudaFreeAsync(d_grad, s);
+  err = cudaStreamSynchronize(s);
+  if (rc == RB_OK && err != cudaSuccess) rc = cuda_fail(err, "synchronise");
+  return rc;
+}
 
 int rb_rebuild_loglike_grad_host(rb_event_t ev, const double* const* data_host, const double* const* psd_host,
                                  const double* theta_host, int64_t W, double* logl_host, double* grad_host, int mode,
@@ -574,6 +593,7 @@ int rb_rebuild_loglike_grad_host(rb_event_t ev, const double* const* data_host, 
   if (W > 0 && (!theta_host || !logl_host)) return set_error(RB_EINVAL, "rb_rebuild_loglike_grad_host: NULL buffer");
   cudaStream_t s = (cudaStream_t)stream;
   double *d_theta = nullptr, *d_logl = nullptr, *d_grad = nullptr;
+  const HostOut out = W > 0 ? mapped_outputs(logl_host, grad_host) : HostOut{};
   int rc = RB_OK;
   cudaError_t err;
   // pinned (mapped) buffers are read by one kernel over the host link, which
@@ -606,12 +626,15 @@ int rb_rebuild_loglike_grad_host(rb_event_t ev, const double* const* data_host, 
     if (err != cudaSuccess || (err = cudaEventRecord(e.ev_data, e.copy)) != cudaSuccess) { rc = cuda_fail(err, "copy strain"); break; }
     if (W > 0) {
       if ((err = ws_alloc(reinterpret_cast<void**>(&d_theta), sizeof(double) * kNPar * W, s)) != cudaSuccess) { rc = cuda_fail(err, "workspace allocation (theta)"); break; }
-      if ((err = ws_alloc(reinterpret_cast<void**>(&d_logl), sizeof(double) * W, s)) != cudaSuccess) { rc = cuda_fail(err, "workspace allocation (logl)"); break; }
-      if (grad_host && (err = ws_alloc(reinterpret_cast<void**>(&d_grad), sizeof(double) * kNPar * W, s)) != cudaSuccess) { rc = cuda_fail(err, "workspace allocation (grad)"); break; }
+      if (!out.direct) {
+        if ((err = ws_alloc(reinterpret_cast<void**>(&d_logl), sizeof(double) * W, s)) != cudaSuccess) { rc = cuda_fail(err, "workspace allocation (logl)"); break; }
+        if (grad_host && (err = ws_alloc(reinterpret_cast<void**>(&d_grad), sizeof(double) * kNPar * W, s)) != cudaSuccess) { rc = cuda_fail(err, "workspace allocation (grad)"); break; }
+      }
       if ((err = cudaMemcpyAsync(d_theta, theta_host, sizeof(double) * kNPar * W, cudaMemcpyHostToDevice, s)) != cudaSuccess) { rc = cuda_fail(err, "copy theta"); break; }
     }
-    rc = rebuild_and_batch(e, d_theta, W, d_logl, d_grad, mode, s, e.ev_data);
-    if (rc != RB_OK || W == 0) break;
+    rc = rebuild_and_batch(e, d_theta, W, out.direct ? out.logl : d_logl, out.direct ? out.grad : d_grad, mode, s,
+                           e.ev_data);
+    if (rc != RB_OK || W == 0 || out.direct) break;
     if ((err = cudaMemcpyAsync(logl_host, d_logl, sizeof(double) * W, cudaMemcpyDeviceToHost, s)) != cudaSuccess) { rc = cuda_fail(err, "copy logl"); break; }
     if (grad_host && (err = cudaMemcpyAsync(grad_host, d_grad, sizeof(double) * kNPar * W, cudaMemcpyDeviceToHost, s)) != cudaSuccess) { rc = cuda_fail(err, "copy grad"); break; }
   } while (false);

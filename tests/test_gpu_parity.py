@@ -549,6 +549,21 @@ def test_host_step_mapped_equals_copied(rb, case, request):
     ref = outs["pageable"]
     np.testing.assert_array_equal(ref[2], ref[0])
     np.testing.assert_array_equal(ref[3], ref[1])
+    # pinned outputs are written by the likelihood kernel itself
+    data, psd = [_pinned(a, 0) for a in arrs], [_pinned(ev["psd"][d], 0) for d in range(D)]
+    Lp = torch.zeros(300, dtype=torch.float64).pin_memory()
+    Gp = torch.zeros(300, 13, dtype=torch.float64).pin_memory()
+    rb.rebuild_loglike_grad_host(c.event, data, psd, th, Lp, Gp, mode="mixed")
+    np.testing.assert_array_equal(Lp.numpy(), ref[0])
+    np.testing.assert_array_equal(Gp.numpy(), ref[1])
+    Lp.zero_()
+    rb.rebuild_loglike_grad_host(c.event, data, psd, th, Lp, None, mode="mixed")
+    np.testing.assert_array_equal(Lp.numpy(), ref[0])
+    Lp.zero_()
+    Gp.zero_()
+    rb.loglike_grad_host(c.event, th, Lp, Gp, mode="mixed")
+    np.testing.assert_array_equal(Lp.numpy(), ref[0])
+    np.testing.assert_array_equal(Gp.numpy(), ref[1])
     for name, o in outs.items():
         for i in (0, 1, 2, 3, 5):
             np.testing.assert_array_equal(o[i], ref[i], err_msg=name)
