@@ -24,36 +24,64 @@ struct MalaBox {
   double eps[kNPar], lo[kNPar], hi[kNPar];
 };
 
-// One thread per chain: proposal, box test, likelihood parameters theta(z')
-// (theta(z) of the current state for a proposal outside the box: it is
-// evaluated but rejected), log u and the Jacobian factors of the two angle
-// coordinates at the proposal.
-__global__ void __launch_bounds__(128) k_mala_propose(const double* __restrict__ z, const double* __restrict__ gz,
-                                                     const double* __restrict__ xi, const double* __restrict__ u,
-                                                     MalaBox box, int64_t W, int init, double* __restrict__ zp,
-                                                     double* __restrict__ theta, double* __restrict__ lu,
-                                                     double* __restrict__ jac, int* __restrict__ inside) {
-  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= W) return;
-  double p[kNPar], c[kNPar];
-  bool in = true;
-  for (int j = 0; j < kNPar; ++j) {
-    const int64_t i = w * kNPar + j;
-    c[j] = z[i];
-    p[j] = init ? c[j] : c[j] + 0.5 * box.eps[j] * box.eps[j] * gz[i] + box.eps[j] * xi[i];
-    in = in && p[j] > box.lo[j] && p[j] < box.hi[j];
-    zp[i] = p[j];
+// Proposal, box test, likelihood parameters theta(z') (theta(z) of the
+// current state for a proposal outside the box: it is evaluated but
+// rejected), log u and the Jacobian factors of the two angle coordinates at
+// the proposal.  A block of four warps takes 32 chains, lane = chain, so every
+// FP64 instruction runs on full warps (the FP64 pipe issues per warp):
+// warp k forms the proposals of parameters k, k + 4, ...; after the box test,
+// the four warps evaluate acos (warp 0), asin (1), the Jacobian factors (2)
+// and log u (3) side by side.
+constexpr int kProposeThreads = 128;
+__global__ void __launch_bounds__(kProposeThreads) k_mala_propose(const double* __restrict__ z,
+                                                                 const double* __restrict__ gz,
+                                                                 const double* __restrict__ xi,
+                                                                 const double* __restrict__ u, MalaBox box, int64_t W,
+                                                                 int init, double* __restrict__ zp,
+                                                                 double* __restrict__ theta, double* __restrict__ lu,
+                                                                 double* __restrict__ jac, int* __restrict__ inside) {
+  __shared__ double sp[kNPar][32], sc[kNPar][32];  // proposal and current state of the block's chains
+  __shared__ int sok[kNPar][32];
+  const int lane = threadIdx.x & 31, k = threadIdx.x >> 5;
+  const int64_t w = (int64_t)blockIdx.x * 32 + lane;
+  const bool live = w < W;
+  for (int j = k; j < kNPar; j += kProposeThreads / 32) {
+    double c = 0.0, p = 0.0;
+    bool ok = true;
+    if (live) {
+      const int64_t i = w * kNPar + j;
+      c = z[i];
+      p = init ? c : c + 0.5 * box.eps[j] * box.eps[j] * gz[i] + box.eps[j] * xi[i];
+      ok = p > box.lo[j] && p < box.hi[j];
+      zp[i] = p;
+    }
+    sp[j][lane] = p;
+    sc[j][lane] = c;
+    sok[j][lane] = ok ? 1 : 0;
   }
-  const double* src = in ? p : c;
-  for (int j = 0; j < kNPar; ++j) theta[w * kNPar + j] = src[j];
-  theta[w * kNPar + 9] = acos(src[9]);
-  theta[w * kNPar + 12] = asin(src[12]);
-  // d iota / d cos iota = -1 / sin iota, d dec / d sin dec = 1 / cos dec
-  // (1 - z^2 as (1 - z)(1 + z): no cancellation next to the box edges)
-  jac[2 * w] = in ? -1.0 / sqrt((1.0 - p[9]) * (1.0 + p[9])) : 0.0;
-  jac[2 * w + 1] = in ? 1.0 / sqrt((1.0 - p[12]) * (1.0 + p[12])) : 0.0;
-  lu[w] = init ? 0.0 : log(u[w]);
-  inside[w] = in ? 1 : 0;
+  __syncthreads();
+  if (!live) return;
+  bool in = true;
+#pragma unroll
+  for (int j = 0; j < kNPar; ++j) in = in && sok[j][lane];
+  if (k == 0) {
+    for (int j = 0; j < kNPar; ++j) {  // all but parameter 12 (warp 1)
+      if (j == 12) continue;
+      const double src = in ? sp[j][lane] : sc[j][lane];
+      theta[w * kNPar + j] = j == 9 ? acos(src) : src;
+    }
+  } else if (k == 1) {
+    theta[w * kNPar + 12] = asin(in ? sp[12][lane] : sc[12][lane]);
+  } else if (k == 2) {
+    // d iota / d cos iota = -1 / sin iota, d dec / d sin dec = 1 / cos dec
+    // (1 - z^2 as (1 - z)(1 + z): no cancellation next to the box edges)
+    const double p9 = sp[9][lane], p12 = sp[12][lane];
+    jac[2 * w] = in ? -1.0 / sqrt((1.0 - p9) * (1.0 + p9)) : 0.0;
+    jac[2 * w + 1] = in ? 1.0 / sqrt((1.0 - p12) * (1.0 + p12)) : 0.0;
+  } else {
+    lu[w] = init ? 0.0 : log(u[w]);
+    inside[w] = in ? 1 : 0;
+  }
 }
 
 // Per-chain workspace of a MALA call (bytes per chain, without the batch's).
@@ -90,8 +118,8 @@ static int mala_run(rb_event_t ev, double* z, double* logp, double* gz, int64_t 
   double* jac = lu + W;
   int* inside = reinterpret_cast<int*>(jac + 2 * W);
   int* acc_scratch = inside + W;
-  k_mala_propose<<<(unsigned)((W + 127) / 128), 128, 0, s>>>(z, gz, xi, u, box, W, init ? 1 : 0, zp, theta, lu, jac,
-                                                               inside);
+  k_mala_propose<<<(unsigned)((W + 31) / 32), kProposeThreads, 0, s>>>(z, gz, xi, u, box, W, init ? 1 : 0, zp, theta,
+                                                                       lu, jac, inside);
   err = cudaGetLastError();
   int rc = RB_OK;
   if (err != cudaSuccess) {
