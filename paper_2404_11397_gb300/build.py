@@ -61,7 +61,7 @@ def build(verbose: bool = False, force: bool = False) -> Path:
         list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB.with_suffix(f".{os.getpid()}.tmp")
-        run([cc, *ARCH, "-shared", "-o", str(tmp), *map(str, objs), "-lpthread"])
+        run([cc, *ARCH, "-shared", "-o", str(tmp), *map(str, objs), "-lpthread", "-ldl"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -231,6 +231,7 @@ static int make_parts(EventEntry& e, cudaStream_t s) {
 }
 
 int rb_event_free(rb_event_t ev) {
+  RB_NVTX("rb_event_free");
   if (!ev) return RB_OK;
   EventEntry& e = ev->e;
   cudaFree(e.d_edges);
@@ -269,6 +270,7 @@ int rb_event_free(rb_event_t ev) {
 }
 
 int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
+  RB_NVTX("rb_build_summary");
   if (!desc || !out) return set_error(RB_EINVAL, "rb_build_summary: NULL descriptor or output");
   *out = nullptr;
   const int D = desc->n_det, B = desc->n_bins;
@@ -411,6 +413,7 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
 
 int rb_event_rebuild(rb_event_t ev, const double* theta_ref_host, const double* const* data, const double* const* psd,
                      int data_on_device, int mode, void* stream) {
+  RB_NVTX("rb_event_rebuild");
   if (!ev) return set_error(RB_EINVAL, "rb_event_rebuild: NULL event");
   if (mode != RB_MIXED && mode != RB_FP64 && mode != RB_MIXED_F64PHASE) return set_error(RB_EINVAL, "rb_event_rebuild: bad mode %d", mode);
   EventEntry& e = ev->e;
@@ -452,6 +455,7 @@ int rb_event_rebuild(rb_event_t ev, const double* theta_ref_host, const double* 
 void rb_set_trace_events(void* before_main, void* after_main) { set_trace_events(before_main, after_main); }
 
 int rb_event_get_info(rb_event_t ev, rb_event_info* info) {
+  RB_NVTX("rb_event_get_info");
   if (!ev || !info) return set_error(RB_EINVAL, "rb_event_get_info: NULL argument");
   const EventEntry& e = ev->e;
   info->n_det = e.n_det;
@@ -467,6 +471,7 @@ int rb_event_get_info(rb_event_t ev, rb_event_info* info) {
 }
 
 int rb_event_get_summary(rb_event_t ev, double* A0, double* A1, double* B0, double* B1, int64_t* edges) {
+  RB_NVTX("rb_event_get_summary");
   if (!ev) return set_error(RB_EINVAL, "rb_event_get_summary: NULL event");
   const EventEntry& e = ev->e;
   const int D = e.n_det, B = e.n_bins;
@@ -486,6 +491,7 @@ int rb_event_get_summary(rb_event_t ev, double* A0, double* A1, double* B0, doub
 
 int rb_loglike_grad_batch(rb_event_t ev, const double* theta_dev, int64_t W, double* logl_dev, double* grad_dev,
                           int mode, void* stream) {
+  RB_NVTX("rb_loglike_grad_batch");
   return rb::run_batch(event_entry(ev), theta_dev, W, logl_dev, grad_dev, mode, (cudaStream_t)stream, nullptr);
 }
 
@@ -502,6 +508,7 @@ static cudaError_t ensure_stream(cudaStream_t& st, cudaEvent_t& ev) {
 
 int rb_rebuild_loglike_grad(rb_event_t ev, const double* theta_dev, int64_t W, double* logl_dev, double* grad_dev,
                             int mode, void* stream) {
+  RB_NVTX("rb_rebuild_loglike_grad");
   using namespace rb;
   if (!ev) return set_error(RB_EINVAL, "rb_rebuild_loglike_grad: NULL event");
   if (W < 0) return set_error(RB_EINVAL, "rb_rebuild_loglike_grad: W < 0");
@@ -512,6 +519,7 @@ int rb_rebuild_loglike_grad(rb_event_t ev, const double* theta_dev, int64_t W, d
 }
 
 int rb_loglike_batch(rb_event_t ev, const double* theta_dev, int64_t W, double* logl_dev, int mode, void* stream) {
+  RB_NVTX("rb_loglike_batch");
   return rb::run_batch(event_entry(ev), theta_dev, W, logl_dev, nullptr, mode, (cudaStream_t)stream, nullptr);
 }
 
@@ -549,6 +557,7 @@ static HostOut mapped_outputs(double* logl_host, double* grad_host) {
 
 int rb_loglike_grad_host(rb_event_t ev, const double* theta_host, int64_t W, double* logl_host, double* grad_host,
                          int mode, void* stream) {
+  RB_NVTX("rb_loglike_grad_host");
   if (!ev) return set_error(RB_EINVAL, "rb_loglike_grad_host: NULL event");
   if (W < 0) return set_error(RB_EINVAL, "rb_loglike_grad_host: W < 0");
   if (W == 0) return RB_OK;
@@ -581,6 +590,7 @@ int rb_loglike_grad_host(rb_event_t ev, const double* theta_host, int64_t W, dou
 int rb_rebuild_loglike_grad_host(rb_event_t ev, const double* const* data_host, const double* const* psd_host,
                                  const double* theta_host, int64_t W, double* logl_host, double* grad_host, int mode,
                                  void* stream) {
+  RB_NVTX("rb_rebuild_loglike_grad_host");
   using namespace rb;
   if (!ev) return set_error(RB_EINVAL, "rb_rebuild_loglike_grad_host: NULL event");
   if (W < 0) return set_error(RB_EINVAL, "rb_rebuild_loglike_grad_host: W < 0");
@@ -650,6 +660,7 @@ int rb_rebuild_loglike_grad_host(rb_event_t ev, const double* const* data_host, 
 
 int rb_strain(const double* geom, double gmst, const double* theta_host, double T, int64_t kmin, int64_t n_freq,
               double* h_dev, void* stream) {
+  RB_NVTX("rb_strain");
   if (!geom || !theta_host || !h_dev) return set_error(RB_EINVAL, "rb_strain: NULL argument");
   if (!(T > 0.0) || n_freq < 1 || kmin < 1) return set_error(RB_EINVAL, "rb_strain: invalid grid");
   cudaStream_t s = (cudaStream_t)stream;

@@ -4,11 +4,23 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "rb.h"
 #include "rb_internal.cuh"
 
 namespace rb {
+
+// NVTX range over one ABI call: named ranges in profiler timelines (nsys,
+// ncu's --nvtx filters); without a tool attached a push/pop costs a few
+// nanoseconds.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define RB_NVTX(name) ::rb::NvtxRange rb_nvtx_range_(name)
 
 // Host record of one event and the device memory it owns.
 struct EventEntry {

@@ -294,6 +294,7 @@ cudaError_t launch_data32(const DataPtrs& in, int64_t N, int D, void* w32, float
 
 extern "C" int rb_loglike_full_batch(rb_event_t ev, const double* theta_dev, int64_t W, double* logl_dev, int mode,
                                      void* stream) {
+  RB_NVTX("rb_loglike_full_batch");
   using namespace rb;
   if (!ev) return set_error(RB_EINVAL, "rb_loglike_full_batch: NULL event");
   if (W < 0) return set_error(RB_EINVAL, "rb_loglike_full_batch: W < 0");

@@ -148,6 +148,7 @@ static int mala_run(rb_event_t ev, double* z, double* logp, double* gz, int64_t 
 
 extern "C" int rb_mala_init(rb_event_t ev, const double* z_dev, int64_t W, const double* lo_host,
                             const double* hi_host, double* logp_dev, double* gz_dev, int mode, void* stream) {
+  RB_NVTX("rb_mala_init");
   return rb::mala_run(ev, const_cast<double*>(z_dev), logp_dev, gz_dev, W, nullptr, lo_host, hi_host, nullptr,
                       nullptr, nullptr, mode, stream, true, "rb_mala_init");
 }
@@ -155,6 +156,7 @@ extern "C" int rb_mala_init(rb_event_t ev, const double* z_dev, int64_t W, const
 extern "C" int rb_mala_step(rb_event_t ev, double* z_dev, double* logp_dev, double* gz_dev, int64_t W,
                             const double* eps_host, const double* lo_host, const double* hi_host, const double* xi_dev,
                             const double* u_dev, int* accepted_dev, int mode, void* stream) {
+  RB_NVTX("rb_mala_step");
   return rb::mala_run(ev, z_dev, logp_dev, gz_dev, W, eps_host, lo_host, hi_host, xi_dev, u_dev, accepted_dev, mode,
                       stream, false, "rb_mala_step");
 }

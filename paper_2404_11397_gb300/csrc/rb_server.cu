@@ -213,6 +213,7 @@ struct rb_server_s {
 extern "C" {
 
 int rb_server_create(const rb_server_opts* opts, rb_server_t* out) {
+  RB_NVTX("rb_server_create");
   if (!out) return set_error(RB_EINVAL, "rb_server_create: NULL output");
   *out = nullptr;
   rb_server_opts o{};
@@ -260,6 +261,7 @@ int rb_server_create(const rb_server_opts* opts, rb_server_t* out) {
 }
 
 int rb_server_destroy(rb_server_t srv) {
+  RB_NVTX("rb_server_destroy");
   if (!srv) return RB_OK;
   Server& S = srv->s;
   {
@@ -285,6 +287,7 @@ int rb_server_destroy(rb_server_t srv) {
 }
 
 int rb_submit(rb_server_t srv, rb_event_t ev, const double* theta_host, int64_t W, int want_grad, uint64_t* ticket) {
+  RB_NVTX("rb_submit");
   if (!srv || !ev || !theta_host || !ticket) return set_error(RB_EINVAL, "rb_submit: NULL argument");
   Server& S = srv->s;
   if (W < 1 || W > S.opts.max_walkers) return set_error(RB_EINVAL, "rb_submit: W=%lld out of range", (long long)W);
@@ -315,6 +318,7 @@ int rb_submit(rb_server_t srv, rb_event_t ev, const double* theta_host, int64_t 
 }
 
 int rb_poll(rb_server_t srv, uint64_t ticket, int64_t timeout_us, double* logl_out, double* grad_out) {
+  RB_NVTX("rb_poll");
   if (!srv) return set_error(RB_EINVAL, "rb_poll: NULL server");
   Server& S = srv->s;
   std::unique_lock<std::mutex> lk(S.mu);
@@ -341,6 +345,7 @@ int rb_poll(rb_server_t srv, uint64_t ticket, int64_t timeout_us, double* logl_o
 }
 
 int rb_server_get_stats(rb_server_t srv, rb_server_stats* stats) {
+  RB_NVTX("rb_server_get_stats");
   if (!srv || !stats) return set_error(RB_EINVAL, "rb_server_get_stats: NULL argument");
   Server& S = srv->s;
   std::lock_guard<std::mutex> lk(S.mu);

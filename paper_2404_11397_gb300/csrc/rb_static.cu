@@ -60,6 +60,7 @@ static int static_workspace(void** out) {
 
 extern "C" int rb_loglike_grad_batch_static(rb_event_t ev, const double* theta_dev, int64_t W, double* logl_dev,
                                             double* grad_dev, int mode, void* stream) {
+  RB_NVTX("rb_loglike_grad_batch_static");
   if (!ev) return rb::set_error(RB_EINVAL, "rb_loglike_grad_batch_static: NULL event");
   if (W < 0) return rb::set_error(RB_EINVAL, "rb_loglike_grad_batch_static: W < 0");
   if (W > RB_STATIC_MAX_WALKERS)
