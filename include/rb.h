@@ -354,6 +354,18 @@ RB_API void rb_set_trace_events(void* before_main, void* after_main);
 RB_API uint64_t rb_kernel_launch_count(void);
 RB_API int rb_abi_version(void);
 
+/* Debug builds (compiled with -DRB_BOUNDS_CHECK, e.g. librb_checked.so): the
+ * number of checked device-side indices found outside their buffers since
+ * the last call -- in the likelihood kernels (walker and tangent records, the
+ * edge and bin tables, shared-memory staging, the outputs) and the summary
+ * kernels (parts, grid points, chunk records, staging) -- with the first
+ * one's site code, index and limit (NULL pointers are skipped); the records
+ * are cleared.  A checked index outside its buffer is replaced by 0, so the
+ * access stays in bounds and the results are wrong but the context is not.
+ * Synchronous.  Returns -1 in normal builds (no checks compiled in), RB_ECUDA
+ * if the records cannot be read. */
+RB_API int rb_debug_bounds(int* site, long long* index, long long* limit);
+
 #ifdef __cplusplus
 }
 #endif

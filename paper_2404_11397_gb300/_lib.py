@@ -3,9 +3,14 @@ only; every computation happens in the library's CUDA kernels."""
 from __future__ import annotations
 
 import ctypes
+import os
 from pathlib import Path
 
 LIB_PATH = Path(__file__).resolve().parent / "librb.so"
+# RB_LIB_VARIANT=checked loads the debug build with device-side bounds checks
+# (build.py --checked); anything else loads the normal library
+if os.environ.get("RB_LIB_VARIANT") == "checked":
+    LIB_PATH = LIB_PATH.with_name("librb_checked.so")
 
 RB_OK, RB_PENDING = 0, 1
 RB_EINVAL, RB_ENOMEM, RB_ECUDA, RB_ETIMEDOUT, RB_EBUSY, RB_ENOTFOUND, RB_ECLOSED = -1, -2, -3, -4, -5, -6, -7
@@ -93,6 +98,8 @@ SIGNATURES = {
     "rb_set_trace_events": (None, [ctypes.c_void_p, ctypes.c_void_p]),
     "rb_kernel_launch_count": (ctypes.c_uint64, []),
     "rb_abi_version": (ctypes.c_int, []),
+    "rb_debug_bounds": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong),
+                                       ctypes.POINTER(ctypes.c_longlong)]),
 }
 
 _lib = None

@@ -36,18 +36,23 @@ def _stale(out: Path, deps) -> bool:
     return any(Path(d).stat().st_mtime > t for d in deps)
 
 
-def build(verbose: bool = False, force: bool = False) -> Path:
-    BUILD.mkdir(exist_ok=True)
+def build(verbose: bool = False, force: bool = False, checked: bool = False) -> Path:
+    """Compile librb.so; with checked=True the debug variant librb_checked.so
+    (device-side bounds checks, -DRB_BOUNDS_CHECK) in its own build folder."""
+    build_dir = BUILD.with_name("_build_checked") if checked else BUILD
+    lib_path = LIB.with_name("librb_checked.so") if checked else LIB
+    flags = FLAGS + (["-DRB_BOUNDS_CHECK"] if checked else [])
+    build_dir.mkdir(exist_ok=True)
     headers = list(CSRC.glob("*.cuh")) + list(CSRC.glob("*.h")) + list(INCLUDE.glob("*.h"))
     cc = nvcc()
     jobs = []
     objs = []
     for src in SOURCES:
         s = CSRC / src
-        o = BUILD / (Path(src).stem + ".o")
+        o = build_dir / (Path(src).stem + ".o")
         objs.append(o)
         if force or _stale(o, [s, *headers]):
-            jobs.append([cc, *ARCH, *FLAGS, "-c", str(s), "-o", str(o)])
+            jobs.append([cc, *ARCH, *flags, "-c", str(s), "-o", str(o)])
 
     def run(cmd):
         if verbose:
@@ -59,13 +64,12 @@ def build(verbose: bool = False, force: bool = False) -> Path:
 
     with ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 1)) as ex:
         list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB.with_suffix(f".{os.getpid()}.tmp")
+    if force or jobs or _stale(lib_path, objs):
+        tmp = lib_path.with_suffix(f".{os.getpid()}.tmp")
         run([cc, *ARCH, "-shared", "-o", str(tmp), *map(str, objs), "-lpthread", "-ldl"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    build(verbose=True, force="--force" in sys.argv)
-    print(LIB)
+    print(build(verbose=True, force="--force" in sys.argv, checked="--checked" in sys.argv))

@@ -176,6 +176,37 @@ extern "C" {
 
 int rb_abi_version(void) { return 1; }
 
+#ifdef RB_BOUNDS_CHECK
+extern "C" int rb_bounds_read_loglike(rb::BoundsRecord* out);
+extern "C" int rb_bounds_read_summary(rb::BoundsRecord* out);
+#endif
+
+int rb_debug_bounds(int* site, long long* index, long long* limit) {
+#ifdef RB_BOUNDS_CHECK
+  int (*const readers[])(rb::BoundsRecord*) = {rb_bounds_read_loglike, rb_bounds_read_summary};
+  long long total = 0;
+  bool first = true;
+  for (auto rd : readers) {
+    rb::BoundsRecord r{};
+    const int e = rd(&r);
+    if (e != 0) return cuda_fail((cudaError_t)e, "rb_debug_bounds");
+    if (r.count && first) {
+      if (site) *site = r.site;
+      if (index) *index = r.index;
+      if (limit) *limit = r.limit;
+      first = false;
+    }
+    total += r.count;
+  }
+  return (int)(total > 0x7fffffff ? 0x7fffffff : total);
+#else
+  (void)site;
+  (void)index;
+  (void)limit;
+  return -1;
+#endif
+}
+
 const char* rb_last_error(void) { return g_err; }
 
 uint64_t rb_kernel_launch_count(void) { return g_launches.load(); }

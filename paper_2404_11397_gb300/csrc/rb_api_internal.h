@@ -74,7 +74,7 @@ struct EventEntry {
   uint64_t uid = 0;  // unique per built event (never reused within a process)
   SummaryOut out() const {
     return SummaryOut{d_summ, d_tab32 + dev.edge32_floats, d_tab64 + (size_t)(kNBasis + 1) * dev.e_pad, d_invdf,
-                      d_share, d_sync, d_base, dev.b_pad, d_parts, d_part_sums};
+                      d_share, d_sync, d_base, dev.b_pad, d_parts, d_part_sums, n_parts};
   }
 };
 

@@ -229,7 +229,48 @@ struct SummaryOut {
   int Bp;
   const PartDesc* parts;  // fast build: [n_parts]
   float* part_sums;       // fast builds: [n_parts][kPartSlots] doubles, or float pairs [n_parts][7 kMaxDet][2]
+  int n_parts;
 };
+
+// ---------------------------------------------------------------------------
+// Bounds checks of the debug build (compiled with -DRB_BOUNDS_CHECK).  A
+// checked index outside [0, n) is recorded -- the first one's site, index and
+// limit, and a count -- and replaced by 0, so the access stays inside the
+// buffer and every lane keeps taking part in the warp's shuffles.  The record
+// is per translation unit (a static device variable); the host reads and
+// clears all of them with rb_debug_bounds().  In the normal build RB_IDX(i,
+// n, site) is i and the checks cost nothing.
+// ---------------------------------------------------------------------------
+struct BoundsRecord {
+  unsigned count;
+  int site;
+  long long index, limit;
+};
+#ifdef RB_BOUNDS_CHECK
+static __device__ BoundsRecord g_bounds_rec;
+__device__ __forceinline__ long long checked_index(long long i, long long n, int site) {
+  if (i >= 0 && i < n) return i;
+  if (atomicAdd(&g_bounds_rec.count, 1u) == 0u) {
+    g_bounds_rec.site = site;
+    g_bounds_rec.index = i;
+    g_bounds_rec.limit = n;
+  }
+  return 0;
+}
+#define RB_IDX(i, n, site) ((decltype(i))::rb::checked_index((long long)(i), (long long)(n), (site)))
+// host side, one per translation unit that checks: copy the unit's record to
+// *out and clear it
+#define RB_BOUNDS_READER(fn)                                                          \
+  extern "C" int fn(::rb::BoundsRecord* out) {                                        \
+    ::rb::BoundsRecord zero{};                                                        \
+    cudaError_t e = cudaMemcpyFromSymbol(out, ::rb::g_bounds_rec, sizeof(zero));     \
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(::rb::g_bounds_rec, &zero, sizeof(zero)); \
+    return (int)e;                                                                    \
+  }
+#else
+#define RB_IDX(i, n, site) (i)
+#define RB_BOUNDS_READER(fn)
+#endif
 // per-part sums of the builds that split bins into parts: 7 kMaxDet float
 // pairs (fast build) or 6 kMaxDet doubles (stored-waveform FP64 build)
 constexpr int kPartSlots = 7 * kMaxDet;

@@ -197,6 +197,13 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
 
   // Stage the tables (16-byte vector copies).
   const float* sbin;
+#ifdef RB_BOUNDS_CHECK
+  unsigned smem_bytes;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(smem_bytes));
+  const size_t smem16 = smem_bytes / 16;
+#else
+  constexpr size_t smem16 = 0;  // unused
+#endif
   const float4* g4 = nullptr;  // [kEdgeQuads][Ep] basis pairs and f_e (float pairs)
   const double* g64 = nullptr;
   const double* f64 = nullptr;
@@ -206,7 +213,7 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
       const float4* src = reinterpret_cast<const float4*>(ev.tab32);
       float4* dst = reinterpret_cast<float4*>(smem_raw);
       const size_t n4 = ev.tab32_floats / 4;
-      for (size_t i = tid; i < n4; i += blockDim.x) dst[i] = src[i];
+      for (size_t i = tid; i < n4; i += blockDim.x) dst[RB_IDX(i, smem16, 104)] = src[i];
       const float* s = reinterpret_cast<const float*>(smem_raw);
       g4 = reinterpret_cast<const float4*>(s);
       sbin = s + ev.edge32_floats;
@@ -214,11 +221,11 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
       const size_t n_e64 = (size_t)(kNBasis + 1) * Ep;  // g[10][Ep], f[Ep]
       const double2* src = reinterpret_cast<const double2*>(ev.tab64);
       double2* dst = reinterpret_cast<double2*>(smem_raw);
-      for (size_t i = tid; i < n_e64 / 2; i += blockDim.x) dst[i] = src[i];
+      for (size_t i = tid; i < n_e64 / 2; i += blockDim.x) dst[RB_IDX(i, smem16, 104)] = src[i];
       const size_t nb = ev.tab32_floats - ev.edge32_floats;
       const float4* bsrc = reinterpret_cast<const float4*>(ev.tab32 + ev.edge32_floats);
       float4* bdst = reinterpret_cast<float4*>(smem_raw + n_e64 * sizeof(double));
-      for (size_t i = tid; i < nb / 4; i += blockDim.x) bdst[i] = bsrc[i];
+      for (size_t i = tid; i < nb / 4; i += blockDim.x) bdst[RB_IDX(i, smem16 - n_e64 / 2, 104)] = bsrc[i];
       g64 = reinterpret_cast<const double*>(smem_raw);
       f64 = g64 + (size_t)kNBasis * Ep;
       sbin = reinterpret_cast<const float*>(smem_raw + n_e64 * sizeof(double));
@@ -254,7 +261,7 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
     {
       float th[kMaxDet], tl[kMaxDet], sg[kMaxDet][2];
       if (!PHASE64) {
-        const WalkerMixed* s = reinterpret_cast<const WalkerMixed*>(a.ws) + w;
+        const WalkerMixed* s = reinterpret_cast<const WalkerMixed*>(a.ws) + RB_IDX(w, a.W, 101);
         valid = s->valid;
 #pragma unroll
         for (int q = 0; q < kNBasis / 2; ++q) {
@@ -311,8 +318,8 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
       const int e = c0 + lane;
       const bool has_edge = e < E;
       const bool has_bin = (lane < 31) && (e < B);
-      const int ee = has_edge ? e : E - 1;
-      const int eb = has_bin ? e : 0;
+      const int ee = RB_IDX(has_edge ? e : E - 1, Ep, 102);
+      const int eb = RB_IDX(has_bin ? e : 0, Bp, 103);
 
       // detector-independent phase sum_k dc_k g_k(f_e) / 2pi [turns]: two
       // float-pair accumulators (even k, odd k) side by side, then merged
@@ -392,7 +399,7 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
     if constexpr (paired) part += ((double)P.acc.x + (double)P.acc_lo.x) + ((double)P.acc.y + (double)P.acc_lo.y);
     const double tot = warp_sum_f64(part);
     const double logl = *ev.base_logl + tot;
-    if (!MALA && lane == 0) a.logl[w] = logl;
+    if (!MALA && lane == 0) a.logl[RB_IDX(w, a.W, 105)] = logl;
     if (GRAD) {
       const float two_pi = 6.28318530717958648f;
       float ac[kNBasis], at[kMaxDet], ar[kMaxDet][2];
@@ -418,11 +425,11 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
       }
       double g = 0.0;
       if (lane < kNPar) {
-        const WalkerTan<float>& tn = reinterpret_cast<const WalkerTan<float>*>(a.tan)[w];
+        const WalkerTan<float>& tn = reinterpret_cast<const WalkerTan<float>*>(a.tan)[RB_IDX(w, a.W, 107)];
         g = chain_rule<float>(lane, D, ac, at, ar, rho, tn);
       }
       if (MALA) mala_finish(a.mala, w, lane, logl, g);
-      else if (lane < kNPar) a.grad[w * kNPar + lane] = g;
+      else if (lane < kNPar) a.grad[RB_IDX(w * kNPar + lane, a.W * kNPar, 106)] = g;
     }
   }
 }
@@ -537,7 +544,7 @@ __global__ void __launch_bounds__(256) k_rb_f64(LaunchArgs a) {
     }
     const double tot = warp_sum_f64(acc);
     const double logl = *ev.base_logl + tot;
-    if (!MALA && lane == 0) a.logl[w] = logl;
+    if (!MALA && lane == 0) a.logl[RB_IDX(w, a.W, 105)] = logl;
     if (GRAD) {
 #pragma unroll
       for (int k = 0; k < kNBasis; ++k) adj_c[k] = kTwoPi * warp_sum_f64(adj_c[k]);
@@ -553,7 +560,7 @@ __global__ void __launch_bounds__(256) k_rb_f64(LaunchArgs a) {
         g = chain_rule<double>(lane, D, adj_c, adj_tau, adj_rho, rho, tn);
       }
       if (MALA) mala_finish(a.mala, w, lane, logl, g);
-      else if (lane < kNPar) a.grad[w * kNPar + lane] = g;
+      else if (lane < kNPar) a.grad[RB_IDX(w * kNPar + lane, a.W * kNPar, 106)] = g;
     }
   }
 }
@@ -666,3 +673,5 @@ cudaError_t launch_rb_f64(const EventDev& ev, const void* ws, const void* tan, i
 }
 
 }  // namespace rb
+
+RB_BOUNDS_READER(rb_bounds_read_loglike)

@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(kStoredThreads) k_summary_stored(DataPtrs in, 
   __shared__ double sblock[6 * kMaxDet];
   __shared__ bool s_last;
   const int pid = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const PartDesc pd = so.parts[pid];
+  const PartDesc pd = so.parts[RB_IDX(pid, so.n_parts, 201)];
   const int b = pd.bin;
   const double fm = 0.5 * (grid_f(kmin, edges[b], T) + grid_f(kmin, edges[b + 1], T));
   const double inv_T = 1.0 / T;
@@ -394,8 +394,8 @@ __global__ void __launch_bounds__(kStoredThreads) k_summary_stored(DataPtrs in, 
     const double df = f - fm;
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
-      const double2 dv = __ldcs(reinterpret_cast<const double2*>(in.data[d]) + k);
-      const double2 hv = __ldcs(reinterpret_cast<const double2*>(h0) + (size_t)d * N + k);
+      const double2 dv = __ldcs(reinterpret_cast<const double2*>(in.data[d]) + RB_IDX(k, N, 222));
+      const double2 hv = __ldcs(reinterpret_cast<const double2*>(h0) + (size_t)d * N + RB_IDX(k, N, 222));
       const double w = rcp_newton(__ldcs(in.psd[d] + k));
       const double hr = hv.x, hi = hv.y, dr = dv.x, di = dv.y;
       const double xr = dr * hr + di * hi, xi = di * hr - dr * hi, hh = hr * hr + hi * hi;
@@ -687,6 +687,7 @@ __global__ void __launch_bounds__(256) k_pull32(DataPtrs src, int64_t N, double*
   float2* __restrict__ ow = w32 + (size_t)d * N;
   float* __restrict__ oi = is32 + (size_t)d * N;
   auto put = [&](int64_t k, double2 dv, double pv) {
+    k = RB_IDX(k, N, 211);
     const float is = __frcp_rn(scaled_float(pv, bS));
     __stcs(od + k, dv);
     __stcs(op + k, pv);
@@ -746,7 +747,7 @@ __global__ void __launch_bounds__(kSumFastThreads, 6)
   __shared__ double s_inv_df;
   __shared__ bool s_last;
   const int pid = (int)blockIdx.x + p_off;  // this block's part
-  const PartDesc pd = so.parts[pid];
+  const PartDesc pd = so.parts[RB_IDX(pid, so.n_parts, 201)];
   const int b = pd.bin;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int e0 = (int)edges[b], e1 = (int)edges[b + 1];
@@ -794,8 +795,8 @@ __global__ void __launch_bounds__(kSumFastThreads, 6)
 #pragma unroll
     for (int d = 0; d < kMaxDet; ++d)
       if (d < D) {
-        dd[d] = __ldcs(w32 + (size_t)d * N + k);
-        pp[d] = __ldcs(is32 + (size_t)d * N + k);
+        dd[d] = __ldcs(w32 + (size_t)d * N + RB_IDX(k, N, 202));
+        pp[d] = __ldcs(is32 + (size_t)d * N + RB_IDX(k, N, 202));
       }
   };
   int k = ks + tid;
@@ -804,7 +805,7 @@ __global__ void __launch_bounds__(kSumFastThreads, 6)
   {
     const float4* src = reinterpret_cast<const float4*>(chunks + (size_t)c0 * kRec);
     float4* dst = reinterpret_cast<float4*>(srec);
-    for (int i = tid; i < nrec * (kRec / 4); i += kSumFastThreads) dst[i] = __ldg(src + i);
+    for (int i = tid; i < nrec * (kRec / 4); i += kSumFastThreads) dst[RB_IDX(i, kPartRecs * kRec / 4, 204)] = __ldg(src + i);
   }
   __syncthreads();
   for (; k < ke; k += kSumFastThreads) {
@@ -814,7 +815,7 @@ __global__ void __launch_bounds__(kSumFastThreads, 6)
       isv[d] = pn[d];
     }
     if (k + kSumFastThreads < ke) load_point(k + kSumFastThreads, dn, pn);
-    const float4* rec = reinterpret_cast<const float4*>(srec + ((k >> 5) - c0) * kRec);
+    const float4* rec = reinterpret_cast<const float4*>(srec + RB_IDX((k >> 5) - c0, kPartRecs, 203) * kRec);
     const float jf = small_int_float((k & (kChunk - 1)) - kChunk / 2);
     const float4 x01 = rec[0];  // X0 pair, X1 pair
     const float4 h0 = rec[1];   // X2 pair, X3, X4
@@ -1027,3 +1028,5 @@ cudaError_t launch_summary_parts(const void* w32, const float* is32, const int* 
 }
 
 }  // namespace rb
+
+RB_BOUNDS_READER(rb_bounds_read_summary)

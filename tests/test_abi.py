@@ -75,3 +75,11 @@ def test_package_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "LIB_PATH", tmp_path / "librb.so")
     with pytest.raises(RuntimeError, match="missing"):
         _lib.load()
+
+
+def test_bounds_record_absent_from_the_normal_build(lib):
+    # the normal library compiles no device-side bounds checks; the debug
+    # variant (build.py --checked) is exercised by the GPU tests
+    site, index, limit = ctypes.c_int(7), ctypes.c_longlong(7), ctypes.c_longlong(7)
+    assert lib.rb_debug_bounds(ctypes.byref(site), ctypes.byref(index), ctypes.byref(limit)) == -1
+    assert (site.value, index.value, limit.value) == (7, 7, 7)
