@@ -107,6 +107,7 @@ typedef struct {
   double T, gmst;
   double base_logl;       /* log L_RB(theta_ref) = sum_d Re sum_b A0 - B0/2 (FP64) */
   size_t device_bytes;    /* device memory held by the event */
+  double theta_ref[RB_NPAR]; /* the current fiducial parameters */
 } rb_event_info;
 
 /* Build an event: grid, bin edges, fiducial waveform h0 on the full grid,
@@ -162,6 +163,22 @@ RB_API int rb_event_get_info(rb_event_t ev, rb_event_info* info);
  * A0, A1: [n_det][n_bins][2]; B0, B1: [n_det][n_bins]; edges: [n_bins+1]
  * grid indices (0 .. n_freq-1).  Any pointer may be NULL.  Synchronous. */
 RB_API int rb_event_get_summary(rb_event_t ev, double* A0, double* A1, double* B0, double* B1, int64_t* edges);
+
+/* Checkpoint and resume an event.  rb_event_save writes to `path` everything
+ * that defines the event: the descriptor (sites, T, band, gmst, n_bins), the
+ * current theta_ref, and the resident FP64 strain [n_det][n_freq][2] and PSD
+ * [n_det][n_freq], behind a fixed header (native byte order).  It first
+ * synchronises the device, so that calls already issued on any stream are
+ * included.  rb_event_load reads such a file and builds a new event from it
+ * with rb_build_summary (host data, `stream` as the build stream, synchronous).
+ * The build is deterministic, so the loaded event's grid, bins, summary data,
+ * tables and log L values are bit-identical to those of an event built from
+ * the same inputs.  Errors: RB_EINVAL (NULL argument, unreadable or unwritable
+ * path, a file that is not a complete event file, or an event whose last
+ * rebuild read caller data in place: it holds no copy of that data);
+ * rb_build_summary's errors on load; RB_ECUDA. */
+RB_API int rb_event_save(rb_event_t ev, const char* path);
+RB_API int rb_event_load(const char* path, void* stream, rb_event_t* out);
 
 /* Batched RB log-likelihood.  theta_dev: device [W][13] row-major FP64;
  * logl_dev: device [W] FP64.  mode: RB_MIXED, RB_FP64 or RB_MIXED_F64PHASE.

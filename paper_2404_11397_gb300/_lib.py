@@ -40,7 +40,8 @@ class EventDesc(ctypes.Structure):
 class EventInfo(ctypes.Structure):
     _fields_ = [("n_det", ctypes.c_int32), ("n_bins", ctypes.c_int32), ("kmin", ctypes.c_int64),
                 ("n_freq", ctypes.c_int64), ("T", ctypes.c_double), ("gmst", ctypes.c_double),
-                ("base_logl", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
+                ("base_logl", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
+                ("theta_ref", ctypes.c_double * 13)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -63,6 +64,8 @@ SIGNATURES = {
     "rb_event_rebuild": (ctypes.c_int, [ctypes.c_void_p, c_double_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_void_p]),
     "rb_event_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(EventInfo)]),
+    "rb_event_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    "rb_event_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "rb_event_get_summary": (ctypes.c_int, [ctypes.c_void_p, c_double_p, c_double_p, c_double_p, c_double_p,
                                             c_int64_p]),
     "rb_loglike_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,

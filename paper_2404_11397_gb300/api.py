@@ -132,7 +132,26 @@ class Event:
         lib = load()
         inf = _lib.EventInfo()
         check(lib.rb_event_get_info(self.handle, ctypes.byref(inf)), "rb_event_get_info")
-        return {f: getattr(inf, f) for f, _ in _lib.EventInfo._fields_}
+        out = {f: getattr(inf, f) for f, _ in _lib.EventInfo._fields_}
+        out["theta_ref"] = np.array(out["theta_ref"][:], dtype=np.float64)
+        return out
+
+    def save(self, path) -> None:
+        """Write the event (descriptor, theta_ref, resident strain and PSD) to a file."""
+        check(load().rb_event_save(self.handle, str(path).encode()), "rb_event_save")
+
+    @classmethod
+    def load(cls, path, stream: Optional[torch.cuda.Stream] = None) -> "Event":
+        """Build an event from a file written by save (bit-identical results)."""
+        lib = load()
+        h = ctypes.c_void_p()
+        sh = _stream_handle(stream) if torch.cuda.is_available() else None
+        check(lib.rb_event_load(str(path).encode(), sh, ctypes.byref(h)), "rb_event_load")
+        ev = cls.__new__(cls)
+        ev._h = h
+        inf = ev.info()
+        ev.n_det, ev.n_bins, ev.theta_ref = int(inf["n_det"]), int(inf["n_bins"]), inf["theta_ref"]
+        return ev
 
     def summary(self) -> dict:
         """FP64 summary data and bin edges copied to the host."""

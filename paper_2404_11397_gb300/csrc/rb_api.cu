@@ -341,6 +341,8 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
     if (d < D) {
       const rb_detector_desc& dd = desc->det[d];
       e.ec.det[d] = make_geom(dd.lat, dd.lon, dd.elev_m, dd.xarm_az, dd.yarm_az);
+      const double row[5] = {dd.lat, dd.lon, dd.elev_m, dd.xarm_az, dd.yarm_az};
+      std::memcpy(e.geom[d], row, sizeof(row));
     } else {
       std::memset(&e.ec.det[d], 0, sizeof(DetGeom));
     }
@@ -496,9 +498,102 @@ int rb_event_get_info(rb_event_t ev, rb_event_info* info) {
   info->T = e.T;
   info->gmst = e.gmst;
   info->device_bytes = e.device_bytes;
+  std::memcpy(info->theta_ref, e.theta_ref, sizeof(info->theta_ref));
   cudaError_t err = cudaMemcpy(&info->base_logl, e.d_base, sizeof(double), cudaMemcpyDeviceToHost);
   if (err != cudaSuccess) return cuda_fail(err, "rb_event_get_info: read base");
   return RB_OK;
+}
+
+// ---- event files: checkpoint and resume ----
+namespace {
+constexpr char kEventMagic[8] = {'R', 'B', 'E', 'V', 'E', 'N', 'T', '1'};
+struct EventFileHeader {  // followed by strain [n_det][n_freq][2] and PSD [n_det][n_freq], FP64
+  char magic[8];
+  int32_t n_det, n_bins;
+  int64_t n_freq;
+  double T, f_low, f_high, gmst;
+  double geom[RB_MAX_DET][5];
+  double theta_ref[RB_NPAR];
+};
+}  // namespace
+
+int rb_event_save(rb_event_t ev, const char* path) {
+  RB_NVTX("rb_event_save");
+  if (!ev || !path) return set_error(RB_EINVAL, "rb_event_save: NULL event or path");
+  const EventEntry& e = ev->e;
+  if (e.last_in_place)
+    return set_error(RB_EINVAL, "rb_event_save: the last rebuild read caller data in place, which the event does not hold");
+  EventFileHeader h{};
+  std::memcpy(h.magic, kEventMagic, sizeof(h.magic));
+  h.n_det = e.n_det;
+  h.n_bins = e.n_bins;
+  h.n_freq = e.N;
+  h.T = e.T;
+  h.f_low = e.f_low;
+  h.f_high = e.f_high;
+  h.gmst = e.gmst;
+  std::memcpy(h.geom, e.geom, sizeof(h.geom));
+  std::memcpy(h.theta_ref, e.theta_ref, sizeof(h.theta_ref));
+  const size_t nd = (size_t)2 * e.n_det * e.N, np = (size_t)e.n_det * e.N;
+  std::vector<double> data(nd), psd(np);
+  // the resident copy, after every call already issued on any stream
+  cudaError_t err = cudaDeviceSynchronize();
+  if (err == cudaSuccess) err = cudaMemcpy(data.data(), e.d_data, sizeof(double) * nd, cudaMemcpyDeviceToHost);
+  if (err == cudaSuccess) err = cudaMemcpy(psd.data(), e.d_psd, sizeof(double) * np, cudaMemcpyDeviceToHost);
+  if (err != cudaSuccess) return cuda_fail(err, "rb_event_save: read the resident data");
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return set_error(RB_EINVAL, "rb_event_save: cannot open %s for writing", path);
+  const bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 && std::fwrite(data.data(), sizeof(double), nd, f) == nd &&
+                  std::fwrite(psd.data(), sizeof(double), np, f) == np;
+  if (std::fclose(f) != 0 || !ok) return set_error(RB_EINVAL, "rb_event_save: write to %s failed", path);
+  return RB_OK;
+}
+
+int rb_event_load(const char* path, void* stream, rb_event_t* out) {
+  RB_NVTX("rb_event_load");
+  if (!path || !out) return set_error(RB_EINVAL, "rb_event_load: NULL path or output");
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return set_error(RB_EINVAL, "rb_event_load: cannot open %s", path);
+  EventFileHeader h{};
+  bool ok = std::fread(&h, sizeof(h), 1, f) == 1 && std::memcmp(h.magic, kEventMagic, sizeof(h.magic)) == 0 &&
+            h.n_det >= 1 && h.n_det <= RB_MAX_DET && h.n_bins >= 1 && h.n_freq >= 2 && h.n_freq <= ((int64_t)1 << 31) &&
+            h.T > 0.0 && std::isfinite(h.T) && h.f_high > h.f_low && h.f_low > 0.0;
+  if (ok) {  // the grid the header's T and band define must be the one the arrays hold
+    const int64_t kmin = (int64_t)std::ceil(h.f_low * h.T - 1e-9), kmax = (int64_t)std::floor(h.f_high * h.T + 1e-9);
+    ok = kmax - kmin + 1 == h.n_freq;
+  }
+  std::vector<double> data, psd;
+  if (ok) {
+    const size_t nd = (size_t)2 * h.n_det * h.n_freq, np = (size_t)h.n_det * h.n_freq;
+    data.resize(nd);
+    psd.resize(np);
+    ok = std::fread(data.data(), sizeof(double), nd, f) == nd && std::fread(psd.data(), sizeof(double), np, f) == np &&
+         std::fgetc(f) == EOF;
+  }
+  std::fclose(f);
+  if (!ok) return set_error(RB_EINVAL, "rb_event_load: %s is not a complete event file", path);
+  rb_event_desc desc{};
+  desc.n_det = h.n_det;
+  desc.n_bins = h.n_bins;
+  desc.T = h.T;
+  desc.f_low = h.f_low;
+  desc.f_high = h.f_high;
+  desc.gmst = h.gmst;
+  desc.data_on_device = 0;
+  desc.cuda_stream = stream;
+  std::memcpy(desc.theta_ref, h.theta_ref, sizeof(desc.theta_ref));
+  for (int d = 0; d < h.n_det; ++d) {
+    rb_detector_desc& dd = desc.det[d];
+    dd.lat = h.geom[d][0];
+    dd.lon = h.geom[d][1];
+    dd.elev_m = h.geom[d][2];
+    dd.xarm_az = h.geom[d][3];
+    dd.yarm_az = h.geom[d][4];
+    dd.data = data.data() + (size_t)2 * d * h.n_freq;
+    dd.psd = psd.data() + (size_t)d * h.n_freq;
+  }
+  return rb_build_summary(&desc, out);
 }
 
 int rb_event_get_summary(rb_event_t ev, double* A0, double* A1, double* B0, double* B1, int64_t* edges) {

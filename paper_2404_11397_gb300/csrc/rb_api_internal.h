@@ -28,6 +28,7 @@ struct EventEntry {
   int64_t kmin = 0, N = 0;
   double T = 0, f_low = 0, f_high = 0, gmst = 0;
   double theta_ref[kNPar] = {};
+  double geom[kMaxDet][5] = {};  // site rows as given: lat, lon, elevation, x/y arm azimuths
   EventConst ec{};
   EventDev dev{};
   int64_t* d_edges = nullptr;

@@ -83,3 +83,16 @@ def test_bounds_record_absent_from_the_normal_build(lib):
     site, index, limit = ctypes.c_int(7), ctypes.c_longlong(7), ctypes.c_longlong(7)
     assert lib.rb_debug_bounds(ctypes.byref(site), ctypes.byref(index), ctypes.byref(limit)) == -1
     assert (site.value, index.value, limit.value) == (7, 7, 7)
+
+
+def test_event_files_are_validated_before_any_device_work(lib, tmp_path):
+    out = ctypes.c_void_p(123)
+    missing = str(tmp_path / "missing.rbev").encode()
+    assert lib.rb_event_load(missing, None, ctypes.byref(out)) == -1 and out.value is None
+    assert b"cannot open" in lib.rb_last_error()
+    bad = tmp_path / "bad.rbev"
+    bad.write_bytes(b"NOTANEVENTFILE" + bytes(400))
+    assert lib.rb_event_load(str(bad).encode(), None, ctypes.byref(out)) == -1
+    assert b"not a complete event file" in lib.rb_last_error()
+    assert lib.rb_event_load(None, None, ctypes.byref(out)) == -1
+    assert lib.rb_event_save(None, str(bad).encode()) == -1
