@@ -246,6 +246,25 @@ def test_edge_cases_batch_shapes(rb, small):
     np.testing.assert_array_equal(part, full[3:40])
 
 
+@pytest.mark.parametrize("mode", MODES)
+def test_large_batch_many_walkers_per_warp(rb, small, mode):
+    """150,000 walkers in one call: the grid is capped by occupancy and every
+    warp takes many walkers in turn.  Each walker's values are those it gets in
+    a small batch, bit for bit (one warp per walker, no cross-walker sums), and
+    sampled walkers agree with the oracle."""
+    W = 150_000
+    th = synth.draw_box(small.ev["theta_inj"], W, seed=161, rel=0.01, abs_width=1e-2 * synth.PRIOR_WIDTH)
+    L, G = rb.loglike_grad(small.event, torch.tensor(th, device="cuda"), mode=mode)
+    L, G = L.cpu().numpy(), G.cpu().numpy()
+    assert L.shape == (W,) and G.shape == (W, 13) and np.all(np.isfinite(L))
+    idx = np.array([0, 1, 2431, 2432, 4863, 77_777, W - 2, W - 1])
+    Ls, Gs = rb.loglike_grad(small.event, torch.tensor(th[idx], device="cuda"), mode=mode)
+    np.testing.assert_array_equal(L[idx], Ls.cpu().numpy())
+    np.testing.assert_array_equal(G[idx], Gs.cpu().numpy())
+    ref, dh, hh = _terms(small.ev, small.s, th[idx])
+    assert np.all(np.abs(L[idx] - ref) <= _tol(mode, dh, hh))
+
+
 def test_one_bin_and_one_point_per_bin(rb):
     for n_bins, kw in ((1, dict(T=4.0, f_high=256.0)), (None, dict(T=1.0, f_low=30.0, f_high=94.0))):
         ev = inject(synth.make_event("C2", **kw))
