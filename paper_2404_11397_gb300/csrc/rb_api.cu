@@ -836,6 +836,10 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
   if ((err = cudaEventRecord(e.ev_fork, s)) != cudaSuccess || (err = cudaStreamWaitEvent(e.side, e.ev_fork, 0)) != cudaSuccess)
     return cuda_fail(err, "rebuild fork");
   int launches = 3;
+  // the float-float reference values head the critical path of the fast
+  // rebuild: enqueued first
+  if (fast && (err = launch_ref_dd(e.d_theta_ref, e.ec, e.d_ref, s)) != cudaSuccess)
+    return cuda_fail(err, "reference values kernel");
   if (ss && ss->grad) {
     // the tangents depend on theta only: on their own stream from the start
     if ((err = cudaStreamWaitEvent(e.tanst, e.ev_fork, 0)) != cudaSuccess) return cuda_fail(err, "rebuild fork");
@@ -846,7 +850,6 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
   if (fast) {
     if (!ss && (err = launch_ref_values(e.d_theta_ref, e.ec, e.d_ref, e.side)) != cudaSuccess)
       return cuda_fail(err, "reference values kernel");
-    if ((err = launch_ref_dd(e.d_theta_ref, e.ec, e.d_ref, s)) != cudaSuccess) return cuda_fail(err, "reference values kernel");
     if (ss) {
       // the walkers' set-up reads the float-float reference values and theta
       // only: on the forked stream, launched as soon as they exist so that its
