@@ -457,6 +457,13 @@ __device__ __forceinline__ void add_acc(V& hi, V& lo, V v) {
 }
 }  // namespace pv
 
+// Device-scope release/acquire fence.  The summary builds publish per-part
+// and per-bin results and then take a ticket with a relaxed atomic; the
+// block that draws the last ticket fences again and reads the others'
+// results.  That publish-then-flag pattern needs release/acquire ordering
+// only, not the sequentially consistent fence of __threadfence().
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 // Sum a float over the warp in FP64 (all lanes get the total).
 __device__ __forceinline__ double warp_sum_f64(double v) {
 #pragma unroll

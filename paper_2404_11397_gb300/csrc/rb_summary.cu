@@ -168,7 +168,7 @@ __device__ void summary_epilogue(const SummaryOut& so, int b, int d0, int nd, in
           atomicOr(&sy->overflow, 1u);
       }
     }
-    __threadfence();
+    fence_acq_rel_gpu();
     __syncwarp();
     if (j == 0) {
       const unsigned ticket = atomicAdd(&sy->counter, 1u);
@@ -177,7 +177,7 @@ __device__ void summary_epilogue(const SummaryOut& so, int b, int d0, int nd, in
   }
   __syncthreads();
   if (!last) return;
-  __threadfence();
+  fence_acq_rel_gpu();
   if (fixed_base && *reinterpret_cast<volatile unsigned*>(&sy->overflow) == 0u) {
     if (threadIdx.x == 0) {
       const unsigned long long acc = atomicExch(&sy->base_acc, 0ull);
@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(kStoredThreads) k_summary_stored(DataPtrs in, 
   if (pd.n_parts > 1) {
     double* ps = reinterpret_cast<double*>(so.part_sums);  // [n_parts][kPartSlots] doubles
     if (tid < 6 * ND) ps[(size_t)pid * kPartSlots + tid] = mine;
-    __threadfence();
+    fence_acq_rel_gpu();
     __syncthreads();
     if (tid == 0) {
       const unsigned ticket = atomicAdd(&so.sync->bin_parts_done[b], 1u);
@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(kStoredThreads) k_summary_stored(DataPtrs in, 
     }
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
+    fence_acq_rel_gpu();
     if (tid < 6 * ND) {
       const double* p0 = ps + (size_t)pd.first * kPartSlots + tid;
       double t = __ldcg(p0);
@@ -919,7 +919,7 @@ __global__ void __launch_bounds__(kSumFastThreads, 6)
       float* ps = so.part_sums + ((size_t)pid * kNAcc + tid) * 2;
       ps[0] = h;
       ps[1] = l;
-      __threadfence();
+      fence_acq_rel_gpu();
     }
   }
   if (multi) {
@@ -932,7 +932,7 @@ __global__ void __launch_bounds__(kSumFastThreads, 6)
     }
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
+    fence_acq_rel_gpu();
     if (tid < kNAcc) {
       const float* ps = so.part_sums + ((size_t)pd.first * kNAcc + tid) * 2;
       float h = __ldcg(ps), l = __ldcg(ps + 1);
