@@ -63,3 +63,6 @@ def test_reference_arm_under_torchrun_prints_once():
     res = json.loads(lines[0])
     assert res["impl"] == "reference" and res["n_gpus"] == 2 and res["value"] > 0
     assert res["cpu_baseline"]["kind"] == "oracle"
+    assert res["warmup"] >= 3 and res["steps"] == 1 and res["higher_is_better"] is True
+    assert 0 < res["cpu_baseline"]["value_1_core"] <= res["value"] * 1.5
+    assert res["e2e"]["value"] == res["value"] and res["e2e"]["h2d_bytes_per_step"] == 0
