@@ -96,3 +96,35 @@ def test_event_files_are_validated_before_any_device_work(lib, tmp_path):
     assert b"not a complete event file" in lib.rb_last_error()
     assert lib.rb_event_load(None, None, ctypes.byref(out)) == -1
     assert lib.rb_event_save(None, str(bad).encode()) == -1
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every struct of include/rb.h has the size and field offsets the ctypes
+    binding uses (a C program compiled against the header prints them)."""
+    import shutil
+    import subprocess
+    from paper_2404_11397_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"rb_detector_desc": _lib.DetectorDesc, "rb_event_desc": _lib.EventDesc,
+               "rb_event_info": _lib.EventInfo, "rb_server_opts": _lib.ServerOpts,
+               "rb_server_stats": _lib.ServerStats}
+    lines = ['#include <stdio.h>', '#include "rb.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", f"-I{ROOT / 'include'}", str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, key, val = ln.split()
+        got[(cname, key)] = int(val)
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
