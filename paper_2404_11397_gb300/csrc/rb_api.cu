@@ -749,8 +749,12 @@ int rb_rebuild_loglike_grad_host(rb_event_t ev, const double* const* data_host, 
     if ((err = cudaEventRecord(e.ev_fork, s)) != cudaSuccess || (err = cudaStreamWaitEvent(e.copy, e.ev_fork, 0)) != cudaSuccess) { rc = cuda_fail(err, "copy fork"); break; }
     if (mapped) {
       err = launch_pull32(src, e.N, e.n_det, e.d_data, e.d_psd, e.d_w32, e.d_is32, e.d_wexp, sm_count(), e.copy);
-      if (err == cudaSuccess) count_launches(1);
-      e.w32_resident = true;  // once ev_data completes
+      if (err == cudaSuccess) {
+        count_launches(1);
+        e.w32_resident = true;  // once ev_data completes
+      } else {
+        e.w32_resident = false;
+      }
     } else {
       e.w32_resident = false;
       for (int d = 0; d < e.n_det && err == cudaSuccess; ++d) {
