@@ -8,6 +8,7 @@ step of the likelihood runs in librb's kernels; nothing here computes it.
 from __future__ import annotations
 
 import ctypes
+import math
 from typing import Optional
 
 import numpy as np
@@ -36,6 +37,22 @@ def _theta_dev(theta: torch.Tensor) -> torch.Tensor:
     return theta.to(torch.float64).contiguous()
 
 
+def _check_host_arrays(data, psd, n_det: int, n_freq: int) -> None:
+    """Per-detector strain ([n_freq][2], or complex [n_freq]) and PSD ([n_freq])
+    host arrays of the right count and size: the library reads exactly that
+    many points from each pointer (pinned buffers from a kernel), so a shorter
+    buffer must be refused here."""
+    if len(data) != n_det or len(psd) != n_det:
+        raise ValueError(f"need {n_det} strain and {n_det} PSD arrays, got {len(data)} and {len(psd)}")
+    for d in range(n_det):
+        a, p = data[d], psd[d]
+        na = a.numel() if isinstance(a, torch.Tensor) else np.asarray(a).size
+        np_ = p.numel() if isinstance(p, torch.Tensor) else np.asarray(p).size
+        cplx = (a.is_complex() if isinstance(a, torch.Tensor) else np.iscomplexobj(a))
+        if (na if cplx else na // 2) != n_freq or (not cplx and na % 2) or np_ != n_freq:
+            raise ValueError(f"detector {d}: strain must hold {n_freq} complex points and the PSD {n_freq} values")
+
+
 class Event:
     """A device-resident event: grid, bin edges, summary data and tables.
 
@@ -49,6 +66,10 @@ class Event:
         lib = load()
         geom = np.asarray(geom, dtype=np.float64).reshape(-1, 5)
         D = geom.shape[0]
+        # the grid the library builds: k = ceil(f_low T) .. floor(f_high T), both ends included
+        n_freq = math.floor(float(f_high) * float(T) + 1e-9) - math.ceil(float(f_low) * float(T) - 1e-9) + 1
+        if n_freq >= 2:
+            _check_host_arrays(data, psd, D, n_freq)
         desc = _lib.EventDesc()
         desc.n_det = D
         desc.n_bins = int(n_bins)
@@ -80,6 +101,9 @@ class Event:
         self.n_det = D
         self.n_bins = int(n_bins)
         self.theta_ref = th.copy()
+        inf = _lib.EventInfo()
+        check(lib.rb_event_get_info(handle, ctypes.byref(inf)), "rb_event_get_info")
+        self.n_freq = int(inf.n_freq)
 
     @classmethod
     def from_synth(cls, ev: dict, n_bins: Optional[int] = None, theta_ref=None, stream=None) -> "Event":
@@ -110,6 +134,7 @@ class Event:
         keep = []
         if data is not None:
             D = self.n_det
+            _check_host_arrays(data, psd, D, self.n_freq)
             dp = (ctypes.c_void_p * D)()
             pp = (ctypes.c_void_p * D)()
             for d in range(D):
@@ -151,6 +176,7 @@ class Event:
         ev._h = h
         inf = ev.info()
         ev.n_det, ev.n_bins, ev.theta_ref = int(inf["n_det"]), int(inf["n_bins"]), inf["theta_ref"]
+        ev.n_freq = int(inf["n_freq"])
         return ev
 
     def summary(self) -> dict:
@@ -211,6 +237,7 @@ def rebuild_loglike_grad_host(event: Event, data, psd, theta: np.ndarray, logl_o
     and [N] float64, ideally pinned) and walkers in, summary rebuilt, log L
     (and gradient) out; synchronises the stream."""
     D = event.n_det
+    _check_host_arrays(data, psd, D, event.n_freq)
     keep = [np.ascontiguousarray(a, dtype=np.float64) if not isinstance(a, torch.Tensor) else a
             for a in list(data) + list(psd)]
     ptrs = [a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data for a in keep]

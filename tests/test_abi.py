@@ -128,3 +128,17 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(cls), cname
         for fname, _ in cls._fields_:
             assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+
+
+def test_host_arrays_are_checked_against_the_grid():
+    from paper_2404_11397_gb300.api import _check_host_arrays
+    N = 17
+    good_ri, good_c, psd = np.zeros((N, 2)), np.zeros(N, dtype=complex), np.ones(N)
+    _check_host_arrays([good_ri, good_c], [psd, psd], 2, N)
+    _check_host_arrays([good_ri.ravel()], [psd], 1, N)  # flat [2N] views are accepted
+    for data, p in (([np.zeros((N - 1, 2))], [psd]), ([good_ri], [np.ones(N + 1)]), ([np.zeros(2 * N + 1)], [psd]),
+                    ([np.zeros(N - 1, dtype=complex)], [psd])):
+        with pytest.raises(ValueError):
+            _check_host_arrays(data, p, 1, N)
+    with pytest.raises(ValueError):
+        _check_host_arrays([good_ri], [psd, psd], 1, N)
