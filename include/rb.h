@@ -159,7 +159,8 @@ RB_API int rb_event_rebuild(rb_event_t ev, const double* theta_ref_host, const d
 
 RB_API int rb_event_get_info(rb_event_t ev, rb_event_info* info);
 
-/* Copy the event's FP64 summary data and bin edges to host buffers:
+/* Copy the event's FP64 summary data (A0, A1, B0, B1 of Sec. II.C, per
+ * detector and bin) and bin edges to host buffers:
  * A0, A1: [n_det][n_bins][2]; B0, B1: [n_det][n_bins]; edges: [n_bins+1]
  * grid indices (0 .. n_freq-1).  Any pointer may be NULL.  Synchronous. */
 RB_API int rb_event_get_summary(rb_event_t ev, double* A0, double* A1, double* B0, double* B1, int64_t* edges);
@@ -180,7 +181,10 @@ RB_API int rb_event_get_summary(rb_event_t ev, double* A0, double* A1, double* B
 RB_API int rb_event_save(rb_event_t ev, const char* path);
 RB_API int rb_event_load(const char* path, void* stream, rb_event_t* out);
 
-/* Batched RB log-likelihood.  theta_dev: device [W][13] row-major FP64;
+/* Batched RB log-likelihood: the network likelihood of Sec. II.A (Eqs. 2-3)
+ * in its relative-binning form (Sec. II.C, Eqs. 4-5), the waveform ratio to
+ * the fiducial waveform linear within each bin and contracted with the
+ * summary data.  theta_dev: device [W][13] row-major FP64;
  * logl_dev: device [W] FP64.  mode: RB_MIXED, RB_FP64 or RB_MIXED_F64PHASE.
  * Asynchronous on `stream` (cudaStream_t).  W = 0 is a no-op.
  * Errors: RB_EINVAL (NULL event/pointers with W > 0, W < 0, bad mode),
@@ -188,14 +192,15 @@ RB_API int rb_event_load(const char* path, void* stream, rb_event_t* out);
 RB_API int rb_loglike_batch(rb_event_t ev, const double* theta_dev, int64_t W, double* logl_dev, int mode,
                      void* stream);
 
-/* Batched RB log-likelihood and its gradient with respect to the 13
+/* Batched RB log-likelihood (as rb_loglike_batch, Sec. II.C) and its
+ * gradient -- the gradient the MALA local sampler of Sec. II.D needs -- with respect to the 13
  * parameters (hand-written reverse sweep over bins and edges, then the chain
  * rule through the per-walker set-up).  grad_dev: device [W][13] FP64.
  * Same conventions and errors as rb_loglike_batch. */
 RB_API int rb_loglike_grad_batch(rb_event_t ev, const double* theta_dev, int64_t W, double* logl_dev, double* grad_dev,
                           int mode, void* stream);
 
-/* rb_event_rebuild from the event's resident data and current theta_ref
+/* rb_event_rebuild (the summary data of Sec. II.C) from the event's resident data and current theta_ref
  * followed by rb_loglike_grad_batch, in one call (grad_dev may be NULL for
  * log L only): the results are those of the two calls in sequence on
  * `stream`.  With RB_MIXED and the chunk-expanded summary (T f_low >= 1024,
@@ -215,7 +220,8 @@ RB_API int rb_loglike_grad_batch(rb_event_t ev, const double* theta_dev, int64_t
 RB_API int rb_rebuild_loglike_grad(rb_event_t ev, const double* theta_dev, int64_t W, double* logl_dev,
                                    double* grad_dev, int mode, void* stream);
 
-/* End-to-end form of rb_rebuild_loglike_grad for host buffers: brings the
+/* End-to-end form of rb_rebuild_loglike_grad (summary data, log L and
+ * gradient of Sec. II.C) for host buffers: brings the
  * new strain data_host[d] ([n_freq][2]) and PSD psd_host[d] ([n_freq]) of
  * every detector into the event's resident copy and theta_host [W][13] to
  * the device, rebuilds the summary data (current theta_ref), evaluates log L
@@ -236,7 +242,8 @@ RB_API int rb_rebuild_loglike_grad_host(rb_event_t ev, const double* const* data
                                         const double* theta_host, int64_t W, double* logl_host, double* grad_host,
                                         int mode, void* stream);
 
-/* End-to-end convenience form of rb_loglike_grad_batch for host buffers:
+/* End-to-end convenience form of rb_loglike_grad_batch (Sec. II.C log L and
+ * its gradient) for host buffers:
  * copies theta_host [W][13] to the device, evaluates, copies logl_host [W]
  * (and grad_host [W][13] unless NULL) back, and synchronises the stream.
  * theta_host/logl_host/grad_host should be pinned for full copy bandwidth;
@@ -308,7 +315,8 @@ RB_API int rb_loglike_full_batch(rb_event_t ev, const double* theta_dev, int64_t
 RB_API int rb_loglike_grad_batch_static(rb_event_t ev, const double* theta_dev, int64_t W, double* logl_dev,
                                         double* grad_dev, int mode, void* stream);
 
-/* TaylorF2 + tidal detector strain h_d(f; theta) (FP64) on the grid
+/* TaylorF2 + tidal detector strain h_d(f; theta) (FP64; the waveform model
+ * of Sec. II.B, projected onto the detector as in Sec. II.A) on the grid
  * f_k = (kmin + k)/T, k = 0..n_freq-1, for one source: geom = {lat, lon,
  * elev_m, xarm_az, yarm_az}, theta_host [13].  h_dev: device [n_freq][2].
  * Asynchronous on `stream`.  Used to inject signals and as the fiducial
@@ -346,7 +354,8 @@ RB_API int rb_server_create(const rb_server_opts* opts, rb_server_t* out);
 /* Stops the scheduler after the in-flight requests finish; pending requests
  * fail with RB_ECLOSED. */
 RB_API int rb_server_destroy(rb_server_t srv);
-/* Enqueue a request: theta_host [W][13] is copied before return.  *ticket
+/* Enqueue a request for log L (Sec. II.C) and, if want_grad, its gradient
+ * for W walkers of one event: theta_host [W][13] is copied before return.  *ticket
  * identifies it for rb_poll.  RB_EBUSY if the queue is full, RB_EINVAL for
  * W < 1, W > max_walkers or a NULL event. */
 RB_API int rb_submit(rb_server_t srv, rb_event_t ev, const double* theta_host, int64_t W, int want_grad,
