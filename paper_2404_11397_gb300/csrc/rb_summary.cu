@@ -354,12 +354,14 @@ constexpr int kStoredThreads = 128;
 // reciprocal, r <- r + r (1 - S r), which doubles the correct bits per step:
 // the seed is the FP32 reciprocal of S scaled to [1, 2) (built and moved back
 // to FP64 with integer operations, ~23 correct bits), two steps give FP64
-// accuracy (within 1 ulp).  Four FP64 FMAs in all; other inputs take the
-// division.
+// accuracy (within 1 ulp).  Four FP64 FMAs in all; inputs outside
+// [2^-1022, 2^1021) take the division.
 __device__ __forceinline__ double rcp_newton(double S) {
   const unsigned hi = (unsigned)__double2hiint(S), lo = (unsigned)__double2loint(S);
   const int ef = (int)((hi >> 20) & 0x7FFu);
-  if (ef == 0 || ef == 0x7FF || (hi >> 31)) return 1.0 / S;
+  // zero, subnormal, infinite or NaN, negative, or so large (>= 2^1021) that
+  // 1/S is at the subnormal edge: the division
+  if (ef == 0 || ef >= 0x7FC || (hi >> 31)) return 1.0 / S;
   const float s1 = __uint_as_float(0x3F800000u | ((hi & 0xFFFFFu) << 3) | (lo >> 29));  // S 2^-e, truncated
   const unsigned rb = __float_as_uint(__frcp_rn(s1));  // in (0.5, 1]
   const int er = (int)((rb >> 23) & 0xFFu) - 127;
