@@ -8,6 +8,8 @@ Each check compares the oracle with something it does not contain:
   (2/M) int_{v_f} (v_f^3 - u^3) E'(u)/F(u) du, re-expanded in v;
 * Lambda-tilde / delta-Lambda-tilde (paper appendix) against the eta-polynomial
   forms of Wade et al. 2014 and the per-body 5PN/6PN forms;
+* the spin-orbit part of phi3 against the same derivation with the leading
+  spin-orbit terms of E(v) and F(v);
 * the chirp time of the phase against the Newtonian time-to-coalescence.
 """
 import math
@@ -120,6 +122,33 @@ def test_tidal_phase_per_body_identity(oracle_mod):
         p12 = sum(X ** 4 * L * (-15895 / 28 + 4595 * X / 28 + 5715 * X ** 2 / 14 - 325 * X ** 3 / 7) for X, L in body)
         assert o["phi10"] == pytest.approx(p10, rel=1e-12)
         assert o["phi12"] == pytest.approx(p12, rel=1e-12)
+
+
+def test_spin_orbit_term_matches_energy_flux_derivation(oracle_mod):
+    """The 1.5PN spin-orbit part of phi3 (= 4 beta) from the leading spin-orbit terms
+    of the binding energy and the flux for aligned spins (Kidder 1995; Blanchet,
+    Living Rev. Relativ. 2014, spin-orbit section), in units M = 1:
+    E gains v^3 [(14/3) S + 2 delta Sigma] and F gains v^3 [-4 S - (5/4) delta Sigma],
+    with S = X1^2 chi1 + X2^2 chi2, Sigma = X2 chi2 - X1 chi1, delta = X1 - X2.
+    The same stationary-phase step as the point-particle pin gives phi3 = 4 a3."""
+    sp = pytest.importorskip("sympy")
+    v, X1, c1, c2 = sp.symbols("v X1 c1 c2")
+    pi, R = sp.pi, sp.Rational
+    X2 = 1 - X1
+    eta = X1 * X2
+    S, Sig, dl = X1 ** 2 * c1 + X2 ** 2 * c2, X2 * c2 - X1 * c1, X1 - X2
+    e2 = -(R(3, 4) + eta / 12)
+    e3 = R(14, 3) * S + 2 * dl * Sig
+    f2 = -R(1247, 336) - R(35, 12) * eta
+    f3 = 4 * pi - 4 * S - R(5, 4) * dl * Sig
+    # d/dv [v^2 (1 + e_k v^k)] / (2 v) = 1 + (k + 2)/2 e_k v^k
+    num = 1 + 2 * e2 * v ** 2 + R(5, 2) * e3 * v ** 3
+    den = 1 + f2 * v ** 2 + f3 * v ** 3
+    a3 = sp.expand(sp.series(num / den, v, 0, 4).removeO().coeff(v, 3))
+    phi3 = sp.lambdify((X1, c1, c2), 4 * a3)
+    for q, x1, x2 in ((1.0, 0.03, -0.01), (0.8, 0.05, 0.05), (0.6, -0.04, 0.02), (0.3, 0.5, -0.7), (0.125, 0.9, 0.2)):
+        o = oracle_mod.intrinsic(_theta(q, chi1=x1, chi2=x2))
+        assert o["phi3"] == pytest.approx(phi3(1.0 / (1.0 + q), x1, x2), rel=1e-13, abs=1e-12), q
 
 
 def test_spin_terms_limits(oracle_mod):
