@@ -53,12 +53,73 @@ def _check_host_arrays(data, psd, n_det: int, n_freq: int) -> None:
             raise ValueError(f"detector {d}: strain must hold {n_freq} complex points and the PSD {n_freq} values")
 
 
+def _host_strain(a, d: int):
+    """One detector's host strain as a contiguous float64 [N][2] buffer (complex
+    input viewed as its (re, im) pairs, so a pinned complex tensor stays pinned)."""
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda:
+            raise ValueError(f"detector {d}: host strain expected, got a CUDA tensor")
+        t = torch.view_as_real(a.to(torch.complex128).resolve_conj()) if a.is_complex() else a.to(torch.float64)
+        return t.contiguous()
+    a = np.asarray(a)
+    if np.iscomplexobj(a):
+        return np.ascontiguousarray(a, dtype=np.complex128).view(np.float64)
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _host_psd(p, d: int):
+    if isinstance(p, torch.Tensor):
+        if p.is_cuda:
+            raise ValueError(f"detector {d}: host PSD expected, got a CUDA tensor")
+        return p.to(torch.float64).contiguous()
+    return np.ascontiguousarray(p, dtype=np.float64)
+
+
+def _host_theta(theta):
+    """Walkers for a host-buffer call: a host [W, 13] float64 array or CPU tensor."""
+    if isinstance(theta, torch.Tensor):
+        if theta.is_cuda:
+            raise ValueError("theta must be a host array for the host-buffer calls")
+        th = theta.to(torch.float64).contiguous()
+    else:
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+    if th.ndim != 2 or th.shape[1] != NPAR:
+        raise ValueError("theta must have shape [W, 13]")
+    return th
+
+
+def _check_host_out(a, n: int, what: str) -> None:
+    """A host output the library writes n float64 values into (a kernel writes
+    pinned buffers directly): it must be that large, float64, contiguous, on
+    the host and writable."""
+    if isinstance(a, torch.Tensor):
+        ok = (not a.is_cuda and a.dtype == torch.float64 and a.is_contiguous() and a.numel() >= n)
+    else:
+        ok = (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous and a.flags.writeable
+              and a.size >= n)
+    if not ok:
+        raise ValueError(f"{what} must be a contiguous, writable float64 host buffer of at least {n} values")
+
+
+def _check_mala_shapes(z, logp, gz, xi, u) -> int:
+    """z, gz, xi [W, 13] and logp, u [W] (xi and u may be None for the initial
+    evaluation): the library reads and writes exactly these extents."""
+    if z.dim() != 2 or z.shape[1] != NPAR:
+        raise ValueError("z must have shape [W, 13]")
+    W = z.shape[0]
+    for name, t, shape in (("logp", logp, (W,)), ("gz", gz, (W, NPAR)), ("xi", xi, (W, NPAR)), ("u", u, (W,))):
+        if t is not None and tuple(t.shape) != shape:
+            raise ValueError(f"{name} must have shape {list(shape)}, got {list(t.shape)}")
+    return W
+
+
 class Event:
     """A device-resident event: grid, bin edges, summary data and tables.
 
     geom: [D][5] site rows (lat, lon [rad], elevation [m], x/y arm azimuth [rad]);
-    data: [D][N] complex strain and psd: [D][N] one-sided PSD, either numpy
-    arrays (host) or CUDA tensors (data complex128, psd float64).
+    data: [D][N] complex strain (or float64 [D][N][2] as (re, im) pairs) and
+    psd: [D][N] one-sided PSD, either all host arrays (numpy or CPU tensors) or
+    all CUDA tensors.
     """
 
     def __init__(self, geom, gmst: float, T: float, f_low: float, f_high: float, data, psd, n_bins: int,
@@ -74,22 +135,25 @@ class Event:
         desc.n_det = D
         desc.n_bins = int(n_bins)
         desc.T, desc.f_low, desc.f_high, desc.gmst = float(T), float(f_low), float(f_high), float(gmst)
-        on_device = isinstance(data, torch.Tensor) and data.is_cuda
+        cuda = [isinstance(data[d], torch.Tensor) and data[d].is_cuda for d in range(D)]
+        cuda += [isinstance(psd[d], torch.Tensor) and psd[d].is_cuda for d in range(D)]
+        if any(cuda) and not all(cuda):
+            raise ValueError("strain and PSD must all be CUDA tensors or all host arrays")
+        on_device = D > 0 and all(cuda)
         desc.data_on_device = 1 if on_device else 0
         keep = []
         for d in range(D):
             row = desc.det[d]
             row.lat, row.lon, row.elev_m, row.xarm_az, row.yarm_az = map(float, geom[d])
             if on_device:
-                dd = torch.view_as_real(data[d].to(torch.complex128).contiguous()).contiguous()
+                a = data[d]
+                dd = (torch.view_as_real(a.to(torch.complex128).resolve_conj()) if a.is_complex()
+                      else a.to(torch.float64)).contiguous()
                 pp = psd[d].to(torch.float64).contiguous()
-                keep += [dd, pp]
-                row.data, row.psd = dd.data_ptr(), pp.data_ptr()
             else:
-                dd = np.ascontiguousarray(np.stack([np.real(data[d]), np.imag(data[d])], axis=-1), dtype=np.float64)
-                pp = np.ascontiguousarray(psd[d], dtype=np.float64)
-                keep += [dd, pp]
-                row.data, row.psd = dd.ctypes.data, pp.ctypes.data
+                dd, pp = _host_strain(data[d], d), _host_psd(psd[d], d)
+            keep += [dd, pp]
+            row.data, row.psd = _host_ptr(dd), _host_ptr(pp)
         th = np.asarray(theta_ref, dtype=np.float64).reshape(NPAR)
         for j in range(NPAR):
             desc.theta_ref[j] = float(th[j])
@@ -137,18 +201,22 @@ class Event:
             _check_host_arrays(data, psd, D, self.n_freq)
             dp = (ctypes.c_void_p * D)()
             pp = (ctypes.c_void_p * D)()
+            cuda = [isinstance(a, torch.Tensor) and a.is_cuda for a in list(data) + list(psd)]
+            if any(cuda) and not all(cuda):
+                raise ValueError("strain and PSD must all be CUDA tensors or all host arrays")
+            on_dev = 1 if all(cuda) else 0
             for d in range(D):
-                if isinstance(data[d], torch.Tensor):
-                    on_dev = 1
+                if on_dev:
                     dd, ps = data[d], psd[d]
+                    if dd.dtype == torch.complex128 and dd.is_contiguous():
+                        dd = torch.view_as_real(dd.resolve_conj())
                     if not (dd.is_contiguous() and ps.is_contiguous() and dd.dtype == torch.float64
                             and ps.dtype == torch.float64):
-                        raise ValueError("device data must be contiguous float64 [N][2] / [N]")
+                        raise ValueError("device data must be contiguous float64 [N][2] (or complex128 [N]) / [N]")
                     dp[d], pp[d] = dd.data_ptr(), ps.data_ptr()
                 else:
-                    dd = np.ascontiguousarray(data[d], dtype=np.float64)
-                    ps = np.ascontiguousarray(psd[d], dtype=np.float64)
-                    dp[d], pp[d] = dd.ctypes.data, ps.ctypes.data
+                    dd, ps = _host_strain(data[d], d), _host_psd(psd[d], d)
+                    dp[d], pp[d] = _host_ptr(dd), _host_ptr(ps)
                 keep += [dd, ps]
         check(lib.rb_event_rebuild(self.handle, th_p, dp, pp, on_dev, _mode(mode), _stream_handle(stream)),
               "rb_event_rebuild")
@@ -238,18 +306,17 @@ def rebuild_loglike_grad_host(event: Event, data, psd, theta: np.ndarray, logl_o
     (and gradient) out; synchronises the stream."""
     D = event.n_det
     _check_host_arrays(data, psd, D, event.n_freq)
-    keep = [np.ascontiguousarray(a, dtype=np.float64) if not isinstance(a, torch.Tensor) else a
-            for a in list(data) + list(psd)]
-    ptrs = [a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data for a in keep]
+    keep = [_host_strain(data[d], d) for d in range(D)] + [_host_psd(psd[d], d) for d in range(D)]
+    ptrs = [_host_ptr(a) for a in keep]
     dp = (ctypes.c_void_p * D)(*ptrs[:D])
     pp = (ctypes.c_void_p * D)(*ptrs[D:])
-    th = theta if isinstance(theta, torch.Tensor) else np.ascontiguousarray(theta, dtype=np.float64)
-    th_ptr = th.data_ptr() if isinstance(th, torch.Tensor) else th.ctypes.data
-    lo_ptr = logl_out.data_ptr() if isinstance(logl_out, torch.Tensor) else logl_out.ctypes.data
-    gr_ptr = None
-    if grad_out is not None:
-        gr_ptr = grad_out.data_ptr() if isinstance(grad_out, torch.Tensor) else grad_out.ctypes.data
+    th = _host_theta(theta)
     W = th.shape[0]
+    _check_host_out(logl_out, W, "logl_out")
+    if grad_out is not None:
+        _check_host_out(grad_out, W * NPAR, "grad_out")
+    th_ptr, lo_ptr = _host_ptr(th), _host_ptr(logl_out)
+    gr_ptr = _host_ptr(grad_out) if grad_out is not None else None
     check(load().rb_rebuild_loglike_grad_host(event.handle, dp, pp, ctypes.c_void_p(th_ptr), W, ctypes.c_void_p(lo_ptr),
                                               ctypes.c_void_p(gr_ptr) if gr_ptr else None, _mode(mode),
                                               _stream_handle(stream)), "rb_rebuild_loglike_grad_host")
@@ -285,9 +352,12 @@ def loglike_grad_host(event: Event, theta: np.ndarray, logl_out, grad_out=None, 
     """End-to-end call on host buffers (numpy arrays or CPU tensors, ideally
     pinned): copies in, evaluates, copies out (pinned outputs are written by
     the kernel directly), synchronises."""
-    th = np.ascontiguousarray(theta, dtype=np.float64)
+    th = _host_theta(theta)
     W = th.shape[0]
-    check(load().rb_loglike_grad_host(event.handle, ctypes.c_void_p(th.ctypes.data), W,
+    _check_host_out(logl_out, W, "logl_out")
+    if grad_out is not None:
+        _check_host_out(grad_out, W * NPAR, "grad_out")
+    check(load().rb_loglike_grad_host(event.handle, ctypes.c_void_p(_host_ptr(th)), W,
                                       ctypes.c_void_p(_host_ptr(logl_out)),
                                       ctypes.c_void_p(_host_ptr(grad_out)) if grad_out is not None else None,
                                       _mode(mode), _stream_handle(stream)), "rb_loglike_grad_host")
@@ -313,7 +383,7 @@ def mala_init(event: Event, z: torch.Tensor, lo, hi, mode="mixed", stream=None):
     """log pi(z) [W] and d log pi / dz [W, 13] for chains in the sampling
     coordinates (cos iota, sin dec) with the uniform prior on lo < z < hi."""
     zz = _theta_dev(z)
-    W = zz.shape[0]
+    W = _check_mala_shapes(zz, None, None, None, None)
     logp = torch.empty(W, dtype=torch.float64, device=zz.device)
     gz = torch.empty(W, NPAR, dtype=torch.float64, device=zz.device)
     lo_, hi_ = _host13(lo), _host13(hi)
@@ -330,7 +400,7 @@ def mala_step(event: Event, z: torch.Tensor, logp: torch.Tensor, gz: torch.Tenso
     for t in (z, logp, gz, xi, u):
         if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
             raise ValueError("mala_step: z, logp, gz, xi, u must be contiguous float64 CUDA tensors")
-    W = z.shape[0]
+    W = _check_mala_shapes(z, logp, gz, xi, u)
     acc = torch.empty(W, dtype=torch.int32, device=z.device)
     eps_, lo_, hi_ = _host13(eps), _host13(lo), _host13(hi)
     check(load().rb_mala_step(event.handle, ctypes.c_void_p(z.data_ptr()), ctypes.c_void_p(logp.data_ptr()),

@@ -142,3 +142,58 @@ def test_host_arrays_are_checked_against_the_grid():
             _check_host_arrays(data, p, 1, N)
     with pytest.raises(ValueError):
         _check_host_arrays([good_ri], [psd, psd], 1, N)
+
+
+def test_host_strain_marshalling_keeps_both_components():
+    """Complex strain goes to the library as its (re, im) pairs and [N][2] float
+    strain as it is: the library reads 2 N float64 values per detector."""
+    import torch
+    from paper_2404_11397_gb300.api import _host_psd, _host_strain
+    rng = np.random.default_rng(5)
+    c = rng.normal(size=9) + 1j * rng.normal(size=9)
+    ri = np.stack([c.real, c.imag], axis=-1)
+    c64 = c.astype(np.complex64)
+    ri64 = np.stack([c64.real, c64.imag], axis=-1).astype(np.float64)
+    for a, expect in ((c, ri), (ri, ri), (c64, ri64), (torch.from_numpy(c), ri), (torch.from_numpy(ri), ri),
+                      (torch.from_numpy(c64), ri64)):
+        out = _host_strain(a, 0)
+        flat = out.numpy().ravel() if isinstance(out, torch.Tensor) else out.ravel()
+        assert flat.dtype == np.float64 and flat.size == 18
+        np.testing.assert_array_equal(flat, expect.ravel())
+    t = torch.from_numpy(c)
+    assert _host_strain(t, 0).data_ptr() == t.data_ptr()  # a contiguous complex128 tensor is viewed, not copied
+    assert _host_strain(t.conj(), 0).numpy()[:, 1].tolist() == (-c.imag).tolist()
+    assert _host_psd([1, 2, 3], 0).dtype == np.float64
+
+
+def test_host_outputs_and_theta_are_checked():
+    import torch
+    from paper_2404_11397_gb300.api import _check_host_out, _host_theta
+    assert _host_theta(np.zeros((4, 13))).shape == (4, 13)
+    assert _host_theta(torch.zeros(4, 13, dtype=torch.float32)).dtype == torch.float64
+    for bad in (np.zeros(13), np.zeros((4, 12)), np.zeros((2, 4, 13))):
+        with pytest.raises(ValueError):
+            _host_theta(bad)
+    _check_host_out(np.zeros(5), 5, "x")
+    _check_host_out(np.zeros(8), 5, "x")  # a larger preallocated buffer is fine
+    _check_host_out(torch.zeros(5, dtype=torch.float64), 5, "x")
+    ro = np.zeros(5)
+    ro.flags.writeable = False
+    for bad in (np.zeros(4), np.zeros(5, dtype=np.float32), np.zeros(10)[::2], ro, [0.0] * 5,
+                torch.zeros(5, dtype=torch.float32), torch.zeros(10, dtype=torch.float64)[::2]):
+        with pytest.raises(ValueError):
+            _check_host_out(bad, 5, "x")
+
+
+def test_mala_shapes_are_checked():
+    import torch
+    from paper_2404_11397_gb300.api import _check_mala_shapes
+    W = 6
+    z, g, xi = (torch.zeros(W, 13) for _ in range(3))
+    lp, u = torch.zeros(W), torch.zeros(W)
+    assert _check_mala_shapes(z, lp, g, xi, u) == W
+    assert _check_mala_shapes(z, None, None, None, None) == W
+    for args in ((torch.zeros(W * 13), lp, g, xi, u), (z, torch.zeros(W + 1), g, xi, u), (z, lp, torch.zeros(W, 12), xi, u),
+                 (z, lp, g, torch.zeros(W - 1, 13), u), (z, lp, g, xi, torch.zeros(W, 1))):
+        with pytest.raises(ValueError):
+            _check_mala_shapes(*args)
