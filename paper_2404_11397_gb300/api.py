@@ -455,22 +455,44 @@ class Server:
         h = ctypes.c_void_p()
         check(lib.rb_server_create(ctypes.byref(o), ctypes.byref(h)), "rb_server_create")
         self._h = h
+        self._req = {}  # ticket -> (W, want_grad) of the requests submitted through this object
 
     def submit(self, event: Event, theta: np.ndarray, want_grad: bool = True) -> int:
-        th = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1, NPAR)
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        if th.ndim == 1 and th.size == NPAR:
+            th = th.reshape(1, NPAR)
+        if th.ndim != 2 or th.shape[1] != NPAR:
+            raise ValueError("theta must have shape [W, 13]")
         t = ctypes.c_uint64()
         check(load().rb_submit(self._h, event.handle, th.ctypes.data_as(_lib.c_double_p), th.shape[0],
                                1 if want_grad else 0, ctypes.byref(t)), "rb_submit")
+        self._req[t.value] = (th.shape[0], bool(want_grad))
         return t.value
 
-    def poll(self, ticket: int, W: int, timeout_us: int = -1, want_grad: bool = True):
-        """Returns (status, logl, grad); status RB_OK, RB_PENDING or RB_ETIMEDOUT (others raise)."""
+    def _poll_shape(self, ticket: int, W: Optional[int], want_grad: Optional[bool]):
+        """The output extents of a poll: the library copies the request's own
+        W values (and 13 W gradient values if it asked for them), so buffers
+        are sized from the submitted request; a W that disagrees is refused."""
+        known = self._req.get(ticket)
+        if known is None:  # not submitted here (or already collected): the library answers for it
+            if W is None:
+                raise ValueError("unknown ticket: give W")
+            return int(W), True if want_grad is None else bool(want_grad)
+        if W is not None and int(W) != known[0]:
+            raise ValueError(f"ticket {ticket} was submitted with W = {known[0]}, not {W}")
+        return known[0], known[1] if want_grad is None else (bool(want_grad) and known[1])
+
+    def poll(self, ticket: int, W: Optional[int] = None, timeout_us: int = -1, want_grad: Optional[bool] = None):
+        """Returns (status, logl, grad); status RB_OK, RB_PENDING or RB_ETIMEDOUT (others raise).
+        W and want_grad default to the request's own; grad is None for a request without it."""
+        W, want_grad = self._poll_shape(ticket, W, want_grad)
         logl = np.zeros(W)
         grad = np.zeros((W, NPAR)) if want_grad else None
         st = load().rb_poll(self._h, ticket, int(timeout_us), logl.ctypes.data_as(_lib.c_double_p),
                             grad.ctypes.data_as(_lib.c_double_p) if grad is not None else None)
         if st in (_lib.RB_PENDING, _lib.RB_ETIMEDOUT):
             return st, None, None
+        self._req.pop(ticket, None)  # collected, or failed: the library has forgotten it either way
         check(st, "rb_poll")
         return st, logl, grad
 
