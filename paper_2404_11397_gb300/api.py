@@ -250,7 +250,8 @@ class Event:
     def summary(self) -> dict:
         """FP64 summary data and bin edges copied to the host."""
         lib = load()
-        D, B = self.n_det, self.n_bins
+        inf = self.info()  # the library's own extents: it copies D x B values per table
+        D, B = int(inf["n_det"]), int(inf["n_bins"])
         A0 = np.zeros((D, B, 2))
         A1 = np.zeros((D, B, 2))
         B0 = np.zeros((D, B))
