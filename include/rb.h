@@ -362,7 +362,9 @@ RB_API int rb_submit(rb_server_t srv, rb_event_t ev, const double* theta_host, i
               uint64_t* ticket);
 /* Wait up to timeout_us (0 = do not wait, < 0 = wait without limit) for a
  * request; on RB_OK copies logl_out [W] and, if the request wanted it and
- * grad_out != NULL, grad_out [W][13], and forgets the ticket.  Returns
+ * grad_out != NULL, grad_out [W][13], W being the request's own (the W given
+ * to rb_submit: the caller's buffers must hold that many), and forgets the
+ * ticket (on a failed request too).  Returns
  * RB_PENDING (timeout_us == 0 and not done), RB_ETIMEDOUT, RB_ENOTFOUND, or
  * the request's own error status. */
 RB_API int rb_poll(rb_server_t srv, uint64_t ticket, int64_t timeout_us, double* logl_out, double* grad_out);
