@@ -21,8 +21,8 @@ def _read(ptr: int, n: int) -> np.ndarray:
 
 
 class _FakeLib:
-    """Records the host buffers of rb_build_summary, rb_event_rebuild and
-    rb_rebuild_loglike_grad_host; every call succeeds."""
+    """Records the host buffers of rb_build_summary, rb_event_rebuild,
+    rb_rebuild_loglike_grad_host and rb_loglike_grad_host; every call succeeds."""
 
     def __init__(self):
         self.seen = {}
@@ -48,6 +48,11 @@ class _FakeLib:
     def rb_rebuild_loglike_grad_host(self, handle, dp, pp, th, W, lo, gr, mode, stream):
         self.seen["data"] = [_read(dp[d], 2 * N) for d in range(len(dp))]
         self.seen["psd"] = [_read(pp[d], N) for d in range(len(pp))]
+        self.seen["theta"] = _read(th.value, W * 13).reshape(W, 13)
+        self.seen["ptrs"] = (lo.value, gr.value if gr is not None else None)
+        return 0
+
+    def rb_loglike_grad_host(self, handle, th, W, lo, gr, mode, stream):
         self.seen["theta"] = _read(th.value, W * 13).reshape(W, 13)
         self.seen["ptrs"] = (lo.value, gr.value if gr is not None else None)
         return 0
@@ -110,6 +115,15 @@ def test_host_step_passes_strain_walkers_and_outputs(fake):
                 np.testing.assert_array_equal(fake.seen["psd"][0], psd)
                 np.testing.assert_array_equal(fake.seen["theta"], th)
                 assert fake.seen["ptrs"] == (L.ctypes.data, G.data_ptr())  # outputs passed in place
+        L, G = torch.zeros(6, dtype=torch.float64), np.zeros((6, 13))
+        api.loglike_grad_host(ev, torch.from_numpy(th.copy()), L, None, stream=_Stream())
+        np.testing.assert_array_equal(fake.seen["theta"], th)
+        assert fake.seen["ptrs"] == (L.data_ptr(), None)
+        api.loglike_grad_host(ev, th, L, G, stream=_Stream())
+        assert fake.seen["ptrs"] == (L.data_ptr(), G.ctypes.data)
+        for bad in ((th[:, :12], L, G), (th, np.zeros(5), G), (th, L, np.zeros((6, 12))), (th, L.float(), G)):
+            with pytest.raises(ValueError):
+                api.loglike_grad_host(ev, *bad, stream=_Stream())
         with pytest.raises(ValueError):
             api.rebuild_loglike_grad_host(ev, [c], [psd], th, np.zeros(5), None, stream=_Stream())
         with pytest.raises(ValueError):
