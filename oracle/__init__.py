@@ -22,8 +22,8 @@ What each function follows (arXiv:2404.11397 and the works it cites):
   the parameters of Table III.
 
 Pins: see ``tests/test_oracle_*.py``.  Waveform parity with LALSuite/ripple is
-unpinned (neither is available); the spin-orbit coefficient is pinned by an
-energy-flux derivation, the spin-spin one only by symmetry and zero-spin limits.
+unpinned (neither is available); the spin-orbit and spin-spin coefficients are
+pinned by energy-flux derivations (tests/test_oracle_pn.py).
 """
 from __future__ import annotations
 

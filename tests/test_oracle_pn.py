@@ -10,6 +10,9 @@ Each check compares the oracle with something it does not contain:
   forms of Wade et al. 2014 and the per-body 5PN/6PN forms;
 * the spin-orbit part of phi3 against the same derivation with the leading
   spin-orbit terms of E(v) and F(v);
+* the 2PN spin-spin sigma (and its weight -10 in phi4) against a derivation from
+  the circular orbit with the spin-spin and spin-induced quadrupole couplings and
+  the quadrupole plus current-quadrupole flux;
 * the chirp time of the phase against the Newtonian time-to-coalescence.
 """
 import math
@@ -149,6 +152,72 @@ def test_spin_orbit_term_matches_energy_flux_derivation(oracle_mod):
     for q, x1, x2 in ((1.0, 0.03, -0.01), (0.8, 0.05, 0.05), (0.6, -0.04, 0.02), (0.3, 0.5, -0.7), (0.125, 0.9, 0.2)):
         o = oracle_mod.intrinsic(_theta(q, chi1=x1, chi2=x2))
         assert o["phi3"] == pytest.approx(phi3(1.0 / (1.0 + q), x1, x2), rel=1e-13, abs=1e-12), q
+
+
+@pytest.fixture(scope="module")
+def spin_spin_sigma():
+    """The 2PN aligned-spin phase term sigma, derived here from the dynamics and the
+    radiation of a circular orbit (units G = c = M = 1, so mu = eta = X1 X2), with
+    spins S_i = X_i^2 chi_i normal to the orbital plane:
+
+    * orbit: the Newtonian potential plus the leading spin-spin (dipole-dipole)
+      coupling [3 (n.S1)(n.S2) - S1.S2] / r^3 (Barker & O'Connell 1975; Kidder 1995)
+      and each body's spin-induced quadrupole Q_i = -kappa_i S_i^2 / m_i (Poisson
+      1998), seen in its equatorial plane, -kappa_i m_j S_i^2 / (2 m_i r^3);
+      a circular orbit has mu w^2 r = dU/dr and E = mu w^2 r^2 / 2 + U;
+    * flux: the quadrupole formula (32/5) mu^2 r^4 w^6 on that orbit, plus the
+      current quadrupole (16/45) <J'''_ij J'''_ij>, whose spin part is
+      (3/2) sum_i [x_i^i S_i^j]^STF (Kidder 1995); for aligned spins both parts of J
+      are multiples of [n^i z^j]^STF, whose square averages to 1/2;
+    * both as series in v = (M w)^{1/3}; the spin-quadratic v^4 coefficients e4 of
+      E / (-mu v^2 / 2) and f4 of F / ((32/5) eta^2 v^10) then enter the same
+      stationary-phase step as the point-particle pin, a4 = 3 e4 - f4, and
+      phi4 picks up 10 a4 = -10 sigma.
+
+    Returns sigma(X1, chi1, chi2, kappa1, kappa2), and the current-quadrupole part
+    of the 1PN flux coefficient as a check of the J normalisation."""
+    sp = pytest.importorskip("sympy")
+    v, a, X1, c1, c2, k1, k2 = sp.symbols("v a X1 c1 c2 k1 k2")
+    r = sp.symbols("r", positive=True)
+    X2 = 1 - X1
+    mu = X1 * X2
+    S1, S2 = X1 ** 2 * c1, X2 ** 2 * c2
+    U = (-X1 * X2 / r - S1 * S2 / r ** 3
+         - k1 * X2 * S1 ** 2 / (2 * X1 * r ** 3) - k2 * X1 * S2 ** 2 / (2 * X2 * r ** 3))
+    w2 = sp.diff(U, r) / (mu * r)
+    E = mu * w2 * r ** 2 / 2 + U
+    # invert v^6 = w^2(r) for x = 1/r = v^2 (1 + a v^4 + ...)
+    resid = sp.expand(sp.series(w2.subs(r, 1 / (v ** 2 * (1 + a * v ** 4))), v, 0, 12).removeO() - v ** 6)
+    a_sol = sp.solve(resid.coeff(v, 10), a)[0]
+    r_v = 1 / (v ** 2 * (1 + a_sol * v ** 4))
+    e_ser = sp.expand(sp.series(E.subs(r, r_v) / (-mu * v ** 2 / 2), v, 0, 6).removeO())
+    w = v ** 3
+    F_I = sp.Rational(32, 5) * mu ** 2 * r_v ** 4 * w ** 6
+    CJ = -mu * (X1 - X2) * r_v ** 3 * w + sp.Rational(3, 2) * r_v * (X2 * S1 - X1 * S2)
+    F_J = sp.Rational(16, 45) * sp.Rational(1, 2) * w ** 6 * CJ ** 2
+    f_ser = sp.expand(sp.series((F_I + F_J) / (sp.Rational(32, 5) * mu ** 2 * v ** 10), v, 0, 6).removeO())
+    e4, f4 = e_ser.coeff(v, 4), f_ser.coeff(v, 4)
+    sigma = sp.expand(sp.cancel(sp.together(f4 - 3 * e4)))
+    # no spin-independent or spin-linear piece may leak into the 2PN spin-spin term
+    assert sp.expand(sigma.subs({c1: 0, c2: 0})) == 0
+    return (sp.lambdify((X1, c1, c2, k1, k2), sigma), sp.simplify(f_ser.coeff(v, 2) - (1 - 4 * mu) / 36))
+
+
+def test_spin_spin_term_matches_orbit_and_flux_derivation(oracle_mod, spin_spin_sigma):
+    """The oracle's 2PN spin-spin sigma (kappa_i = 1), and its weight -10 in phi4, equal
+    the derivation of the spin_spin_sigma fixture.  Swapping the two S1 S2 coefficients
+    (721/48, 247/48) or changing a self-spin factor ((720 kappa - 1), (240 kappa - 7))
+    moves sigma by 2 eta chi1 chi2 or more, far outside these tolerances."""
+    sigma, j_check = spin_spin_sigma
+    # the current-quadrupole normalisation reproduces its known share (1 - 4 eta)/36 of
+    # the 1PN flux coefficient -1247/336 - 35 eta/12 (Blanchet, Living Rev. Relativ. 2014)
+    assert j_check == 0
+    for q, x1, x2 in ((1.0, 0.6, -0.4), (0.8, 0.05, 0.05), (0.6, -0.9, 0.3), (0.3, 0.5, 0.8), (0.125, 0.9, -0.7)):
+        o = oracle_mod.intrinsic(_theta(q, chi1=x1, chi2=x2))
+        z = oracle_mod.intrinsic(_theta(q))
+        expect = sigma(1.0 / (1.0 + q), x1, x2, 1.0, 1.0)
+        assert o["sigma"] == pytest.approx(expect, rel=1e-13, abs=1e-15), q
+        assert o["phi4"] - z["phi4"] == pytest.approx(-10.0 * expect, rel=1e-10), q
 
 
 def test_spin_terms_limits(oracle_mod):
