@@ -300,8 +300,9 @@ RB_API int rb_loglike_full_batch(rb_event_t ev, const double* theta_dev, int64_t
 
 /* Allocation-free form of rb_loglike_grad_batch (the paper has no
  * counterpart: it is an interface for callers that cannot allocate device
- * memory at call time -- e.g. inside a stream capture in global mode, or
- * under a host framework that owns the device memory).  Same arguments,
+ * memory at call time -- e.g. a host framework whose own allocator owns all
+ * device memory and forbids other allocations, or a latency-critical sampler
+ * loop that must not pay for, or synchronise on, an allocation).  Same arguments,
  * results and errors as rb_loglike_grad_batch (grad_dev may be NULL for log L
  * only), but the per-walker workspace is a fixed device array inside the
  * library (RB_STATIC_MAX_WALKERS records, about 7.5 MiB, held on every device

@@ -3,11 +3,9 @@
 // memory taken from an allocator.
 //
 // Some callers cannot allocate device memory at the point where they need a
-// likelihood: a sampler that runs inside a stream capture in global capture
-// mode (where allocation calls are refused), a host framework whose own
-// allocator owns all device memory and forbids others from taking more, or a
-// latency-critical loop that must not pay for, or synchronise on, an
-// allocation.  This entry point allocates nothing: the set-up kernel writes
+// likelihood: a host framework whose own allocator owns all device memory and
+// forbids others from taking more, or a latency-critical sampler loop that
+// must not pay for, or synchronise on, an allocation.  This entry point allocates nothing: the set-up kernel writes
 // its per-walker records into g_static_ws, a file-scope __device__ array of
 // RB_STATIC_MAX_WALKERS records of the largest layout (about 7.5 MiB), which
 // every GPU that loads the library holds until the process exits.
