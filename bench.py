@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--no-full", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-summary-build", action="store_true")
+    p.add_argument("--no-configs", action="store_true", help="skip the C1 / C3 / C4 and FP64-phase legs")
     p.add_argument("--profile", action="store_true",
                    help="fixed short warm-up and no extra legs (for profiler launch lists)")
     return p.parse_args()
@@ -165,19 +166,38 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# Algorithmic work of the main likelihood+gradient kernel (mixed precision).
-# FP32 flops per unit (FMA = 2), counted from the algorithm: float-float
-# phase dot product (10 terms x 15 flops per edge), per (edge, detector)
-# delay term, reduction, half-angle sin/cos, ratio (70 flops), per (bin,
-# detector) contraction (25 flops); the gradient adds per (bin, detector)
-# 16, per (edge, detector) 17 and per edge 20 flops.
+# Algorithmic work of the relative-binning likelihood per walker (D detectors,
+# B bins, E = B + 1 edges, K = 10 phase-basis functions as built), counted
+# from the method, not from this implementation:
+#   FP64-class: the basis dot product E * 2K, the delay term and range
+#     reduction 8 D E, the per-walker set-up ~300; the gradient adds E K;
+#   FP32-class: r0, r1 and the contraction 22 D B, the complex scaling of the
+#     ratio 6 D E; the gradient triples it;
+#   SFU: one sin/cos per (edge, detector).
+# The mixed path runs all three classes on the FP32 pipe (FP64-class work as
+# float-float), so the roofline adds them and divides by the FP32 peak.
 # ---------------------------------------------------------------------------
-def main_kernel_flops(W: int, D: int, B: int, grad: bool) -> float:
+N_BASIS = 10
+
+
+def algorithmic_work(D: int, B: int, grad: bool) -> dict:
+    E = B + 1
+    fp64 = E * 2 * N_BASIS + 8 * D * E + 300 + (E * N_BASIS if grad else 0)
+    fp32 = (22 * D * B + 6 * D * E) * (3 if grad else 1)
+    sfu = D * E
+    return {"fp64": fp64, "fp32": fp32, "sfu_sincos": sfu, "total": fp64 + fp32 + sfu}
+
+
+# This implementation's own FP32 flop count of the same kernel (the float-float
+# emulation of the FP64-class work included): 150 per edge for the phase dot
+# product, 70 per (edge, detector) for delay, reduction, sin/cos and ratio, 25
+# per (bin, detector) for the contraction; the gradient adds 16 D B + 17 D E + 20 E.
+def impl_flops_per_walker(D: int, B: int, grad: bool) -> int:
     E = B + 1
     f = E * 150 + D * E * 70 + D * B * 25
     if grad:
         f += D * B * 16 + D * E * 17 + E * 20
-    return float(W) * f
+    return f
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
@@ -193,13 +213,46 @@ FULL_FLOPS_PER_WALKER_POINT = 92
 
 
 def fp32_peak_tflops() -> float:
+    """Derived from the unit counts and the maximum SM clock."""
     return N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 
+# FFMA issue rate measured on this GPU by a microbenchmark (lane operations per
+# clock per SM): 117.6 of the nominal 128.
+FFMA_LANE_OPS_PER_CLK_SM = 117.6
+# FP64 pipe: about 1.58 lane operations per clock per SM measured the same way.
+FP64_LANE_OPS_PER_CLK_SM = 1.58
+
+
+def ffma_measured_tflops() -> float:
+    return N_SM * FFMA_LANE_OPS_PER_CLK_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def fp64_measured_tflops() -> float:
+    return N_SM * FP64_LANE_OPS_PER_CLK_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def roofline_main(W: int, D: int, B: int, grad: bool, main_s: float) -> dict:
+    """Main kernel against the FP32-pipe roofline with the method's algorithmic work."""
+    work = algorithmic_work(D, B, grad)
+    achieved = W * work["total"] / main_s / 1e12
+    peak = fp32_peak_tflops()
+    impl = impl_flops_per_walker(D, B, grad)
+    return {"bound": "alu", "kernel": "k_rb_mixed (FP32 pipe)", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": MAIN_KERNEL_TRAFFIC_BYTES if grad else None,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+            "work_per_walker": work, "work_source": "algorithmic: FP64-class + FP32-class flops + sin/cos per walker",
+            "peak_measured_ffma": ffma_measured_tflops(), "frac_of_measured_ffma": achieved / ffma_measured_tflops(),
+            "fp64_class_tflops": W * work["fp64"] / main_s / 1e12,
+            "fp64_class_frac_of_fp64_pipe": W * work["fp64"] / main_s / 1e12 / fp64_measured_tflops(),
+            "impl_flops_per_walker": impl, "impl_tflops": W * impl / main_s / 1e12,
+            "impl_frac": W * impl / main_s / 1e12 / peak}
+
+
 # ---------------------------------------------------------------------------
-def make_inputs(rb, torch, device):
+def make_inputs(rb, torch, device, cfg="C2"):
     import synth
-    ev = synth.make_event("C2")
+    ev = synth.make_event(cfg)
     D, N = ev["geom"].shape[0], ev["N"]
     # inject the signal with the library's own strain kernel (on the device)
     noise = torch.tensor(np.stack([ev["noise"].real, ev["noise"].imag], -1), device=device)
@@ -329,9 +382,6 @@ def run_gb300(args, dist: Dist):
     total_s = sum(step_ms) / 1e3
     max_total_s, value = whole_job_rate(dist, total_s, W * args.steps, device)
     main_avg_s = float(np.mean(main_ms)) / 1e3
-    flops = main_kernel_flops(W, D, B, grad=True)
-    achieved = flops / main_avg_s / 1e12
-    peak = fp32_peak_tflops()
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_total_s * 1e3 / args.steps, "higher_is_better": True,
@@ -349,9 +399,7 @@ def run_gb300(args, dist: Dist):
                          "two_call_step_median": float(np.median(two_ms)),
                          "main_kernel_avg": main_avg_s * 1e3,
                          "batch_evals_per_s_main_kernel_only": W / main_avg_s},
-        "roofline": {"bound": "alu", "kernel": "k_rb_mixed<grad> (fp32 pipe)", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": MAIN_KERNEL_TRAFFIC_BYTES,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"},
+        "roofline": roofline_main(W, D, B, True, main_avg_s),
     }
     if not args.no_fp64 and args.mode != "fp64":
         K64 = max(3, min(args.steps, 20))
@@ -361,12 +409,23 @@ def run_gb300(args, dist: Dist):
         result["fp64_path"] = {"value": v64, "unit": UNIT, "ms_per_step": t64 * 1e3 / K64,
                                "main_kernel_ms": float(np.mean(m64)),
                                "speedup_of_mixed": value / v64}
+    if not args.no_configs and args.mode == "mixed":
+        K3 = max(3, min(args.steps, 20))
+        s3, _ = timed("mixed_f64phase", K3, 2)
+        m3 = main_kernel_ms("mixed_f64phase", 5)
+        t3, v3 = whole_job_rate(dist, sum(s3) / 1e3, W * K3, device)
+        result["f64phase_path"] = {"value": v3, "unit": UNIT, "ms_per_step": t3 * 1e3 / K3,
+                                   "main_kernel_ms": float(np.mean(m3)), "mode": "mixed_f64phase",
+                                   "step": "the same rb_rebuild_loglike_grad step with the phase accumulated "
+                                           "in native FP64 (the rest as the mixed path)",
+                                   "cost_vs_mixed": value / v3}
     if not args.no_mala:
         result["mala_step"] = run_mala(rb, torch, event, ev, W, args, dist, device, flush)
     if not args.no_full and args.mode == "mixed":
         result["full_grid"] = run_full(rb, torch, event, ev, args, dist, device, flush, value)
     if not args.no_e2e:
         result["e2e"] = run_e2e(rb, torch, event, ev, data, psd, theta, W, args, dist, device)
+        result["e2e_theta_only"] = run_e2e_theta(rb, torch, event, theta, W, args, dist, device)
     if not args.no_serving and dist.rank == 0:
         try:
             result["serving"] = run_serving(rb, torch, device)
@@ -375,7 +434,154 @@ def run_gb300(args, dist: Dist):
     if not args.no_summary_build:
         result["summary_build"] = run_summary_build(rb, torch, event, ev, flush)
     event.free()
+    if not args.no_configs and args.mode == "mixed":
+        result["configs"] = run_configs(rb, torch, args, dist, device, flush)
     return result
+
+
+def batch_leg(rb, torch, lib, event, th, grad, mode, K, flush, dist, device):
+    """rb_loglike_batch / rb_loglike_grad_batch on device buffers: one call
+    captured as a CUDA graph and replayed K times after an L2 flush each (the
+    summary data are not rebuilt), and the main kernel's mean duration from
+    the library's trace events over 5 eager calls."""
+    import ctypes
+    W = th.shape[0]
+    lo = torch.empty(W, dtype=torch.float64, device=device)
+    gr = torch.empty(W, 13, dtype=torch.float64, device=device)
+    m = rb.MODES[mode]
+
+    def call():
+        sh = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        if grad:
+            rc = lib.rb_loglike_grad_batch(event.handle, ctypes.c_void_p(th.data_ptr()), W,
+                                           ctypes.c_void_p(lo.data_ptr()), ctypes.c_void_p(gr.data_ptr()), m, sh)
+        else:
+            rc = lib.rb_loglike_batch(event.handle, ctypes.c_void_p(th.data_ptr()), W, ctypes.c_void_p(lo.data_ptr()),
+                                      m, sh)
+        if rc != 0:
+            raise RuntimeError(lib.rb_last_error().decode())
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            call()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="relaxed"):
+        call()
+    torch.cuda.synchronize()
+    for _ in range(3):
+        g.replay()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.zero_()
+        starts[k].record()
+        g.replay()
+        ends[k].record()
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    mains = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for a, b in mains:
+        a.record()
+        b.record()
+    torch.cuda.synchronize()
+    for a, b in mains:
+        flush.zero_()
+        rb.set_trace_events(a, b)
+        call()
+    rb.set_trace_events(None, None)
+    torch.cuda.synchronize()
+    main_s = float(np.mean([a.elapsed_time(b) for a, b in mains])) / 1e3
+    del g
+    t, v = whole_job_rate(dist, sum(ms) / 1e3, W * K, device)
+    return {"value": v, "unit": UNIT, "walkers": W, "ms_per_call": t * 1e3 / K, "main_kernel_ms": main_s * 1e3,
+            "mode": mode, "grad": grad}, main_s
+
+
+def run_configs(rb, torch, args, dist, device, flush):
+    """The other configurations the metric is stated for, each on its own
+    synthetic event (the library's strain kernel injects the signal):
+    * C1: 1 detector, T = 64 s, 20-1024 Hz, 100 bins, 1000 walkers in a +-1 %
+      box; log L, mixed and plain FP64;
+    * C3: the same event, 4096 walkers, log L + gradient;
+    * C4: 3 detectors, T = 256 s, 20-2048 Hz, 1000 bins, 16384 prior draws,
+      log L + gradient, as the headline step (summary rebuild + batch in one
+      captured call) and as the batch alone, plus the summary build in GB/s."""
+    import ctypes
+    import synth
+    lib = rb.load()
+    out = {}
+    K = max(3, min(args.steps, 10))
+    ev1, data1, psd1 = make_inputs(rb, torch, device, "C1")
+    e1 = rb.Event(ev1["geom"], ev1["gmst"], ev1["T"], ev1["f_low"], ev1["f_high"], torch.view_as_complex(data1), psd1,
+                  ev1["n_bins"], ev1["theta_inj"])
+    th1 = torch.tensor(synth.walkers("C1"), device=device)
+    c1, m1 = batch_leg(rb, torch, lib, e1, th1, False, "mixed", K, flush, dist, device)
+    c1f, _ = batch_leg(rb, torch, lib, e1, th1, False, "fp64", K, flush, dist, device)
+    c1["roofline"] = roofline_main(th1.shape[0], 1, ev1["n_bins"], False, m1)
+    c1["fp64_path"] = c1f
+    c1["config"] = "1 det (H1), T=64 s, 20-1024 Hz, 100 bins, 1000 walkers (+-1 % box), log L"
+    out["C1"] = c1
+    th3 = torch.tensor(synth.walkers("C3"), device=device)
+    c3, m3 = batch_leg(rb, torch, lib, e1, th3, True, "mixed", K, flush, dist, device)
+    c3["roofline"] = roofline_main(th3.shape[0], 1, ev1["n_bins"], True, m3)
+    c3["config"] = "C1's event, 4096 walkers (+-1 % box), log L + gradient"
+    out["C3"] = c3
+    e1.free()
+    del data1, psd1
+    ev4, data4, psd4 = make_inputs(rb, torch, device, "C4")
+    D4, B4 = ev4["geom"].shape[0], ev4["n_bins"]
+    e4 = rb.Event(ev4["geom"], ev4["gmst"], ev4["T"], ev4["f_low"], ev4["f_high"], torch.view_as_complex(data4), psd4,
+                  B4, ev4["theta_inj"])
+    th4 = torch.tensor(synth.walkers("C4"), device=device)
+    W4 = th4.shape[0]
+    c4, m4 = batch_leg(rb, torch, lib, e4, th4, True, "mixed", K, flush, dist, device)
+    c4["roofline"] = roofline_main(W4, D4, B4, True, m4)
+    c4["roofline"]["traffic"] = None
+    # the headline step on this event: rebuild + batch in one captured call
+    lo = torch.empty(W4, dtype=torch.float64, device=device)
+    gr = torch.empty(W4, 13, dtype=torch.float64, device=device)
+
+    def step4():
+        sh = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        rc = lib.rb_rebuild_loglike_grad(e4.handle, ctypes.c_void_p(th4.data_ptr()), W4, ctypes.c_void_p(lo.data_ptr()),
+                                         ctypes.c_void_p(gr.data_ptr()), rb.RB_MIXED, sh)
+        if rc != 0:
+            raise RuntimeError(lib.rb_last_error().decode())
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            step4()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="relaxed"):
+        step4()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    for k in range(K):
+        flush.zero_()
+        starts[k].record()
+        g.replay()
+        ends[k].record()
+    torch.cuda.synchronize()
+    del g
+    t4, v4 = whole_job_rate(dist, sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / 1e3, W4 * K, device)
+    c4["step"] = {"value": v4, "unit": UNIT, "ms_per_step": t4 * 1e3 / K,
+                  "call": "rb_rebuild_loglike_grad (summary rebuild + log L + gradient), one captured graph"}
+    c4["summary_build"] = run_summary_build(rb, torch, e4, ev4, flush)
+    c4["config"] = "3 det, T=256 s, 20-2048 Hz, 1000 bins, 16384 prior draws (Mc 1.42-1.46), log L + gradient"
+    out["C4"] = c4
+    e4.free()
+    return out
 
 
 def hbm_peak_gbs():
@@ -577,6 +783,40 @@ def run_e2e(rb, torch, event, ev, data, psd, theta, W, args, dist, device):
             "h2d_bytes_per_step": int(D * N * 3 * 8 + W * 13 * 8), "d2h_bytes_per_step": int(W * 14 * 8)}
 
 
+def run_e2e_theta(rb, torch, event, theta, W, args, dist, device):
+    """The sampler's form of the end-to-end call (rb_loglike_grad_host): the
+    event's data stay resident; each step copies the walkers in from pinned
+    host memory and writes log L and the gradient to pinned host outputs, then
+    synchronises.  No summary rebuild."""
+    import ctypes
+    h_theta = theta.cpu().pin_memory()
+    h_logl = torch.empty(W, dtype=torch.float64).pin_memory()
+    h_grad = torch.empty(W, 13, dtype=torch.float64).pin_memory()
+    lib = rb.load()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def step():
+        rc = lib.rb_loglike_grad_host(event.handle, ctypes.c_void_p(h_theta.data_ptr()), W,
+                                      ctypes.c_void_p(h_logl.data_ptr()), ctypes.c_void_p(h_grad.data_ptr()),
+                                      rb.MODES[args.mode], stream)
+        if rc != 0:
+            raise RuntimeError(lib.rb_last_error().decode())
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    K = args.steps
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        step()
+    torch.cuda.synchronize()
+    el, rate = whole_job_rate(dist, time.perf_counter() - t0, W * K, device)
+    return {"value": rate, "unit": UNIT, "ms_per_step": el * 1e3 / K, "h2d_bytes_per_step": int(W * 13 * 8),
+            "d2h_bytes_per_step": int(W * 14 * 8),
+            "call": "rb_loglike_grad_host: walkers in, log L + gradient out, event resident (no rebuild)"}
+
+
 def run_serving(rb, torch, device, seconds: float = 6.0):
     """Continuous-batching serving loop over 8 resident events with mixed
     durations, detector sets and bin counts; Poisson arrivals of 256-8192
@@ -747,7 +987,7 @@ def main():
     args = parse()
     if args.profile:
         args.no_e2e = args.no_cpu = args.no_serving = args.no_fp64 = args.no_mala = args.no_full = True
-        args.no_summary_build = True
+        args.no_summary_build = args.no_configs = True
     dist = Dist()
     if args.impl == "reference":
         dist.init("gloo")
