@@ -63,6 +63,10 @@ extern "C" {
 #define RB_ENOTFOUND (-6)   /* unknown ticket */
 #define RB_ECLOSED (-7)     /* server shut down */
 
+/* ---- bin placement (rb_event_desc.bin_scheme) ------------------------------ */
+#define RB_BINS_PN 0        /* PN phase-bound ansatz (Sec. II.C) */
+#define RB_BINS_AGNOSTIC 1  /* the waveform model's own phase directions (no PN ansatz) */
+
 /* ---- evaluation modes ---------------------------------------------------- */
 #define RB_MIXED 0          /* phase in float-float (FP32 pairs), trig/ratio/contraction FP32, sums FP64 */
 #define RB_FP64 1           /* everything in native FP64 (comparison path) */
@@ -96,7 +100,7 @@ typedef struct {
   rb_detector_desc det[RB_MAX_DET];
   double T, f_low, f_high, gmst;
   int32_t data_on_device;
-  int32_t reserved;
+  int32_t bin_scheme; /* RB_BINS_PN (0) or RB_BINS_AGNOSTIC */
   void* cuda_stream; /* cudaStream_t used for the build; NULL = default stream */
   double theta_ref[RB_NPAR];
 } rb_event_desc;
@@ -108,24 +112,34 @@ typedef struct {
   double base_logl;       /* log L_RB(theta_ref) = sum_d Re sum_b A0 - B0/2 (FP64) */
   size_t device_bytes;    /* device memory held by the event */
   double theta_ref[RB_NPAR]; /* the current fiducial parameters */
+  int32_t bin_scheme;     /* the placement the edges were built with */
+  int32_t reserved;
+  double epsilon;         /* the placement measure's range over the band / n_bins [rad] */
 } rb_event_info;
 
 /* Build an event: grid, bin edges, fiducial waveform h0 on the full grid,
  * summary data A0, A1, B0, B1 per (detector, bin) in FP64, and the
  * device-resident edge and bin tables used by the batch calls.
  *
- * Bin placement (Sec. II.C; Zackay et al. 2018): B+1 edges equally spaced in
- * the PN phase bound 2 pi sum_g sgn(g) (f/f*_g)^g, g in {-5/3,-2/3,1,5/3,7/3},
- * inverted by linear interpolation on the grid, snapped to the nearest grid
- * point, then made strictly increasing.  Bin b holds grid points
- * edges[b] <= k < edges[b+1]; the last bin also holds edges[B].
+ * Bin placement, RB_BINS_PN (Sec. II.C; Zackay et al. 2018): B+1 edges equally
+ * spaced in the PN phase bound 2 pi sum_g sgn(g) (f/f*_g)^g,
+ * g in {-5/3,-2/3,1,5/3,7/3}, inverted by linear interpolation on the grid,
+ * snapped to the nearest grid point, then made strictly increasing.
+ * RB_BINS_AGNOSTIC (the outlook of Sec. V: bins without prior assumptions on
+ * the waveform): the same placement in the measure
+ * M(f) = 2 pi sum_j V_j(f) / V_j(f_high), V_j the total variation over the
+ * grid of the model's phase direction dPsi(f; theta_ref)/dtheta_j for
+ * j = Mc, q, chi1, chi2, Lambda1, Lambda2, t_c (directions without variation
+ * left out); the edges stay fixed when a rebuild changes theta_ref.
+ * epsilon = (range of the measure) / B is reported by rb_event_get_info.
+ * Bin b holds grid points edges[b] <= k < edges[b+1]; the last bin also holds edges[B].
  * Summary data: A0 = 4 df sum_b d conj(h0) / S, A1 = same times (f - f_m(b)),
  * B0 = 4 df sum_b |h0|^2 / S, B1 = same times (f - f_m(b)), f_m = edge midpoint.
  *
  * The inputs are copied; the caller may free them after return (the call
  * synchronises desc->cuda_stream).  Errors: RB_EINVAL (n_det not in 1..3,
  * n_bins out of range, T or band invalid, NULL pointers, unphysical
- * theta_ref), RB_ENOMEM, RB_ECUDA. */
+ * theta_ref, unknown bin_scheme), RB_ENOMEM, RB_ECUDA. */
 RB_API int rb_build_summary(const rb_event_desc* desc, rb_event_t* out);
 
 /* Release an event's device memory.  The caller must make sure no batch call

@@ -15,6 +15,9 @@ What each function follows (arXiv:2404.11397 and the works it cites):
 * ``summary``       -- A0, A1, B0, B1 (and B2) sums implied by Sec. II.C.
 * ``bin_edges``     -- PN-ansatz phase-bound bin placement (Sec. II.C and the
   epsilon <-> bin-count statement of Sec. IV.B).
+* ``bin_edges_agnostic`` / ``phase_directions`` / ``direction_measure`` -- bin
+  placement without the PN ansatz (the outlook of Sec. V asks for one): the
+  model's own phase derivatives, each given 2 pi of total variation.
 * ``strain`` / ``polarizations`` / ``tf2_phase`` / ``intrinsic`` -- TaylorF2 with
   tides (Sec. II.B; coefficients from the cited PN literature); Lambda-tilde and
   delta-Lambda-tilde from the appendix.
@@ -85,6 +88,10 @@ def _load():
     lib.orc_bin_edges.restype = c_int
     lib.orc_dpsi_max.argtypes = [d, d, d]
     lib.orc_dpsi_max.restype = d
+    lib.orc_bin_edges_agnostic.argtypes = [d, i64, i64, dp, c_int, ip, dp]
+    lib.orc_bin_edges_agnostic.restype = c_int
+    lib.orc_phase_directions.argtypes = [d, i64, i64, dp, dp]
+    lib.orc_direction_measure.argtypes = [c_int, i64, dp, dp]
     lib.orc_summary.argtypes = [c_int, dp, d, d, i64, i64, dp, dp, dp, c_int, ip, dp, dp, dp, dp, dp]
     lib.orc_summary.restype = c_int
     lib.orc_loglike_rb.argtypes = [c_int, dp, d, d, i64, i64, c_int, ip, dp, dp, dp, dp, dp, dp, dp, i64, dp,
@@ -220,6 +227,39 @@ def bin_edges(ev, n_bins: int) -> np.ndarray:
     if rc != 0:
         raise ValueError("invalid bin count")
     return edges
+
+
+PHASE_DIRECTIONS = ("Mc", "q", "chi1", "chi2", "Lambda1", "Lambda2", "tc")
+
+
+def phase_directions(ev, theta_ref) -> np.ndarray:
+    """[7][N] dPsi(f; theta_ref) / dtheta_j on the grid (j: PHASE_DIRECTIONS)."""
+    lib = _load()
+    W = np.zeros((len(PHASE_DIRECTIONS), ev["N"]))
+    lib.orc_phase_directions(ev["T"], ev["kmin"], ev["N"], _p(_f64(theta_ref)), _p(W))
+    return W
+
+
+def direction_measure(W) -> np.ndarray:
+    """M [N] = 2 pi sum_j V_j / V_j(end) for direction functions W [n][N] (V_j: total variation)."""
+    lib = _load()
+    W = _f64(np.atleast_2d(W))
+    M = np.zeros(W.shape[1])
+    lib.orc_direction_measure(W.shape[0], W.shape[1], _p(W), _p(M))
+    return M
+
+
+def bin_edges_agnostic(ev, n_bins: int, theta_ref=None):
+    """Edges uniform in the direction measure of the model's phase at theta_ref
+    (default: the event's injection); returns (edges, epsilon = M(f_high) / B)."""
+    lib = _load()
+    edges = np.zeros(n_bins + 1, dtype=np.int64)
+    eps = ctypes.c_double(0.0)
+    th = ev["theta_inj"] if theta_ref is None else theta_ref
+    rc = lib.orc_bin_edges_agnostic(ev["T"], ev["kmin"], ev["N"], _p(_f64(th)), n_bins, _p(edges), ctypes.byref(eps))
+    if rc != 0:
+        raise ValueError("invalid bin count")
+    return edges, eps.value
 
 
 def summary(ev, theta_ref, edges, with_b2: bool = False) -> dict:

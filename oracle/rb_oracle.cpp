@@ -382,24 +382,90 @@ double dpsi_max(double f, double f_low, double f_high) {
   return 2.0 * kPi * s;
 }
 
-void bin_edges(const Grid& grid, double f_low, double f_high, int B, int64_t* edges) {
-  const int64_t N = grid.N;
-  std::vector<double> P(N);
-  for (int64_t k = 0; k < N; ++k) P[k] = dpsi_max(grid.f(k), f_low, f_high);
+// Edges uniform in an increasing measure P tabulated on the grid: the target
+// of edge e is P[0] + (P[N-1] - P[0]) e / B, located by linear interpolation
+// between grid points and snapped to the nearest one; then at least one grid
+// point per bin (clamp into the feasible window, make strictly increasing).
+void place_edges(const std::vector<double>& P, int B, int64_t* edges) {
+  const int64_t N = int64_t(P.size());
   edges[0] = 0;
   edges[B] = N - 1;
   for (int e = 1; e < B; ++e) {
     double tau = P[0] + (P[N - 1] - P[0]) * double(e) / double(B);
-    // largest k with P[k] <= tau  (P is increasing)
+    // largest k with P[k] <= tau  (P is non-decreasing)
     int64_t k = int64_t(std::upper_bound(P.begin(), P.end(), tau) - P.begin()) - 1;
     k = std::max<int64_t>(0, std::min<int64_t>(k, N - 2));
     double frac = (tau - P[k]) / (P[k + 1] - P[k]);
     edges[e] = frac < 0.5 ? k : k + 1;
   }
-  // At least one grid point per bin: clamp into the feasible window, then make
-  // the sequence strictly increasing.
   for (int e = 0; e <= B; ++e) edges[e] = std::max<int64_t>(e, std::min<int64_t>(edges[e], N - 1 - (B - e)));
   for (int e = 1; e <= B; ++e) edges[e] = std::max(edges[e], edges[e - 1] + 1);
+}
+
+void bin_edges(const Grid& grid, double f_low, double f_high, int B, int64_t* edges) {
+  const int64_t N = grid.N;
+  std::vector<double> P(N);
+  for (int64_t k = 0; k < N; ++k) P[k] = dpsi_max(grid.f(k), f_low, f_high);
+  place_edges(P, B, edges);
+}
+
+// ----------------------------------------------------------------------------
+// Bin placement without the PN ansatz (the paper's outlook asks for bins built
+// without prior assumptions about the waveform).  Reading taken here: the
+// ansatz bounds the phase of the ratio by one power law per PN order, each
+// scaled to about 2 pi across the band; in its place take the waveform
+// model's own phase directions
+//     w_j(f) = dPsi(f; theta_ref) / dtheta_j,  j in {Mc, q, chi1, chi2,
+//              Lambda1, Lambda2, t_c}
+// (the intrinsic parameters and the time shift; exact derivatives by
+// forward-mode dual numbers through the model's phase), give each the same
+// 2 pi of total variation across the band, and place the edges uniformly in
+//     M(f) = 2 pi sum_j V_j(f) / V_j(f_high),  V_j(f) = total variation of w_j
+//            on [f_low, f] (the sum over grid steps of |w_j(f_k+1) - w_j(f_k)|),
+// directions with no variation left out.  epsilon = M(f_high) / B.
+// ----------------------------------------------------------------------------
+constexpr int kNDir = 7;
+constexpr int kDirParam[kNDir] = {0, 1, 2, 3, 4, 5, 7};
+
+// W [kNDir][N]: w_j at every grid frequency.
+void phase_directions(const Grid& grid, const double* theta_ref, double* W) {
+  using D7 = Dual<kNDir>;
+  D7 th[kNPar];
+  for (int i = 0; i < kNPar; ++i) th[i] = D7(theta_ref[i]);
+  for (int j = 0; j < kNDir; ++j) th[kDirParam[j]].d[j] = 1.0;
+  const Theta<D7> t = theta_from(th);
+  const Intrinsic<D7> s = intrinsic(t);
+  for (int64_t k = 0; k < grid.N; ++k) {
+    const D7 psi = tf2_phase(s, t.tc, t.phic, grid.f(k));
+    for (int j = 0; j < kNDir; ++j) W[j * grid.N + k] = psi.d[j];
+  }
+}
+
+// M [N] from n_dir direction functions W [n_dir][N] on the grid.
+void direction_measure(int n_dir, int64_t N, const double* W, double* M) {
+  std::vector<double> V(size_t(n_dir) * N);
+  for (int j = 0; j < n_dir; ++j) {
+    const double* w = W + size_t(j) * N;
+    double* v = V.data() + size_t(j) * N;
+    v[0] = 0.0;
+    for (int64_t k = 1; k < N; ++k) v[k] = v[k - 1] + std::fabs(w[k] - w[k - 1]);
+  }
+  for (int64_t k = 0; k < N; ++k) {
+    double m = 0.0;
+    for (int j = 0; j < n_dir; ++j) {
+      const double vend = V[size_t(j) * N + N - 1];
+      if (vend > 0.0) m += V[size_t(j) * N + k] / vend;
+    }
+    M[k] = 2.0 * kPi * m;
+  }
+}
+
+void bin_edges_agnostic(const Grid& grid, const double* theta_ref, int B, int64_t* edges, double* eps) {
+  std::vector<double> W(size_t(kNDir) * grid.N), M(grid.N);
+  phase_directions(grid, theta_ref, W.data());
+  direction_measure(kNDir, grid.N, W.data(), M.data());
+  place_edges(M, B, edges);
+  if (eps) *eps = M[grid.N - 1] / double(B);
 }
 
 // Run fn(i) for i in [0, n) on up to nthreads std::threads (contiguous chunks).
@@ -577,6 +643,23 @@ int orc_bin_edges(double f_low, double f_high, double T, int64_t kmin, int64_t N
 }
 
 double orc_dpsi_max(double f, double f_low, double f_high) { return dpsi_max(f, f_low, f_high); }
+
+// Agnostic bin placement (see bin_edges_agnostic); eps_out (may be NULL)
+// receives M(f_high) / B.
+int orc_bin_edges_agnostic(double T, int64_t kmin, int64_t N, const double* theta_ref, int B, int64_t* edges,
+                           double* eps_out) {
+  if (B < 1 || B > N - 1) return -1;
+  bin_edges_agnostic(Grid{T, kmin, N}, theta_ref, B, edges, eps_out);
+  return 0;
+}
+
+// The model's phase directions W [7][N] (Mc, q, chi1, chi2, Lambda1, Lambda2, t_c).
+void orc_phase_directions(double T, int64_t kmin, int64_t N, const double* theta_ref, double* W) {
+  phase_directions(Grid{T, kmin, N}, theta_ref, W);
+}
+
+// The normalised total-variation measure M [N] of n_dir direction functions W [n_dir][N].
+void orc_direction_measure(int n_dir, int64_t N, const double* W, double* M) { direction_measure(n_dir, N, W, M); }
 
 // Summary data per detector and bin, h0 = h_d(theta_ref):
 //   A0 = 4 df sum d conj(h0)/S,  A1 = 4 df sum d conj(h0)/S (f - f_m)       [D][B][2]

@@ -15,6 +15,8 @@ if os.environ.get("RB_LIB_VARIANT") == "checked":
 RB_OK, RB_PENDING = 0, 1
 RB_EINVAL, RB_ENOMEM, RB_ECUDA, RB_ETIMEDOUT, RB_EBUSY, RB_ENOTFOUND, RB_ECLOSED = -1, -2, -3, -4, -5, -6, -7
 RB_MIXED, RB_FP64, RB_MIXED_F64PHASE = 0, 1, 2
+RB_BINS_PN, RB_BINS_AGNOSTIC = 0, 1
+BIN_SCHEMES = {"pn": RB_BINS_PN, "agnostic": RB_BINS_AGNOSTIC}
 MODES = {"mixed": RB_MIXED, "fp64": RB_FP64, "mixed_f64phase": RB_MIXED_F64PHASE}
 NPAR = 13
 MAX_DET = 3
@@ -33,7 +35,7 @@ class DetectorDesc(ctypes.Structure):
 class EventDesc(ctypes.Structure):
     _fields_ = [("n_det", ctypes.c_int32), ("n_bins", ctypes.c_int32), ("det", DetectorDesc * MAX_DET),
                 ("T", ctypes.c_double), ("f_low", ctypes.c_double), ("f_high", ctypes.c_double),
-                ("gmst", ctypes.c_double), ("data_on_device", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("gmst", ctypes.c_double), ("data_on_device", ctypes.c_int32), ("bin_scheme", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p), ("theta_ref", ctypes.c_double * NPAR)]
 
 
@@ -41,7 +43,8 @@ class EventInfo(ctypes.Structure):
     _fields_ = [("n_det", ctypes.c_int32), ("n_bins", ctypes.c_int32), ("kmin", ctypes.c_int64),
                 ("n_freq", ctypes.c_int64), ("T", ctypes.c_double), ("gmst", ctypes.c_double),
                 ("base_logl", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
-                ("theta_ref", ctypes.c_double * 13)]
+                ("theta_ref", ctypes.c_double * 13), ("bin_scheme", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("epsilon", ctypes.c_double)]
 
 
 class ServerOpts(ctypes.Structure):

@@ -123,7 +123,7 @@ class Event:
     """
 
     def __init__(self, geom, gmst: float, T: float, f_low: float, f_high: float, data, psd, n_bins: int,
-                 theta_ref, stream: Optional[torch.cuda.Stream] = None):
+                 theta_ref, stream: Optional[torch.cuda.Stream] = None, bins: str = "pn"):
         lib = load()
         geom = np.asarray(geom, dtype=np.float64).reshape(-1, 5)
         D = geom.shape[0]
@@ -131,9 +131,12 @@ class Event:
         n_freq = math.floor(float(f_high) * float(T) + 1e-9) - math.ceil(float(f_low) * float(T) - 1e-9) + 1
         if n_freq >= 2:
             _check_host_arrays(data, psd, D, n_freq)
+        if bins not in _lib.BIN_SCHEMES:
+            raise ValueError(f"bins must be one of {sorted(_lib.BIN_SCHEMES)}")
         desc = _lib.EventDesc()
         desc.n_det = D
         desc.n_bins = int(n_bins)
+        desc.bin_scheme = _lib.BIN_SCHEMES[bins]
         desc.T, desc.f_low, desc.f_high, desc.gmst = float(T), float(f_low), float(f_high), float(gmst)
         cuda = [isinstance(data[d], torch.Tensor) and data[d].is_cuda for d in range(D)]
         cuda += [isinstance(psd[d], torch.Tensor) and psd[d].is_cuda for d in range(D)]
@@ -170,11 +173,12 @@ class Event:
         self.n_freq = int(inf.n_freq)
 
     @classmethod
-    def from_synth(cls, ev: dict, n_bins: Optional[int] = None, theta_ref=None, stream=None) -> "Event":
+    def from_synth(cls, ev: dict, n_bins: Optional[int] = None, theta_ref=None, stream=None,
+                   bins: str = "pn") -> "Event":
         """Build from a ``synth.make_event`` dict that carries ``data``."""
         return cls(ev["geom"], ev["gmst"], ev["T"], ev["f_low"], ev["f_high"], ev["data"], ev["psd"],
                    n_bins if n_bins is not None else ev["n_bins"],
-                   ev["theta_inj"] if theta_ref is None else theta_ref, stream=stream)
+                   ev["theta_inj"] if theta_ref is None else theta_ref, stream=stream, bins=bins)
 
     @property
     def handle(self) -> ctypes.c_void_p:

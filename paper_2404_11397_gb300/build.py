@@ -16,7 +16,7 @@ INCLUDE = ROOT / "include"
 BUILD = PKG / "_build"
 LIB = PKG / "librb.so"
 SOURCES = ["rb_setup.cu", "rb_loglike.cu", "rb_summary.cu", "rb_api.cu", "rb_server.cu", "rb_static.cu", "rb_mala.cu",
-           "rb_full.cu"]
+           "rb_full.cu", "rb_bins.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          f"-I{INCLUDE}", f"-I{CSRC}"]

@@ -28,7 +28,10 @@ cudaError_t launch_rb_mixed(const EventDev& ev, const void* ws, const void* tan,
 cudaError_t launch_rb_f64(const EventDev& ev, const void* ws, const void* tan, int64_t W, double* logl, double* grad,
                           cudaStream_t s, int n_sm, const MalaArgs* mala);
 cudaError_t launch_bin_edges(double f_low, double f_high, double T, int64_t kmin, int64_t N, int B, int64_t* edges,
-                             cudaStream_t s);
+                             double* span, cudaStream_t s);
+size_t bin_edges_agnostic_scratch_bytes(int64_t N);
+cudaError_t launch_bin_edges_agnostic(const double* theta_ref_dev, double T, int64_t kmin, int64_t N, int B,
+                                      int64_t* edges, double* span, void* scratch, cudaStream_t s);
 cudaError_t launch_summary(const DataPtrs& in, int64_t kmin, int64_t N, double T, int D, int B,
                            const int64_t* edges, const RefValues* ref, const SummaryOut& so, double* h0_out,
                            cudaStream_t s);
@@ -174,7 +177,7 @@ const EventEntry* event_entry(::rb_event_s* ev) { return ev ? &ev->e : nullptr; 
 
 extern "C" {
 
-int rb_abi_version(void) { return 1; }
+int rb_abi_version(void) { return 2; }
 
 #ifdef RB_BOUNDS_CHECK
 extern "C" int rb_bounds_read_loglike(rb::BoundsRecord* out);
@@ -318,6 +321,9 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
   for (int d = 0; d < D; ++d)
     if (!desc->det[d].data || !desc->det[d].psd) return set_error(RB_EINVAL, "rb_build_summary: detector %d has NULL data/psd", d);
   if (!theta_ok(desc->theta_ref)) return set_error(RB_EINVAL, "rb_build_summary: unphysical theta_ref");
+  if (desc->bin_scheme != RB_BINS_PN && desc->bin_scheme != RB_BINS_AGNOSTIC)
+    return set_error(RB_EINVAL, "rb_build_summary: bin_scheme=%d is neither RB_BINS_PN nor RB_BINS_AGNOSTIC",
+                     desc->bin_scheme);
 
   rb_event_t ev = new (std::nothrow) rb_event_s();
   if (!ev) return set_error(RB_ENOMEM, "rb_build_summary: host allocation");
@@ -332,6 +338,7 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
   e.f_low = desc->f_low;
   e.f_high = desc->f_high;
   e.gmst = desc->gmst;
+  e.bin_scheme = desc->bin_scheme;
   std::memcpy(e.theta_ref, desc->theta_ref, sizeof(e.theta_ref));
   e.ec.n_det = D;
   e.ec.pad = 0;
@@ -372,6 +379,8 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
 
   int rc = RB_OK;
   cudaError_t err;
+  void* bins_scratch = nullptr;  // build-time only (agnostic bin placement)
+  double* d_span = nullptr;
   do {
     struct { void** p; size_t n; const char* what; } allocs[] = {
         {(void**)&e.d_edges, sizeof(int64_t) * E, "edges"},
@@ -427,14 +436,29 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
     if (rc != RB_OK) break;
     if ((err = cudaMemcpyAsync(e.d_theta_ref, e.theta_ref, sizeof(double) * kNPar, cudaMemcpyHostToDevice, s)) != cudaSuccess) { rc = cuda_fail(err, "copy theta_ref"); break; }
     if ((err = cudaMemsetAsync(e.d_sync, 0, offsetof(SummarySync, bin_parts_done) + sizeof(unsigned) * B, s)) != cudaSuccess) { rc = cuda_fail(err, "zero counters"); break; }
-    if ((err = launch_bin_edges(e.f_low, e.f_high, e.T, kmin, N, B, e.d_edges, s)) != cudaSuccess) { rc = cuda_fail(err, "bin edge kernels"); break; }
+    if ((err = cudaMalloc((void**)&d_span, sizeof(double))) != cudaSuccess) { rc = cuda_fail(err, "bin span"); break; }
+    if (e.bin_scheme == RB_BINS_AGNOSTIC) {
+      if ((err = cudaMalloc(&bins_scratch, bin_edges_agnostic_scratch_bytes(N))) != cudaSuccess) { rc = cuda_fail(err, "bin placement scratch"); break; }
+      if ((err = launch_bin_edges_agnostic(e.d_theta_ref, e.T, kmin, N, B, e.d_edges, d_span, bins_scratch, s)) != cudaSuccess) { rc = cuda_fail(err, "agnostic bin edge kernels"); break; }
+      count_launches(8);
+    } else {
+      if ((err = launch_bin_edges(e.f_low, e.f_high, e.T, kmin, N, B, e.d_edges, d_span, s)) != cudaSuccess) { rc = cuda_fail(err, "bin edge kernels"); break; }
+    }
     if ((rc = make_parts(e, s)) != RB_OK) break;
     if ((err = launch_edge_tables(kmin, e.T, D, B, Ep, Bp, e.d_edges, e.d_tab32, edge32, e.d_tab64, e.d_invdf, s)) != cudaSuccess) { rc = cuda_fail(err, "edge table kernel"); break; }
     if ((err = launch_chunk_q(kmin, e.T, N, e.d_chunkq, s)) != cudaSuccess) { rc = cuda_fail(err, "chunk matrix kernel"); break; }
     count_launches(4);
     if ((rc = rebuild_event(e, nullptr, RB_FP64, s)) != RB_OK) break;
     if ((err = cudaStreamSynchronize(s)) != cudaSuccess) { rc = cuda_fail(err, "build synchronise"); break; }
+    double span = 0.0;
+    if ((err = cudaMemcpy(&span, d_span, sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess) { rc = cuda_fail(err, "read bin span"); break; }
+    e.epsilon = span / (double)B;
   } while (false);
+  if (bins_scratch || d_span) {
+    cudaStreamSynchronize(s);
+    cudaFree(bins_scratch);
+    cudaFree(d_span);
+  }
   if (rc != RB_OK) {
     cudaStreamSynchronize(s);
     rb_event_free(ev);
@@ -499,6 +523,9 @@ int rb_event_get_info(rb_event_t ev, rb_event_info* info) {
   info->gmst = e.gmst;
   info->device_bytes = e.device_bytes;
   std::memcpy(info->theta_ref, e.theta_ref, sizeof(info->theta_ref));
+  info->bin_scheme = e.bin_scheme;
+  info->reserved = 0;
+  info->epsilon = e.epsilon;
   cudaError_t err = cudaMemcpy(&info->base_logl, e.d_base, sizeof(double), cudaMemcpyDeviceToHost);
   if (err != cudaSuccess) return cuda_fail(err, "rb_event_get_info: read base");
   return RB_OK;
@@ -506,7 +533,7 @@ int rb_event_get_info(rb_event_t ev, rb_event_info* info) {
 
 // ---- event files: checkpoint and resume ----
 namespace {
-constexpr char kEventMagic[8] = {'R', 'B', 'E', 'V', 'E', 'N', 'T', '1'};
+constexpr char kEventMagic[8] = {'R', 'B', 'E', 'V', 'E', 'N', 'T', '2'};
 struct EventFileHeader {  // followed by strain [n_det][n_freq][2] and PSD [n_det][n_freq], FP64
   char magic[8];
   int32_t n_det, n_bins;
@@ -514,6 +541,7 @@ struct EventFileHeader {  // followed by strain [n_det][n_freq][2] and PSD [n_de
   double T, f_low, f_high, gmst;
   double geom[RB_MAX_DET][5];
   double theta_ref[RB_NPAR];
+  int32_t bin_scheme, reserved;
 };
 }  // namespace
 
@@ -534,6 +562,7 @@ int rb_event_save(rb_event_t ev, const char* path) {
   h.gmst = e.gmst;
   std::memcpy(h.geom, e.geom, sizeof(h.geom));
   std::memcpy(h.theta_ref, e.theta_ref, sizeof(h.theta_ref));
+  h.bin_scheme = e.bin_scheme;
   const size_t nd = (size_t)2 * e.n_det * e.N, np = (size_t)e.n_det * e.N;
   std::vector<double> data(nd), psd(np);
   // the resident copy, after every call already issued on any stream
@@ -581,6 +610,7 @@ int rb_event_load(const char* path, void* stream, rb_event_t* out) {
   desc.f_high = h.f_high;
   desc.gmst = h.gmst;
   desc.data_on_device = 0;
+  desc.bin_scheme = h.bin_scheme;
   desc.cuda_stream = stream;
   std::memcpy(desc.theta_ref, h.theta_ref, sizeof(desc.theta_ref));
   for (int d = 0; d < h.n_det; ++d) {

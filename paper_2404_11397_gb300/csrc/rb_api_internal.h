@@ -27,6 +27,8 @@ struct EventEntry {
   int n_det = 0, n_bins = 0;
   int64_t kmin = 0, N = 0;
   double T = 0, f_low = 0, f_high = 0, gmst = 0;
+  int bin_scheme = RB_BINS_PN;
+  double epsilon = 0;  // the placement measure's range over the band / n_bins
   double theta_ref[kNPar] = {};
   double geom[kMaxDet][5] = {};  // site rows as given: lat, lon, elevation, x/y arm azimuths
   EventConst ec{};

@@ -972,6 +972,25 @@ cudaError_t launch_tangents(const double* theta, int64_t W, const EventConst& ec
   return cudaGetLastError();
 }
 
+// Phase directions of the fiducial waveform for the bin placement without the
+// PN ansatz: dc_k / dtheta_j at theta_ref (the FP64 dual numbers of the FP64
+// set-up's tangents), out[k][j] for j = Mc, q, chi1, chi2, Lambda1, Lambda2.
+// With the basis functions g_k they give dPsi(f) / dtheta_j = sum_k out[k][j] g_k(f);
+// the constant phase does not vary with f and is not needed.
+__global__ void k_ref_phase_tangents(const double* __restrict__ theta_ref, double* __restrict__ out) {
+  const int part = threadIdx.x;
+  if (part >= 3) return;
+  WalkerTan<double> t;
+  tangents_intrinsic<double>(theta_ref, part, t);
+  for (int k = 0; k < kNBasis; ++k)
+    for (int j = 2 * part; j < 2 * part + 2; ++j) out[k * kNTanIntr + j] = t.dc[k][j];
+}
+
+cudaError_t launch_ref_phase_tangents(const double* theta_ref_dev, double* out, cudaStream_t s) {
+  k_ref_phase_tangents<<<1, 32, 0, s>>>(theta_ref_dev, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ref_dd(const double* theta_ref_dev, const EventConst& ec, RefValues* out, cudaStream_t s) {
   k_ref_dd<<<1, kDdRoleThreads, 0, s>>>(theta_ref_dev, ec, out);
   return cudaGetLastError();

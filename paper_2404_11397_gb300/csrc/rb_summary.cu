@@ -32,10 +32,14 @@ __device__ double dpsi_max(double f, double f_low, double f_high) {
 // One thread per interior edge: largest k with P(k) <= tau_e by bisection,
 // then snap to the nearer of k, k+1 by linear interpolation.
 __global__ void k_bin_edges(double f_low, double f_high, double T, int64_t kmin, int64_t N, int B,
-                            int64_t* __restrict__ edges) {
+                            int64_t* __restrict__ edges, double* __restrict__ span) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e > B) return;
-  if (e == 0) { edges[0] = 0; return; }
+  if (e == 0) {
+    edges[0] = 0;
+    if (span) *span = dpsi_max(grid_f(kmin, N - 1, T), f_low, f_high) - dpsi_max(grid_f(kmin, 0, T), f_low, f_high);
+    return;
+  }
   if (e == B) { edges[B] = N - 1; return; }
   const double P0 = dpsi_max(grid_f(kmin, 0, T), f_low, f_high);
   const double PN = dpsi_max(grid_f(kmin, N - 1, T), f_low, f_high);
@@ -320,14 +324,20 @@ __global__ void k_strain(const RefValues* __restrict__ src, int64_t kmin, int64_
 }
 
 // ---------------------------------------------------------------------------
-cudaError_t launch_bin_edges(double f_low, double f_high, double T, int64_t kmin, int64_t N, int B, int64_t* edges,
-                             cudaStream_t s) {
-  const int bs = 32;
-  k_bin_edges<<<(B + 1 + bs - 1) / bs, bs, 0, s>>>(f_low, f_high, T, kmin, N, B, edges);
-  cudaError_t err = cudaGetLastError();
-  if (err != cudaSuccess) return err;
+cudaError_t launch_bin_edges_fix(int64_t N, int B, int64_t* edges, cudaStream_t s) {
   k_bin_edges_fix<<<1, 32, 0, s>>>(N, B, edges);
   return cudaGetLastError();
+}
+
+// span (device, may be NULL): the phase bound's range over the band, so that
+// epsilon = span / B.
+cudaError_t launch_bin_edges(double f_low, double f_high, double T, int64_t kmin, int64_t N, int B, int64_t* edges,
+                             double* span, cudaStream_t s) {
+  const int bs = 32;
+  k_bin_edges<<<(B + 1 + bs - 1) / bs, bs, 0, s>>>(f_low, f_high, T, kmin, N, B, edges, span);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  return launch_bin_edges_fix(N, B, edges, s);
 }
 
 cudaError_t launch_summary(const DataPtrs& in, int64_t kmin, int64_t N, double T, int D, int B,

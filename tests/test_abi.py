@@ -39,7 +39,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_status_strings_and_version(lib):
-    assert lib.rb_abi_version() == 1
+    assert lib.rb_abi_version() == 2
     assert lib.rb_strerror(0) == b"ok"
     assert lib.rb_strerror(-5).startswith(b"busy")
     assert lib.rb_strerror(12345) == b"unknown status"
