@@ -344,30 +344,47 @@ RB_API int rb_strain(const double* geom, double gmst, const double* theta_host, 
  * pinned staging buffers.  Clients submit likelihood(+gradient) requests for
  * resident events from any thread; requests that arrive while others are on
  * the GPU are admitted as soon as a slot and enough of the device-memory
- * budget are free, and run concurrently on separate streams.  Each slot
- * launch is a CUDA-graph replay of the captured (set-up, likelihood) pair for
- * the request's event and walker-count bucket.  Results are returned by
- * rb_poll; each is identical to the same request evaluated alone. */
+ * budget are free, and run concurrently on separate streams.  When a slot
+ * frees up, the scheduler takes the oldest pending request and packs into
+ * the same launch the later pending requests for the same event and
+ * gradient flag, up to max_walkers walkers and the memory budget; the
+ * launch runs the packed walkers rounded up to a multiple of 256 (the extra
+ * walkers are copies of the first, their results dropped), and each request
+ * gets its own walkers' results back.  A launch is a CUDA graph: copy-in,
+ * set-up, likelihood kernel, copy-out and a completion node, captured for the
+ * launch and applied to the slot's instantiated graph for the same detector
+ * count and gradient flag (cudaGraphExecUpdate; a new instantiation only when
+ * the update is refused).  Results are returned by rb_poll; each is
+ * identical to the same request evaluated alone (one warp per walker, no
+ * cross-walker arithmetic). */
 typedef struct {
   size_t hbm_budget_bytes;  /* device bytes the in-flight requests may hold (0 = 1 GiB) */
   int32_t max_slots;        /* concurrent requests on the GPU (streams), 1..64 (0 = 8) */
   int32_t max_queue;        /* pending requests before rb_submit returns RB_EBUSY (0 = 4096) */
   int32_t use_graphs;       /* 1 = replay captured CUDA graphs (default), 0 = plain launches */
   int32_t mode;             /* RB_MIXED / RB_FP64 / RB_MIXED_F64PHASE */
-  int64_t max_walkers;      /* largest request accepted (0 = 65536) */
+  int64_t max_walkers;      /* largest request accepted, and the most walkers one launch packs (0 = 65536) */
 } rb_server_opts;
 
 typedef struct {
-  uint64_t submitted, completed, rejected, graph_launches, plain_launches, graphs_captured;
-  int32_t in_flight, queued;
+  uint64_t submitted, completed, rejected;
+  uint64_t graph_launches, plain_launches; /* launches (each may carry several packed requests) */
+  uint64_t graphs_captured;   /* graph instantiations */
+  int32_t in_flight, queued;  /* launches on the GPU, requests waiting */
   size_t hbm_in_use;
-  int32_t max_in_flight;  /* largest number of requests on the GPU at once so far */
+  int32_t max_in_flight;      /* largest number of launches on the GPU at once so far */
   int32_t reserved;
+  uint64_t graph_updates;     /* launches that updated an instantiated graph in place */
+  uint64_t walkers_requested; /* walkers of the completed requests */
+  uint64_t walkers_run;       /* walkers their launches ran (requested + padding) */
 } rb_server_stats;
 
 RB_API int rb_server_create(const rb_server_opts* opts, rb_server_t* out);
-/* Stops the scheduler after the in-flight requests finish; pending requests
- * fail with RB_ECLOSED. */
+/* Stops the scheduler after the in-flight launches finish; pending requests
+ * fail with RB_ECLOSED.  A launch whose stream reports a CUDA error fails its
+ * requests (RB_ECUDA) instead of being waited for, and after 30 s without
+ * completion the remaining in-flight requests fail with RB_ETIMEDOUT and their
+ * slots' buffers are left allocated (never freed under a running kernel). */
 RB_API int rb_server_destroy(rb_server_t srv);
 /* Enqueue a request for log L (Sec. II.C) and, if want_grad, its gradient
  * for W walkers of one event: theta_host [W][13] is copied before return.  *ticket
@@ -383,7 +400,19 @@ RB_API int rb_submit(rb_server_t srv, rb_event_t ev, const double* theta_host, i
  * RB_PENDING (timeout_us == 0 and not done), RB_ETIMEDOUT, RB_ENOTFOUND, or
  * the request's own error status. */
 RB_API int rb_poll(rb_server_t srv, uint64_t ticket, int64_t timeout_us, double* logl_out, double* grad_out);
+/* The walker count and gradient flag of a request not yet collected, so that
+ * the caller can size rb_poll's buffers: RB_OK, or RB_ENOTFOUND. */
+RB_API int rb_ticket_info(rb_server_t srv, uint64_t ticket, int64_t* W, int32_t* want_grad);
 RB_API int rb_server_get_stats(rb_server_t srv, rb_server_stats* stats);
+/* Latency of the requests completed since the last reset, measured by the
+ * server: part 0 from rb_submit to the moment the results are in host memory
+ * (what rb_poll then copies), and its three parts: 1 waiting for a slot (and
+ * budget), 2 the host staging and issuing the launch, 3 the device work and
+ * the completion node.  count, and nearest-rank p50, p99 and maximum in ms (0
+ * with no requests).  reset != 0 forgets all parts afterwards.  At most 4 Mi
+ * requests are kept between resets. */
+RB_API int rb_server_latency(rb_server_t srv, int part, int reset, int64_t* count, double* p50_ms, double* p99_ms,
+                             double* max_ms);
 
 /* ---- diagnostics ---------------------------------------------------------- */
 RB_API const char* rb_strerror(int status);

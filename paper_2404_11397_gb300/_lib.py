@@ -57,7 +57,9 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
                 ("graph_launches", ctypes.c_uint64), ("plain_launches", ctypes.c_uint64),
                 ("graphs_captured", ctypes.c_uint64), ("in_flight", ctypes.c_int32), ("queued", ctypes.c_int32),
-                ("hbm_in_use", ctypes.c_size_t), ("max_in_flight", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("hbm_in_use", ctypes.c_size_t), ("max_in_flight", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("graph_updates", ctypes.c_uint64), ("walkers_requested", ctypes.c_uint64),
+                ("walkers_run", ctypes.c_uint64)]
 
 
 # name -> (restype, argtypes); the order follows include/rb.h
@@ -98,7 +100,10 @@ SIGNATURES = {
     "rb_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, c_double_p, ctypes.c_int64, ctypes.c_int,
                                  ctypes.POINTER(ctypes.c_uint64)]),
     "rb_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, c_double_p, c_double_p]),
+    "rb_ticket_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, c_int64_p, ctypes.POINTER(ctypes.c_int32)]),
     "rb_server_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerStats)]),
+    "rb_server_latency": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, c_int64_p, c_double_p, c_double_p,
+                                         c_double_p]),
     "rb_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "rb_last_error": (ctypes.c_char_p, []),
     "rb_set_trace_events": (None, [ctypes.c_void_p, ctypes.c_void_p]),

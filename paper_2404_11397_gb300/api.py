@@ -477,12 +477,13 @@ class Server:
     def _poll_shape(self, ticket: int, W: Optional[int], want_grad: Optional[bool]):
         """The output extents of a poll: the library copies the request's own
         W values (and 13 W gradient values if it asked for them), so buffers
-        are sized from the submitted request; a W that disagrees is refused."""
+        are sized from the request as the library holds it; a W that disagrees
+        is refused, and an unknown ticket raises RB_ENOTFOUND."""
         known = self._req.get(ticket)
-        if known is None:  # not submitted here (or already collected): the library answers for it
-            if W is None:
-                raise ValueError("unknown ticket: give W")
-            return int(W), True if want_grad is None else bool(want_grad)
+        if known is None:  # not submitted through this object: ask the library for its shape
+            w, g = ctypes.c_int64(0), ctypes.c_int32(0)
+            check(load().rb_ticket_info(self._h, ticket, ctypes.byref(w), ctypes.byref(g)), "rb_ticket_info")
+            known = (int(w.value), bool(g.value))
         if W is not None and int(W) != known[0]:
             raise ValueError(f"ticket {ticket} was submitted with W = {known[0]}, not {W}")
         return known[0], known[1] if want_grad is None else (bool(want_grad) and known[1])
@@ -500,6 +501,23 @@ class Server:
         self._req.pop(ticket, None)  # collected, or failed: the library has forgotten it either way
         check(st, "rb_poll")
         return st, logl, grad
+
+    LATENCY_PARTS = ("total", "queue", "issue", "device")
+
+    def latency(self, reset: bool = False) -> dict:
+        """Server-side latency of the requests completed since the last reset:
+        total (rb_submit to results in host memory) and its parts -- waiting for a
+        slot, issuing the launch, device work and completion -- each as
+        {count, p50_ms, p99_ms, max_ms}."""
+        out = {}
+        for part, name in enumerate(self.LATENCY_PARTS):
+            n = ctypes.c_int64(0)
+            q = [ctypes.c_double(0.0) for _ in range(3)]
+            last = part == len(self.LATENCY_PARTS) - 1
+            check(load().rb_server_latency(self._h, part, 1 if (reset and last) else 0, ctypes.byref(n),
+                                           *(ctypes.byref(x) for x in q)), "rb_server_latency")
+            out[name] = {"count": int(n.value), "p50_ms": q[0].value, "p99_ms": q[1].value, "max_ms": q[2].value}
+        return out
 
     def stats(self) -> dict:
         s = _lib.ServerStats()

@@ -202,7 +202,10 @@ def test_mala_shapes_are_checked():
 def test_server_poll_buffers_follow_the_submitted_request():
     """rb_poll copies the request's own W values (13 W more with the gradient),
     so the binding sizes its buffers from the submitted request and refuses a
-    W that disagrees; submit refuses walkers that are not [W, 13]."""
+    W that disagrees; a ticket it did not record is sized by the library
+    (rb_ticket_info), never from a caller's W; submit refuses walkers that are
+    not [W, 13]."""
+    from paper_2404_11397_gb300 import RBError
     from paper_2404_11397_gb300.api import Server
     srv = Server.__new__(Server)  # the bookkeeping only: no library server behind it
     srv._h, srv._req = None, {7: (300, True), 8: (5, False)}
@@ -211,9 +214,9 @@ def test_server_poll_buffers_follow_the_submitted_request():
     assert srv._poll_shape(8, None, True) == (5, False)  # no gradient to copy for a request without it
     with pytest.raises(ValueError):
         srv._poll_shape(7, 299, None)
-    assert srv._poll_shape(9, 64, None) == (64, True)  # unknown here: the library answers (RB_ENOTFOUND)
-    with pytest.raises(ValueError):
-        srv._poll_shape(9, None, None)
+    for W in (64, None):  # unknown here: the library is asked (no server behind this object: refused)
+        with pytest.raises(RBError):
+            srv._poll_shape(9, W, None)
     for bad in (np.zeros(12), np.zeros((4, 12)), np.zeros((2, 2, 13))):
         with pytest.raises(ValueError):
             srv.submit(None, bad)

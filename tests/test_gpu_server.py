@@ -2,7 +2,8 @@
 several resident events of different durations, detector sets and bin counts.
 
 * every result in the mix equals the same request evaluated alone (bitwise:
-  each walker is computed by one warp, independent of the others);
+  each walker is computed by one warp, independent of the others), also when
+  several requests share one launch and the launch is padded;
 * requests overlap on the device (more than one in flight) when slots and the
   memory budget allow it, and are serialised when the budget admits one;
 * admission refusal (RB_EBUSY), poll timeouts and unknown tickets.
@@ -55,18 +56,47 @@ def test_mix_equals_alone(rb, events, use_graphs):
         off = int(rng.integers(0, 3000 - W + 1))
         th = pool[off:off + W]
         reqs.append((srv.submit(events[e], th, want_grad=True), e, th))
-    for t, e, th in reqs:
-        st, L, G = srv.poll(t, th.shape[0], timeout_us=-1)
+    for i, (t, e, th) in enumerate(reqs):
+        if i == 12:
+            srv._req.clear()  # the rest are sized from the library's record of each ticket
+        st, L, G = srv.poll(t, timeout_us=-1)
         assert st == rb.RB_OK
         La, Ga = _alone(rb, events[e], th)
         np.testing.assert_array_equal(L, La)
         np.testing.assert_array_equal(G, Ga)
     stats = srv.stats()
     assert stats["completed"] == stats["submitted"] == 24
+    launches = stats["graph_launches"] if use_graphs else stats["plain_launches"]
+    assert 1 <= launches <= 24
     if use_graphs:
-        assert stats["graph_launches"] == 24 and stats["graphs_captured"] >= 1
-    else:
-        assert stats["plain_launches"] == 24
+        assert stats["graphs_captured"] >= 1 and stats["graphs_captured"] + stats["graph_updates"] == launches
+    assert stats["walkers_requested"] == sum(th.shape[0] for _, _, th in reqs)
+    assert 0 <= stats["walkers_run"] - stats["walkers_requested"] < 256 * launches
+    srv.close()
+
+
+def test_pending_requests_share_launches(rb, events):
+    """With one slot, requests for the same event that queue behind a running
+    launch are packed into the next one; each still gets its own results."""
+    pool = synth.walkers("C2", 4096)
+    srv = rb.Server(max_slots=1, max_walkers=8192)
+    rng = np.random.default_rng(11)
+    reqs = []
+    for i in range(40):
+        W = int(rng.integers(1, 700))
+        th = pool[(37 * i) % 3000:(37 * i) % 3000 + W]
+        e = 1 if i % 4 else 3
+        reqs.append((srv.submit(events[e], th, want_grad=i % 5 != 0), e, th, i % 5 != 0))
+    for t, e, th, g in reqs:
+        st, L, G = srv.poll(t, timeout_us=-1)
+        assert st == rb.RB_OK and (G is not None) == g
+        La, Ga = _alone(rb, events[e], th)
+        np.testing.assert_array_equal(L, La)
+        if g:
+            np.testing.assert_array_equal(G, Ga)
+    stats = srv.stats()
+    assert stats["completed"] == 40
+    assert stats["graph_launches"] < 40  # some launches carried several requests
     srv.close()
 
 
@@ -110,6 +140,10 @@ def test_admission_refusal_and_polls(rb, events):
         assert st == rb.RB_OK
     with pytest.raises(rb.RBError) as e:
         srv.poll(accepted[0], 4096)  # already collected
+    assert e.value.status == rb.RB_ENOTFOUND
+    srv._req.clear()
+    with pytest.raises(rb.RBError) as e:
+        srv.poll(accepted[0])  # nor known to the library
     assert e.value.status == rb.RB_ENOTFOUND
     assert srv.stats()["rejected"] == busy
     srv.close()
