@@ -42,16 +42,14 @@ cudaError_t launch_edge_tables(int64_t kmin, double T, int D, int B, int Ep, int
 cudaError_t launch_chunk_q(int64_t kmin, double T, int64_t N, void* cq, cudaStream_t s);
 size_t chunk_q_bytes(int64_t N);
 cudaError_t launch_strain(const RefValues* src, int64_t kmin, int64_t N, double T, double* h, cudaStream_t s);
-cudaError_t launch_chunk_coef(int64_t N, int D, const RefValues* ref, const void* cq, void* chunk_coef, cudaStream_t s);
 cudaError_t launch_summary_parts(const void* w32, const float* is32, const int* exps, int64_t N, double T, int D, int B,
-                                 const int64_t* edges, const RefValues* ref, const void* chunk_coef,
+                                 const int64_t* edges, const RefValues* ref, const void* chunk_q,
                                  const SummaryOut& so, int p0, int p1, cudaStream_t s);
 cudaError_t launch_ref_dd(const double* theta_ref_dev, const EventConst& ec, RefValues* out, cudaStream_t s);
 cudaError_t launch_tangents(const double* theta, int64_t W, const EventConst& ec, void* tan, cudaStream_t s);
 cudaError_t launch_data32(const DataPtrs& in, int64_t N, int D, void* w32, float* is32, int* exps, cudaStream_t s);
 cudaError_t launch_pull32(const DataPtrs& src, int64_t N, int D, double* data, double* psd, void* w32, float* is32,
                           int* exps, int n_sm, cudaStream_t s);
-size_t chunk_coef_bytes(int64_t N);
 
 // ---- diagnostics ----
 static thread_local char g_err[512] = "no error";
@@ -278,7 +276,6 @@ int rb_event_free(rb_event_t ev) {
   cudaFree(e.d_psd);
   cudaFree(e.d_theta_ref);
   cudaFree(e.d_chunkq);
-  cudaFree(e.d_chunks);
   cudaFree(e.d_invdf);
   cudaFree(e.d_share);
   cudaFree(e.step_ws);
@@ -394,7 +391,6 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
         {(void**)&e.d_h0, sizeof(double) * 2 * D * N, "stored fiducial waveform"},
         {(void**)&e.d_theta_ref, sizeof(double) * kNPar, "theta_ref"},
         {(void**)&e.d_chunkq, chunk_q_bytes(N), "chunk matrices"},
-        {(void**)&e.d_chunks, chunk_coef_bytes(N), "chunk coefficients"},
         {(void**)&e.d_invdf, sizeof(double) * B, "bin widths"},
         {(void**)&e.d_share, sizeof(double) * D * B, "base shares"},
         {(void**)&e.d_sync, offsetof(SummarySync, bin_parts_done) + sizeof(unsigned) * B, "build counters"},
@@ -869,7 +865,7 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
   // one this summary does not read runs on a forked stream, joined below.
   if ((err = cudaEventRecord(e.ev_fork, s)) != cudaSuccess || (err = cudaStreamWaitEvent(e.side, e.ev_fork, 0)) != cudaSuccess)
     return cuda_fail(err, "rebuild fork");
-  int launches = 3;
+  int launches = 3;  // the two reference-value kernels and the summary kernel
   // the float-float reference values head the critical path of the fast
   // rebuild: enqueued first
   if (fast && (err = launch_ref_dd(e.d_theta_ref, e.ec, e.d_ref, s)) != cudaSuccess)
@@ -910,10 +906,6 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
     // the FP32 working copy follows the data the sums are taken over: data
     // read in place are converted every time, the resident data only after
     // they change
-    // the chunk coefficients need the reference values only: ahead of any
-    // wait for the data
-    if ((err = launch_chunk_coef(e.N, e.n_det, e.d_ref, e.d_chunkq, e.d_chunks, s)) != cudaSuccess)
-      return cuda_fail(err, "chunk coefficient kernel");
     if (ss && ss->data_ready && (err = cudaStreamWaitEvent(s, ss->data_ready, 0)) != cudaSuccess)
       return cuda_fail(err, "rebuild: wait for the data copies");
     if (in_opt || !e.w32_resident) {
@@ -924,8 +916,7 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
     }
     e.w32_current = true;
     err = launch_summary_parts(e.d_w32, e.d_is32, e.d_wexp, e.N, e.T, e.n_det, e.n_bins, e.d_edges, e.d_ref,
-                               e.d_chunks, e.out(), 0, e.n_parts, s);
-    ++launches;
+                               e.d_chunkq, e.out(), 0, e.n_parts, s);
   } else if (e.h0_valid) {
     // FP64 sums from the fiducial waveform stored by the last inline build
     // for this theta_ref: strain, PSD and h0 streamed, no waveform arithmetic

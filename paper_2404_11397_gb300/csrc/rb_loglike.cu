@@ -33,8 +33,28 @@
 
 namespace rb {
 
-constexpr int kThreads = 512;
+#ifndef RB_MIXED_THREADS
+#define RB_MIXED_THREADS 512
+#endif
+constexpr int kThreads = RB_MIXED_THREADS;  // threads per block of the mixed likelihood kernel
 constexpr unsigned kFull = 0xffffffffu;
+// Per-warp copy of the current walker's constants in shared memory (read by
+// broadcast loads in every chunk instead of held in registers), as float4:
+//   [0..4] {dc_hi[2q], dc_hi[2q+1], dc_lo[2q], dc_lo[2q+1]}
+//   [5] {tau_hi0, tau_hi1, tau_lo0, tau_lo1}   detectors 0, 1
+//   [6] {rho_r0, rho_r1, rho_i0, rho_i1}       [7] {sig_r0, sig_r1, sig_i0, sig_i1}
+//   [8] {tau_hi, tau_lo, 0, 0}                  detector D-1 when D is odd
+//   [9] {rho_r, rho_i, sig_r, sig_i}
+constexpr int kWcQuads = 10;
+
+// Shared-memory load that the compiler may not hoist out of a loop.
+__device__ __forceinline__ float4 lds4(const float4* p) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"((unsigned)__cvta_generic_to_shared(p)));
+  return v;
+}
 
 struct LaunchArgs {
   EventDev ev;
@@ -234,6 +254,13 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
   __syncthreads();
 
   const int lane = threadIdx.x & 31;
+  float4* wc;  // this warp's walker constants, after the tables
+  {
+    const size_t tab_bytes = !PHASE64 ? ev.tab32_floats * sizeof(float)
+                                      : (size_t)(kNBasis + 1) * Ep * sizeof(double) +
+                                            (ev.tab32_floats - ev.edge32_floats) * sizeof(float);
+    wc = reinterpret_cast<float4*>(smem_raw + tab_bytes) + (threadIdx.x >> 5) * kWcQuads;
+  }
   // detectors 0 and 1 form a pair when D >= 2; an odd detector count leaves
   // detector D - 1 single (bin table layout in EventDev)
   constexpr bool paired = D >= 2;
@@ -250,23 +277,22 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
   const int64_t nwarps = blockDim.x >> 5;
 
   for (int64_t w = warp0; w < w_end; w += nwarps) {
-    // ---- per-walker constants (uniform across the warp) ----
-    float2 dch[kNBasis / 2], dcl[kNBasis / 2];  // basis coefficients 2q, 2q+1
+    // ---- per-walker constants (uniform across the warp), to shared memory ----
     double dc64[kNBasis];
     double tau64[kMaxDet];
-    float rho[kMaxDet][2];
-    pv::DetState<float2> P;  // detectors 0, 1
+    pv::DetState<float2> P;  // detectors 0, 1: accumulators (constants come from wc)
     pv::DetState<float> S;   // detector ds
     int valid;
     {
-      float th[kMaxDet], tl[kMaxDet], sg[kMaxDet][2];
+      float th[kMaxDet], tl[kMaxDet], rho[kMaxDet][2], sg[kMaxDet][2];
+      float dh[kNBasis], dl[kNBasis];
       if (!PHASE64) {
         const WalkerMixed* s = reinterpret_cast<const WalkerMixed*>(a.ws) + RB_IDX(w, a.W, 101);
         valid = s->valid;
 #pragma unroll
-        for (int q = 0; q < kNBasis / 2; ++q) {
-          dch[q] = make_float2(s->dc_hi[2 * q], s->dc_hi[2 * q + 1]);
-          dcl[q] = make_float2(s->dc_lo[2 * q], s->dc_lo[2 * q + 1]);
+        for (int k = 0; k < kNBasis; ++k) {
+          dh[k] = s->dc_hi[k];
+          dl[k] = s->dc_lo[k];
         }
 #pragma unroll
         for (int d = 0; d < kMaxDet; ++d) {
@@ -278,7 +304,10 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
         const WalkerF64* s = reinterpret_cast<const WalkerF64*>(a.ws) + w;
         valid = s->valid;
 #pragma unroll
-        for (int k = 0; k < kNBasis; ++k) dc64[k] = s->dc[k];
+        for (int k = 0; k < kNBasis; ++k) {
+          dc64[k] = s->dc[k];
+          dh[k] = dl[k] = 0.f;
+        }
 #pragma unroll
         for (int d = 0; d < kMaxDet; ++d) {
           tau64[d] = s->tau[d];
@@ -287,13 +316,18 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
           sg[d][0] = (float)s->sig[d][0]; sg[d][1] = (float)s->sig[d][1];
         }
       }
-      P.tau_h = make_float2(th[0], th[1]); P.tau_l = make_float2(tl[0], tl[1]);
-      P.rho_r = make_float2(rho[0][0], rho[1][0]); P.rho_i = make_float2(rho[0][1], rho[1][1]);
-      P.sig_r = make_float2(sg[0][0], sg[1][0]); P.sig_i = make_float2(sg[0][1], sg[1][1]);
       constexpr int dss = ds < 0 ? 0 : ds;
-      S.tau_h = th[dss]; S.tau_l = tl[dss];
-      S.rho_r = rho[dss][0]; S.rho_i = rho[dss][1];
-      S.sig_r = sg[dss][0]; S.sig_i = sg[dss][1];
+      __syncwarp();  // the previous walker's last reads of wc are done
+      if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < kNBasis / 2; ++q) wc[q] = make_float4(dh[2 * q], dh[2 * q + 1], dl[2 * q], dl[2 * q + 1]);
+        wc[5] = make_float4(th[0], th[1], tl[0], tl[1]);
+        wc[6] = make_float4(rho[0][0], rho[1][0], rho[0][1], rho[1][1]);
+        wc[7] = make_float4(sg[0][0], sg[1][0], sg[0][1], sg[1][1]);
+        wc[8] = make_float4(th[dss], tl[dss], 0.f, 0.f);
+        wc[9] = make_float4(rho[dss][0], rho[dss][1], sg[dss][0], sg[dss][1]);
+      }
+      __syncwarp();
     }
     if (!valid) {
       if (MALA) {
@@ -330,7 +364,8 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
 #pragma unroll
         for (int q = 0; q < kNBasis / 2; ++q) {
           const float4 g = g4[q * Ep + ee];  // {g_hi[2q], g_hi[2q+1], g_lo[2q], g_lo[2q+1]}
-          pv::fma_acc(dch[q], dcl[q], make_float2(g.x, g.y), make_float2(g.z, g.w), sh, sl);
+          const float4 c = lds4(wc + q);     // {dc_hi[2q], dc_hi[2q+1], dc_lo[2q], dc_lo[2q+1]}
+          pv::fma_acc(make_float2(c.x, c.y), make_float2(c.z, c.w), make_float2(g.x, g.y), make_float2(g.z, g.w), sh, sl);
         }
         xh = __fadd_rn(sh.x, sh.y);  // two-sum of the high parts
         const float bb = __fsub_rn(xh, sh.x);
@@ -348,10 +383,14 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
 
       float adj_x = 0.f;
       if constexpr (paired) {
+        const float4 rr = lds4(wc + 6), ss = lds4(wc + 7);
+        P.rho_r = make_float2(rr.x, rr.y); P.rho_i = make_float2(rr.z, rr.w);
+        P.sig_r = make_float2(ss.x, ss.y); P.sig_i = make_float2(ss.z, ss.w);
         float2 y;
         if (!PHASE64) {
+          const float4 tt = lds4(wc + 5);
           float2 yh = make_float2(xh, xh), yl = make_float2(xl, xl);
-          pv::fma_acc(P.tau_h, P.tau_l, make_float2(fe, fe), make_float2(fe_lo, fe_lo), yh, yl);
+          pv::fma_acc(make_float2(tt.x, tt.y), make_float2(tt.z, tt.w), make_float2(fe, fe), make_float2(fe_lo, fe_lo), yh, yl);
           y = pv::frac(yh, yl);
         } else {
           const double x0 = ::fma(f64[ee], tau64[0], x64), x1 = ::fma(f64[ee], tau64[1], x64);
@@ -364,10 +403,13 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
         adj_x = __fadd_rn(g.x, g.y);
       }
       if constexpr (ds >= 0) {
+        const float4 rs = lds4(wc + 9);
+        S.rho_r = rs.x; S.rho_i = rs.y; S.sig_r = rs.z; S.sig_i = rs.w;
         float y;
         if (!PHASE64) {
+          const float4 tt = lds4(wc + 8);
           float yh = xh, yl = xl;
-          pv::fma_acc(S.tau_h, S.tau_l, fe, fe_lo, yh, yl);
+          pv::fma_acc(tt.x, tt.y, fe, fe_lo, yh, yl);
           y = pv::frac(yh, yl);
         } else {
           const double xd = ::fma(f64[ee], tau64[ds], x64);
@@ -422,6 +464,14 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
         at[ds] = two_pi * warp_sum_f32(S.adj_tau);
         ar[ds][0] = warp_sum_f32(S.adj_rr);
         ar[ds][1] = warp_sum_f32(S.adj_ri);
+      }
+      float rho[kMaxDet][2];
+      {
+        const float4 r01 = lds4(wc + 6), rs = lds4(wc + 9);
+        rho[0][0] = r01.x; rho[1][0] = r01.y; rho[0][1] = r01.z; rho[1][1] = r01.w;
+        constexpr int dss = ds < 0 ? 0 : ds;
+        if (ds >= 0) { rho[dss][0] = rs.x; rho[dss][1] = rs.y; }
+        if (D < kMaxDet) rho[kMaxDet - 1][0] = rho[kMaxDet - 1][1] = 0.f;
       }
       double g = 0.0;
       if (lane < kNPar) {
@@ -569,8 +619,9 @@ __global__ void __launch_bounds__(256) k_rb_f64(LaunchArgs a) {
 // Launchers
 // ---------------------------------------------------------------------------
 size_t mixed_smem_bytes(const EventDev& ev, bool phase64) {
-  if (!phase64) return ev.tab32_floats * sizeof(float);
-  return (size_t)(kNBasis + 1) * ev.e_pad * sizeof(double) + (ev.tab32_floats - ev.edge32_floats) * sizeof(float);
+  const size_t wc = (size_t)(kThreads / 32) * kWcQuads * sizeof(float4);
+  if (!phase64) return ev.tab32_floats * sizeof(float) + wc;
+  return (size_t)(kNBasis + 1) * ev.e_pad * sizeof(double) + (ev.tab32_floats - ev.edge32_floats) * sizeof(float) + wc;
 }
 
 // Occupancy per (kernel, shared-memory size), cached in a fixed table (no

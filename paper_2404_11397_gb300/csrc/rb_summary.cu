@@ -579,17 +579,14 @@ __device__ __forceinline__ float scaled_float(double x, unsigned bias) {
 // from this record and the offset factor from a 32-entry table per block.
 constexpr int kRec = 32;
 
-// X_n = sum_k (c_k / 2pi) Q_kn (float-pair dot products) for 32 chunks per
-// block: warp 0 forms orders 0 and 1 and the per-detector chunk factors,
-// warp 1 order 2 and the amplitude series, warp 2 orders 3..8.  Each lane
-// reads its chunk's matrix row with 16-byte loads issued before use.
-__global__ void __launch_bounds__(96) k_chunk_coef(const RefValues* __restrict__ ref, const float* __restrict__ q,
-                                                   int D, int n_chunks, float* __restrict__ out) {
-  const int c = blockIdx.x * 32 + (threadIdx.x & 31);
-  const int task = threadIdx.x >> 5;
-  if (c >= n_chunks) return;
-  const float4* row = reinterpret_cast<const float4*>(q + (size_t)c * kQRow);
-  float* rec = out + (size_t)c * kRec;
+// The record of one chunk from its Taylor matrix row and the float-float
+// reference values: X_n = sum_k (c_k / 2pi) Q_kn by float-pair dot products.
+// task 0 forms orders 0 and 1 and the per-detector chunk factors, task 1
+// order 2 and the amplitude series, task 2 orders 3..8; each reads its part
+// of the 512-byte row with 16-byte loads issued before use.  rec: kRec floats,
+// 16-byte aligned.
+__device__ __forceinline__ void chunk_record(const RefValues* __restrict__ ref, const float4* __restrict__ row, int D,
+                                             int task, float* __restrict__ rec) {
   if (task == 0) {
     float4 m[kNBasis];
 #pragma unroll
@@ -731,9 +728,11 @@ constexpr int kPartRecs = kPartPoints / kChunk + 1;  // chunk records a part can
 static_assert(kPartPoints % kSumFastThreads == 0, "parts are whole rounds of the block");
 
 // One block per part of a bin (at most kPartPoints grid points), all
-// detectors, reading the FP32 data copy (w = d'/S', 1/S').  The part's chunk
-// records are staged in shared memory; each thread evaluates every 128th
-// point, with the next point's data loads in flight while the current one is
+// detectors, reading the FP32 data copy (w = d'/S', 1/S').  The records of
+// the part's chunks are formed in shared memory from the event's chunk
+// matrices and the reference values (three threads per chunk, while the
+// first data loads are in flight); each thread evaluates every 128th point,
+// with the next point's data loads in flight while the current one is
 // evaluated.  Per point: the
 // intrinsic fiducial phase from the chunk's Taylor coefficients, one
 // sine/cosine, the detector factors exp(2 pi i f_c tau_d) (record) and
@@ -744,7 +743,7 @@ static_assert(kPartPoints % kSumFastThreads == 0, "parts are whole rounds of the
 template <int ND>
 __global__ void __launch_bounds__(kSumFastThreads, 6)
     k_summary_fast(const float2* __restrict__ w32, const float* __restrict__ is32, const int* __restrict__ exps,
-                   int N, const float* __restrict__ chunks, double T, float invT_hi, float invT_lo, int B, int D,
+                   int N, const float* __restrict__ q, double T, float invT_hi, float invT_lo, int B, int D,
                    const int64_t* __restrict__ edges, const RefValues* __restrict__ ref, SummaryOut so, int p_off) {
   __shared__ __align__(16) float srec[kPartRecs * kRec];
   // exp(2 pi i j df tau_d), indexed by k mod 32: detectors 0 and 1 as
@@ -814,10 +813,11 @@ __global__ void __launch_bounds__(kSumFastThreads, 6)
   int k = ks + tid;
   if (k < ke) load_point(k, dn, pn);  // in flight across the staging below
   const int c0 = ks >> 5, nrec = ((ke - 1) >> 5) - c0 + 1;
-  {
-    const float4* src = reinterpret_cast<const float4*>(chunks + (size_t)c0 * kRec);
-    float4* dst = reinterpret_cast<float4*>(srec);
-    for (int i = tid; i < nrec * (kRec / 4); i += kSumFastThreads) dst[RB_IDX(i, kPartRecs * kRec / 4, 204)] = __ldg(src + i);
+  if (tid < 3 * kPartRecs) {
+    const int r = tid % kPartRecs, task = tid / kPartRecs;
+    if (r < nrec)
+      chunk_record(ref, reinterpret_cast<const float4*>(q + (size_t)(c0 + r) * kQRow), D, task,
+                   srec + RB_IDX(r, kPartRecs, 204) * kRec);
   }
   __syncthreads();
   for (; k < ke; k += kSumFastThreads) {
@@ -1011,30 +1011,21 @@ cudaError_t launch_chunk_q(int64_t kmin, double T, int64_t N, void* cq, cudaStre
   return cudaGetLastError();
 }
 
-size_t chunk_coef_bytes(int64_t N) { return sizeof(float) * kRec * (size_t)n_chunks_of(N); }
-
 cudaError_t launch_data32(const DataPtrs& in, int64_t N, int D, void* w32, float* is32, int* exps, cudaStream_t s) {
   dim3 grid((unsigned)((N + 255) / 256), (unsigned)D);
   k_data32<<<grid, 256, 0, s>>>(in, N, D, static_cast<float2*>(w32), is32, exps);
   return cudaGetLastError();
 }
 
-cudaError_t launch_chunk_coef(int64_t N, int D, const RefValues* ref, const void* cq, void* chunk_coef, cudaStream_t s) {
-  const int nc = (int)n_chunks_of(N);
-  k_chunk_coef<<<(unsigned)((nc + 31) / 32), 96, 0, s>>>(ref, static_cast<const float*>(cq), D, nc,
-                                                        static_cast<float*>(chunk_coef));
-  return cudaGetLastError();
-}
-
 cudaError_t launch_summary_parts(const void* w32, const float* is32, const int* exps, int64_t N, double T, int D, int B,
-                                 const int64_t* edges, const RefValues* ref, const void* chunk_coef,
+                                 const int64_t* edges, const RefValues* ref, const void* chunk_q,
                                  const SummaryOut& so, int p0, int p1, cudaStream_t s) {
   if (p0 < 0 || p1 <= p0) return cudaErrorInvalidValue;
   const double invT = 1.0 / T;
   const float ih = (float)invT, il = (float)(invT - (double)ih);
   auto kf = D == 1 ? k_summary_fast<1> : D == 2 ? k_summary_fast<2> : k_summary_fast<3>;
   kf<<<(unsigned)(p1 - p0), kSumFastThreads, 0, s>>>(static_cast<const float2*>(w32), is32, exps, (int)N,
-                                                      static_cast<const float*>(chunk_coef), T, ih, il, B, D, edges,
+                                                      static_cast<const float*>(chunk_q), T, ih, il, B, D, edges,
                                                       ref, so, p0);
   return cudaGetLastError();
 }
