@@ -13,6 +13,11 @@
 // alpha0 = A0/2, alpha1 = A1/df_b, beta0 = B0/2, beta1 = B1/df_b and the FP64
 // constant base = sum_d (Re sum_b A0 - sum_b B0/2) = log L(theta_ref).  At the
 // fiducial point delta = 0 exactly and the result is base, bit for bit.
+// With the Newtonian amplitude the ratio has the same modulus |rho_d| at every
+// edge, so Re(r0 r1*) = (|r_{b+1}|^2 - |r_b|^2) / (2 df_b) = 0: the beta1 term
+// (Re t + Re(s t*)/2 = (|1 + delta_{b+1}|^2 - |1 + delta_b|^2) / 2) and its
+// derivatives vanish identically.  The mixed kernel leaves it out (in FP32 it
+// is rounding noise about zero); the plain FP64 kernel keeps the general form.
 // delta is formed without cancellation from the half angle:
 //   exp(-2 pi i x) - 1 = -2 sin^2(pi x) - 2 i sin(pi x) cos(pi x),
 //   delta = rho (exp(-2 pi i x) - 1) + (rho - 1).
@@ -159,25 +164,24 @@ __device__ __forceinline__ V det_edge(V y, DetState<V>& st, const V* bt, bool ha
   const V nr = shfl_down(dr), ni = shfl_down(di);
   V Ur = splat<V>(0.f), Ui = Ur, Vr = Ur, Vi = Ur;
   if (has_bin) {
-    // bt: alpha0 (re, im), alpha1 (re, im), -beta0, -beta1
+    // bt: alpha0 (re, im), alpha1 (re, im), -beta0 (the -beta1 entry is not
+    // needed: the beta1 term vanishes for a ratio of constant modulus)
     const V sr = add(dr, nr), si = add(di, ni), tr = sub(nr, dr), ti = sub(ni, di);
     V v = mul(bt[0], sr);
     v = fma(bt[1], si, v);
     v = fma(bt[2], tr, v);
     v = fma(bt[3], ti, v);
     v = fma(bt[4], fma(splat<V>(0.25f), fma(sr, sr, mul(si, si)), sr), v);
-    v = fma(bt[5], fma(splat<V>(0.5f), fma(sr, tr, mul(si, ti)), tr), v);
     const V s = add(st.acc, v);  // two-sum into (acc, acc_lo)
     const V bb = sub(s, st.acc);
     st.acc_lo = add(st.acc_lo, add(sub(st.acc, sub(s, bb)), sub(v, bb)));
     st.acc = s;
     if (GRAD) {
       const V hs_r = fma(splat<V>(0.5f), sr, splat<V>(1.f)), hs_i = mul(splat<V>(0.5f), si);  // 1 + s/2
-      const V hb1 = mul(splat<V>(0.5f), bt[5]);
-      Ur = fma(bt[4], hs_r, fma(hb1, tr, bt[0]));
-      Ui = fma(bt[4], hs_i, fma(hb1, ti, bt[1]));
-      Vr = fma(bt[5], hs_r, bt[2]);
-      Vi = fma(bt[5], hs_i, bt[3]);
+      Ur = fma(bt[4], hs_r, bt[0]);
+      Ui = fma(bt[4], hs_i, bt[1]);
+      Vr = bt[2];
+      Vi = bt[3];
     }
   }
   V dldx = splat<V>(0.f);
