@@ -30,6 +30,8 @@ cudaError_t launch_rb_f64(const EventDev& ev, const void* ws, const void* tan, i
 cudaError_t launch_bin_edges(double f_low, double f_high, double T, int64_t kmin, int64_t N, int B, int64_t* edges,
                              double* span, cudaStream_t s);
 size_t bin_edges_agnostic_scratch_bytes(int64_t N);
+size_t chunk_coef_bytes(int64_t N);
+cudaError_t launch_chunk_coef(int64_t N, int D, const RefValues* ref, const void* cq, void* chunk_coef, cudaStream_t s);
 cudaError_t launch_bin_edges_agnostic(const double* theta_ref_dev, double T, int64_t kmin, int64_t N, int B,
                                       int64_t* edges, double* span, void* scratch, cudaStream_t s);
 cudaError_t launch_summary(const DataPtrs& in, int64_t kmin, int64_t N, double T, int D, int B,
@@ -43,7 +45,7 @@ cudaError_t launch_chunk_q(int64_t kmin, double T, int64_t N, void* cq, cudaStre
 size_t chunk_q_bytes(int64_t N);
 cudaError_t launch_strain(const RefValues* src, int64_t kmin, int64_t N, double T, double* h, cudaStream_t s);
 cudaError_t launch_summary_parts(const void* w32, const float* is32, const int* exps, int64_t N, double T, int D, int B,
-                                 const int64_t* edges, const RefValues* ref, const void* chunk_q,
+                                 const int64_t* edges, const RefValues* ref, const void* chunk_q, const void* recs,
                                  const SummaryOut& so, int p0, int p1, cudaStream_t s);
 cudaError_t launch_ref_dd(const double* theta_ref_dev, const EventConst& ec, RefValues* out, cudaStream_t s);
 cudaError_t launch_tangents(const double* theta, int64_t W, const EventConst& ec, void* tan, cudaStream_t s);
@@ -276,6 +278,7 @@ int rb_event_free(rb_event_t ev) {
   cudaFree(e.d_psd);
   cudaFree(e.d_theta_ref);
   cudaFree(e.d_chunkq);
+  cudaFree(e.d_chunks);
   cudaFree(e.d_invdf);
   cudaFree(e.d_share);
   cudaFree(e.step_ws);
@@ -391,6 +394,7 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
         {(void**)&e.d_h0, sizeof(double) * 2 * D * N, "stored fiducial waveform"},
         {(void**)&e.d_theta_ref, sizeof(double) * kNPar, "theta_ref"},
         {(void**)&e.d_chunkq, chunk_q_bytes(N), "chunk matrices"},
+        {(void**)&e.d_chunks, chunk_coef_bytes(N), "chunk records"},
         {(void**)&e.d_invdf, sizeof(double) * B, "bin widths"},
         {(void**)&e.d_share, sizeof(double) * D * B, "base shares"},
         {(void**)&e.d_sync, offsetof(SummarySync, bin_parts_done) + sizeof(unsigned) * B, "build counters"},
@@ -915,8 +919,16 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
       ++launches;
     }
     e.w32_current = true;
+    // with the walkers' set-up on the forked stream (rebuild + batch), the
+    // chunk records are a launch of their own that overlaps the set-up;
+    // otherwise the summary kernel forms them in-block
+    if (ss) {
+      if ((err = launch_chunk_coef(e.N, e.n_det, e.d_ref, e.d_chunkq, e.d_chunks, s)) != cudaSuccess)
+        return cuda_fail(err, "chunk record kernel");
+      ++launches;
+    }
     err = launch_summary_parts(e.d_w32, e.d_is32, e.d_wexp, e.N, e.T, e.n_det, e.n_bins, e.d_edges, e.d_ref,
-                               e.d_chunkq, e.out(), 0, e.n_parts, s);
+                               e.d_chunkq, ss ? e.d_chunks : nullptr, e.out(), 0, e.n_parts, s);
   } else if (e.h0_valid) {
     // FP64 sums from the fiducial waveform stored by the last inline build
     // for this theta_ref: strain, PSD and h0 streamed, no waveform arithmetic

@@ -45,6 +45,7 @@ struct EventEntry {
   bool h0_valid = false;      // d_h0 holds h0 for the current theta_ref
   double* d_theta_ref = nullptr;
   void* d_chunkq = nullptr;   // event-constant per-chunk Taylor matrices (fast summary build)
+  void* d_chunks = nullptr;   // per-rebuild chunk records (rebuild + batch step)
   double* d_invdf = nullptr;  // [B] 1 / bin width
   double* d_share = nullptr;  // [D][B] per-bin shares of log L(theta_ref)
   SummarySync* d_sync = nullptr;  // build counters (zero between builds)

@@ -641,6 +641,18 @@ __device__ __forceinline__ void chunk_record(const RefValues* __restrict__ ref, 
   }
 }
 
+// The chunk records of all chunks, to global memory (32 chunks per block,
+// one task per warp).  The rebuild + batch step launches this ahead of the
+// summary sums, where it overlaps the walkers' set-up on the other stream;
+// a rebuild on its own forms the records inside the summary kernel instead.
+__global__ void __launch_bounds__(96) k_chunk_coef(const RefValues* __restrict__ ref, const float* __restrict__ q,
+                                                   int D, int n_chunks, float* __restrict__ out) {
+  const int c = blockIdx.x * 32 + (threadIdx.x & 31);
+  if (c >= n_chunks) return;
+  chunk_record(ref, reinterpret_cast<const float4*>(q + (size_t)c * kQRow), D, threadIdx.x >> 5,
+               out + (size_t)c * kRec);
+}
+
 // Integer -> float on the FMA pipe (exact for |i| < 2^22; larger |i| < 2^31
 // are split in two parts and rounded once).
 __device__ __forceinline__ float int_float_fma(int i) {
@@ -729,18 +741,19 @@ static_assert(kPartPoints % kSumFastThreads == 0, "parts are whole rounds of the
 
 // One block per part of a bin (at most kPartPoints grid points), all
 // detectors, reading the FP32 data copy (w = d'/S', 1/S').  The records of
-// the part's chunks are formed in shared memory from the event's chunk
-// matrices and the reference values (three threads per chunk, while the
-// first data loads are in flight); each thread evaluates every 128th point,
-// with the next point's data loads in flight while the current one is
-// evaluated.  Per point: the
+// the part's chunks go to shared memory: with INBLOCK formed there from the
+// event's chunk matrices q and the reference values (three threads per
+// chunk, while the first data loads are in flight), otherwise copied from
+// the records k_chunk_coef wrote (q then points to them).  Each thread
+// evaluates every 128th point, with the next point's data loads in flight
+// while the current one is evaluated.  Per point: the
 // intrinsic fiducial phase from the chunk's Taylor coefficients, one
 // sine/cosine, the detector factors exp(2 pi i f_c tau_d) (record) and
 // exp(2 pi i j df tau_d) (block table).  Per-thread sums are FP32 (B1, which
 // nearly cancels within a bin, a float pair); block sums are float pairs in a
 // fixed order; the parts of a bin are added in index order by the last of
 // them to finish, which then runs the FP64 epilogue.
-template <int ND>
+template <int ND, bool INBLOCK>
 __global__ void __launch_bounds__(kSumFastThreads, 6)
     k_summary_fast(const float2* __restrict__ w32, const float* __restrict__ is32, const int* __restrict__ exps,
                    int N, const float* __restrict__ q, double T, float invT_hi, float invT_lo, int B, int D,
@@ -813,11 +826,17 @@ __global__ void __launch_bounds__(kSumFastThreads, 6)
   int k = ks + tid;
   if (k < ke) load_point(k, dn, pn);  // in flight across the staging below
   const int c0 = ks >> 5, nrec = ((ke - 1) >> 5) - c0 + 1;
-  if (tid < 3 * kPartRecs) {
-    const int r = tid % kPartRecs, task = tid / kPartRecs;
-    if (r < nrec)
-      chunk_record(ref, reinterpret_cast<const float4*>(q + (size_t)(c0 + r) * kQRow), D, task,
-                   srec + RB_IDX(r, kPartRecs, 204) * kRec);
+  if (INBLOCK) {
+    if (tid < 3 * kPartRecs) {
+      const int r = tid % kPartRecs, task = tid / kPartRecs;
+      if (r < nrec)
+        chunk_record(ref, reinterpret_cast<const float4*>(q + (size_t)(c0 + r) * kQRow), D, task,
+                     srec + RB_IDX(r, kPartRecs, 204) * kRec);
+    }
+  } else {
+    const float4* src = reinterpret_cast<const float4*>(q + (size_t)c0 * kRec);
+    float4* dst = reinterpret_cast<float4*>(srec);
+    for (int i = tid; i < nrec * (kRec / 4); i += kSumFastThreads) dst[RB_IDX(i, kPartRecs * kRec / 4, 204)] = __ldg(src + i);
   }
   __syncthreads();
   for (; k < ke; k += kSumFastThreads) {
@@ -1003,6 +1022,14 @@ static TaylorTables make_taylor_tables() {
 
 int64_t n_chunks_of(int64_t N) { return (N + kChunk - 1) / kChunk; }
 size_t chunk_q_bytes(int64_t N) { return sizeof(float) * 128 * (size_t)n_chunks_of(N); }
+size_t chunk_coef_bytes(int64_t N) { return sizeof(float) * kRec * (size_t)n_chunks_of(N); }
+
+cudaError_t launch_chunk_coef(int64_t N, int D, const RefValues* ref, const void* cq, void* chunk_coef, cudaStream_t s) {
+  const int nc = (int)n_chunks_of(N);
+  k_chunk_coef<<<(unsigned)((nc + 31) / 32), 96, 0, s>>>(ref, static_cast<const float*>(cq), D, nc,
+                                                        static_cast<float*>(chunk_coef));
+  return cudaGetLastError();
+}
 
 cudaError_t launch_chunk_q(int64_t kmin, double T, int64_t N, void* cq, cudaStream_t s) {
   static const TaylorTables tt = make_taylor_tables();
@@ -1017,16 +1044,20 @@ cudaError_t launch_data32(const DataPtrs& in, int64_t N, int D, void* w32, float
   return cudaGetLastError();
 }
 
+// recs: the chunk records k_chunk_coef wrote, or NULL to form them in-block
+// from the chunk matrices chunk_q.
 cudaError_t launch_summary_parts(const void* w32, const float* is32, const int* exps, int64_t N, double T, int D, int B,
-                                 const int64_t* edges, const RefValues* ref, const void* chunk_q,
+                                 const int64_t* edges, const RefValues* ref, const void* chunk_q, const void* recs,
                                  const SummaryOut& so, int p0, int p1, cudaStream_t s) {
   if (p0 < 0 || p1 <= p0) return cudaErrorInvalidValue;
   const double invT = 1.0 / T;
   const float ih = (float)invT, il = (float)(invT - (double)ih);
-  auto kf = D == 1 ? k_summary_fast<1> : D == 2 ? k_summary_fast<2> : k_summary_fast<3>;
+  const bool inblock = recs == nullptr;
+  auto kf = inblock ? (D == 1 ? k_summary_fast<1, true> : D == 2 ? k_summary_fast<2, true> : k_summary_fast<3, true>)
+                    : (D == 1 ? k_summary_fast<1, false> : D == 2 ? k_summary_fast<2, false> : k_summary_fast<3, false>);
   kf<<<(unsigned)(p1 - p0), kSumFastThreads, 0, s>>>(static_cast<const float2*>(w32), is32, exps, (int)N,
-                                                      static_cast<const float*>(chunk_q), T, ih, il, B, D, edges,
-                                                      ref, so, p0);
+                                                      static_cast<const float*>(inblock ? chunk_q : recs), T, ih, il, B,
+                                                      D, edges, ref, so, p0);
   return cudaGetLastError();
 }
 
