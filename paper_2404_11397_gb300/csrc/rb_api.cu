@@ -31,6 +31,7 @@ cudaError_t launch_bin_edges(double f_low, double f_high, double T, int64_t kmin
                              double* span, cudaStream_t s);
 size_t bin_edges_agnostic_scratch_bytes(int64_t N);
 size_t chunk_coef_bytes(int64_t N);
+size_t mixed_smem_slot_bytes();
 cudaError_t launch_chunk_coef(int64_t N, int D, const RefValues* ref, const void* cq, void* chunk_coef, cudaStream_t s);
 cudaError_t launch_bin_edges_agnostic(const double* theta_ref_dev, double T, int64_t kmin, int64_t N, int B,
                                       int64_t* edges, double* span, void* scratch, cudaStream_t s);
@@ -368,8 +369,10 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
       delete ev;
       return cuda_fail(qerr, "rb_build_summary: device query");
     }
+    // (plus the per-warp walker slots of the mixed kernel)
     const size_t need = std::max(tab32 * sizeof(float), (size_t)(kNBasis + 1) * Ep * sizeof(double) +
-                                                            (size_t)D * 6 * Bp * sizeof(float));
+                                                            (size_t)D * 6 * Bp * sizeof(float)) +
+                        mixed_smem_slot_bytes();
     if (need > (size_t)smem_max) {
       delete ev;
       return set_error(RB_EINVAL, "rb_build_summary: %d bins x %d detectors need %zu B of shared memory (max %d)",

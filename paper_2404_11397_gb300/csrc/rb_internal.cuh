@@ -111,15 +111,27 @@ struct RefValues {
   double K[kMaxDet][2];     // A_ref P_d: h0_d = K_d f^-7/6 exp(-2 pi i x_d(f))
 };
 
-// Per-walker set-up output for the mixed (float-float) path.
-struct WalkerMixed {
-  float dc_hi[kNBasis], dc_lo[kNBasis];  // c_k - c_k,ref as float pairs
-  float tau_hi[kMaxDet], tau_lo[kMaxDet];  // tau_d - tau_d,ref [s] as float pairs
-  float rho[kMaxDet][2];   // C_d(theta) / C_d(theta_ref)
-  float sig[kMaxDet][2];   // rho - 1, computed as (Q - Q_ref) / Q_ref
+// Per-walker set-up output for the mixed (float-float) path, laid out as the
+// likelihood kernel's per-warp constants so that it is copied to shared
+// memory as it is.  dc = c_k - c_k,ref and tau_d - tau_d,ref [s] as float
+// pairs (hi, lo); rho_d = C_d(theta) / C_d(theta_ref), sig_d = rho_d - 1
+// computed as (Q - Q_ref) / Q_ref (complex: r, i).  Detectors 0 and 1 side
+// by side; detector s = D - 1 alone when the detector count D is odd:
+//   q[0..4] {dc_hi[2k], dc_hi[2k+1], dc_lo[2k], dc_lo[2k+1]}
+//   q[5] {tau_hi0, tau_hi1, tau_lo0, tau_lo1}
+//   q[6] {rho_r0, rho_r1, rho_i0, rho_i1}    q[7] {sig_r0, sig_r1, sig_i0, sig_i1}
+//   q[8] {tau_hi_s, tau_lo_s, 0, 0}          q[9] {rho_r_s, rho_i_s, sig_r_s, sig_i_s}
+// (detector slots beyond D, and q[8], q[9] when D is even, are zero).
+constexpr int kWalkerQuads = 10;
+struct __align__(16) WalkerMixed {
+  float4 q[kWalkerQuads];
   int valid;
   int pad[3];
 };
+// float offsets into WalkerMixed::q
+__host__ __device__ constexpr int wm_dc_hi(int k) { return 4 * (k >> 1) + (k & 1); }
+__host__ __device__ constexpr int wm_dc_lo(int k) { return 4 * (k >> 1) + 2 + (k & 1); }
+constexpr int kWmTauPair = 20, kWmRhoPair = 24, kWmSigPair = 28, kWmSingle = 32;
 
 // Per-walker set-up output for the FP64 and FP64-phase paths.
 struct WalkerF64 {

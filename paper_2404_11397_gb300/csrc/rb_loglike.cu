@@ -43,14 +43,10 @@ namespace rb {
 #endif
 constexpr int kThreads = RB_MIXED_THREADS;  // threads per block of the mixed likelihood kernel
 constexpr unsigned kFull = 0xffffffffu;
-// Per-warp copy of the current walker's constants in shared memory (read by
-// broadcast loads in every chunk instead of held in registers), as float4:
-//   [0..4] {dc_hi[2q], dc_hi[2q+1], dc_lo[2q], dc_lo[2q+1]}
-//   [5] {tau_hi0, tau_hi1, tau_lo0, tau_lo1}   detectors 0, 1
-//   [6] {rho_r0, rho_r1, rho_i0, rho_i1}       [7] {sig_r0, sig_r1, sig_i0, sig_i1}
-//   [8] {tau_hi, tau_lo, 0, 0}                  detector D-1 when D is odd
-//   [9] {rho_r, rho_i, sig_r, sig_i}
-constexpr int kWcQuads = 10;
+// The current walker's constants sit in shared memory (read by broadcast
+// loads in every chunk instead of held in registers), as the set-up wrote
+// them (WalkerMixed: float4 quads, detectors 0 and 1 paired, detector D - 1
+// alone when D is odd).
 
 // Shared-memory load that the compiler may not hoist out of a loop.
 __device__ __forceinline__ float4 lds4(const float4* p) {
@@ -59,6 +55,72 @@ __device__ __forceinline__ float4 lds4(const float4* p) {
                : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
                : "r"((unsigned)__cvta_generic_to_shared(p)));
   return v;
+}
+
+// Asynchronous global -> shared copies (cp.async): the copies of a thread
+// complete, in issue order, by its next cp_async_wait_all().
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem)), "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(smem)), "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Per-warp shared-memory slot after the tables: two buffers for a walker's
+// set-up record (its constants, WalkerMixed) and tangents, so that the next
+// walker's are fetched while this one runs.
+constexpr int kTanBytes = 384;
+struct __align__(16) WarpSlot {
+  WalkerMixed rec[2];
+  unsigned char tan[2][kTanBytes];
+};
+static_assert(sizeof(WalkerMixed) % 16 == 0, "record copied in 16-byte pieces");
+static_assert(sizeof(WalkerTan<float>) <= kTanBytes && sizeof(WalkerTan<float>) % 8 == 0, "tangent buffer");
+
+// Issue (the whole warp) the copies of one walker's record (unless PHASE64,
+// whose FP64 record is read directly) and tangents into buffer buf, as one
+// cp.async group.  Global addresses: records 16-byte, tangents 8-byte
+// aligned (checked by the launcher).
+template <bool GRAD, bool PHASE64>
+__device__ __forceinline__ void prefetch_walker(WarpSlot* slot, int buf, const void* rec, const void* tan, int lane) {
+  if (!PHASE64 && lane < (int)(sizeof(WalkerMixed) / 16))
+    cp_async16(reinterpret_cast<unsigned char*>(&slot->rec[buf]) + 16 * lane, static_cast<const unsigned char*>(rec) + 16 * lane);
+  if (GRAD) {
+    constexpr int n = (int)(sizeof(WalkerTan<float>) / 8);
+#pragma unroll
+    for (int i = lane; i < n; i += 32) cp_async8(slot->tan[buf] + 8 * i, static_cast<const unsigned char*>(tan) + 8 * i);
+  }
+  cp_async_commit();
+}
+
+// Float-pair warp sum: (h, l) on entry is a lane's value as an unevaluated
+// sum; every lane returns the warp total (two-sum of the high parts, the low
+// parts added, renormalised at each step), all on the FP32 pipe.
+__device__ __forceinline__ void warp_sum_ff(float& h, float& l) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+    const float s = __fadd_rn(h, oh);
+    const float bb = __fsub_rn(s, h);
+    const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(oh, bb));
+    const float lo = __fadd_rn(__fadd_rn(l, ol), e);
+    h = __fadd_rn(s, lo);
+    l = __fsub_rn(lo, __fsub_rn(h, s));
+  }
+}
+
+// Adds the float pair (bh, bl) to (h, l) (two-sum of the high parts).
+__device__ __forceinline__ void ff_add(float& h, float& l, float bh, float bl) {
+  const float s = __fadd_rn(h, bh);
+  const float bb = __fsub_rn(s, h);
+  const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+  const float lo = __fadd_rn(__fadd_rn(l, bl), e);
+  h = __fadd_rn(s, lo);
+  l = __fsub_rn(lo, __fsub_rn(h, s));
 }
 
 struct LaunchArgs {
@@ -135,6 +197,43 @@ __device__ __forceinline__ double chain_rule(int j, int n_det, const T* adj_c, c
     g += Gr * lr - Gi * li;
   }
   return (double)g;
+}
+
+// The same chain rule for the mixed kernel, with the tangents in shared
+// memory: every lane runs one instruction stream (the lane's tangent entries
+// picked by index and select, no divergent branches).
+template <int D>
+__device__ __forceinline__ float chain_rule_lanes(int j, const float* adj_c, const float* adj_tau,
+                                                  const float (*adj_rho)[2], const float (*rho)[2],
+                                                  const WalkerTan<float>& tn) {
+  const float* t = reinterpret_cast<const float*>(&tn);
+  constexpr int oDc = offsetof(WalkerTan<float>, dc) / 4, oPhi = offsetof(WalkerTan<float>, dphi0) / 4;
+  constexpr int oDtd = offsetof(WalkerTan<float>, dtd) / 4, oLnP = offsetof(WalkerTan<float>, dlnP) / 4;
+  constexpr int oMc = offsetof(WalkerTan<float>, lnamp_Mc) / 4, oDl = offsetof(WalkerTan<float>, lnamp_dL) / 4;
+  const bool intr = j < kNTanIntr, radec = j == 11 || j == 12, ext = j >= 9;
+  const int ji = intr ? j : 0, jr = radec ? j - 11 : 0, je = ext ? j - 9 : 0;
+  float g = 0.f;
+#pragma unroll
+  for (int k = 0; k < kNBasis; ++k) {
+    const float v = t[oDc + k * kNTanIntr + ji];
+    g = fmaf(adj_c[k], intr ? v : 0.f, g);
+  }
+  // d ln rho_d = lr + i li: ln amplitude (Mc, dL), -dPhi0 (Mc, q), phi_c, antenna (iota, psi, ra, dec)
+  const int ir = j == 0 ? oMc : (j == 6 ? oDl : oMc);
+  const float lr_own = (j == 0 || j == 6) ? t[ir] : 0.f;
+  const int ii = j == 1 ? oPhi + 1 : oPhi;
+  const float li_own = (j == 0 || j == 1) ? -t[ii] : (j == 8 ? 1.f : 0.f);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const float td = t[oDtd + 2 * d + jr];
+    g = fmaf(adj_tau[d], radec ? td : (j == 7 ? 1.f : 0.f), g);
+    const float Gr = adj_rho[d][0] * rho[d][0] + adj_rho[d][1] * rho[d][1];
+    const float Gi = adj_rho[d][0] * rho[d][1] - adj_rho[d][1] * rho[d][0];
+    const float pr = t[oLnP + 8 * d + 2 * je], pi = t[oLnP + 8 * d + 2 * je + 1];
+    const float lr = ext ? pr : lr_own, li = ext ? pi : li_own;
+    g += Gr * lr - Gi * li;
+  }
+  return g;
 }
 
 namespace pv {
@@ -219,7 +318,7 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
   constexpr int D = ND;
   const int Ep = ev.e_pad, Bp = ev.b_pad, B = ev.n_bins, E = ev.n_edges;
 
-  // Stage the tables (16-byte vector copies).
+  // Stage the tables (16-byte asynchronous copies, all in flight at once).
   const float* sbin;
 #ifdef RB_BOUNDS_CHECK
   unsigned smem_bytes;
@@ -237,7 +336,7 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
       const float4* src = reinterpret_cast<const float4*>(ev.tab32);
       float4* dst = reinterpret_cast<float4*>(smem_raw);
       const size_t n4 = ev.tab32_floats / 4;
-      for (size_t i = tid; i < n4; i += blockDim.x) dst[RB_IDX(i, smem16, 104)] = src[i];
+      for (size_t i = tid; i < n4; i += blockDim.x) cp_async16(&dst[RB_IDX(i, smem16, 104)], &src[i]);
       const float* s = reinterpret_cast<const float*>(smem_raw);
       g4 = reinterpret_cast<const float4*>(s);
       sbin = s + ev.edge32_floats;
@@ -245,30 +344,31 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
       const size_t n_e64 = (size_t)(kNBasis + 1) * Ep;  // g[10][Ep], f[Ep]
       const double2* src = reinterpret_cast<const double2*>(ev.tab64);
       double2* dst = reinterpret_cast<double2*>(smem_raw);
-      for (size_t i = tid; i < n_e64 / 2; i += blockDim.x) dst[RB_IDX(i, smem16, 104)] = src[i];
+      for (size_t i = tid; i < n_e64 / 2; i += blockDim.x) cp_async16(&dst[RB_IDX(i, smem16, 104)], &src[i]);
       const size_t nb = ev.tab32_floats - ev.edge32_floats;
       const float4* bsrc = reinterpret_cast<const float4*>(ev.tab32 + ev.edge32_floats);
       float4* bdst = reinterpret_cast<float4*>(smem_raw + n_e64 * sizeof(double));
-      for (size_t i = tid; i < nb / 4; i += blockDim.x) bdst[RB_IDX(i, smem16 - n_e64 / 2, 104)] = bsrc[i];
+      for (size_t i = tid; i < nb / 4; i += blockDim.x) cp_async16(&bdst[RB_IDX(i, smem16 - n_e64 / 2, 104)], &bsrc[i]);
       g64 = reinterpret_cast<const double*>(smem_raw);
       f64 = g64 + (size_t)kNBasis * Ep;
       sbin = reinterpret_cast<const float*>(smem_raw + n_e64 * sizeof(double));
     }
   }
-  __syncthreads();
+  cp_async_commit();
 
   const int lane = threadIdx.x & 31;
-  float4* wc;  // this warp's walker constants, after the tables
+  WarpSlot* slot;  // this warp's slot, after the tables
   {
     const size_t tab_bytes = !PHASE64 ? ev.tab32_floats * sizeof(float)
                                       : (size_t)(kNBasis + 1) * Ep * sizeof(double) +
                                             (ev.tab32_floats - ev.edge32_floats) * sizeof(float);
-    wc = reinterpret_cast<float4*>(smem_raw + tab_bytes) + (threadIdx.x >> 5) * kWcQuads;
+    slot = reinterpret_cast<WarpSlot*>(smem_raw + tab_bytes) + (threadIdx.x >> 5);
   }
   // detectors 0 and 1 form a pair when D >= 2; an odd detector count leaves
   // detector D - 1 single (bin table layout in EventDev)
   constexpr bool paired = D >= 2;
   constexpr int ds = (D & 1) ? D - 1 : -1;
+  constexpr int dss = ds < 0 ? 0 : ds;
   const float4* binP = reinterpret_cast<const float4*>(sbin);                                // [3][Bp]
   const float4* binS4 = reinterpret_cast<const float4*>(sbin + (paired ? 12 * Bp : 0));      // [Bp]
   const float2* binS2 = reinterpret_cast<const float2*>(sbin + (paired ? 12 * Bp : 0) + 4 * Bp);  // [Bp]
@@ -279,59 +379,64 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
   const int64_t w_end = w_begin + per_blk + ((int64_t)blockIdx.x < rem_blk ? 1 : 0);
   const int64_t warp0 = w_begin + (threadIdx.x >> 5);
   const int64_t nwarps = blockDim.x >> 5;
+  const double base_logl = *ev.base_logl;
+  const unsigned char* rec_g = static_cast<const unsigned char*>(a.ws);
+  const unsigned char* tan_g = static_cast<const unsigned char*>(a.tan);
+  // the first walker's record and tangents travel with the tables
+  if (warp0 < w_end)
+    prefetch_walker<GRAD, PHASE64>(slot, 0, PHASE64 ? nullptr : rec_g + sizeof(WalkerMixed) * RB_IDX(warp0, a.W, 101),
+                                   GRAD ? tan_g + sizeof(WalkerTan<float>) * RB_IDX(warp0, a.W, 107) : nullptr, lane);
+  cp_async_wait_all();
+  __syncthreads();
 
-  for (int64_t w = warp0; w < w_end; w += nwarps) {
-    // ---- per-walker constants (uniform across the warp), to shared memory ----
+  int buf = 0;
+  for (int64_t w = warp0; w < w_end; w += nwarps, buf ^= 1) {
+    cp_async_wait_all();  // this walker's record and tangents
+    __syncwarp();         // ... visible to the warp; the previous walker's reads of wc and of buffer buf ^ 1 done
+    // ---- per-walker constants (uniform across the warp), in shared memory ----
+    float4* const wc = slot->rec[buf].q;
     double dc64[kNBasis];
     double tau64[kMaxDet];
     pv::DetState<float2> P;  // detectors 0, 1: accumulators (constants come from wc)
     pv::DetState<float> S;   // detector ds
     int valid;
-    {
-      float th[kMaxDet], tl[kMaxDet], rho[kMaxDet][2], sg[kMaxDet][2];
-      float dh[kNBasis], dl[kNBasis];
-      if (!PHASE64) {
-        const WalkerMixed* s = reinterpret_cast<const WalkerMixed*>(a.ws) + RB_IDX(w, a.W, 101);
-        valid = s->valid;
+    if (!PHASE64) {
+      valid = slot->rec[buf].valid;
 #pragma unroll
-        for (int k = 0; k < kNBasis; ++k) {
-          dh[k] = s->dc_hi[k];
-          dl[k] = s->dc_lo[k];
-        }
+      for (int k = 0; k < kNBasis; ++k) dc64[k] = 0.0;
 #pragma unroll
-        for (int d = 0; d < kMaxDet; ++d) {
-          th[d] = s->tau_hi[d]; tl[d] = s->tau_lo[d];
-          rho[d][0] = s->rho[d][0]; rho[d][1] = s->rho[d][1];
-          sg[d][0] = s->sig[d][0]; sg[d][1] = s->sig[d][1];
-        }
-      } else {
-        const WalkerF64* s = reinterpret_cast<const WalkerF64*>(a.ws) + w;
-        valid = s->valid;
+      for (int d = 0; d < kMaxDet; ++d) tau64[d] = 0.0;
+    } else {
+      float rho[kMaxDet][2], sg[kMaxDet][2];
+      const WalkerF64* s = reinterpret_cast<const WalkerF64*>(a.ws) + w;
+      valid = s->valid;
 #pragma unroll
-        for (int k = 0; k < kNBasis; ++k) {
-          dc64[k] = s->dc[k];
-          dh[k] = dl[k] = 0.f;
-        }
+      for (int k = 0; k < kNBasis; ++k) dc64[k] = s->dc[k];
 #pragma unroll
-        for (int d = 0; d < kMaxDet; ++d) {
-          tau64[d] = s->tau[d];
-          th[d] = tl[d] = 0.f;
-          rho[d][0] = (float)s->rho[d][0]; rho[d][1] = (float)s->rho[d][1];
-          sg[d][0] = (float)s->sig[d][0]; sg[d][1] = (float)s->sig[d][1];
-        }
+      for (int d = 0; d < kMaxDet; ++d) {
+        tau64[d] = s->tau[d];
+        rho[d][0] = (float)s->rho[d][0]; rho[d][1] = (float)s->rho[d][1];
+        sg[d][0] = (float)s->sig[d][0]; sg[d][1] = (float)s->sig[d][1];
       }
-      constexpr int dss = ds < 0 ? 0 : ds;
-      __syncwarp();  // the previous walker's last reads of wc are done
+      __syncwarp();  // the previous walker's reads of this buffer are done
       if (lane == 0) {
+        // the phase and delay quads are not read on this path
 #pragma unroll
-        for (int q = 0; q < kNBasis / 2; ++q) wc[q] = make_float4(dh[2 * q], dh[2 * q + 1], dl[2 * q], dl[2 * q + 1]);
-        wc[5] = make_float4(th[0], th[1], tl[0], tl[1]);
+        for (int q = 0; q < 6; ++q) wc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         wc[6] = make_float4(rho[0][0], rho[1][0], rho[0][1], rho[1][1]);
         wc[7] = make_float4(sg[0][0], sg[1][0], sg[0][1], sg[1][1]);
-        wc[8] = make_float4(th[dss], tl[dss], 0.f, 0.f);
+        wc[8] = make_float4(0.f, 0.f, 0.f, 0.f);
         wc[9] = make_float4(rho[dss][0], rho[dss][1], sg[dss][0], sg[dss][1]);
       }
-      __syncwarp();
+    }
+    __syncwarp();
+    {
+      // the next walker's record and tangents, into the other buffer (issued
+      // after this walker's shared-memory reads above)
+      const int64_t wn = w + nwarps;
+      if (wn < w_end)
+        prefetch_walker<GRAD, PHASE64>(slot, buf ^ 1, PHASE64 ? nullptr : rec_g + sizeof(WalkerMixed) * RB_IDX(wn, a.W, 101),
+                                       GRAD ? tan_g + sizeof(WalkerTan<float>) * RB_IDX(wn, a.W, 107) : nullptr, lane);
     }
     if (!valid) {
       if (MALA) {
@@ -441,10 +546,14 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
       }
     }
 
-    double part = (double)S.acc + (double)S.acc_lo;
-    if constexpr (paired) part += ((double)P.acc.x + (double)P.acc_lo.x) + ((double)P.acc.y + (double)P.acc_lo.y);
-    const double tot = warp_sum_f64(part);
-    const double logl = *ev.base_logl + tot;
+    // the walker's sum as a float pair (FP32 pipe); FP64 only for the result
+    float lh = S.acc, ll = S.acc_lo;
+    if constexpr (paired) {
+      ff_add(lh, ll, P.acc.x, P.acc_lo.x);
+      ff_add(lh, ll, P.acc.y, P.acc_lo.y);
+    }
+    warp_sum_ff(lh, ll);
+    const double logl = base_logl + ((double)lh + (double)ll);
     if (!MALA && lane == 0) a.logl[RB_IDX(w, a.W, 105)] = logl;
     if (GRAD) {
       const float two_pi = 6.28318530717958648f;
@@ -473,14 +582,13 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
       {
         const float4 r01 = lds4(wc + 6), rs = lds4(wc + 9);
         rho[0][0] = r01.x; rho[1][0] = r01.y; rho[0][1] = r01.z; rho[1][1] = r01.w;
-        constexpr int dss = ds < 0 ? 0 : ds;
         if (ds >= 0) { rho[dss][0] = rs.x; rho[dss][1] = rs.y; }
         if (D < kMaxDet) rho[kMaxDet - 1][0] = rho[kMaxDet - 1][1] = 0.f;
       }
       double g = 0.0;
       if (lane < kNPar) {
-        const WalkerTan<float>& tn = reinterpret_cast<const WalkerTan<float>*>(a.tan)[RB_IDX(w, a.W, 107)];
-        g = chain_rule<float>(lane, D, ac, at, ar, rho, tn);
+        const WalkerTan<float>& tn = *reinterpret_cast<const WalkerTan<float>*>(slot->tan[buf]);  // prefetched
+        g = (double)chain_rule_lanes<D>(lane, ac, at, ar, rho, tn);
       }
       if (MALA) mala_finish(a.mala, w, lane, logl, g);
       else if (lane < kNPar) a.grad[RB_IDX(w * kNPar + lane, a.W * kNPar, 106)] = g;
@@ -622,8 +730,10 @@ __global__ void __launch_bounds__(256) k_rb_f64(LaunchArgs a) {
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+size_t mixed_smem_slot_bytes() { return (size_t)(kThreads / 32) * sizeof(WarpSlot); }
+
 size_t mixed_smem_bytes(const EventDev& ev, bool phase64) {
-  const size_t wc = (size_t)(kThreads / 32) * kWcQuads * sizeof(float4);
+  const size_t wc = (size_t)(kThreads / 32) * sizeof(WarpSlot);
   if (!phase64) return ev.tab32_floats * sizeof(float) + wc;
   return (size_t)(kNBasis + 1) * ev.e_pad * sizeof(double) + (ev.tab32_floats - ev.edge32_floats) * sizeof(float) + wc;
 }
@@ -672,6 +782,9 @@ static cudaError_t blocks_per_sm(const void* fn, int threads, size_t smem, int* 
 
 template <int ND, bool GRAD, bool PHASE64, bool MALA>
 static cudaError_t launch_mixed_nd(const LaunchArgs& a, cudaStream_t s, int n_sm) {
+  // the kernel copies records in 16-byte and tangents in 8-byte asynchronous copies
+  if (reinterpret_cast<uintptr_t>(a.ws) % 16 != 0 || (GRAD && reinterpret_cast<uintptr_t>(a.tan) % 8 != 0))
+    return cudaErrorMisalignedAddress;
   const size_t smem = mixed_smem_bytes(a.ev, PHASE64);
   const void* fn = reinterpret_cast<const void*>(k_rb_mixed<ND, GRAD, PHASE64, MALA>);
   int per_sm = 0;

@@ -865,16 +865,28 @@ __global__ void __launch_bounds__(kDdRoleThreads + kTanWarps * 32) k_setup_dd(co
     S.E[0][l] = st2(fx::add(fx::two_sum(1.f, er), ei * t));
     S.E[1][l] = st2(fx::two_sum(ei, -(1.f + er) * t));
   } else if (warp == 4 && mine) {
+    // delays: detectors 0, 1 into their pair slots, detector D - 1 (D odd) alone
+    float* f = reinterpret_cast<float*>(o->q);
+    const int ds = (ec.n_det & 1) ? ec.n_det - 1 : -1;
+    f[kWmSingle] = f[kWmSingle + 1] = f[kWmSingle + 2] = f[kWmSingle + 3] = 0.f;
+    if (ds < 0) f[kWmSingle + 4] = f[kWmSingle + 5] = f[kWmSingle + 6] = f[kWmSingle + 7] = 0.f;
     for (int d = 0; d < kMaxDet; ++d) {
       const dd dt = (d < ec.n_det) ? fx::sub(ld2(S.tau[d][l]), ldp(r.tau[d])) : dd{0.f, 0.f};
-      o->tau_hi[d] = dt.h;
-      o->tau_lo[d] = dt.l;
+      if (d < 2) {
+        f[kWmTauPair + d] = dt.h;
+        f[kWmTauPair + 2 + d] = dt.l;
+      }
+      if (d == ds) {
+        f[kWmSingle] = dt.h;
+        f[kWmSingle + 1] = dt.l;
+      }
     }
   } else if (warp == 5 && mine) {
+    float* f = reinterpret_cast<float*>(o->q);
     for (int k = 0; k < kNBasis; ++k) {
       const dd c = fx::sub(ld2(S.c[k][l]), ldp(r.c[k]));
-      o->dc_hi[k] = c.h;
-      o->dc_lo[k] = c.l;
+      f[wm_dc_hi(k)] = c.h;
+      f[wm_dc_lo(k)] = c.l;
     }
     o->valid = S.valid[l];
     o->pad[0] = o->pad[1] = o->pad[2] = 0;
@@ -900,10 +912,19 @@ __global__ void __launch_bounds__(kDdRoleThreads + kTanWarps * 32) k_setup_dd(co
       sig_r = mul(add(mul(xr, rr), mul(xi, ri)), iden).h;
       sig_i = mul(sub(mul(xi, rr), mul(xr, ri)), iden).h;
     }
-    o->rho[d][0] = rho_r;
-    o->rho[d][1] = rho_i;
-    o->sig[d][0] = sig_r;
-    o->sig[d][1] = sig_i;
+    float* f = reinterpret_cast<float*>(o->q);
+    if (d < 2) {
+      f[kWmRhoPair + d] = rho_r;
+      f[kWmRhoPair + 2 + d] = rho_i;
+      f[kWmSigPair + d] = sig_r;
+      f[kWmSigPair + 2 + d] = sig_i;
+    }
+    if ((ec.n_det & 1) && d == ec.n_det - 1) {
+      f[kWmSingle + 4] = rho_r;
+      f[kWmSingle + 5] = rho_i;
+      f[kWmSingle + 6] = sig_r;
+      f[kWmSingle + 7] = sig_i;
+    }
   }
 }
 
