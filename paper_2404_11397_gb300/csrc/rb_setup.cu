@@ -801,6 +801,10 @@ __device__ __noinline__ void setup_absolute_dd(const double* __restrict__ theta,
 // complex h0 prefactor K_d = A_ref P_d in FP64).
 __global__ void __launch_bounds__(kDdRoleThreads) k_ref_dd(const double* theta, EventConst ec, RefValues* out) {
   __shared__ DdSmem S;
+  // a kernel launched programmatically after this one (the chunk records of
+  // the rebuild + batch step) may start and load its own inputs now; it waits
+  // for this grid's completion before it reads the reference values
+  asm volatile("griddepcontrol.launch_dependents;");
   setup_absolute_dd(theta, 0, 1, ec, S);
   const int j = threadIdx.x;
   RefDD& R = out->dd;

@@ -585,6 +585,10 @@ constexpr int kRec = 32;
 // order 2 and the amplitude series, task 2 orders 3..8; each reads its part
 // of the 512-byte row with 16-byte loads issued before use.  rec: kRec floats,
 // 16-byte aligned.
+// WAIT: the reference values come from the preceding kernel of the stream and
+// this grid was launched programmatically: the matrix row is loaded first,
+// then the grid waits for that kernel before it reads them.
+template <bool WAIT = false>
 __device__ __forceinline__ void chunk_record(const RefValues* __restrict__ ref, const float4* __restrict__ row, int D,
                                              int task, float* __restrict__ rec) {
   if (task == 0) {
@@ -592,6 +596,7 @@ __device__ __forceinline__ void chunk_record(const RefValues* __restrict__ ref, 
 #pragma unroll
     for (int k = 0; k < kNBasis; ++k) m[k] = __ldcs(row + (kQ01 / 4) + k);
     const float4 fc = __ldcs(row + kQfc / 4);
+    if (WAIT) asm volatile("griddepcontrol.wait;" ::: "memory");
     float x0h = ref->phi0t[0], x0l = ref->phi0t[1], x1h = 0.f, x1l = 0.f;
 #pragma unroll
     for (int k = 0; k < kNBasis; ++k) {
@@ -614,6 +619,7 @@ __device__ __forceinline__ void chunk_record(const RefValues* __restrict__ ref, 
 #pragma unroll
     for (int i = 0; i < kNBasis / 2; ++i) m[i] = __ldcs(row + kQ2 / 4 + i);
     const float4 a0 = __ldcs(row + kQfc / 4), a1 = __ldcs(row + kQfc / 4 + 1);
+    if (WAIT) asm volatile("griddepcontrol.wait;" ::: "memory");
     float xh = 0.f, xl = 0.f;
 #pragma unroll
     for (int i = 0; i < kNBasis / 2; ++i) {
@@ -627,6 +633,7 @@ __device__ __forceinline__ void chunk_record(const RefValues* __restrict__ ref, 
     float4 m[(kOrd - 2) * kNBasis / 4];
 #pragma unroll
     for (int i = 0; i < (kOrd - 2) * kNBasis / 4; ++i) m[i] = __ldcs(row + kQh / 4 + i);
+    if (WAIT) asm volatile("griddepcontrol.wait;" ::: "memory");
     const float* mf = reinterpret_cast<const float*>(m);
     float xn[kOrd - 2];
 #pragma unroll
@@ -649,8 +656,8 @@ __global__ void __launch_bounds__(96) k_chunk_coef(const RefValues* __restrict__
                                                    int D, int n_chunks, float* __restrict__ out) {
   const int c = blockIdx.x * 32 + (threadIdx.x & 31);
   if (c >= n_chunks) return;
-  chunk_record(ref, reinterpret_cast<const float4*>(q + (size_t)c * kQRow), D, threadIdx.x >> 5,
-               out + (size_t)c * kRec);
+  chunk_record<true>(ref, reinterpret_cast<const float4*>(q + (size_t)c * kQRow), D, threadIdx.x >> 5,
+                     out + (size_t)c * kRec);
 }
 
 // Integer -> float on the FMA pipe (exact for |i| < 2^22; larger |i| < 2^31
@@ -1026,9 +1033,18 @@ size_t chunk_coef_bytes(int64_t N) { return sizeof(float) * kRec * (size_t)n_chu
 
 cudaError_t launch_chunk_coef(int64_t N, int D, const RefValues* ref, const void* cq, void* chunk_coef, cudaStream_t s) {
   const int nc = (int)n_chunks_of(N);
-  k_chunk_coef<<<(unsigned)((nc + 31) / 32), 96, 0, s>>>(ref, static_cast<const float*>(cq), D, nc,
-                                                        static_cast<float*>(chunk_coef));
-  return cudaGetLastError();
+  // programmatic launch: the blocks may start while the reference-value
+  // kernel before them runs, load their matrix rows, then wait for it
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)((nc + 31) / 32));
+  cfg.blockDim = dim3(96);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_chunk_coef, ref, static_cast<const float*>(cq), D, nc, static_cast<float*>(chunk_coef));
 }
 
 cudaError_t launch_chunk_q(int64_t kmin, double T, int64_t N, void* cq, cudaStream_t s) {
