@@ -77,6 +77,7 @@ constexpr int kTanBytes = 384;
 struct __align__(16) WarpSlot {
   WalkerMixed rec[2];
   unsigned char tan[2][kTanBytes];
+  float red[32];  // the walker's adjoint sums
 };
 static_assert(sizeof(WalkerMixed) % 16 == 0, "record copied in 16-byte pieces");
 static_assert(sizeof(WalkerTan<float>) <= kTanBytes && sizeof(WalkerTan<float>) % 8 == 0, "tangent buffer");
@@ -111,6 +112,50 @@ __device__ __forceinline__ void warp_sum_ff(float& h, float& l) {
     h = __fadd_rn(s, lo);
     l = __fsub_rn(lo, __fsub_rn(h, s));
   }
+}
+
+// One level of a transposed warp sum: lanes whose bit o is clear keep values
+// [0, M) of `in` and send [M, N), lanes whose bit is set keep [M, N) (zero
+// beyond N) and send [0, M); each adds what its partner sent.
+template <int N, int M>
+__device__ __forceinline__ void tsum_level(const float (&in)[N], float (&out)[M], int lane, int o) {
+  const bool up = (lane & o) != 0;
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const float lo = in[i], hi = (M + i < N) ? in[M + i] : 0.f;
+    const float keep = up ? hi : lo, send = up ? lo : hi;
+    out[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, o));
+  }
+}
+
+// Warp sums of NV <= 32 values per lane, each a fixed-order five-level tree:
+// after five halving levels every lane holds the total of one value, which
+// it writes to out[index] (shared memory); 31 shuffles for 32 values against
+// 5 NV for NV separate butterflies.
+template <int NV>
+__device__ __forceinline__ void warp_transposed_sums(const float (&v)[NV], int lane, float* out) {
+  static_assert(NV >= 1 && NV <= 32, "up to 32 values");
+  constexpr int m1 = (NV + 1) / 2, m2 = (m1 + 1) / 2, m3 = (m2 + 1) / 2, m4 = (m3 + 1) / 2, m5 = (m4 + 1) / 2;
+  static_assert(m5 == 1, "five levels reduce to one value");
+  float a[m1], b[m2], c[m3], d[m4], e[m5];
+  tsum_level<NV, m1>(v, a, lane, 16);
+  tsum_level<m1, m2>(a, b, lane, 8);
+  tsum_level<m2, m3>(b, c, lane, 4);
+  tsum_level<m3, m4>(c, d, lane, 2);
+  tsum_level<m4, m5>(d, e, lane, 1);
+  // the value's index: the positions this lane kept, from the last level back
+  // (a lane whose kept half was padding at some level holds no value)
+  int idx = (lane & 1) ? m5 : 0;
+  bool ok = idx < m4;
+  idx += (lane & 2) ? m4 : 0;
+  ok = ok && idx < m3;
+  idx += (lane & 4) ? m3 : 0;
+  ok = ok && idx < m2;
+  idx += (lane & 8) ? m2 : 0;
+  ok = ok && idx < m1;
+  idx += (lane & 16) ? m1 : 0;
+  ok = ok && idx < NV;
+  if (ok) out[idx] = e[0];
 }
 
 // Adds the float pair (bh, bl) to (h, l) (two-sum of the high parts).
@@ -557,26 +602,38 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
     if (!MALA && lane == 0) a.logl[RB_IDX(w, a.W, 105)] = logl;
     if (GRAD) {
       const float two_pi = 6.28318530717958648f;
-      float ac[kNBasis], at[kMaxDet], ar[kMaxDet][2];
+      // the walker's adjoint sums (basis coefficients, then per detector the
+      // delay and the prefactor ratio re/im) by one transposed warp sum
+      constexpr int kNV = kNBasis + 3 * D;
+      float v[kNV];
 #pragma unroll
       for (int q = 0; q < kNBasis / 2; ++q) {
-        ac[2 * q] = two_pi * warp_sum_f32(adj_c[q].x);
-        ac[2 * q + 1] = two_pi * warp_sum_f32(adj_c[q].y);
+        v[2 * q] = adj_c[q].x;
+        v[2 * q + 1] = adj_c[q].y;
       }
-#pragma unroll
-      for (int d = 0; d < kMaxDet; ++d) at[d] = ar[d][0] = ar[d][1] = 0.f;
       if constexpr (paired) {
-        at[0] = two_pi * warp_sum_f32(P.adj_tau.x);
-        at[1] = two_pi * warp_sum_f32(P.adj_tau.y);
-        ar[0][0] = warp_sum_f32(P.adj_rr.x);
-        ar[1][0] = warp_sum_f32(P.adj_rr.y);
-        ar[0][1] = warp_sum_f32(P.adj_ri.x);
-        ar[1][1] = warp_sum_f32(P.adj_ri.y);
+        v[kNBasis + 0] = P.adj_tau.x;
+        v[kNBasis + 1] = P.adj_tau.y;
+        v[kNBasis + D + 0] = P.adj_rr.x;
+        v[kNBasis + D + 1] = P.adj_rr.y;
+        v[kNBasis + 2 * D + 0] = P.adj_ri.x;
+        v[kNBasis + 2 * D + 1] = P.adj_ri.y;
       }
       if constexpr (ds >= 0) {
-        at[ds] = two_pi * warp_sum_f32(S.adj_tau);
-        ar[ds][0] = warp_sum_f32(S.adj_rr);
-        ar[ds][1] = warp_sum_f32(S.adj_ri);
+        v[kNBasis + ds] = S.adj_tau;
+        v[kNBasis + D + ds] = S.adj_rr;
+        v[kNBasis + 2 * D + ds] = S.adj_ri;
+      }
+      warp_transposed_sums<kNV>(v, lane, slot->red);
+      __syncwarp();
+      float ac[kNBasis], at[kMaxDet], ar[kMaxDet][2];
+#pragma unroll
+      for (int k = 0; k < kNBasis; ++k) ac[k] = two_pi * slot->red[k];
+#pragma unroll
+      for (int d = 0; d < kMaxDet; ++d) {
+        at[d] = d < D ? two_pi * slot->red[kNBasis + d] : 0.f;
+        ar[d][0] = d < D ? slot->red[kNBasis + D + d] : 0.f;
+        ar[d][1] = d < D ? slot->red[kNBasis + 2 * D + d] : 0.f;
       }
       float rho[kMaxDet][2];
       {
