@@ -48,7 +48,8 @@ cudaError_t launch_strain(const RefValues* src, int64_t kmin, int64_t N, double 
 cudaError_t launch_summary_parts(const void* w32, const float* is32, const int* exps, int64_t N, double T, int D, int B,
                                  const int64_t* edges, const RefValues* ref, const void* chunk_q, const void* recs,
                                  const SummaryOut& so, int p0, int p1, cudaStream_t s);
-cudaError_t launch_ref_dd(const double* theta_ref_dev, const EventConst& ec, RefValues* out, cudaStream_t s);
+cudaError_t launch_ref_dd(const double* theta_ref_dev, const EventConst& ec, RefValues* out, SummarySync* base_reset,
+                          cudaStream_t s);
 cudaError_t launch_tangents(const double* theta, int64_t W, const EventConst& ec, void* tan, cudaStream_t s);
 cudaError_t launch_data32(const DataPtrs& in, int64_t N, int D, void* w32, float* is32, int* exps, cudaStream_t s);
 cudaError_t launch_pull32(const DataPtrs& src, int64_t N, int D, double* data, double* psd, void* w32, float* is32,
@@ -426,6 +427,8 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
     e.dev.n_freq = N;
     e.dev.T = e.T;
     e.dev.base_logl = e.d_base;
+    e.dev.sync = e.d_sync;
+    e.dev.share = e.d_share;
     e.dev.tab32 = e.d_tab32;
     e.dev.tab32_floats = tab32;
     e.dev.edge32_floats = edge32;
@@ -529,7 +532,23 @@ int rb_event_get_info(rb_event_t ev, rb_event_info* info) {
   info->bin_scheme = e.bin_scheme;
   info->reserved = 0;
   info->epsilon = e.epsilon;
-  cudaError_t err = cudaMemcpy(&info->base_logl, e.d_base, sizeof(double), cudaMemcpyDeviceToHost);
+  // log L(theta_ref) as the kernels read it (event_base_logl): the fast build
+  // leaves the fixed-point sum of the shares, the FP64 builds the value
+  SummarySync hs{};
+  cudaError_t err = cudaMemcpy(&hs, e.d_sync, offsetof(SummarySync, bin_parts_done), cudaMemcpyDeviceToHost);
+  if (err == cudaSuccess) {
+    if (hs.base_in_acc == 0u) {
+      err = cudaMemcpy(&info->base_logl, e.d_base, sizeof(double), cudaMemcpyDeviceToHost);
+    } else if (hs.overflow == 0u) {
+      info->base_logl = (double)(long long)hs.base_acc * (1.0 / 4294967296.0);
+    } else {
+      std::vector<double> sh((size_t)e.n_det * e.n_bins);
+      err = cudaMemcpy(sh.data(), e.d_share, sizeof(double) * sh.size(), cudaMemcpyDeviceToHost);
+      double t = 0.0;
+      for (double v : sh) t += v;
+      info->base_logl = t;
+    }
+  }
   if (err != cudaSuccess) return cuda_fail(err, "rb_event_get_info: read base");
   return RB_OK;
 }
@@ -875,7 +894,7 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
   int launches = 3;  // the two reference-value kernels and the summary kernel
   // the float-float reference values head the critical path of the fast
   // rebuild: enqueued first
-  if (fast && (err = launch_ref_dd(e.d_theta_ref, e.ec, e.d_ref, s)) != cudaSuccess)
+  if (fast && (err = launch_ref_dd(e.d_theta_ref, e.ec, e.d_ref, e.d_sync, s)) != cudaSuccess)
     return cuda_fail(err, "reference values kernel");
   if (ss && ss->grad) {
     // the tangents depend on theta only: on their own stream from the start
@@ -902,7 +921,7 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
       ++launches;
     }
   } else {
-    if ((err = launch_ref_dd(e.d_theta_ref, e.ec, e.d_ref, e.side)) != cudaSuccess) return cuda_fail(err, "reference values kernel");
+    if ((err = launch_ref_dd(e.d_theta_ref, e.ec, e.d_ref, nullptr, e.side)) != cudaSuccess) return cuda_fail(err, "reference values kernel");
     // the streamed FP64 build (stored h0) does not read the reference values:
     // they are then rebuilt on the forked stream too
     if ((err = launch_ref_values(e.d_theta_ref, e.ec, e.d_ref, e.h0_valid ? e.side : s)) != cudaSuccess)
@@ -934,7 +953,11 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
                                e.d_chunkq, ss ? e.d_chunks : nullptr, e.out(), 0, e.n_parts, s);
   } else if (e.h0_valid) {
     // FP64 sums from the fiducial waveform stored by the last inline build
-    // for this theta_ref: strain, PSD and h0 streamed, no waveform arithmetic
+    // for this theta_ref: strain, PSD and h0 streamed, no waveform arithmetic;
+    // its fixed-point sum starts from zero (a fast build leaves it set)
+    if ((err = cudaMemsetAsync(&e.d_sync->base_acc, 0, sizeof(unsigned long long), s)) != cudaSuccess ||
+        (err = cudaMemsetAsync(&e.d_sync->overflow, 0, sizeof(unsigned), s)) != cudaSuccess)
+      return cuda_fail(err, "zero counters");
     err = launch_summary_stored(in, e.d_h0, e.kmin, e.N, e.T, e.n_det, e.n_bins, e.d_edges, e.out(), e.n_parts, s);
     e.w32_current = !in_opt && e.w32_resident;
   } else {

@@ -166,11 +166,15 @@ struct WalkerTan {
 };
 
 // Device-side event tables.  Offsets are in elements of the table type.
+struct SummarySync;
+
 struct EventDev {
   int n_det, n_bins, n_edges, e_pad, b_pad;
   int64_t kmin, n_freq;
   double T;
-  const double* base_logl;  // device: sum_d (Re sum_b A0 - sum_b B0 / 2) = log L(theta_ref)
+  const double* base_logl;  // device: sum_d (Re sum_b A0 - sum_b B0 / 2) = log L(theta_ref) (event_base_logl)
+  const SummarySync* sync;  // where the fast build leaves it
+  const double* share;      // [D][B] the bins' shares
   // float image copied to shared memory by the mixed kernels, laid out for
   // 16-byte loads (lane l reads edge / bin c0 + l: consecutive 16 B, no bank
   // conflicts) whose halves are ready operands of the paired FP32
@@ -227,8 +231,36 @@ struct SummarySync {
   unsigned counter;              // bins (or blocks) finished
   unsigned overflow;             // a bin's share did not fit the fixed-point sum
   unsigned long long base_acc;   // sum of the bins' shares, fixed point 2^-32
+  unsigned base_in_acc;          // 1: log L(theta_ref) is left in base_acc (fast build), 0: in EventDev::base_logl
+  unsigned pad;
   unsigned bin_parts_done[1];    // [B] parts finished per bin (allocated with B entries)
 };
+
+// log L(theta_ref) of the event's last summary build.  The fast build leaves
+// it as the fixed-point sum of the bins' shares, converted here by each
+// reader (no block of the build waits to convert it); the FP64 builds store
+// the value.  A share too large for the fixed-point sum sends the readers of a
+// fast build to the fixed-order FP64 sum of the D x B shares.
+// The loads are split from the conversion so that a kernel can issue them at
+// its start and use the value after its own staging.
+struct BaseRead {
+  unsigned in_acc, overflow;
+  unsigned long long acc;
+  double stored;
+};
+__device__ __forceinline__ BaseRead event_base_read(const EventDev& ev) {
+  const SummarySync* sy = ev.sync;
+  return BaseRead{sy->base_in_acc, sy->overflow, sy->base_acc, *ev.base_logl};
+}
+__device__ __forceinline__ double event_base_value(const EventDev& ev, const BaseRead& r) {
+  if (r.in_acc == 0u) return r.stored;
+  if (r.overflow == 0u) return (double)(long long)r.acc * (1.0 / 4294967296.0);
+  double t = 0.0;
+  const int n = ev.n_det * ev.n_bins;
+  for (int i = 0; i < n; ++i) t += ev.share[i];
+  return t;
+}
+__device__ __forceinline__ double event_base_logl(const EventDev& ev) { return event_base_value(ev, event_base_read(ev)); }
 
 struct SummaryOut {
   double* summ;          // [D][B][6] FP64 summary: A0 re/im, A1 re/im, B0, B1

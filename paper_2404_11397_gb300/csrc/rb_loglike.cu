@@ -362,6 +362,7 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
   const EventDev& ev = a.ev;
   constexpr int D = ND;
   const int Ep = ev.e_pad, Bp = ev.b_pad, B = ev.n_bins, E = ev.n_edges;
+  const BaseRead base_read = event_base_read(ev);  // in flight across the staging
 
   // Stage the tables (16-byte asynchronous copies, all in flight at once).
   const float* sbin;
@@ -424,7 +425,6 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
   const int64_t w_end = w_begin + per_blk + ((int64_t)blockIdx.x < rem_blk ? 1 : 0);
   const int64_t warp0 = w_begin + (threadIdx.x >> 5);
   const int64_t nwarps = blockDim.x >> 5;
-  const double base_logl = *ev.base_logl;
   const unsigned char* rec_g = static_cast<const unsigned char*>(a.ws);
   const unsigned char* tan_g = static_cast<const unsigned char*>(a.tan);
   // the first walker's record and tangents travel with the tables
@@ -433,6 +433,7 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
                                    GRAD ? tan_g + sizeof(WalkerTan<float>) * RB_IDX(warp0, a.W, 107) : nullptr, lane);
   cp_async_wait_all();
   __syncthreads();
+  const double base_logl = event_base_value(ev, base_read);
 
   int buf = 0;
   for (int64_t w = warp0; w < w_end; w += nwarps, buf ^= 1) {
@@ -673,6 +674,7 @@ __global__ void __launch_bounds__(256) k_rb_f64(LaunchArgs a) {
   const int64_t w_end = w_begin + per_blk + ((int64_t)blockIdx.x < rem_blk ? 1 : 0);
   const int64_t warp0 = w_begin + (threadIdx.x >> 5);
   const int64_t nwarps = blockDim.x >> 5;
+  const double base_logl = event_base_logl(ev);
   for (int64_t w = warp0; w < w_end; w += nwarps) {
     const WalkerF64* s = reinterpret_cast<const WalkerF64*>(a.ws) + w;
     if (!s->valid) {
@@ -762,7 +764,7 @@ __global__ void __launch_bounds__(256) k_rb_f64(LaunchArgs a) {
       }
     }
     const double tot = warp_sum_f64(acc);
-    const double logl = *ev.base_logl + tot;
+    const double logl = base_logl + tot;
     if (!MALA && lane == 0) a.logl[RB_IDX(w, a.W, 105)] = logl;
     if (GRAD) {
 #pragma unroll

@@ -799,8 +799,16 @@ __device__ __noinline__ void setup_absolute_dd(const double* __restrict__ theta,
 // block, every lane evaluates theta_ref; also writes the reference copies
 // used by the summary build (c/2pi, Phi0/2pi, tau as float pairs and the
 // complex h0 prefactor K_d = A_ref P_d in FP64).
-__global__ void __launch_bounds__(kDdRoleThreads) k_ref_dd(const double* theta, EventConst ec, RefValues* out) {
+__global__ void __launch_bounds__(kDdRoleThreads) k_ref_dd(const double* theta, EventConst ec, RefValues* out,
+                                                          SummarySync* base_reset) {
   __shared__ DdSmem S;
+  // a fast summary build follows on the same stream: it leaves log L(theta_ref)
+  // in the fixed-point accumulator, zeroed here
+  if (base_reset && threadIdx.x == 0) {
+    base_reset->base_acc = 0ull;
+    base_reset->overflow = 0u;
+    base_reset->base_in_acc = 1u;
+  }
   // a kernel launched programmatically after this one (the chunk records of
   // the rebuild + batch step) may start and load its own inputs now; it waits
   // for this grid's completion before it reads the reference values
@@ -1016,8 +1024,9 @@ cudaError_t launch_ref_phase_tangents(const double* theta_ref_dev, double* out, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_ref_dd(const double* theta_ref_dev, const EventConst& ec, RefValues* out, cudaStream_t s) {
-  k_ref_dd<<<1, kDdRoleThreads, 0, s>>>(theta_ref_dev, ec, out);
+cudaError_t launch_ref_dd(const double* theta_ref_dev, const EventConst& ec, RefValues* out, SummarySync* base_reset,
+                          cudaStream_t s) {
+  k_ref_dd<<<1, kDdRoleThreads, 0, s>>>(theta_ref_dev, ec, out, base_reset);
   return cudaGetLastError();
 }
 

@@ -124,11 +124,14 @@ __device__ __forceinline__ void strain_f64(const Values& v, int d, double f, dou
 //     detectors) to a 64-bit fixed-point accumulator (2^-32 units; integer
 //     addition does not depend on the order) and the last block converts it;
 //     if a share does not fit (|share| >= 2^31) the last block falls back to
-//     the fixed-order FP64 sum.
+//     the fixed-order FP64 sum;
+//   fixed_base = true, ticket = false (fast build): no block waits to find the
+//     last one: the accumulator (zeroed by the reference-value kernel at the
+//     start of the build) is converted by its readers (event_base_logl).
 // ---------------------------------------------------------------------------
 __device__ void summary_epilogue(const SummaryOut& so, int b, int d0, int nd, int B, int D, const double* sblock,
                                  const double* scale, bool scaled_form, unsigned n_blocks, double inv_df_b,
-                                 bool fixed_base) {
+                                 bool fixed_base, bool ticket = true) {
   __shared__ bool last;
   SummarySync* sy = so.sync;
   if (threadIdx.x < 32) {
@@ -172,13 +175,15 @@ __device__ void summary_epilogue(const SummaryOut& so, int b, int d0, int nd, in
           atomicOr(&sy->overflow, 1u);
       }
     }
+    if (!ticket) return;
     fence_acq_rel_gpu();
     __syncwarp();
     if (j == 0) {
-      const unsigned ticket = atomicAdd(&sy->counter, 1u);
-      last = (ticket == n_blocks - 1u);
+      const unsigned done = atomicAdd(&sy->counter, 1u);
+      last = (done == n_blocks - 1u);
     }
   }
+  if (!ticket) return;
   __syncthreads();
   if (!last) return;
   fence_acq_rel_gpu();
@@ -186,6 +191,7 @@ __device__ void summary_epilogue(const SummaryOut& so, int b, int d0, int nd, in
     if (threadIdx.x == 0) {
       const unsigned long long acc = atomicExch(&sy->base_acc, 0ull);
       *so.base = (double)(long long)acc * (1.0 / 4294967296.0);
+      sy->base_in_acc = 0u;
       sy->counter = 0u;
     }
     return;
@@ -211,6 +217,7 @@ __device__ void summary_epilogue(const SummaryOut& so, int b, int d0, int nd, in
     double t = 0.0;
     for (int i = 0; i < nw; ++i) t += part[i];
     *so.base = t;
+    sy->base_in_acc = 0u;
     sy->counter = 0u;
     sy->overflow = 0u;
     sy->base_acc = 0ull;
@@ -993,7 +1000,7 @@ __global__ void __launch_bounds__(kSumFastThreads, 6)
     sblock[tid] = (double)h + (double)l;
   }
   __syncthreads();
-  summary_epilogue(so, b, 0, D, B, D, sblock, &scale[0][0], true, (unsigned)B, s_inv_df, true);
+  summary_epilogue(so, b, 0, D, B, D, sblock, &scale[0][0], true, (unsigned)B, s_inv_df, true, false);
 }
 
 static TaylorTables make_taylor_tables() {
