@@ -462,13 +462,16 @@ __device__ __forceinline__ void fma_acc(V a_hi, V a_lo, V b_hi, V b_lo, V& s_hi,
   s_lo = add(s_lo, add(err, e));
 }
 
-// Fractional part of hi + lo in turns (as frac_turns).
+// hi + lo in turns with the whole turns of hi removed: hi - rint(hi) is
+// exact, so the result is within |lo| (below an ulp of hi, at most a few
+// 1e-3 turns for |hi| ~ 1e4) of [-1/2, 1/2].  The half-angle sine and cosine
+// that take it are accurate slightly beyond +-1/2 and periodic in the result,
+// so the sum is not reduced a second time.
 template <class V>
 __device__ __forceinline__ V frac(V hi, V lo) {
   const V m = splat<V>(12582912.0f);  // 1.5 * 2^23: round to nearest on the FMA pipe
   const V r = sub(hi, sub(add(hi, m), m));
-  const V y = add(r, lo);
-  return sub(y, sub(add(y, m), m));
+  return add(r, lo);
 }
 
 // sin(pi y), cos(pi y) for |y| <= 1/2 (the polynomials of sincos_pi_half).
