@@ -743,16 +743,22 @@ int rb_loglike_grad_host(rb_event_t ev, const double* theta_host, int64_t W, dou
   cudaStream_t s = (cudaStream_t)stream;
   double *d_theta = nullptr, *d_logl = nullptr, *d_grad = nullptr;
   const rb::HostOut out = rb::mapped_outputs(logl_host, grad_host);
+  // pinned (mapped) walkers are read by the set-up kernel over the host link;
+  // others are copied in first
+  const double* theta_in = rb::mapped_host(theta_host, 8);
   int rc = RB_OK;
   cudaError_t err;
   do {
-    if ((err = ws_alloc(reinterpret_cast<void**>(&d_theta), sizeof(double) * kNPar * W, s)) != cudaSuccess) { rc = cuda_fail(err, "workspace allocation (theta)"); break; }
+    if (!theta_in) {
+      if ((err = ws_alloc(reinterpret_cast<void**>(&d_theta), sizeof(double) * kNPar * W, s)) != cudaSuccess) { rc = cuda_fail(err, "workspace allocation (theta)"); break; }
+      if ((err = cudaMemcpyAsync(d_theta, theta_host, sizeof(double) * kNPar * W, cudaMemcpyHostToDevice, s)) != cudaSuccess) { rc = cuda_fail(err, "copy theta"); break; }
+      theta_in = d_theta;
+    }
     if (!out.direct) {
       if ((err = ws_alloc(reinterpret_cast<void**>(&d_logl), sizeof(double) * W, s)) != cudaSuccess) { rc = cuda_fail(err, "workspace allocation (logl)"); break; }
       if (grad_host && (err = ws_alloc(reinterpret_cast<void**>(&d_grad), sizeof(double) * kNPar * W, s)) != cudaSuccess) { rc = cuda_fail(err, "workspace allocation (grad)"); break; }
     }
-    if ((err = cudaMemcpyAsync(d_theta, theta_host, sizeof(double) * kNPar * W, cudaMemcpyHostToDevice, s)) != cudaSuccess) { rc = cuda_fail(err, "copy theta"); break; }
-    rc = rb::run_batch(&ev->e, d_theta, W, out.direct ? out.logl : d_logl, out.direct ? out.grad : d_grad, mode, s, nullptr);
+    rc = rb::run_batch(&ev->e, theta_in, W, out.direct ? out.logl : d_logl, out.direct ? out.grad : d_grad, mode, s, nullptr);
     if (rc != RB_OK || out.direct) break;
     if ((err = cudaMemcpyAsync(logl_host, d_logl, sizeof(double) * W, cudaMemcpyDeviceToHost, s)) != cudaSuccess) { rc = cuda_fail(err, "copy logl"); break; }
     if (grad_host && (err = cudaMemcpyAsync(grad_host, d_grad, sizeof(double) * kNPar * W, cudaMemcpyDeviceToHost, s)) != cudaSuccess) { rc = cuda_fail(err, "copy grad"); break; }

@@ -364,6 +364,15 @@ def test_host_entry_point_matches_device(rb, small):
     rb.loglike_grad_host(small.event, th, Lh, Gh, mode="mixed")
     np.testing.assert_array_equal(Lh, Ld.cpu().numpy())
     np.testing.assert_array_equal(Gh, Gd.cpu().numpy())
+    # pinned walkers and outputs: read and written by the kernels over the host link
+    th_p = torch.tensor(th).pin_memory()
+    Lp = torch.zeros(100, dtype=torch.float64).pin_memory()
+    Gp = torch.zeros(100, 13, dtype=torch.float64).pin_memory()
+    for mode in ("mixed", "fp64"):
+        Ld, Gd = rb.loglike_grad(small.event, torch.tensor(th, device="cuda"), mode=mode)
+        rb.loglike_grad_host(small.event, th_p, Lp, Gp, mode=mode)
+        np.testing.assert_array_equal(Lp.numpy(), Ld.cpu().numpy())
+        np.testing.assert_array_equal(Gp.numpy(), Gd.cpu().numpy())
 
 
 def test_library_errors(rb, small):
