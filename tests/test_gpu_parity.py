@@ -388,6 +388,31 @@ def test_library_errors(rb, small):
         rb.Event.from_synth(ev, n_bins=10, theta_ref=bad)
 
 
+def test_reference_loglike_across_build_kinds(rb, c2):
+    """log L(theta_ref) through a sequence of builds of every kind (the fast
+    build leaves it as a fixed-point sum that its readers convert, the FP64
+    builds store it): after each, rb_event_get_info and a batch of walkers at
+    theta_ref agree bit for bit in every mode, and the value matches the full
+    likelihood at theta_ref (FP64 builds: 1e-9 relative; fast build: the
+    FP32 summary's 2e-6 of the shares' scale)."""
+    ev = c2.ev
+    event = rb.Event.from_synth(ev)
+    full = oracle.loglike_full(ev, ev["theta_inj"])[0]
+    th = torch.tensor(np.tile(ev["theta_inj"], (40, 1)), device="cuda")
+    scale = abs(full) + np.sum(np.abs(c2.s["B0"]))
+    steps = [dict(mode="mixed"), dict(mode="fp64", theta_ref=ev["theta_inj"]), dict(mode="fp64"),
+             dict(mode="mixed"), dict(mode="mixed"), dict(mode="fp64")]
+    for kw in steps:
+        event.rebuild(**kw)
+        base = event.info()["base_logl"]
+        tol = 1e-9 * abs(full) if kw["mode"] == "fp64" else 2e-6 * scale
+        assert abs(base - full) <= tol, (kw, base, full)
+        for mode in MODES:
+            L = rb.loglike(event, th, mode=mode).cpu().numpy()
+            assert np.all(L == base), (kw, mode)
+    event.free()
+
+
 # ---------------------------------------------------------------------------
 # In-place rebuild (rb_event_rebuild): FP64 and fast (Taylor-chunk) summary
 # ---------------------------------------------------------------------------
