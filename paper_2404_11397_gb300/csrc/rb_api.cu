@@ -285,6 +285,9 @@ int rb_event_free(rb_event_t ev) {
   cudaFree(e.d_share);
   cudaFree(e.step_ws);
   for (int i = 0; i < e.n_step_ws_old; ++i) cudaFree(e.step_ws_old[i]);
+  if (e.hg_exec) cudaGraphExecDestroy(e.hg_exec);
+  if (e.hg_stream) cudaStreamDestroy(e.hg_stream);
+  cudaFree(e.hg_ws);
   if (e.ev_fork) cudaEventDestroy(e.ev_fork);
   if (e.ev_join) cudaEventDestroy(e.ev_join);
   if (e.ev_ref) cudaEventDestroy(e.ev_ref);
@@ -724,6 +727,58 @@ struct HostOut {
   double* grad = nullptr;
   bool direct = false;
 };
+
+bool trace_events_set();
+
+// The host-buffer batch's launches as a graph: captured (not run) for the
+// walkers' and outputs' mapped addresses, W and mode on the event's capture
+// stream, with a workspace of its own; replaced when the call changes.
+// Returns false (nothing cached) if anything fails: the caller then launches
+// the kernels directly.
+static std::mutex g_hg_mu;
+static bool host_batch_graph(EventEntry& e, const double* theta, int64_t W, double* logl, double* grad, int mode) {
+  if (e.hg_exec && e.hg_theta == theta && e.hg_logl == logl && e.hg_grad == grad && e.hg_W == W && e.hg_mode == mode)
+    return true;
+  if (e.hg_exec) {
+    cudaGraphExecDestroy(e.hg_exec);
+    e.hg_exec = nullptr;
+  }
+  cudaError_t err = cudaSuccess;
+  if (!e.hg_stream) err = cudaStreamCreateWithFlags(&e.hg_stream, cudaStreamNonBlocking);
+  const size_t need = walker_ws_bytes(mode, grad != nullptr) * (size_t)W;
+  if (err == cudaSuccess && e.hg_ws_bytes < need) {
+    cudaFree(e.hg_ws);
+    e.hg_ws = nullptr;
+    e.hg_ws_bytes = 0;
+    if ((err = cudaMalloc(&e.hg_ws, need)) == cudaSuccess) e.hg_ws_bytes = need;
+  }
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(e.hg_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const int rc = run_batch(&e, theta, W, logl, grad, mode, e.hg_stream, e.hg_ws);
+  count_launches((uint64_t)0 - 2u);  // the capture launched nothing
+  err = cudaStreamEndCapture(e.hg_stream, &g);
+  cudaGraphExec_t exec = nullptr;
+  if (rc == RB_OK && err == cudaSuccess && g) err = cudaGraphInstantiate(&exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (rc != RB_OK || err != cudaSuccess || !exec) {
+    cudaGetLastError();
+    return false;
+  }
+  e.hg_exec = exec;
+  e.hg_theta = theta;
+  e.hg_logl = logl;
+  e.hg_grad = grad;
+  e.hg_W = W;
+  e.hg_mode = mode;
+  return false;  // captured for the next call; this one launches directly
+}
 static HostOut mapped_outputs(double* logl_host, double* grad_host) {
   HostOut o;
   o.logl = const_cast<double*>(mapped_host(logl_host, 8));
@@ -748,6 +803,21 @@ int rb_loglike_grad_host(rb_event_t ev, const double* theta_host, int64_t W, dou
   const double* theta_in = rb::mapped_host(theta_host, 8);
   int rc = RB_OK;
   cudaError_t err;
+  // everything pinned (a sampler's steady state): the launches replayed from
+  // a graph captured for these buffers at the previous such call
+  if (theta_in && out.direct && !rb::trace_events_set()) {
+    bool replay;
+    {
+      std::lock_guard<std::mutex> lk(rb::g_hg_mu);
+      replay = rb::host_batch_graph(ev->e, theta_in, W, out.logl, out.grad, mode);
+      if (replay && (err = cudaGraphLaunch(ev->e.hg_exec, s)) != cudaSuccess) return cuda_fail(err, "graph launch");
+    }
+    if (replay) {
+      rb::count_launches(2);
+      err = cudaStreamSynchronize(s);
+      return err == cudaSuccess ? RB_OK : cuda_fail(err, "synchronise");
+    }
+  }
   do {
     if (!theta_in) {
       if ((err = ws_alloc(reinterpret_cast<void**>(&d_theta), sizeof(double) * kNPar * W, s)) != cudaSuccess) { rc = cuda_fail(err, "workspace allocation (theta)"); break; }
@@ -984,6 +1054,7 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
 }
 
 static std::atomic<void*> g_trace_before{nullptr}, g_trace_after{nullptr};
+bool trace_events_set() { return g_trace_before.load() != nullptr || g_trace_after.load() != nullptr; }
 void set_trace_events(void* before, void* after) {
   g_trace_before.store(before);
   g_trace_after.store(after);

@@ -70,6 +70,17 @@ struct EventEntry {
   cudaEvent_t ev_tan = nullptr;
   cudaStream_t copy = nullptr;    // host-buffer rebuild + batch: strain/PSD copies in
   cudaEvent_t ev_data = nullptr;  // ... and their completion
+  // host-buffer batch with pinned walkers and outputs: its set-up and
+  // likelihood launches, captured once for (buffers, W, mode) and replayed
+  cudaGraphExec_t hg_exec = nullptr;
+  cudaStream_t hg_stream = nullptr;  // the capture stream
+  const double* hg_theta = nullptr;
+  double* hg_logl = nullptr;
+  double* hg_grad = nullptr;
+  int64_t hg_W = 0;
+  int hg_mode = -1;
+  void* hg_ws = nullptr;             // the captured launches' workspace
+  size_t hg_ws_bytes = 0;
   PartDesc* d_parts = nullptr;    // fast build: parts of bins
   float* d_part_sums = nullptr;   // fast build: per-part float-pair sums
   int n_parts = 0;

@@ -368,11 +368,21 @@ def test_host_entry_point_matches_device(rb, small):
     th_p = torch.tensor(th).pin_memory()
     Lp = torch.zeros(100, dtype=torch.float64).pin_memory()
     Gp = torch.zeros(100, 13, dtype=torch.float64).pin_memory()
-    for mode in ("mixed", "fp64"):
+    for mode in ("mixed", "fp64", "mixed"):
         Ld, Gd = rb.loglike_grad(small.event, torch.tensor(th, device="cuda"), mode=mode)
-        rb.loglike_grad_host(small.event, th_p, Lp, Gp, mode=mode)
-        np.testing.assert_array_equal(Lp.numpy(), Ld.cpu().numpy())
-        np.testing.assert_array_equal(Gp.numpy(), Gd.cpu().numpy())
+        for _ in range(3):  # launched directly, then replayed from the graph captured for these buffers
+            Lp.zero_()
+            Gp.zero_()
+            rb.loglike_grad_host(small.event, th_p, Lp, Gp, mode=mode)
+            np.testing.assert_array_equal(Lp.numpy(), Ld.cpu().numpy())
+            np.testing.assert_array_equal(Gp.numpy(), Gd.cpu().numpy())
+    # new walkers in the same pinned buffer: the replay reads them
+    th2 = synth.draw_box(small.ev["theta_inj"], 100, seed=103, rel=1e-3, abs_width=1e-3 * synth.PRIOR_WIDTH)
+    th_p.copy_(torch.tensor(th2))
+    Ld, Gd = rb.loglike_grad(small.event, torch.tensor(th2, device="cuda"), mode="mixed")
+    rb.loglike_grad_host(small.event, th_p, Lp, Gp, mode="mixed")
+    np.testing.assert_array_equal(Lp.numpy(), Ld.cpu().numpy())
+    np.testing.assert_array_equal(Gp.numpy(), Gd.cpu().numpy())
 
 
 def test_library_errors(rb, small):
