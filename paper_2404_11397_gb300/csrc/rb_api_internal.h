@@ -81,6 +81,17 @@ struct EventEntry {
   int hg_mode = -1;
   void* hg_ws = nullptr;             // the captured launches' workspace
   size_t hg_ws_bytes = 0;
+  // host-buffer rebuild + batch with everything pinned: the whole call
+  // (host-link read, rebuild, batch), captured once per buffers and replayed
+  cudaGraphExec_t hs_exec = nullptr;
+  const double* hs_data[RB_MAX_DET] = {};
+  const double* hs_psd[RB_MAX_DET] = {};
+  const double* hs_theta = nullptr;
+  double* hs_logl = nullptr;
+  double* hs_grad = nullptr;
+  int64_t hs_W = 0;
+  int hs_mode = -1;
+  uint64_t hs_launches = 0;
   PartDesc* d_parts = nullptr;    // fast build: parts of bins
   float* d_part_sums = nullptr;   // fast build: per-part float-pair sums
   int n_parts = 0;
