@@ -249,9 +249,16 @@ RB_API int rb_rebuild_loglike_grad(rb_event_t ev, const double* theta_dev, int64
  * buffers are copied by the copy engine and then converted.  Both give the
  * same bits.  When logl_host (and grad_host, if not NULL) are pinned, mapped
  * buffers starting on 8-byte boundaries, the likelihood kernel writes them
- * directly and no copy back is made.  Results equal rb_event_rebuild with the
- * same host data followed by rb_loglike_grad_host.  Errors: those of the two
- * calls. */
+ * directly and no copy back is made.  When every buffer is pinned and mapped
+ * (theta_host too, read by the set-up kernel over the host link), the call's
+ * launches are captured as a CUDA graph the first time for these buffers, W
+ * and mode, and replayed by the following calls with the same ones (the
+ * graph reads whatever the buffers hold at each call; a call with other
+ * buffers captures anew; the graph lives as long as the event; calls on one
+ * event from several host threads are serialised for the capture).  Not
+ * with trace events set (rb_set_trace_events).  Results equal rb_event_rebuild
+ * with the same host data followed by rb_loglike_grad_host.  Errors: those of
+ * the two calls. */
 RB_API int rb_rebuild_loglike_grad_host(rb_event_t ev, const double* const* data_host, const double* const* psd_host,
                                         const double* theta_host, int64_t W, double* logl_host, double* grad_host,
                                         int mode, void* stream);
@@ -260,9 +267,12 @@ RB_API int rb_rebuild_loglike_grad_host(rb_event_t ev, const double* const* data
  * its gradient) for host buffers:
  * copies theta_host [W][13] to the device, evaluates, copies logl_host [W]
  * (and grad_host [W][13] unless NULL) back, and synchronises the stream.
- * theta_host/logl_host/grad_host should be pinned for full copy bandwidth;
- * pinned, mapped, 8-byte-aligned logl_host/grad_host are written by the
- * likelihood kernel directly (no copy back). */
+ * pinned, mapped, 8-byte-aligned theta_host is read by the set-up kernel
+ * over the host link (no copy in), and such logl_host/grad_host are written
+ * by the likelihood kernel directly (no copy back).  With all three pinned,
+ * the set-up and likelihood launches are captured as a CUDA graph the first
+ * time for these buffers, W and mode, and replayed by the following calls
+ * with the same ones (as for rb_rebuild_loglike_grad_host). */
 RB_API int rb_loglike_grad_host(rb_event_t ev, const double* theta_host, int64_t W, double* logl_host, double* grad_host,
                          int mode, void* stream);
 
