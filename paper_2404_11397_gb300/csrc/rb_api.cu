@@ -1093,6 +1093,15 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
   }
   if ((err = cudaEventRecord(e.ev_join, e.side)) != cudaSuccess) return cuda_fail(err, "rebuild join");
   if (fast) {
+    // with the walkers' set-up on the forked stream (rebuild + batch), the
+    // chunk records are a launch of their own that overlaps the set-up (and
+    // any data copies still in flight: they read the reference values only);
+    // otherwise the summary kernel forms them in-block
+    if (ss) {
+      if ((err = launch_chunk_coef(e.N, e.n_det, e.d_ref, e.d_chunkq, e.d_chunks, s)) != cudaSuccess)
+        return cuda_fail(err, "chunk record kernel");
+      ++launches;
+    }
     // the FP32 working copy follows the data the sums are taken over: data
     // read in place are converted every time, the resident data only after
     // they change
@@ -1105,14 +1114,6 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
       ++launches;
     }
     e.w32_current = true;
-    // with the walkers' set-up on the forked stream (rebuild + batch), the
-    // chunk records are a launch of their own that overlaps the set-up;
-    // otherwise the summary kernel forms them in-block
-    if (ss) {
-      if ((err = launch_chunk_coef(e.N, e.n_det, e.d_ref, e.d_chunkq, e.d_chunks, s)) != cudaSuccess)
-        return cuda_fail(err, "chunk record kernel");
-      ++launches;
-    }
     err = launch_summary_parts(e.d_w32, e.d_is32, e.d_wexp, e.N, e.T, e.n_det, e.n_bins, e.d_edges, e.d_ref,
                                e.d_chunkq, ss ? e.d_chunks : nullptr, e.out(), 0, e.n_parts, s);
   } else if (e.h0_valid) {

@@ -703,7 +703,10 @@ __global__ void __launch_bounds__(256) k_data32(DataPtrs in, int64_t N, int D, f
 // mapped into the device address space (one pass over the host link), stored
 // as the event's resident FP64 copies and converted to the FP32 working copy
 // with the k_data32 arithmetic.  Block row d = detector; the blocks of a row
-// stride over the points with two points in flight per thread.
+// stride over the points with two points in flight per thread.  Half a block
+// per SM in all: the host link, not the SMs, sets the rate (2 blocks per SM
+// read no faster), and the rebuild's data-independent kernels launched beside
+// it find free SMs at once instead of ~55 us later.
 __global__ void __launch_bounds__(256) k_pull32(DataPtrs src, int64_t N, double* __restrict__ data,
                                                 double* __restrict__ psd, float2* __restrict__ w32,
                                                 float* __restrict__ is32, int* __restrict__ exps) {
@@ -742,7 +745,7 @@ __global__ void __launch_bounds__(256) k_pull32(DataPtrs src, int64_t N, double*
 
 cudaError_t launch_pull32(const DataPtrs& src, int64_t N, int D, double* data, double* psd, void* w32, float* is32,
                           int* exps, int n_sm, cudaStream_t s) {
-  dim3 grid((unsigned)std::max(1, (2 * n_sm + D - 1) / D), (unsigned)D);
+  dim3 grid((unsigned)std::max(1, (n_sm / 2 + D - 1) / D), (unsigned)D);
   k_pull32<<<grid, 256, 0, s>>>(src, N, data, psd, static_cast<float2*>(w32), is32, exps);
   return cudaGetLastError();
 }
