@@ -41,7 +41,8 @@ cudaError_t launch_summary(const DataPtrs& in, int64_t kmin, int64_t N, double T
 cudaError_t launch_summary_stored(const DataPtrs& in, const double* h0, int64_t kmin, int64_t N, double T, int D, int B,
                                   const int64_t* edges, const SummaryOut& so, int n_parts, cudaStream_t s);
 cudaError_t launch_edge_tables(int64_t kmin, double T, int D, int B, int Ep, int Bp, const int64_t* edges,
-                               float* tab32, size_t edge32_floats, double* tab64, double* inv_df, cudaStream_t s);
+                               float* tab32, size_t edge32_floats, double* tab64, double* inv_df, float* slot32,
+                               int n_slots, cudaStream_t s);
 cudaError_t launch_chunk_q(int64_t kmin, double T, int64_t N, void* cq, cudaStream_t s);
 size_t chunk_q_bytes(int64_t N);
 cudaError_t launch_strain(const RefValues* src, int64_t kmin, int64_t N, double T, double* h, cudaStream_t s);
@@ -273,6 +274,7 @@ int rb_event_free(rb_event_t ev) {
   cudaFree(e.d_edges);
   cudaFree(e.d_summ);
   cudaFree(e.d_tab32);
+  cudaFree(e.d_slot32);
   cudaFree(e.d_tab64);
   cudaFree(e.d_ref);
   cudaFree(e.d_base);
@@ -365,6 +367,8 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
   const size_t edge32 = (size_t)4 * kEdgeQuads * Ep;
   const size_t tab32 = edge32 + (size_t)D * 6 * Bp;
   const size_t tab64 = (size_t)(kNBasis + 1) * Ep + (size_t)D * 6 * Bp;
+  const int NS = slot_count(B);
+  const size_t slot32 = (size_t)NS * (4 * (kNBasis + 1) + kSlotBinFloats * D);
   {
     // the batch kernels stage all edge and bin tables in shared memory
     int dev = 0, smem_max = 0;
@@ -375,8 +379,8 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
       return cuda_fail(qerr, "rb_build_summary: device query");
     }
     // (plus the per-warp walker slots of the mixed kernel)
-    const size_t need = std::max(tab32 * sizeof(float), (size_t)(kNBasis + 1) * Ep * sizeof(double) +
-                                                            (size_t)D * 6 * Bp * sizeof(float)) +
+    const size_t need = std::max(slot32 * sizeof(float), (size_t)(kNBasis + 1) * Ep * sizeof(double) +
+                                                             (size_t)D * 6 * Bp * sizeof(float)) +
                         mixed_smem_slot_bytes();
     if (need > (size_t)smem_max) {
       delete ev;
@@ -394,6 +398,7 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
         {(void**)&e.d_edges, sizeof(int64_t) * E, "edges"},
         {(void**)&e.d_summ, sizeof(double) * 6 * D * B, "summary"},
         {(void**)&e.d_tab32, sizeof(float) * tab32, "tab32"},
+        {(void**)&e.d_slot32, sizeof(float) * slot32, "slot image"},
         {(void**)&e.d_tab64, sizeof(double) * tab64, "tab64"},
         {(void**)&e.d_ref, sizeof(RefValues), "ref"},
         {(void**)&e.d_base, sizeof(double), "base"},
@@ -436,6 +441,9 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
     e.dev.tab32 = e.d_tab32;
     e.dev.tab32_floats = tab32;
     e.dev.edge32_floats = edge32;
+    e.dev.slot32 = e.d_slot32;
+    e.dev.slot32_floats = slot32;
+    e.dev.n_slots = NS;
     e.dev.tab64 = e.d_tab64;
     e.dev.ref = e.d_ref;
     const cudaMemcpyKind kind = desc->data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -455,7 +463,7 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
       if ((err = launch_bin_edges(e.f_low, e.f_high, e.T, kmin, N, B, e.d_edges, d_span, s)) != cudaSuccess) { rc = cuda_fail(err, "bin edge kernels"); break; }
     }
     if ((rc = make_parts(e, s)) != RB_OK) break;
-    if ((err = launch_edge_tables(kmin, e.T, D, B, Ep, Bp, e.d_edges, e.d_tab32, edge32, e.d_tab64, e.d_invdf, s)) != cudaSuccess) { rc = cuda_fail(err, "edge table kernel"); break; }
+    if ((err = launch_edge_tables(kmin, e.T, D, B, Ep, Bp, e.d_edges, e.d_tab32, edge32, e.d_tab64, e.d_invdf, e.d_slot32, NS, s)) != cudaSuccess) { rc = cuda_fail(err, "edge table kernel"); break; }
     if ((err = launch_chunk_q(kmin, e.T, N, e.d_chunkq, s)) != cudaSuccess) { rc = cuda_fail(err, "chunk matrix kernel"); break; }
     count_launches(4);
     if ((rc = rebuild_event(e, nullptr, RB_FP64, s)) != RB_OK) break;

@@ -36,6 +36,7 @@ struct EventEntry {
   int64_t* d_edges = nullptr;
   double* d_summ = nullptr;
   float* d_tab32 = nullptr;
+  float* d_slot32 = nullptr;  // slot image of the float-float mixed kernel
   double* d_tab64 = nullptr;
   RefValues* d_ref = nullptr;
   double* d_base = nullptr;
@@ -99,7 +100,8 @@ struct EventEntry {
   uint64_t uid = 0;  // unique per built event (never reused within a process)
   SummaryOut out() const {
     return SummaryOut{d_summ, d_tab32 + dev.edge32_floats, d_tab64 + (size_t)(kNBasis + 1) * dev.e_pad, d_invdf,
-                      d_share, d_sync, d_base, dev.b_pad, d_parts, d_part_sums, n_parts};
+                      d_share, d_sync, d_base, dev.b_pad, d_parts, d_part_sums, n_parts,
+                      d_slot32 + (size_t)4 * (kNBasis + 1) * dev.n_slots, dev.n_slots};
   }
 };
 

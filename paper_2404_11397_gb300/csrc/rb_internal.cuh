@@ -30,6 +30,15 @@ constexpr int kEdgeQuads = kNBasis / 2 + 1;  // float4 groups per edge in the fl
 static_assert(kNBasis % 2 == 0, "basis pairs per float4 of the edge tables");
 constexpr int kNTanIntr = 6;  // Mc, q, chi1, chi2, Lambda1, Lambda2
 
+// Edge slots of the mixed likelihood kernel: in iteration i of a walker's
+// loop, lane l holds two bin edges, e_A = 63 i + l and e_B = 63 i + 32 + l,
+// each with the bin on its right (b = e; lane 31's e_B has no bin and is
+// the next iteration's e_A), as the two halves of one paired FP32 value.
+// Slot s = 32 i + l.
+constexpr int kSlotBins = 63;        // bins per iteration
+constexpr int kSlotBinFloats = 10;   // bin-table floats per slot and detector
+__host__ __device__ constexpr int slot_count(int n_bins) { return 32 * ((n_bins + kSlotBins - 1) / kSlotBins); }
+
 constexpr double kPi = 3.141592653589793238462643383279502884;
 constexpr double kTwoPi = 6.283185307179586476925286766559005768;
 constexpr double kEulerGamma = 0.577215664901532860606512090082402431;
@@ -192,6 +201,18 @@ struct EventDev {
   const float* tab32;
   size_t tab32_floats;   // multiple of 4
   size_t edge32_floats;  // length of the edge part (4*kEdgeQuads*Ep)
+  // slot image of the float-float mixed kernel (NS = slot_count(B) slots;
+  // halves A, B of a pair are the slot's edges e_A, e_B and their bins):
+  //   edge part, float4 [kNBasis + 1][NS]: quad k < kNBasis holds
+  //     {g_hi_k(e_A), g_hi_k(e_B), g_lo_k(e_A), g_lo_k(e_B)}, quad kNBasis
+  //     {f_hi(e_A), f_hi(e_B), f_lo(e_A), f_lo(e_B)};
+  //   bin part, per detector d (kSlotBinFloats * NS floats): float4 [2][NS]
+  //     {a0r_A, a0r_B, a0i_A, a0i_B}, {a1r_A, a1r_B, a1i_A, a1i_B}, then
+  //     float2 [NS] {-b0_A, -b0_B};
+  //   zero for edges past the last and where an edge has no bin.
+  const float* slot32;
+  size_t slot32_floats;  // multiple of 4
+  int n_slots;           // NS
   // FP64 tables: g[k][e] (10*Ep), f[e] (Ep), then per detector 6 rows of Bp
   const double* tab64;
   const RefValues* ref;
@@ -274,6 +295,8 @@ struct SummaryOut {
   const PartDesc* parts;  // fast build: [n_parts]
   float* part_sums;       // fast builds: [n_parts][kPartSlots] doubles, or float pairs [n_parts][7 kMaxDet][2]
   int n_parts;
+  float* slot_bin32;      // bin part of the slot image (EventDev::slot32)
+  int n_slots;
 };
 
 // ---------------------------------------------------------------------------

@@ -78,6 +78,11 @@ struct __align__(16) WarpSlot {
   WalkerMixed rec[2];
   unsigned char tan[2][kTanBytes];
   float red[32];  // the walker's adjoint sums
+  // the current walker's constants, each value in both halves of a pair
+  // (float-float path): {hi, hi, lo, lo} of dc_k (k < kNBasis), then per
+  // detector {tau_hi, tau_hi, tau_lo, tau_lo}, {rho_r, rho_r, rho_i, rho_i},
+  // {sig_r, sig_r, sig_i, sig_i}
+  float4 dup[kNBasis + 3 * kMaxDet];
 };
 static_assert(sizeof(WalkerMixed) % 16 == 0, "record copied in 16-byte pieces");
 static_assert(sizeof(WalkerTan<float>) <= kTanBytes && sizeof(WalkerTan<float>) % 8 == 0, "tangent buffer");
@@ -347,6 +352,57 @@ __device__ __forceinline__ V det_edge(V y, DetState<V>& st, const V* bt, bool ha
   }
   return dldx;
 }
+// The same for the two edges of a slot (halves A and B: edges e_A = 63 i + l
+// and e_B = e_A + 32 of lane l) and one detector: the right neighbour of
+// lane l's edges is lane l + 1's, except that lane 31's e_A is followed by
+// lane 0's e_B; the bin on the left of lane 0's e_B is lane 31's A bin, and
+// lane 0's e_A collects no left bin in this iteration (it is lane 31's e_B
+// of the previous one).  Edges without a bin, and slots past the last
+// edge, have zero tables, so they add nothing.  vsum collects the bin terms
+// of log L, adj_x d log L / dy (times 1/2pi) for the basis adjoint.
+template <bool GRAD>
+__device__ __forceinline__ void det_edge_slot(float2 y, float4 rho, float4 sig, const float2 (&bt)[5], int lane,
+                                              float2 fe, float2& vsum, float2& adj_x, float2& adj_tau, float2& adj_rr,
+                                              float2& adj_ri) {
+  const float2 rho_r = make_float2(rho.x, rho.y), rho_i = make_float2(rho.z, rho.w);
+  const float2 sig_r = make_float2(sig.x, sig.y), sig_i = make_float2(sig.z, sig.w);
+  float2 sn, cs;
+  sincos_half(y, sn, cs);
+  const float2 t2 = mul(splat<float2>(-2.f), sn);
+  const float2 em_r = mul(t2, sn), em_i = mul(t2, cs);  // e^{-2 pi i y} - 1
+  const float2 dr = fma(rho_r, em_r, fma(neg(rho_i), em_i, sig_r));
+  const float2 di = fma(rho_r, em_i, fma(rho_i, em_r, sig_i));
+  const int up = (lane + 1) & 31, dn = (lane + 31) & 31;
+  const float nrA = __shfl_sync(0xffffffffu, dr.x, up), nrB = __shfl_sync(0xffffffffu, dr.y, up);
+  const float niA = __shfl_sync(0xffffffffu, di.x, up), niB = __shfl_sync(0xffffffffu, di.y, up);
+  const float2 nr = make_float2(lane == 31 ? nrB : nrA, nrB), ni = make_float2(lane == 31 ? niB : niA, niB);
+  // bt: alpha0 (re, im), alpha1 (re, im), -beta0 (the beta1 term vanishes
+  // for a ratio of constant modulus)
+  const float2 sr = add(dr, nr), si = add(di, ni), tr = sub(nr, dr), ti = sub(ni, di);
+  float2 v = mul(bt[0], sr);
+  v = fma(bt[1], si, v);
+  v = fma(bt[2], tr, v);
+  v = fma(bt[3], ti, v);
+  v = fma(bt[4], fma(splat<float2>(0.25f), fma(sr, sr, mul(si, si)), sr), v);
+  vsum = add(vsum, v);
+  if (GRAD) {
+    const float2 hs_r = fma(splat<float2>(0.5f), sr, splat<float2>(1.f)), hs_i = mul(splat<float2>(0.5f), si);  // 1 + s/2
+    const float2 Ur = fma(bt[4], hs_r, bt[0]), Ui = fma(bt[4], hs_i, bt[1]);
+    float2 gr = sub(Ur, bt[2]), gi = sub(Ui, bt[3]);  // own bin (edge on its left)
+    const float2 pr = add(Ur, bt[2]), pi = add(Ui, bt[3]);  // U + V: the bin's right edge
+    const float lrA = __shfl_sync(0xffffffffu, pr.x, dn), lrB = __shfl_sync(0xffffffffu, pr.y, dn);
+    const float liA = __shfl_sync(0xffffffffu, pi.x, dn), liB = __shfl_sync(0xffffffffu, pi.y, dn);
+    gr = add(gr, make_float2(lane == 0 ? 0.f : lrA, lane == 0 ? lrA : lrB));
+    gi = add(gi, make_float2(lane == 0 ? 0.f : liA, lane == 0 ? liA : liB));
+    const float2 rr = add(splat<float2>(1.f), dr);
+    const float2 dldx = fma(gr, di, mul(neg(gi), rr));  // Im(conj(gbar) r); times 2 pi later
+    adj_x = add(adj_x, dldx);
+    adj_tau = fma(dldx, fe, adj_tau);
+    const float2 Er = add(splat<float2>(1.f), em_r);  // gbar_rho += gbar conj(E)
+    adj_rr = fma(gr, Er, fma(gi, em_i, adj_rr));
+    adj_ri = fma(gi, Er, fma(neg(gr), em_i, adj_ri));
+  }
+}
 }  // namespace pv
 
 // ---------------------------------------------------------------------------
@@ -373,19 +429,19 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
 #else
   constexpr size_t smem16 = 0;  // unused
 #endif
-  const float4* g4 = nullptr;  // [kEdgeQuads][Ep] basis pairs and f_e (float pairs)
+  const float4* g4 = nullptr;  // slot image: [kNBasis + 1][NS] basis values and f_e of the slots' edge pairs
   const double* g64 = nullptr;
   const double* f64 = nullptr;
   {
     const int tid = threadIdx.x;
     if (!PHASE64) {
-      const float4* src = reinterpret_cast<const float4*>(ev.tab32);
+      const float4* src = reinterpret_cast<const float4*>(ev.slot32);
       float4* dst = reinterpret_cast<float4*>(smem_raw);
-      const size_t n4 = ev.tab32_floats / 4;
+      const size_t n4 = ev.slot32_floats / 4;
       for (size_t i = tid; i < n4; i += blockDim.x) cp_async16(&dst[RB_IDX(i, smem16, 104)], &src[i]);
       const float* s = reinterpret_cast<const float*>(smem_raw);
       g4 = reinterpret_cast<const float4*>(s);
-      sbin = s + ev.edge32_floats;
+      sbin = s + (size_t)4 * (kNBasis + 1) * ev.n_slots;
     } else {
       const size_t n_e64 = (size_t)(kNBasis + 1) * Ep;  // g[10][Ep], f[Ep]
       const double2* src = reinterpret_cast<const double2*>(ev.tab64);
@@ -405,7 +461,7 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
   const int lane = threadIdx.x & 31;
   WarpSlot* slot;  // this warp's slot, after the tables
   {
-    const size_t tab_bytes = !PHASE64 ? ev.tab32_floats * sizeof(float)
+    const size_t tab_bytes = !PHASE64 ? ev.slot32_floats * sizeof(float)
                                       : (size_t)(kNBasis + 1) * Ep * sizeof(double) +
                                             (ev.tab32_floats - ev.edge32_floats) * sizeof(float);
     slot = reinterpret_cast<WarpSlot*>(smem_raw + tab_bytes) + (threadIdx.x >> 5);
@@ -452,6 +508,27 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
       for (int k = 0; k < kNBasis; ++k) dc64[k] = 0.0;
 #pragma unroll
       for (int d = 0; d < kMaxDet; ++d) tau64[d] = 0.0;
+      // each constant in both halves of a pair (the slot loop's operands):
+      // lane k < kNBasis takes dc_k, lane kNBasis + 3 d + m the delay (m = 0),
+      // prefactor ratio (1) or its difference from 1 (2) of detector d
+      if (lane < kNBasis + 3 * D) {
+        const float* f = reinterpret_cast<const float*>(wc);
+        int iu, iv;
+        if (lane < kNBasis) {
+          iu = wm_dc_hi(lane);
+          iv = wm_dc_lo(lane);
+        } else {
+          const int j = lane - kNBasis, d = j / 3, m = j - 3 * d;
+          if (d == ds) {
+            iu = kWmSingle + (m == 0 ? 0 : 2 + 2 * m);
+          } else {
+            iu = (m == 0 ? kWmTauPair : (m == 1 ? kWmRhoPair : kWmSigPair)) + d;
+          }
+          iv = iu + (d == ds ? 1 : 2);
+        }
+        const float u = f[iu], v = f[iv];
+        slot->dup[lane] = make_float4(u, u, v, v);
+      }
     } else {
       float rho[kMaxDet][2], sg[kMaxDet][2];
       const WalkerF64* s = reinterpret_cast<const WalkerF64*>(a.ws) + w;
@@ -497,116 +574,123 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
     // float-pair accumulators: for walkers far from the fiducial point the
     // per-bin terms add up to about -log L(theta_ref), so a single float would
     // lose ~1e-3 of absolute precision
-    P.acc = P.acc_lo = P.adj_tau = P.adj_rr = P.adj_ri = make_float2(0.f, 0.f);
-    S.acc = S.acc_lo = S.adj_tau = S.adj_rr = S.adj_ri = 0.f;
-    float2 adj_c[kNBasis / 2];
+    constexpr int kNV = kNBasis + 3 * D;
+    float lh, ll;   // the lane's share of log L - log L(theta_ref), a float pair
+    float v[kNV];   // the lane's adjoint sums: basis coefficients, then per detector the delay and the ratio re/im
+    if constexpr (!PHASE64) {
+      // slot loop: both halves of every paired value are edges of this walker
+      const int NS = ev.n_slots;
+      const float4* const wd = slot->dup;
+      float2 acc = make_float2(0.f, 0.f), acc_lo = acc;
+      float2 adj_c[kNBasis], adj_tau[D], adj_rr[D], adj_ri[D];
 #pragma unroll
-    for (int q = 0; q < kNBasis / 2; ++q) adj_c[q] = make_float2(0.f, 0.f);
-
-    for (int c0 = 0; c0 < B; c0 += 31) {
-      const int e = c0 + lane;
-      const bool has_edge = e < E;
-      const bool has_bin = (lane < 31) && (e < B);
-      const int ee = RB_IDX(has_edge ? e : E - 1, Ep, 102);
-      const int eb = RB_IDX(has_bin ? e : 0, Bp, 103);
-
-      // detector-independent phase sum_k dc_k g_k(f_e) / 2pi [turns]: two
-      // float-pair accumulators (even k, odd k) side by side, then merged
-      float xh, xl, fe, fe_lo = 0.f;
-      double x64 = 0.0;
-      if (!PHASE64) {
-        float2 sh = make_float2(0.f, 0.f), sl = sh;
+      for (int k = 0; k < kNBasis; ++k) adj_c[k] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int q = 0; q < kNBasis / 2; ++q) {
-          const float4 g = g4[q * Ep + ee];  // {g_hi[2q], g_hi[2q+1], g_lo[2q], g_lo[2q+1]}
-          const float4 c = lds4(wc + q);     // {dc_hi[2q], dc_hi[2q+1], dc_lo[2q], dc_lo[2q+1]}
-          pv::fma_acc(make_float2(c.x, c.y), make_float2(c.z, c.w), make_float2(g.x, g.y), make_float2(g.z, g.w), sh, sl);
+      for (int d = 0; d < D; ++d) adj_tau[d] = adj_rr[d] = adj_ri[d] = make_float2(0.f, 0.f);
+      for (int s0 = 0; s0 < NS; s0 += 32) {
+        const int sl = RB_IDX(s0 + lane, NS, 102);
+        // detector-independent phase sum_k dc_k g_k(f_e) / 2pi [turns] of the two edges
+        float2 sh = make_float2(0.f, 0.f), sl_lo = sh;
+#pragma unroll
+        for (int k = 0; k < kNBasis; ++k) {
+          const float4 g = g4[k * NS + sl];  // {g_hi(e_A), g_hi(e_B), g_lo(e_A), g_lo(e_B)}
+          const float4 c = lds4(wd + k);     // {dc_hi, dc_hi, dc_lo, dc_lo}
+          pv::fma_acc(make_float2(c.x, c.y), make_float2(c.z, c.w), make_float2(g.x, g.y), make_float2(g.z, g.w), sh,
+                      sl_lo);
         }
-        xh = __fadd_rn(sh.x, sh.y);  // two-sum of the high parts
-        const float bb = __fsub_rn(xh, sh.x);
-        const float err = __fadd_rn(__fsub_rn(sh.x, __fsub_rn(xh, bb)), __fsub_rn(sh.y, bb));
-        xl = __fadd_rn(err, __fadd_rn(sl.x, sl.y));
-        const float2 f2 = *reinterpret_cast<const float2*>(g4 + (kEdgeQuads - 1) * Ep + ee);
-        fe = f2.x;
-        fe_lo = f2.y;
-      } else {
+        const float4 f4 = g4[kNBasis * NS + sl];
+        const float2 fe = make_float2(f4.x, f4.y), fe_lo = make_float2(f4.z, f4.w);
+        float2 vsum = make_float2(0.f, 0.f), adj_x = vsum;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          const float4 tt = lds4(wd + kNBasis + 3 * d);
+          float2 yh = sh, yl = sl_lo;
+          pv::fma_acc(make_float2(tt.x, tt.y), make_float2(tt.z, tt.w), fe, fe_lo, yh, yl);
+          const float2 y = pv::frac(yh, yl);
+          const float* sb = sbin + (size_t)d * kSlotBinFloats * NS;
+          const float4 q0 = reinterpret_cast<const float4*>(sb)[sl], q1 = reinterpret_cast<const float4*>(sb)[NS + sl];
+          const float2 q2 = reinterpret_cast<const float2*>(sb + 8 * NS)[sl];
+          const float2 bt[5] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y),
+                                make_float2(q1.z, q1.w), q2};
+          pv::det_edge_slot<GRAD>(y, lds4(wd + kNBasis + 3 * d + 1), lds4(wd + kNBasis + 3 * d + 2), bt, lane, fe, vsum,
+                                  adj_x, adj_tau[d], adj_rr[d], adj_ri[d]);
+        }
+        pv::add_acc(acc, acc_lo, vsum);
+        if (GRAD) {
+#pragma unroll
+          for (int k = 0; k < kNBasis; ++k) {
+            const float4 g = g4[k * NS + sl];
+            adj_c[k] = pv::fma(adj_x, make_float2(g.x, g.y), adj_c[k]);
+          }
+        }
+      }
+      lh = acc.x;
+      ll = acc_lo.x;
+      ff_add(lh, ll, acc.y, acc_lo.y);
+#pragma unroll
+      for (int k = 0; k < kNBasis; ++k) v[k] = __fadd_rn(adj_c[k].x, adj_c[k].y);
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        v[kNBasis + d] = __fadd_rn(adj_tau[d].x, adj_tau[d].y);
+        v[kNBasis + D + d] = __fadd_rn(adj_rr[d].x, adj_rr[d].y);
+        v[kNBasis + 2 * D + d] = __fadd_rn(adj_ri[d].x, adj_ri[d].y);
+      }
+    } else {
+      // FP64 phase: one edge per lane, lane l of chunk c at edge 31 c + l
+      P.acc = P.acc_lo = P.adj_tau = P.adj_rr = P.adj_ri = make_float2(0.f, 0.f);
+      S.acc = S.acc_lo = S.adj_tau = S.adj_rr = S.adj_ri = 0.f;
+      float2 adj_c[kNBasis / 2];
+#pragma unroll
+      for (int q = 0; q < kNBasis / 2; ++q) adj_c[q] = make_float2(0.f, 0.f);
+
+      for (int c0 = 0; c0 < B; c0 += 31) {
+        const int e = c0 + lane;
+        const bool has_edge = e < E;
+        const bool has_bin = (lane < 31) && (e < B);
+        const int ee = RB_IDX(has_edge ? e : E - 1, Ep, 102);
+        const int eb = RB_IDX(has_bin ? e : 0, Bp, 103);
+        double x64 = 0.0;
 #pragma unroll
         for (int k = 0; k < kNBasis; ++k) x64 = ::fma(dc64[k], g64[k * Ep + ee], x64);
-        fe = (float)f64[ee];
-        xh = xl = 0.f;
-      }
+        const float fe = (float)f64[ee];
 
-      float adj_x = 0.f;
-      if constexpr (paired) {
-        const float4 rr = lds4(wc + 6), ss = lds4(wc + 7);
-        P.rho_r = make_float2(rr.x, rr.y); P.rho_i = make_float2(rr.z, rr.w);
-        P.sig_r = make_float2(ss.x, ss.y); P.sig_i = make_float2(ss.z, ss.w);
-        float2 y;
-        if (!PHASE64) {
-          const float4 tt = lds4(wc + 5);
-          float2 yh = make_float2(xh, xh), yl = make_float2(xl, xl);
-          pv::fma_acc(make_float2(tt.x, tt.y), make_float2(tt.z, tt.w), make_float2(fe, fe), make_float2(fe_lo, fe_lo), yh, yl);
-          y = pv::frac(yh, yl);
-        } else {
+        float adj_x = 0.f;
+        if constexpr (paired) {
+          const float4 rr = lds4(wc + 6), ss = lds4(wc + 7);
+          P.rho_r = make_float2(rr.x, rr.y); P.rho_i = make_float2(rr.z, rr.w);
+          P.sig_r = make_float2(ss.x, ss.y); P.sig_i = make_float2(ss.z, ss.w);
           const double x0 = ::fma(f64[ee], tau64[0], x64), x1 = ::fma(f64[ee], tau64[1], x64);
-          y = make_float2((float)(x0 - rint(x0)), (float)(x1 - rint(x1)));
+          const float2 y = make_float2((float)(x0 - rint(x0)), (float)(x1 - rint(x1)));
+          const float4 q0 = binP[eb], q1 = binP[Bp + eb], q2 = binP[2 * Bp + eb];
+          const float2 bt[6] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y),
+                                make_float2(q1.z, q1.w), make_float2(q2.x, q2.y), make_float2(q2.z, q2.w)};
+          const float2 g = pv::det_edge<GRAD>(y, P, bt, has_bin, has_edge, lane, make_float2(fe, fe));
+          adj_x = __fadd_rn(g.x, g.y);
         }
-        const float4 q0 = binP[eb], q1 = binP[Bp + eb], q2 = binP[2 * Bp + eb];
-        const float2 bt[6] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y),
-                              make_float2(q1.z, q1.w), make_float2(q2.x, q2.y), make_float2(q2.z, q2.w)};
-        const float2 g = pv::det_edge<GRAD>(y, P, bt, has_bin, has_edge, lane, make_float2(fe, fe));
-        adj_x = __fadd_rn(g.x, g.y);
-      }
-      if constexpr (ds >= 0) {
-        const float4 rs = lds4(wc + 9);
-        S.rho_r = rs.x; S.rho_i = rs.y; S.sig_r = rs.z; S.sig_i = rs.w;
-        float y;
-        if (!PHASE64) {
-          const float4 tt = lds4(wc + 8);
-          float yh = xh, yl = xl;
-          pv::fma_acc(tt.x, tt.y, fe, fe_lo, yh, yl);
-          y = pv::frac(yh, yl);
-        } else {
+        if constexpr (ds >= 0) {
+          const float4 rs = lds4(wc + 9);
+          S.rho_r = rs.x; S.rho_i = rs.y; S.sig_r = rs.z; S.sig_i = rs.w;
           const double xd = ::fma(f64[ee], tau64[ds], x64);
-          y = (float)(xd - rint(xd));
+          const float y = (float)(xd - rint(xd));
+          const float4 q0 = binS4[eb];
+          const float2 q1 = binS2[eb];
+          const float bt[6] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y};
+          adj_x = __fadd_rn(adj_x, pv::det_edge<GRAD>(y, S, bt, has_bin, has_edge, lane, fe));
         }
-        const float4 q0 = binS4[eb];
-        const float2 q1 = binS2[eb];
-        const float bt[6] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y};
-        adj_x = __fadd_rn(adj_x, pv::det_edge<GRAD>(y, S, bt, has_bin, has_edge, lane, fe));
-      }
-      if (GRAD && has_edge) {
-        const float2 ax = make_float2(adj_x, adj_x);
-        if (!PHASE64) {
-#pragma unroll
-          for (int q = 0; q < kNBasis / 2; ++q) {
-            const float4 g = g4[q * Ep + ee];
-            adj_c[q] = pv::fma(ax, make_float2(g.x, g.y), adj_c[q]);
-          }
-        } else {
+        if (GRAD && has_edge) {
+          const float2 ax = make_float2(adj_x, adj_x);
 #pragma unroll
           for (int q = 0; q < kNBasis / 2; ++q)
             adj_c[q] = pv::fma(ax, make_float2((float)g64[2 * q * Ep + ee], (float)g64[(2 * q + 1) * Ep + ee]),
                                adj_c[q]);
         }
       }
-    }
-
-    // the walker's sum as a float pair (FP32 pipe); FP64 only for the result
-    float lh = S.acc, ll = S.acc_lo;
-    if constexpr (paired) {
-      ff_add(lh, ll, P.acc.x, P.acc_lo.x);
-      ff_add(lh, ll, P.acc.y, P.acc_lo.y);
-    }
-    warp_sum_ff(lh, ll);
-    const double logl = base_logl + ((double)lh + (double)ll);
-    if (!MALA && lane == 0) a.logl[RB_IDX(w, a.W, 105)] = logl;
-    if (GRAD) {
-      const float two_pi = 6.28318530717958648f;
-      // the walker's adjoint sums (basis coefficients, then per detector the
-      // delay and the prefactor ratio re/im) by one transposed warp sum
-      constexpr int kNV = kNBasis + 3 * D;
-      float v[kNV];
+      lh = S.acc;
+      ll = S.acc_lo;
+      if constexpr (paired) {
+        ff_add(lh, ll, P.acc.x, P.acc_lo.x);
+        ff_add(lh, ll, P.acc.y, P.acc_lo.y);
+      }
 #pragma unroll
       for (int q = 0; q < kNBasis / 2; ++q) {
         v[2 * q] = adj_c[q].x;
@@ -625,6 +709,16 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
         v[kNBasis + D + ds] = S.adj_rr;
         v[kNBasis + 2 * D + ds] = S.adj_ri;
       }
+    }
+
+    // the walker's sum as a float pair (FP32 pipe); FP64 only for the result
+    warp_sum_ff(lh, ll);
+    const double logl = base_logl + ((double)lh + (double)ll);
+    if (!MALA && lane == 0) a.logl[RB_IDX(w, a.W, 105)] = logl;
+    if (GRAD) {
+      const float two_pi = 6.28318530717958648f;
+      // the walker's adjoint sums (basis coefficients, then per detector the
+      // delay and the prefactor ratio re/im) by one transposed warp sum
       warp_transposed_sums<kNV>(v, lane, slot->red);
       __syncwarp();
       float ac[kNBasis], at[kMaxDet], ar[kMaxDet][2];
@@ -793,7 +887,7 @@ size_t mixed_smem_slot_bytes() { return (size_t)(kThreads / 32) * sizeof(WarpSlo
 
 size_t mixed_smem_bytes(const EventDev& ev, bool phase64) {
   const size_t wc = (size_t)(kThreads / 32) * sizeof(WarpSlot);
-  if (!phase64) return ev.tab32_floats * sizeof(float) + wc;
+  if (!phase64) return ev.slot32_floats * sizeof(float) + wc;
   return (size_t)(kNBasis + 1) * ev.e_pad * sizeof(double) + (ev.tab32_floats - ev.edge32_floats) * sizeof(float) + wc;
 }
 

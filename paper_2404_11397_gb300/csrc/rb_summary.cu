@@ -161,6 +161,12 @@ __device__ void summary_epilogue(const SummaryOut& so, int b, int d0, int nd, in
         const size_t base = (D >= 2) ? 12 * Bp : 0;
         so.bin32[f < 4 ? base + (size_t)b * 4 + f : base + 4 * Bp + (size_t)b * 2 + (f - 4)] = t32;
       }
+      // slot image: bin b is half h of slot sl (the -beta1 entry is not used)
+      const int it = b / kSlotBins, r = b - kSlotBins * it, h = r >= 32 ? 1 : 0, sl = 32 * it + r - 32 * h;
+      const size_t NS = so.n_slots;
+      float* sb = so.slot_bin32 + (size_t)d * kSlotBinFloats * NS;
+      if (f < 4) sb[((size_t)(f >> 1) * NS + sl) * 4 + (f & 1) * 2 + h] = t32;
+      else if (f == 4) sb[8 * NS + (size_t)sl * 2 + h] = t32;
     }
     const double b0 = __shfl_sync(0xffffffffu, o, (6 * g + 4) & 31);
     const double sh = (mine && f == 0) ? o - 0.5 * b0 : 0.0;
@@ -273,26 +279,32 @@ __global__ void __launch_bounds__(kSumThreads) k_summary(DataPtrs in, int64_t km
 
 // ---------------------------------------------------------------------------
 // Event-constant edge tables (built once per event): g_k(f_e) / 2pi as float
-// pairs and FP64, f_e, and 1 / df_b per bin; pad entries are zero.
+// pairs and FP64, f_e, and 1 / df_b per bin; pad entries are zero.  The same
+// values go to the edge part of the slot image (layout in EventDev).
 // ---------------------------------------------------------------------------
+// g_k(f_e) / 2pi and f_e of edge e (zero past the last edge).
+__device__ void edge_basis(int64_t kmin, double T, int E, const int64_t* __restrict__ edges, int e, double (&g)[kNBasis],
+                           double& f) {
+  f = 0.0;
+  for (int k = 0; k < kNBasis; ++k) g[k] = 0.0;
+  if (e >= E) return;
+  f = grid_f(kmin, edges[e], T);
+  const double lf = log(f), cf = cbrt(f), icf = 1.0 / cf, icf2 = icf * icf;
+  const double gg[kNBasis] = {icf2 * icf2 * icf, 1.0 / f, icf2, icf, lf, cf, cf * lf, cf * cf, f * cf * cf, f * f * cf};
+  const double inv2pi = 1.0 / kTwoPi;
+  for (int k = 0; k < kNBasis; ++k) g[k] = gg[k] * inv2pi;
+}
+
 __global__ void k_edge_tables(int64_t kmin, double T, int D, int B, int Ep, int Bp,
                               const int64_t* __restrict__ edges, float* __restrict__ tab32, size_t edge32_floats,
-                              double* __restrict__ tab64, double* __restrict__ inv_df) {
+                              double* __restrict__ tab64, double* __restrict__ inv_df, float* __restrict__ slot32,
+                              int NS) {
   const int E = B + 1;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
-  const double inv2pi = 1.0 / kTwoPi;
   for (int e = tid; e < Ep; e += nth) {
-    double g[kNBasis], f = 0.0;
-    if (e < E) {
-      f = grid_f(kmin, edges[e], T);
-      const double lf = log(f), cf = cbrt(f), icf = 1.0 / cf, icf2 = icf * icf;
-      const double gg[kNBasis] = {icf2 * icf2 * icf, 1.0 / f, icf2, icf, lf, cf, cf * lf, cf * cf, f * cf * cf,
-                                  f * f * cf};
-      for (int k = 0; k < kNBasis; ++k) g[k] = gg[k] * inv2pi;
-    } else {
-      for (int k = 0; k < kNBasis; ++k) g[k] = 0.0;
-    }
+    double g[kNBasis], f;
+    edge_basis(kmin, T, E, edges, e, g, f);
     float4* t4 = reinterpret_cast<float4*>(tab32);  // [kEdgeQuads][Ep]
     for (int q = 0; q < kNBasis / 2; ++q) {
       tab64[(size_t)(2 * q) * Ep + e] = g[2 * q];
@@ -304,6 +316,18 @@ __global__ void k_edge_tables(int64_t kmin, double T, int D, int B, int Ep, int 
     const f2x fp = f2x_from(f);
     t4[(size_t)(kEdgeQuads - 1) * Ep + e] = make_float4(fp.hi, fp.lo, 0.f, 0.f);
   }
+  // slot image, edge part: slot s = 32 i + l, half h holds edge 63 i + 32 h + l
+  for (int t = tid; t < 2 * NS; t += nth) {
+    const int sl = t >> 1, h = t & 1;
+    const int e = kSlotBins * (sl >> 5) + 32 * h + (sl & 31);
+    double g[kNBasis], f;
+    edge_basis(kmin, T, E, edges, e, g, f);
+    for (int k = 0; k <= kNBasis; ++k) {
+      const f2x v = f2x_from(k < kNBasis ? g[k] : f);
+      slot32[((size_t)k * NS + sl) * 4 + h] = v.hi;
+      slot32[((size_t)k * NS + sl) * 4 + 2 + h] = v.lo;
+    }
+  }
   for (int b = tid; b < B; b += nth) inv_df[b] = T / (double)(edges[b + 1] - edges[b]);
   // bin tables: zero the padding once (the summary kernels write b < B)
   double* bin64 = tab64 + (size_t)(kNBasis + 1) * Ep;
@@ -312,6 +336,8 @@ __global__ void k_edge_tables(int64_t kmin, double T, int D, int B, int Ep, int 
     bin64[i] = 0.0;
     bin32[i] = 0.f;
   }
+  float* slot_bins = slot32 + (size_t)4 * (kNBasis + 1) * NS;
+  for (int i = tid; i < D * kSlotBinFloats * NS; i += nth) slot_bins[i] = 0.f;
 }
 
 // Detector strain for one source on a grid (FP64).
@@ -475,8 +501,9 @@ cudaError_t launch_summary_stored(const DataPtrs& in, const double* h0, int64_t 
 }
 
 cudaError_t launch_edge_tables(int64_t kmin, double T, int D, int B, int Ep, int Bp, const int64_t* edges,
-                               float* tab32, size_t edge32_floats, double* tab64, double* inv_df, cudaStream_t s) {
-  k_edge_tables<<<16, 256, 0, s>>>(kmin, T, D, B, Ep, Bp, edges, tab32, edge32_floats, tab64, inv_df);
+                               float* tab32, size_t edge32_floats, double* tab64, double* inv_df, float* slot32,
+                               int n_slots, cudaStream_t s) {
+  k_edge_tables<<<16, 256, 0, s>>>(kmin, T, D, B, Ep, Bp, edges, tab32, edge32_floats, tab64, inv_df, slot32, n_slots);
   return cudaGetLastError();
 }
 
