@@ -36,7 +36,7 @@ constexpr int kNTanIntr = 6;  // Mc, q, chi1, chi2, Lambda1, Lambda2
 // the next iteration's e_A), as the two halves of one paired FP32 value.
 // Slot s = 32 i + l.
 constexpr int kSlotBins = 63;        // bins per iteration
-constexpr int kSlotBinFloats = 10;   // bin-table floats per slot and detector
+constexpr int kSlotBinFloats = 12;   // bin-table floats per slot and detector
 __host__ __device__ constexpr int slot_count(int n_bins) { return 32 * ((n_bins + kSlotBins - 1) / kSlotBins); }
 
 constexpr double kPi = 3.141592653589793238462643383279502884;
@@ -206,9 +206,12 @@ struct EventDev {
   //   edge part, float4 [kNBasis + 1][NS]: quad k < kNBasis holds
   //     {g_hi_k(e_A), g_hi_k(e_B), g_lo_k(e_A), g_lo_k(e_B)}, quad kNBasis
   //     {f_hi(e_A), f_hi(e_B), f_lo(e_A), f_lo(e_B)};
-  //   bin part, per detector d (kSlotBinFloats * NS floats): float4 [2][NS]
-  //     {a0r_A, a0r_B, a0i_A, a0i_B}, {a1r_A, a1r_B, a1i_A, a1i_B}, then
-  //     float2 [NS] {-b0_A, -b0_B};
+  //   bin part, per detector d (kSlotBinFloats * NS floats), the bin's
+  //     coefficients of its left and right edge values: float4 [3][NS]
+  //     {gmr_A, gmr_B, gpr_A, gpr_B}, {gmi_A, gmi_B, gpi_A, gpi_B},
+  //     {h_A, h_B, q_A, q_B} with gmr = a0r - b0 - a1r, gpr = a0r - b0 + a1r,
+  //     gmi = a0i - a1i, gpi = a0i + a1i, h = -b0/2, q = -b0/4 (a = alpha,
+  //     b = beta of the float image above);
   //   zero for edges past the last and where an edge has no bin.
   const float* slot32;
   size_t slot32_floats;  // multiple of 4

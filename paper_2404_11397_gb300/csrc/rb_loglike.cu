@@ -103,6 +103,18 @@ __device__ __forceinline__ void prefetch_walker(WarpSlot* slot, int buf, const v
   cp_async_commit();
 }
 
+// Exact float -> double conversion on the integer pipe: an SMSP's FP64 unit
+// takes ~65 clocks per warp instruction, conversions included, and the warps
+// of a block reach their epilogues together.  Normal numbers: the exponent
+// rebiased by 1023 - 127 and the mantissa moved up 29 bits; zero, subnormals,
+// infinities and NaN take the regular conversion.
+__device__ __forceinline__ double f2d_int(float x) {
+  const unsigned u = __float_as_uint(x), m = u & 0x7fffffffu;
+  if (m - 0x00800000u < 0x7f000000u)
+    return __hiloint2double((int)((u & 0x80000000u) | ((m >> 3) + 0x38000000u)), (int)(m << 29));
+  return (double)x;
+}
+
 // Float-pair warp sum: (h, l) on entry is a lane's value as an unevaluated
 // sum; every lane returns the warp total (two-sum of the high parts, the low
 // parts added, renormalised at each step), all on the FP32 pipe.
@@ -360,8 +372,15 @@ __device__ __forceinline__ V det_edge(V y, DetState<V>& st, const V* bt, bool ha
 // of the previous one).  Edges without a bin, and slots past the last
 // edge, have zero tables, so they add nothing.  vsum collects the bin terms
 // of log L, adj_x d log L / dy (times 1/2pi) for the basis adjoint.
+// The bin's term in the coefficients of its edge values (q0 = {gmr, gpr},
+// q1 = {gmi, gpi}, q2 = {h, q} of the slot image): with d = delta at the
+// left edge and n at the right one,
+//   Re(alpha0 s*) + Re(alpha1 t*) - beta0 (Re s + |s|^2/4)
+//     = gmr dr + gpr nr + gmi di + gpi ni + q |s|^2,
+// and the cotangents of the left and right edge values are
+//   (gmr + h sr, gmi + h si) and (gpr + h sr, gpi + h si).
 template <bool GRAD>
-__device__ __forceinline__ void det_edge_slot(float2 y, float4 rho, float4 sig, const float2 (&bt)[5], int lane,
+__device__ __forceinline__ void det_edge_slot(float2 y, float4 rho, float4 sig, const float2 (&bt)[6], int lane,
                                               float2 fe, float2& vsum, float2& adj_x, float2& adj_tau, float2& adj_rr,
                                               float2& adj_ri) {
   const float2 rho_r = make_float2(rho.x, rho.y), rho_i = make_float2(rho.z, rho.w);
@@ -376,20 +395,18 @@ __device__ __forceinline__ void det_edge_slot(float2 y, float4 rho, float4 sig, 
   const float nrA = __shfl_sync(0xffffffffu, dr.x, up), nrB = __shfl_sync(0xffffffffu, dr.y, up);
   const float niA = __shfl_sync(0xffffffffu, di.x, up), niB = __shfl_sync(0xffffffffu, di.y, up);
   const float2 nr = make_float2(lane == 31 ? nrB : nrA, nrB), ni = make_float2(lane == 31 ? niB : niA, niB);
-  // bt: alpha0 (re, im), alpha1 (re, im), -beta0 (the beta1 term vanishes
-  // for a ratio of constant modulus)
-  const float2 sr = add(dr, nr), si = add(di, ni), tr = sub(nr, dr), ti = sub(ni, di);
-  float2 v = mul(bt[0], sr);
-  v = fma(bt[1], si, v);
-  v = fma(bt[2], tr, v);
-  v = fma(bt[3], ti, v);
-  v = fma(bt[4], fma(splat<float2>(0.25f), fma(sr, sr, mul(si, si)), sr), v);
+  // bt: gmr, gpr, gmi, gpi, h, q (the beta1 term vanishes for a ratio of
+  // constant modulus)
+  const float2 sr = add(dr, nr), si = add(di, ni);
+  float2 v = mul(bt[0], dr);
+  v = fma(bt[1], nr, v);
+  v = fma(bt[2], di, v);
+  v = fma(bt[3], ni, v);
+  v = fma(bt[5], fma(sr, sr, mul(si, si)), v);
   vsum = add(vsum, v);
   if (GRAD) {
-    const float2 hs_r = fma(splat<float2>(0.5f), sr, splat<float2>(1.f)), hs_i = mul(splat<float2>(0.5f), si);  // 1 + s/2
-    const float2 Ur = fma(bt[4], hs_r, bt[0]), Ui = fma(bt[4], hs_i, bt[1]);
-    float2 gr = sub(Ur, bt[2]), gi = sub(Ui, bt[3]);  // own bin (edge on its left)
-    const float2 pr = add(Ur, bt[2]), pi = add(Ui, bt[3]);  // U + V: the bin's right edge
+    float2 gr = fma(bt[4], sr, bt[0]), gi = fma(bt[4], si, bt[2]);  // own bin (edge on its left)
+    const float2 pr = fma(bt[4], sr, bt[1]), pi = fma(bt[4], si, bt[3]);  // the bin's right edge
     const float lrA = __shfl_sync(0xffffffffu, pr.x, dn), lrB = __shfl_sync(0xffffffffu, pr.y, dn);
     const float liA = __shfl_sync(0xffffffffu, pi.x, dn), liB = __shfl_sync(0xffffffffu, pi.y, dn);
     gr = add(gr, make_float2(lane == 0 ? 0.f : lrA, lane == 0 ? lrA : lrB));
@@ -607,21 +624,20 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
           float2 yh = sh, yl = sl_lo;
           pv::fma_acc(make_float2(tt.x, tt.y), make_float2(tt.z, tt.w), fe, fe_lo, yh, yl);
           const float2 y = pv::frac(yh, yl);
-          const float* sb = sbin + (size_t)d * kSlotBinFloats * NS;
-          const float4 q0 = reinterpret_cast<const float4*>(sb)[sl], q1 = reinterpret_cast<const float4*>(sb)[NS + sl];
-          const float2 q2 = reinterpret_cast<const float2*>(sb + 8 * NS)[sl];
-          const float2 bt[5] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y),
-                                make_float2(q1.z, q1.w), q2};
+          const float4* sb = reinterpret_cast<const float4*>(sbin + (size_t)d * kSlotBinFloats * NS);
+          const float4 q0 = sb[sl], q1 = sb[NS + sl], q2 = sb[2 * NS + sl];
+          const float2 bt[6] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y),
+                                make_float2(q1.z, q1.w), make_float2(q2.x, q2.y), make_float2(q2.z, q2.w)};
           pv::det_edge_slot<GRAD>(y, lds4(wd + kNBasis + 3 * d + 1), lds4(wd + kNBasis + 3 * d + 2), bt, lane, fe, vsum,
                                   adj_x, adj_tau[d], adj_rr[d], adj_ri[d]);
         }
         pv::add_acc(acc, acc_lo, vsum);
         if (GRAD) {
+          // the high halves only: 8-byte loads (shared-memory bandwidth is
+          // about as busy as the FMA pipe in this loop)
+          const float2* g2 = reinterpret_cast<const float2*>(g4);
 #pragma unroll
-          for (int k = 0; k < kNBasis; ++k) {
-            const float4 g = g4[k * NS + sl];
-            adj_c[k] = pv::fma(adj_x, make_float2(g.x, g.y), adj_c[k]);
-          }
+          for (int k = 0; k < kNBasis; ++k) adj_c[k] = pv::fma(adj_x, g2[2 * (k * NS + sl)], adj_c[k]);
         }
       }
       lh = acc.x;
@@ -713,7 +729,7 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
 
     // the walker's sum as a float pair (FP32 pipe); FP64 only for the result
     warp_sum_ff(lh, ll);
-    const double logl = base_logl + ((double)lh + (double)ll);
+    const double logl = base_logl + (f2d_int(lh) + f2d_int(ll));
     if (!MALA && lane == 0) a.logl[RB_IDX(w, a.W, 105)] = logl;
     if (GRAD) {
       const float two_pi = 6.28318530717958648f;
@@ -740,7 +756,7 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
       double g = 0.0;
       if (lane < kNPar) {
         const WalkerTan<float>& tn = *reinterpret_cast<const WalkerTan<float>*>(slot->tan[buf]);  // prefetched
-        g = (double)chain_rule_lanes<D>(lane, ac, at, ar, rho, tn);
+        g = f2d_int(chain_rule_lanes<D>(lane, ac, at, ar, rho, tn));
       }
       if (MALA) mala_finish(a.mala, w, lane, logl, g);
       else if (lane < kNPar) a.grad[RB_IDX(w * kNPar + lane, a.W * kNPar, 106)] = g;

@@ -138,7 +138,7 @@ __device__ void summary_epilogue(const SummaryOut& so, int b, int d0, int nd, in
     const int j = threadIdx.x;
     const int g = j / 6, f = j - 6 * g, d = d0 + g;
     const bool mine = j < 6 * nd;
-    double o = 0.0;
+    double o = 0.0, t = 0.0;
     if (mine) {
       o = sblock[j];
       if (scaled_form) {
@@ -150,7 +150,7 @@ __device__ void summary_epilogue(const SummaryOut& so, int b, int d0, int nd, in
         else o = sc[1] * (Kr * Kr + Ki * Ki) * o;
       }
       so.summ[((size_t)d * B + b) * 6 + f] = o;
-      const double t = (f == 2 || f == 3 || f == 5) ? o * inv_df_b : 0.5 * o;
+      t = (f == 2 || f == 3 || f == 5) ? o * inv_df_b : 0.5 * o;
       so.bin64[((size_t)d * 6 + f) * so.Bp + b] = t;
       // float image (layout in EventDev), with beta0 and beta1 negated
       const float t32 = (float)(f >= 4 ? -t : t);
@@ -161,12 +161,22 @@ __device__ void summary_epilogue(const SummaryOut& so, int b, int d0, int nd, in
         const size_t base = (D >= 2) ? 12 * Bp : 0;
         so.bin32[f < 4 ? base + (size_t)b * 4 + f : base + 4 * Bp + (size_t)b * 2 + (f - 4)] = t32;
       }
-      // slot image: bin b is half h of slot sl (the -beta1 entry is not used)
-      const int it = b / kSlotBins, r = b - kSlotBins * it, h = r >= 32 ? 1 : 0, sl = 32 * it + r - 32 * h;
-      const size_t NS = so.n_slots;
-      float* sb = so.slot_bin32 + (size_t)d * kSlotBinFloats * NS;
-      if (f < 4) sb[((size_t)(f >> 1) * NS + sl) * 4 + (f & 1) * 2 + h] = t32;
-      else if (f == 4) sb[8 * NS + (size_t)sl * 2 + h] = t32;
+    }
+    // slot image: bin b is half h of slot sl; lane 6 g + m (m < 6) of the
+    // detector's six lanes writes entry m of {gmr, gpr, gmi, gpi, h, q}
+    {
+      double tv[5];
+#pragma unroll
+      for (int m = 0; m < 5; ++m) tv[m] = __shfl_sync(0xffffffffu, t, (6 * g + m) & 31);
+      if (mine) {
+        const double a0r = tv[0], a0i = tv[1], a1r = tv[2], a1i = tv[3], b0 = tv[4];
+        const double val = f == 0 ? a0r - b0 - a1r : f == 1 ? a0r - b0 + a1r : f == 2 ? a0i - a1i
+                         : f == 3 ? a0i + a1i : f == 4 ? -0.5 * b0 : -0.25 * b0;
+        const int it = b / kSlotBins, r = b - kSlotBins * it, h = r >= 32 ? 1 : 0, sl = 32 * it + r - 32 * h;
+        const size_t NS = so.n_slots;
+        float* sb = so.slot_bin32 + (size_t)d * kSlotBinFloats * NS;
+        sb[((size_t)(f >> 1) * NS + sl) * 4 + (f & 1) * 2 + h] = (float)val;
+      }
     }
     const double b0 = __shfl_sync(0xffffffffu, o, (6 * g + 4) & 31);
     const double sh = (mine && f == 0) ? o - 0.5 * b0 : 0.0;
