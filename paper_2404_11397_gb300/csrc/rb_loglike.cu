@@ -932,12 +932,16 @@ static cudaError_t blocks_per_sm(const void* fn, int threads, size_t smem, int* 
   bool raised = false;
   for (int i = 0; i < g_smem_raised_n; ++i) raised = raised || g_smem_raised[i] == fn;
   if (!raised) {
-    // allow any dynamic shared-memory size up to the device limit once, so
-    // that launches for different events never shrink it for one another
+    // allow any dynamic shared-memory size up to the device limit (less the
+    // kernel's static shared memory) once, so that launches for different
+    // events never shrink it for one another
     int dev = 0, smem_max = 0;
+    cudaFuncAttributes fa{};
     err = cudaGetDevice(&dev);
     if (err == cudaSuccess) err = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (err == cudaSuccess) err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+    if (err == cudaSuccess) err = cudaFuncGetAttributes(&fa, fn);
+    if (err == cudaSuccess)
+      err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max - (int)fa.sharedSizeBytes);
     if (err != cudaSuccess) return err;
     if (g_smem_raised_n < 16) g_smem_raised[g_smem_raised_n++] = fn;
   }
