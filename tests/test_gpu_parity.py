@@ -106,13 +106,14 @@ def c2(rb):
 
 @pytest.fixture(scope="module")
 def small(rb):
-    # a few thousand grid points, 3 detectors, 45 bins (several 31-bin chunks + a ragged tail)
+    # a few thousand grid points, 3 detectors, 45 bins (one ragged 63-bin iteration of the
+    # float-float kernel, two 31-bin chunks of the FP64-phase kernel)
     return Case(rb, "C2", n_bins=45, T=8.0, f_low=20.0, f_high=512.0)
 
 
 @pytest.fixture(scope="module")
 def two(rb):
-    # two detectors: the pair-only layout of the mixed kernel's bin tables
+    # two detectors: no odd detector (the FP64-phase kernel's pair-only bin tables)
     return Case(rb, "C2", n_bins=150, T=32.0, sites=("H1", "L1"))
 
 
