@@ -444,6 +444,19 @@ int rb_build_summary(const rb_event_desc* desc, rb_event_t* out) {
     e.dev.slot32 = e.d_slot32;
     e.dev.slot32_floats = slot32;
     e.dev.n_slots = NS;
+    {
+      // each |g_k| is largest at an end of the grid (the powers are monotonic,
+      // |ln f| and |f^1/3 ln f| quasi-convex); 1 % added
+      const double fe[2] = {(double)kmin / e.T, (double)(kmin + N - 1) / e.T};
+      double gm[kNBasis + 1] = {};
+      for (double f : fe) {
+        const double lf = std::log(f), cf = std::cbrt(f);
+        const double g[kNBasis + 1] = {std::pow(f, -5.0 / 3.0), 1.0 / f, std::pow(f, -2.0 / 3.0), 1.0 / cf, lf, cf,
+                                       cf * lf, cf * cf, f * cf * cf, f * f * cf, f * kTwoPi};
+        for (int k = 0; k <= kNBasis; ++k) gm[k] = std::max(gm[k], std::fabs(g[k]) / kTwoPi);
+      }
+      for (int k = 0; k <= kNBasis; ++k) e.dev.gmax[k] = (float)(1.01 * gm[k]);
+    }
     e.dev.tab64 = e.d_tab64;
     e.dev.ref = e.d_ref;
     const cudaMemcpyKind kind = desc->data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;

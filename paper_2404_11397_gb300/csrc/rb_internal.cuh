@@ -216,6 +216,9 @@ struct EventDev {
   const float* slot32;
   size_t slot32_floats;  // multiple of 4
   int n_slots;           // NS
+  // upper bounds of |g_k(f) / 2pi| (k < kNBasis) and of f over the event's
+  // grid: the mixed kernel's per-walker bound on its phase terms
+  float gmax[kNBasis + 1];
   // FP64 tables: g[k][e] (10*Ep), f[e] (Ep), then per detector 6 rows of Bp
   const double* tab64;
   const RefValues* ref;
@@ -486,6 +489,21 @@ __device__ __forceinline__ void fma_acc(V a_hi, V a_lo, V b_hi, V b_lo, V& s_hi,
   const V err = add(sub(s_hi, sub(s, bb)), sub(p, bb));
   s_hi = s;
   s_lo = add(s_lo, add(err, e));
+}
+
+// H + L += (a_hi + a_lo)(b_hi + b_lo) with H kept exact: m = 1.5 * 2^23 q for a
+// power of two q, and |a_hi b_hi| < 2^22 q.  One FMA against m rounds the
+// product's high part to a multiple h of q (the sum lands in m's binade, whose
+// ulp is q); the multiples add exactly while |H| < 2^24 q.  The remainder
+// a_hi b_hi - h (|.| <= q/2, rounded once) and the cross terms go to L.  The
+// low-by-low term (~2^-48 of the product) is dropped.
+template <class V>
+__device__ __forceinline__ void split_acc(V a_hi, V a_lo, V b_hi, V b_lo, V m, V& H, V& L) {
+  const V h = sub(fma(a_hi, b_hi, m), m);
+  H = add(H, h);
+  L = add(L, fma(a_hi, b_hi, neg(h)));
+  L = fma(a_hi, b_lo, L);
+  L = fma(a_lo, b_hi, L);
 }
 
 // hi + lo in turns with the whole turns of hi removed: hi - rint(hi) is

@@ -81,8 +81,9 @@ struct __align__(16) WarpSlot {
   // the current walker's constants, each value in both halves of a pair
   // (float-float path): {hi, hi, lo, lo} of dc_k (k < kNBasis), then per
   // detector {tau_hi, tau_hi, tau_lo, tau_lo}, {rho_r, rho_r, rho_i, rho_i},
-  // {sig_r, sig_r, sig_i, sig_i}
-  float4 dup[kNBasis + 3 * kMaxDet];
+  // {sig_r, sig_r, sig_i, sig_i}, and last the walker's rounding constant m
+  // of the phase sums (split_acc) in all four
+  float4 dup[kNBasis + 3 * kMaxDet + 1];
 };
 static_assert(sizeof(WalkerMixed) % 16 == 0, "record copied in 16-byte pieces");
 static_assert(sizeof(WalkerTan<float>) <= kTanBytes && sizeof(WalkerTan<float>) % 8 == 0, "tangent buffer");
@@ -528,12 +529,14 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
       // each constant in both halves of a pair (the slot loop's operands):
       // lane k < kNBasis takes dc_k, lane kNBasis + 3 d + m the delay (m = 0),
       // prefactor ratio (1) or its difference from 1 (2) of detector d
+      float mag = 0.f;  // the lane's bound on |its phase term| [turns]
       if (lane < kNBasis + 3 * D) {
         const float* f = reinterpret_cast<const float*>(wc);
-        int iu, iv;
+        int iu, iv, gk = -1;
         if (lane < kNBasis) {
           iu = wm_dc_hi(lane);
           iv = wm_dc_lo(lane);
+          gk = lane;
         } else {
           const int j = lane - kNBasis, d = j / 3, m = j - 3 * d;
           if (d == ds) {
@@ -542,9 +545,22 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
             iu = (m == 0 ? kWmTauPair : (m == 1 ? kWmRhoPair : kWmSigPair)) + d;
           }
           iv = iu + (d == ds ? 1 : 2);
+          if (m == 0) gk = kNBasis;
         }
         const float u = f[iu], v = f[iv];
         slot->dup[lane] = make_float4(u, u, v, v);
+        if (gk >= 0) mag = fabsf(u) * ev.gmax[gk];
+      }
+      // the walker's rounding constant m = 1.5 * 2^23 q with q = 2^-20 of a
+      // power of two above every phase term (at least 2^-62 turns): then each
+      // product's high part is below 2^22 q, and the eleven of a detector's
+      // phase (ten basis terms and the delay) add to less than 2^24 q
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mag = fmaxf(mag, __shfl_xor_sync(0xffffffffu, mag, o));
+      const unsigned ex = min(max((__float_as_uint(mag) >> 23) & 0xffu, 64u), 250u);  // mag < 2^(ex - 126)
+      if (lane == 0) {
+        const float m = __uint_as_float(((ex + 4u) << 23) | 0x400000u);  // 1.5 * 2^(ex - 123)
+        slot->dup[kNBasis + 3 * kMaxDet] = make_float4(m, m, m, m);
       }
     } else {
       float rho[kMaxDet][2], sg[kMaxDet][2];
@@ -606,14 +622,18 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
       for (int d = 0; d < D; ++d) adj_tau[d] = adj_rr[d] = adj_ri[d] = make_float2(0.f, 0.f);
       for (int s0 = 0; s0 < NS; s0 += 32) {
         const int sl = RB_IDX(s0 + lane, NS, 102);
-        // detector-independent phase sum_k dc_k g_k(f_e) / 2pi [turns] of the two edges
+        // detector-independent phase sum_k dc_k g_k(f_e) / 2pi [turns] of the
+        // two edges, as an exact sum of multiples of the walker's q (sh) and a
+        // small remainder (sl_lo)
+        const float4 mq = lds4(wd + kNBasis + 3 * kMaxDet);
+        const float2 m2 = make_float2(mq.x, mq.y);
         float2 sh = make_float2(0.f, 0.f), sl_lo = sh;
 #pragma unroll
         for (int k = 0; k < kNBasis; ++k) {
           const float4 g = g4[k * NS + sl];  // {g_hi(e_A), g_hi(e_B), g_lo(e_A), g_lo(e_B)}
           const float4 c = lds4(wd + k);     // {dc_hi, dc_hi, dc_lo, dc_lo}
-          pv::fma_acc(make_float2(c.x, c.y), make_float2(c.z, c.w), make_float2(g.x, g.y), make_float2(g.z, g.w), sh,
-                      sl_lo);
+          pv::split_acc(make_float2(c.x, c.y), make_float2(c.z, c.w), make_float2(g.x, g.y), make_float2(g.z, g.w), m2, sh,
+                        sl_lo);
         }
         const float4 f4 = g4[kNBasis * NS + sl];
         const float2 fe = make_float2(f4.x, f4.y), fe_lo = make_float2(f4.z, f4.w);
@@ -622,7 +642,7 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
         for (int d = 0; d < D; ++d) {
           const float4 tt = lds4(wd + kNBasis + 3 * d);
           float2 yh = sh, yl = sl_lo;
-          pv::fma_acc(make_float2(tt.x, tt.y), make_float2(tt.z, tt.w), fe, fe_lo, yh, yl);
+          pv::split_acc(make_float2(tt.x, tt.y), make_float2(tt.z, tt.w), fe, fe_lo, m2, yh, yl);
           const float2 y = pv::frac(yh, yl);
           const float4* sb = reinterpret_cast<const float4*>(sbin + (size_t)d * kSlotBinFloats * NS);
           const float4 q0 = sb[sl], q1 = sb[NS + sl], q2 = sb[2 * NS + sl];
