@@ -194,12 +194,13 @@ def algorithmic_work(D: int, B: int, grad: bool) -> dict:
 # per (bin, detector) for the contraction; the gradient adds 16 D B + 17 D E + 20 E.
 def impl_flops_per_walker(D: int, B: int, grad: bool) -> int:
     # FP32 flops the mixed kernel spends per walker (FMA = 2): per edge the
-    # float-float phase sum (15 per basis term); per edge and detector the
-    # float-float delay term and reduction to [-1/2, 1/2] (19), sin/cos (30),
-    # the ratio and the bin's term (26); with the gradient the edge
-    # cotangents and adjoint sums (26 per edge and detector, 20 per edge)
+    # float-pair phase sum (11 per basis term: high part rounded to the
+    # walker's quantum, exact high sum, low sum); per edge and detector the
+    # delay term and reduction to [-1/2, 1/2] (15), sin/cos (30), the ratio and
+    # the bin's term (26); with the gradient the edge cotangents and adjoint
+    # sums (26 per edge and detector, 20 per edge)
     E = B + 1
-    f = E * 150 + D * E * 75
+    f = E * 110 + D * E * 71
     if grad:
         f += D * E * 26 + E * 20
     return f
@@ -208,7 +209,7 @@ def impl_flops_per_walker(D: int, B: int, grad: bool) -> int:
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the main kernel on this workload, from an ncu capture of this kernel version
 # (None once the kernel changes and until it is captured again).
-MAIN_KERNEL_TRAFFIC_BYTES = 2382592
+MAIN_KERNEL_TRAFFIC_BYTES = None
 
 
 # Algorithmic FP32 flops of the full-grid sum per (walker, grid point) with 3
