@@ -31,10 +31,10 @@ static_assert(kNBasis % 2 == 0, "basis pairs per float4 of the edge tables");
 constexpr int kNTanIntr = 6;  // Mc, q, chi1, chi2, Lambda1, Lambda2
 
 // Edge slots of the mixed likelihood kernel: in iteration i of a walker's
-// loop, lane l holds two bin edges, e_A = 63 i + l and e_B = 63 i + 32 + l,
-// each with the bin on its right (b = e; lane 31's e_B has no bin and is
-// the next iteration's e_A), as the two halves of one paired FP32 value.
-// Slot s = 32 i + l.
+// loop, lane l holds two neighbouring bin edges, e_A = 63 i + 2 l and
+// e_B = e_A + 1, each with the bin on its right (b = e; lane 31's e_B has no
+// bin and is the next iteration's e_A of lane 0), as the two halves of one
+// paired FP32 value.  Slot s = 32 i + l.
 constexpr int kSlotBins = 63;        // bins per iteration
 constexpr int kSlotBinFloats = 12;   // bin-table floats per slot and detector
 __host__ __device__ constexpr int slot_count(int n_bins) { return 32 * ((n_bins + kSlotBins - 1) / kSlotBins); }

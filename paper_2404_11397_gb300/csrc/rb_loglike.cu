@@ -23,14 +23,17 @@
 //   delta = rho (exp(-2 pi i x) - 1) + (rho - 1).
 //
 // Mapping: one warp per walker (persistent: each block takes a contiguous,
-// equal share of the walkers and its warps take them in turn);
-// lane l handles edge 31 c + l of chunk c and bin 31 c + l (lanes 0..30), so
-// each bin's right edge comes from the next lane by one shuffle and every
-// chunk overlaps the next by one edge.  Edge and bin tables live in shared
-// memory.  The adjoint reuses the same chunking: each lane's edge collects
-// U - V from its own bin and U + V from the bin on its left (shuffle up); an
-// edge shared by two chunks collects the two halves in two passes, which is
-// exact because the adjoint is linear in the per-edge cotangent.
+// equal share of the walkers and its warps take them in turn).  Float-float
+// path: in iteration i lane l holds edges 63 i + 2 l and 63 i + 2 l + 1 and
+// the bins on their right as the two halves of paired FP32 values (the slot
+// image, EventDev::slot32); FP64-phase path: lane l handles edge 31 c + l of
+// chunk c and bin 31 c + l (lanes 0..30).  Either way a bin's right edge is
+// at most one shuffle away and consecutive iterations overlap by one edge.
+// Edge and bin tables live in shared memory.  The adjoint reuses the same
+// mapping: each edge collects the cotangent from its own bin and from the
+// bin on its left; an edge shared by two iterations collects the two halves
+// in two passes, which is exact because the adjoint is linear in the per-edge
+// cotangent.
 #include <algorithm>
 #include <mutex>
 
@@ -365,14 +368,14 @@ __device__ __forceinline__ V det_edge(V y, DetState<V>& st, const V* bt, bool ha
   }
   return dldx;
 }
-// The same for the two edges of a slot (halves A and B: edges e_A = 63 i + l
-// and e_B = e_A + 32 of lane l) and one detector: the right neighbour of
-// lane l's edges is lane l + 1's, except that lane 31's e_A is followed by
-// lane 0's e_B; the bin on the left of lane 0's e_B is lane 31's A bin, and
-// lane 0's e_A collects no left bin in this iteration (it is lane 31's e_B
-// of the previous one).  Edges without a bin, and slots past the last
-// edge, have zero tables, so they add nothing.  vsum collects the bin terms
-// of log L, adj_x d log L / dy (times 1/2pi) for the basis adjoint.
+// The same for the two edges of a slot (halves A and B: edges e_A = 63 i + 2 l
+// and e_B = e_A + 1 of lane l) and one detector: e_A's right neighbour is
+// the lane's own e_B, e_B's is lane l + 1's e_A (one shuffle); e_B's left
+// bin is the lane's own A bin, e_A's is lane l - 1's B bin, none for lane 0
+// (its e_A is lane 31's e_B of the previous iteration, which collected it).
+// Edges without a bin, and slots past the last edge, have zero tables, so
+// they add nothing.  vsum collects the bin terms of log L, adj_x
+// d log L / dy (times 1/2pi) for the basis adjoint.
 // The bin's term in the coefficients of its edge values (q0 = {gmr, gpr},
 // q1 = {gmi, gpi}, q2 = {h, q} of the slot image): with d = delta at the
 // left edge and n at the right one,
@@ -392,10 +395,8 @@ __device__ __forceinline__ void det_edge_slot(float2 y, float4 rho, float4 sig, 
   const float2 em_r = mul(t2, sn), em_i = mul(t2, cs);  // e^{-2 pi i y} - 1
   const float2 dr = fma(rho_r, em_r, fma(neg(rho_i), em_i, sig_r));
   const float2 di = fma(rho_r, em_i, fma(rho_i, em_r, sig_i));
-  const int up = (lane + 1) & 31, dn = (lane + 31) & 31;
-  const float nrA = __shfl_sync(0xffffffffu, dr.x, up), nrB = __shfl_sync(0xffffffffu, dr.y, up);
-  const float niA = __shfl_sync(0xffffffffu, di.x, up), niB = __shfl_sync(0xffffffffu, di.y, up);
-  const float2 nr = make_float2(lane == 31 ? nrB : nrA, nrB), ni = make_float2(lane == 31 ? niB : niA, niB);
+  const float2 nr = make_float2(dr.y, __shfl_down_sync(0xffffffffu, dr.x, 1));
+  const float2 ni = make_float2(di.y, __shfl_down_sync(0xffffffffu, di.x, 1));
   // bt: gmr, gpr, gmi, gpi, h, q (the beta1 term vanishes for a ratio of
   // constant modulus)
   const float2 sr = add(dr, nr), si = add(di, ni);
@@ -408,10 +409,9 @@ __device__ __forceinline__ void det_edge_slot(float2 y, float4 rho, float4 sig, 
   if (GRAD) {
     float2 gr = fma(bt[4], sr, bt[0]), gi = fma(bt[4], si, bt[2]);  // own bin (edge on its left)
     const float2 pr = fma(bt[4], sr, bt[1]), pi = fma(bt[4], si, bt[3]);  // the bin's right edge
-    const float lrA = __shfl_sync(0xffffffffu, pr.x, dn), lrB = __shfl_sync(0xffffffffu, pr.y, dn);
-    const float liA = __shfl_sync(0xffffffffu, pi.x, dn), liB = __shfl_sync(0xffffffffu, pi.y, dn);
-    gr = add(gr, make_float2(lane == 0 ? 0.f : lrA, lane == 0 ? lrA : lrB));
-    gi = add(gi, make_float2(lane == 0 ? 0.f : liA, lane == 0 ? liA : liB));
+    const float lr = __shfl_up_sync(0xffffffffu, pr.y, 1), li = __shfl_up_sync(0xffffffffu, pi.y, 1);
+    gr = add(gr, make_float2(lane == 0 ? 0.f : lr, pr.x));
+    gi = add(gi, make_float2(lane == 0 ? 0.f : li, pi.x));
     const float2 rr = add(splat<float2>(1.f), dr);
     const float2 dldx = fma(gr, di, mul(neg(gi), rr));  // Im(conj(gbar) r); times 2 pi later
     adj_x = add(adj_x, dldx);

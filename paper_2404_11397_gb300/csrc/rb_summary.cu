@@ -172,7 +172,7 @@ __device__ void summary_epilogue(const SummaryOut& so, int b, int d0, int nd, in
         const double a0r = tv[0], a0i = tv[1], a1r = tv[2], a1i = tv[3], b0 = tv[4];
         const double val = f == 0 ? a0r - b0 - a1r : f == 1 ? a0r - b0 + a1r : f == 2 ? a0i - a1i
                          : f == 3 ? a0i + a1i : f == 4 ? -0.5 * b0 : -0.25 * b0;
-        const int it = b / kSlotBins, r = b - kSlotBins * it, h = r >= 32 ? 1 : 0, sl = 32 * it + r - 32 * h;
+        const int it = b / kSlotBins, r = b - kSlotBins * it, h = r & 1, sl = 32 * it + (r >> 1);
         const size_t NS = so.n_slots;
         float* sb = so.slot_bin32 + (size_t)d * kSlotBinFloats * NS;
         sb[((size_t)(f >> 1) * NS + sl) * 4 + (f & 1) * 2 + h] = (float)val;
@@ -326,10 +326,10 @@ __global__ void k_edge_tables(int64_t kmin, double T, int D, int B, int Ep, int 
     const f2x fp = f2x_from(f);
     t4[(size_t)(kEdgeQuads - 1) * Ep + e] = make_float4(fp.hi, fp.lo, 0.f, 0.f);
   }
-  // slot image, edge part: slot s = 32 i + l, half h holds edge 63 i + 32 h + l
+  // slot image, edge part: slot s = 32 i + l, half h holds edge 63 i + 2 l + h
   for (int t = tid; t < 2 * NS; t += nth) {
     const int sl = t >> 1, h = t & 1;
-    const int e = kSlotBins * (sl >> 5) + 32 * h + (sl & 31);
+    const int e = kSlotBins * (sl >> 5) + 2 * (sl & 31) + h;
     double g[kNBasis], f;
     edge_basis(kmin, T, E, edges, e, g, f);
     for (int k = 0; k <= kNBasis; ++k) {
