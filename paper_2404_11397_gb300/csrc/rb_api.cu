@@ -1077,6 +1077,7 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
   if ((err = cudaEventRecord(e.ev_fork, s)) != cudaSuccess || (err = cudaStreamWaitEvent(e.side, e.ev_fork, 0)) != cudaSuccess)
     return cuda_fail(err, "rebuild fork");
   int launches = 3;  // the two reference-value kernels and the summary kernel
+  cudaStream_t ref_stream = e.side;  // where the FP64 reference set runs (joined by ev_join)
   // the float-float reference values head the critical path of the fast
   // rebuild: enqueued first
   if (fast && (err = launch_ref_dd(e.d_theta_ref, e.ec, e.d_ref, e.d_sync, s)) != cudaSuccess)
@@ -1094,14 +1095,17 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
     if (ss) {
       // the walkers' set-up reads the float-float reference values and theta
       // only: on the forked stream, launched as soon as they exist so that its
-      // blocks are resident before the summary sums fill the GPU; the FP64
-      // set (off the critical path) follows it
+      // blocks are resident before the summary sums fill the GPU
       if ((err = cudaEventRecord(e.ev_ref, s)) != cudaSuccess || (err = cudaStreamWaitEvent(e.side, e.ev_ref, 0)) != cudaSuccess)
         return cuda_fail(err, "rebuild fork");
       if ((err = launch_setup(RB_MIXED, ss->theta, ss->W, e.ec, e.d_ref, ss->ws, nullptr, false, e.side)) != cudaSuccess)
         return cuda_fail(err, "set-up kernel");
       if ((err = cudaEventRecord(e.ev_setup, e.side)) != cudaSuccess) return cuda_fail(err, "rebuild join");
-      if ((err = launch_ref_values(e.d_theta_ref, e.ec, e.d_ref, e.side)) != cudaSuccess)
+      // the FP64 set (off the critical path) behind the tangents, which end
+      // early: behind the set-up it ran into the start of the likelihood
+      // kernel, whose blocks each need a whole SM, and held one back
+      ref_stream = ss->grad ? e.tanst : e.side;
+      if ((err = launch_ref_values(e.d_theta_ref, e.ec, e.d_ref, ref_stream)) != cudaSuccess)
         return cuda_fail(err, "reference values kernel");
       ++launches;
     }
@@ -1112,7 +1116,7 @@ int rebuild_event(EventEntry& e, const DataPtrs* in_opt, int mode, cudaStream_t 
     if ((err = launch_ref_values(e.d_theta_ref, e.ec, e.d_ref, e.h0_valid ? e.side : s)) != cudaSuccess)
       return cuda_fail(err, "reference values kernel");
   }
-  if ((err = cudaEventRecord(e.ev_join, e.side)) != cudaSuccess) return cuda_fail(err, "rebuild join");
+  if ((err = cudaEventRecord(e.ev_join, ref_stream)) != cudaSuccess) return cuda_fail(err, "rebuild join");
   if (fast) {
     // with the walkers' set-up on the forked stream (rebuild + batch), the
     // chunk records are a launch of their own that overlaps the set-up (and
