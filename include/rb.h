@@ -71,6 +71,13 @@ extern "C" {
 #define RB_MIXED 0          /* phase in float-float (FP32 pairs), trig/ratio/contraction FP32, sums FP64 */
 #define RB_FP64 1           /* everything in native FP64 (comparison path) */
 #define RB_MIXED_F64PHASE 2 /* phase accumulated in native FP64, rest as RB_MIXED */
+/* RB_MIXED sums each walker's phase from FP32 pairs with exact high parts
+ * scaled to the walker's largest phase term |dc_k g_k(f)|, |dtau_d f| over the
+ * band.  A walker with such a term beyond 2^18 turns (~1.6e6 rad: far outside
+ * where relative binning holds, the ratio to the fiducial waveform then
+ * oscillating within bins) is not evaluated: its log L and gradient are NaN
+ * (and the MALA step rejects it).  RB_FP64 and RB_MIXED_F64PHASE have no such
+ * limit. */
 
 #define RB_NPAR 13
 #define RB_MAX_DET 3

@@ -518,6 +518,13 @@ __device__ __forceinline__ V frac(V hi, V lo) {
   return add(r, lo);
 }
 
+// x with its whole turns removed (|x| < 2^22).
+template <class V>
+__device__ __forceinline__ V frac1(V x) {
+  const V m = splat<V>(12582912.0f);
+  return sub(x, sub(add(x, m), m));
+}
+
 // sin(pi y), cos(pi y) for |y| <= 1/2 (the polynomials of sincos_pi_half).
 template <class V>
 __device__ __forceinline__ void sincos_half(V y, V& s, V& c) {

@@ -36,6 +36,7 @@
 // cotangent.
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "rb_internal.cuh"
 
@@ -520,6 +521,7 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
     pv::DetState<float2> P;  // detectors 0, 1: accumulators (constants come from wc)
     pv::DetState<float> S;   // detector ds
     int valid;
+    unsigned walker_ex = 0;  // float-float path: exponent field of the walker's phase-term bound
     if (!PHASE64) {
       valid = slot->rec[buf].valid;
 #pragma unroll
@@ -558,6 +560,7 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) mag = fmaxf(mag, __shfl_xor_sync(0xffffffffu, mag, o));
       const unsigned ex = min(max((__float_as_uint(mag) >> 23) & 0xffu, 64u), 250u);  // mag < 2^(ex - 126)
+      walker_ex = ex;
       if (lane == 0) {
         const float m = __uint_as_float(((ex + 4u) << 23) | 0x400000u);  // 1.5 * 2^(ex - 123)
         slot->dup[kNBasis + 3 * kMaxDet] = make_float4(m, m, m, m);
@@ -603,6 +606,18 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
       }
       continue;
     }
+    if (!PHASE64 && walker_ex > 126u + 18u) {
+      // a phase term beyond 2^18 turns (~1.6e6 rad): past the range of the
+      // float-pair phase sums' whole-turn reductions; not evaluated (NaN,
+      // rejected by the MALA step)
+      if (MALA) {
+        mala_finish(a.mala, w, lane, -INFINITY, 0.0);
+      } else {
+        if (lane == 0) a.logl[w] = __longlong_as_double(0x7ff8000000000000ll);
+        if (GRAD && lane < kNPar) a.grad[w * kNPar + lane] = __longlong_as_double(0x7ff8000000000000ll);
+      }
+      continue;
+    }
 
     // float-pair accumulators: for walkers far from the fiducial point the
     // per-bin terms add up to about -log L(theta_ref), so a single float would
@@ -620,6 +635,12 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
       for (int k = 0; k < kNBasis; ++k) adj_c[k] = make_float2(0.f, 0.f);
 #pragma unroll
       for (int d = 0; d < D; ++d) adj_tau[d] = adj_rr[d] = adj_ri[d] = make_float2(0.f, 0.f);
+      // walkers whose phase terms reach beyond 2^12 turns take a second
+      // whole-turn reduction of the phase (the low sum can then carry it past
+      // the half-angle polynomials' range): a second copy of the loop, so
+      // that the others pay nothing for it
+      auto slot_loop = [&](auto wide_c) {
+      constexpr bool WIDE = decltype(wide_c)::value;
       for (int s0 = 0; s0 < NS; s0 += 32) {
         const int sl = RB_IDX(s0 + lane, NS, 102);
         // detector-independent phase sum_k dc_k g_k(f_e) / 2pi [turns] of the
@@ -643,7 +664,8 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
           const float4 tt = lds4(wd + kNBasis + 3 * d);
           float2 yh = sh, yl = sl_lo;
           pv::split_acc(make_float2(tt.x, tt.y), make_float2(tt.z, tt.w), fe, fe_lo, m2, yh, yl);
-          const float2 y = pv::frac(yh, yl);
+          float2 y = pv::frac(yh, yl);
+          if constexpr (WIDE) y = pv::frac1(y);
           const float4* sb = reinterpret_cast<const float4*>(sbin + (size_t)d * kSlotBinFloats * NS);
           const float4 q0 = sb[sl], q1 = sb[NS + sl], q2 = sb[2 * NS + sl];
           const float2 bt[6] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y),
@@ -660,6 +682,9 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
           for (int k = 0; k < kNBasis; ++k) adj_c[k] = pv::fma(adj_x, g2[2 * (k * NS + sl)], adj_c[k]);
         }
       }
+      };
+      if (walker_ex > 126u + 12u) slot_loop(std::true_type{});
+      else slot_loop(std::false_type{});
       lh = acc.x;
       ll = acc_lo.x;
       ff_add(lh, ll, acc.y, acc_lo.y);

@@ -235,6 +235,38 @@ def test_gradient_prior_draws(rb, c2, mode):
     assert n_floor <= 16, n_floor
 
 
+@pytest.mark.parametrize("mode", ("mixed", "mixed_f64phase"))
+def test_wide_phase_walkers(rb, c1, c2, mode):
+    """Walkers far from the fiducial point (chirp mass x 0.5 ... 0.1: phase terms of
+    2^13 to 2^17 turns), which take the mixed kernel's second whole-turn reduction:
+    log L within the prior-draw bound, gradients within 1e-4 norm-wise."""
+    for c in (c1, c2):
+        th = np.repeat(c.ev["theta_inj"][None, :], 5, 0)
+        th[:, 0] *= np.array([0.5, 0.4, 0.3, 0.2, 0.1])
+        L, G = rb.loglike_grad(c.event, torch.tensor(th, device="cuda"), mode=mode)
+        ref, dh, hh = _terms(c.ev, c.s, th)
+        assert np.all(np.abs(L.cpu().numpy() - ref) <= _tol(mode, dh, hh)), (mode, np.abs(L.cpu().numpy() - ref))
+        _, ref_G = oracle.loglike_rb(c.ev, c.s, th, grad=True)
+        nw = np.max(np.abs(G.cpu().numpy() - ref_G), axis=1) / np.max(np.abs(ref_G), axis=1)
+        assert np.all(nw <= 1e-4), (mode, nw)
+
+
+def test_phase_terms_beyond_range_are_nan(rb, c1):
+    """A walker whose phase terms reach past 2^18 turns (chirp mass x 0.05) is not
+    evaluated by the float-pair phase sums: NaN log L and gradient in RB_MIXED; the
+    FP64 path still evaluates it."""
+    th = c1.ev["theta_inj"][None, :].copy()
+    th[0, 0] *= 0.05
+    th = np.concatenate([th, c1.ev["theta_inj"][None, :]])
+    L, G = rb.loglike_grad(c1.event, torch.tensor(th, device="cuda"), mode="mixed")
+    L, G = L.cpu().numpy(), G.cpu().numpy()
+    assert np.isnan(L[0]) and np.all(np.isnan(G[0]))
+    assert np.isfinite(L[1]) and np.all(np.isfinite(G[1]))
+    L64, _ = rb.loglike_grad(c1.event, torch.tensor(th, device="cuda"), mode="fp64")
+    ref = oracle.loglike_rb(c1.ev, c1.s, th)
+    assert np.all(np.abs(L64.cpu().numpy() - ref) <= 1e-8 + 1e-9 * np.abs(ref))
+
+
 def test_c3_box_walkers_with_gradient(rb, c1):
     """C3: C1's event, 4096 walkers in the +-1 % box, log L + gradient in one launch;
     every log L within 1e-3 absolute, 64 gradients against the oracle's."""
