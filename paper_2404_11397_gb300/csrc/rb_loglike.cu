@@ -88,6 +88,9 @@ struct __align__(16) WarpSlot {
   // {sig_r, sig_r, sig_i, sig_i}, and last the walker's rounding constant m
   // of the phase sums (split_acc) in all four
   float4 dup[kNBasis + 3 * kMaxDet + 1];
+  // per lane: the bound on |g_k| or f that the lane's phase term takes in the
+  // record expansion (constant over the launch)
+  float lane_gmax[32];
 };
 static_assert(sizeof(WalkerMixed) % 16 == 0, "record copied in 16-byte pieces");
 static_assert(sizeof(WalkerTan<float>) <= kTanBytes && sizeof(WalkerTan<float>) % 8 == 0, "tangent buffer");
@@ -510,6 +513,16 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
   __syncthreads();
   const double base_logl = event_base_value(ev, base_read);
 
+  // the bound on |g_k| or f that this lane's phase term takes (the record
+  // expansion below: lane k < kNBasis basis k, lane kNBasis + 3 d detector d's
+  // delay), read once into the warp's slot: indexed by lane, a constant-bank
+  // load serialises
+  if (!PHASE64) {
+    const int j = lane - kNBasis;
+    const int gk = lane < kNBasis ? lane : (j < 3 * D && j % 3 == 0 ? kNBasis : -1);
+    slot->lane_gmax[lane] = gk >= 0 ? ev.gmax[gk] : 0.f;
+  }
+
   int buf = 0;
   for (int64_t w = warp0; w < w_end; w += nwarps, buf ^= 1) {
     cp_async_wait_all();  // this walker's record and tangents
@@ -534,11 +547,10 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
       float mag = 0.f;  // the lane's bound on |its phase term| [turns]
       if (lane < kNBasis + 3 * D) {
         const float* f = reinterpret_cast<const float*>(wc);
-        int iu, iv, gk = -1;
+        int iu, iv;
         if (lane < kNBasis) {
           iu = wm_dc_hi(lane);
           iv = wm_dc_lo(lane);
-          gk = lane;
         } else {
           const int j = lane - kNBasis, d = j / 3, m = j - 3 * d;
           if (d == ds) {
@@ -547,11 +559,10 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
             iu = (m == 0 ? kWmTauPair : (m == 1 ? kWmRhoPair : kWmSigPair)) + d;
           }
           iv = iu + (d == ds ? 1 : 2);
-          if (m == 0) gk = kNBasis;
         }
         const float u = f[iu], v = f[iv];
         slot->dup[lane] = make_float4(u, u, v, v);
-        if (gk >= 0) mag = fabsf(u) * ev.gmax[gk];
+        mag = fabsf(u) * slot->lane_gmax[lane];
       }
       // the walker's rounding constant m = 1.5 * 2^23 q with q = 2^-20 of a
       // power of two above every phase term (at least 2^-62 turns): then each
