@@ -48,9 +48,10 @@ namespace rb {
 constexpr int kThreads = RB_MIXED_THREADS;  // threads per block of the mixed likelihood kernel
 constexpr unsigned kFull = 0xffffffffu;
 // The current walker's constants sit in shared memory (read by broadcast
-// loads in every chunk instead of held in registers), as the set-up wrote
+// loads in every iteration instead of held in registers): as the set-up wrote
 // them (WalkerMixed: float4 quads, detectors 0 and 1 paired, detector D - 1
-// alone when D is odd).
+// alone when D is odd), and for the float-float loop expanded into {x, x, y, y}
+// quads (WarpSlot::dup).
 
 // Shared-memory load that the compiler may not hoist out of a loop.
 __device__ __forceinline__ float4 lds4(const float4* p) {
