@@ -184,10 +184,11 @@ struct EventDev {
   const double* base_logl;  // device: sum_d (Re sum_b A0 - sum_b B0 / 2) = log L(theta_ref) (event_base_logl)
   const SummarySync* sync;  // where the fast build leaves it
   const double* share;      // [D][B] the bins' shares
-  // float image copied to shared memory by the mixed kernels, laid out for
-  // 16-byte loads (lane l reads edge / bin c0 + l: consecutive 16 B, no bank
-  // conflicts) whose halves are ready operands of the paired FP32
-  // instructions:
+  // float image, laid out for 16-byte loads (lane l reads edge / bin c0 + l:
+  // consecutive 16 B, no bank conflicts) whose halves are ready operands of
+  // the paired FP32 instructions; the FP64-phase mixed kernel copies its bin
+  // part to shared memory (the float-float kernel reads the slot image
+  // below, and no kernel reads the edge part, written at event creation):
   //   edge part, float4 [kEdgeQuads][Ep]: quad q < 5 holds
   //     {g_hi[2q], g_hi[2q+1], g_lo[2q], g_lo[2q+1]}  (g_k(f_e)/2pi as float pairs),
   //     quad 5 holds {f_hi, f_lo, 0, 0};
