@@ -390,8 +390,8 @@ __device__ __forceinline__ V det_edge(V y, DetState<V>& st, const V* bt, bool ha
 //   (gmr + h sr, gmi + h si) and (gpr + h sr, gpi + h si).
 template <bool GRAD>
 __device__ __forceinline__ void det_edge_slot(float2 y, float4 rho, float4 sig, const float2 (&bt)[6], int lane,
-                                              float2 fe, float2& vsum, float2& adj_x, float2& adj_tau, float2& adj_rr,
-                                              float2& adj_ri) {
+                                              float2 fe, float2& vsum, float2& adj_x, float& adj_tau, float& adj_rr,
+                                              float& adj_ri) {
   const float2 rho_r = make_float2(rho.x, rho.y), rho_i = make_float2(rho.z, rho.w);
   const float2 sig_r = make_float2(sig.x, sig.y), sig_i = make_float2(sig.z, sig.w);
   float2 sn, cs;
@@ -420,10 +420,11 @@ __device__ __forceinline__ void det_edge_slot(float2 y, float4 rho, float4 sig, 
     const float2 rr = add(splat<float2>(1.f), dr);
     const float2 dldx = fma(gr, di, mul(neg(gi), rr));  // Im(conj(gbar) r); times 2 pi later
     adj_x = add(adj_x, dldx);
-    adj_tau = fma(dldx, fe, adj_tau);
+    adj_tau = __fmaf_rn(dldx.x, fe.x, __fmaf_rn(dldx.y, fe.y, adj_tau));
     const float2 Er = add(splat<float2>(1.f), em_r);  // gbar_rho += gbar conj(E)
-    adj_rr = fma(gr, Er, fma(gi, em_i, adj_rr));
-    adj_ri = fma(gi, Er, fma(neg(gr), em_i, adj_ri));
+    const float2 r2 = fma(gr, Er, mul(gi, em_i)), i2 = fma(gi, Er, mul(neg(gr), em_i));
+    adj_rr = __fadd_rn(adj_rr, __fadd_rn(r2.x, r2.y));
+    adj_ri = __fadd_rn(adj_ri, __fadd_rn(i2.x, i2.y));
   }
 }
 }  // namespace pv
@@ -642,11 +643,14 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
       const int NS = ev.n_slots;
       const float4* const wd = slot->dup;
       float2 acc = make_float2(0.f, 0.f), acc_lo = acc;
-      float2 adj_c[kNBasis], adj_tau[D], adj_rr[D], adj_ri[D];
+      // the adjoint sums of a lane's two edges in one float each (as pairs,
+      // the extra registers spilled)
+      float adj_c[kNBasis];
+      float adj_tau[D], adj_rr[D], adj_ri[D];
 #pragma unroll
-      for (int k = 0; k < kNBasis; ++k) adj_c[k] = make_float2(0.f, 0.f);
+      for (int k = 0; k < kNBasis; ++k) adj_c[k] = 0.f;
 #pragma unroll
-      for (int d = 0; d < D; ++d) adj_tau[d] = adj_rr[d] = adj_ri[d] = make_float2(0.f, 0.f);
+      for (int d = 0; d < D; ++d) adj_tau[d] = adj_rr[d] = adj_ri[d] = 0.f;
       // walkers whose phase terms reach beyond 2^12 turns take a second
       // whole-turn reduction of the phase (the low sum can then carry it past
       // the half-angle polynomials' range): a second copy of the loop, so
@@ -691,7 +695,10 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
           // about as busy as the FMA pipe in this loop)
           const float2* g2 = reinterpret_cast<const float2*>(g4);
 #pragma unroll
-          for (int k = 0; k < kNBasis; ++k) adj_c[k] = pv::fma(adj_x, g2[2 * (k * NS + sl)], adj_c[k]);
+          for (int k = 0; k < kNBasis; ++k) {
+            const float2 g = g2[2 * (k * NS + sl)];
+            adj_c[k] = __fmaf_rn(adj_x.x, g.x, __fmaf_rn(adj_x.y, g.y, adj_c[k]));
+          }
         }
       }
       };
@@ -701,12 +708,12 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
       ll = acc_lo.x;
       ff_add(lh, ll, acc.y, acc_lo.y);
 #pragma unroll
-      for (int k = 0; k < kNBasis; ++k) v[k] = __fadd_rn(adj_c[k].x, adj_c[k].y);
+      for (int k = 0; k < kNBasis; ++k) v[k] = adj_c[k];
 #pragma unroll
       for (int d = 0; d < D; ++d) {
-        v[kNBasis + d] = __fadd_rn(adj_tau[d].x, adj_tau[d].y);
-        v[kNBasis + D + d] = __fadd_rn(adj_rr[d].x, adj_rr[d].y);
-        v[kNBasis + 2 * D + d] = __fadd_rn(adj_ri[d].x, adj_ri[d].y);
+        v[kNBasis + d] = adj_tau[d];
+        v[kNBasis + D + d] = adj_rr[d];
+        v[kNBasis + 2 * D + d] = adj_ri[d];
       }
     } else {
       // FP64 phase: one edge per lane, lane l of chunk c at edge 31 c + l
