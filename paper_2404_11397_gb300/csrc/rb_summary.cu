@@ -807,8 +807,12 @@ static_assert(kPartPoints % kSumFastThreads == 0, "parts are whole rounds of the
 // nearly cancels within a bin, a float pair); block sums are float pairs in a
 // fixed order; the parts of a bin are added in index order by the last of
 // them to finish, which then runs the FP64 epilogue.
+// Registers: with the records copied (the rebuild + batch step) the kernel
+// is held to 64 per thread, so that six blocks still fit on an SM that also
+// holds a block of the walkers' set-up, which runs beside it there: at 78,
+// such SMs took five and the C2 build (868 parts) needed a second wave.
 template <int ND, bool INBLOCK>
-__global__ void __launch_bounds__(kSumFastThreads, 6)
+__global__ void __launch_bounds__(kSumFastThreads, INBLOCK ? 6 : 8)
     k_summary_fast(const float2* __restrict__ w32, const float* __restrict__ is32, const int* __restrict__ exps,
                    int N, const float* __restrict__ q, double T, float invT_hi, float invT_lo, int B, int D,
                    const int64_t* __restrict__ edges, const RefValues* __restrict__ ref, SummaryOut so, int p_off) {
