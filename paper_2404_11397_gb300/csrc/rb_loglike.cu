@@ -272,10 +272,10 @@ __device__ __forceinline__ double chain_rule(int j, int n_det, const T* adj_c, c
 
 // The same chain rule for the mixed kernel, with the tangents in shared
 // memory: every lane runs one instruction stream (the lane's tangent entries
-// picked by index and select, no divergent branches).
+// picked by index and select, no divergent branches).  G_d = conj(gbar_rho_d)
+// rho_d, the prefactor's adjoint in the form d log L = Re(G_d dln rho_d).
 template <int D>
-__device__ __forceinline__ float chain_rule_lanes(int j, const float* adj_c, const float* adj_tau,
-                                                  const float (*adj_rho)[2], const float (*rho)[2],
+__device__ __forceinline__ float chain_rule_lanes(int j, const float* adj_c, const float* adj_tau, const float (*G)[2],
                                                   const WalkerTan<float>& tn) {
   const float* t = reinterpret_cast<const float*>(&tn);
   constexpr int oDc = offsetof(WalkerTan<float>, dc) / 4, oPhi = offsetof(WalkerTan<float>, dphi0) / 4;
@@ -298,11 +298,9 @@ __device__ __forceinline__ float chain_rule_lanes(int j, const float* adj_c, con
   for (int d = 0; d < D; ++d) {
     const float td = t[oDtd + 2 * d + jr];
     g = fmaf(adj_tau[d], radec ? td : (j == 7 ? 1.f : 0.f), g);
-    const float Gr = adj_rho[d][0] * rho[d][0] + adj_rho[d][1] * rho[d][1];
-    const float Gi = adj_rho[d][0] * rho[d][1] - adj_rho[d][1] * rho[d][0];
     const float pr = t[oLnP + 8 * d + 2 * je], pi = t[oLnP + 8 * d + 2 * je + 1];
     const float lr = ext ? pr : lr_own, li = ext ? pi : li_own;
-    g += Gr * lr - Gi * li;
+    g += G[d][0] * lr - G[d][1] * li;  // Re(G_d dln rho_d)
   }
   return g;
 }
@@ -380,7 +378,8 @@ __device__ __forceinline__ V det_edge(V y, DetState<V>& st, const V* bt, bool ha
 // (its e_A is lane 31's e_B of the previous iteration, which collected it).
 // Edges without a bin, and slots past the last edge, have zero tables, so
 // they add nothing.  vsum collects the bin terms of log L, adj_x
-// d log L / dy (times 1/2pi) for the basis adjoint.
+// d log L / dy (times 1/2pi) for the basis adjoint, (adj_rr, adj_ri) the sum
+// of conj(gbar) r over the edges (the prefactor's adjoint times rho: G_d).
 // The bin's term in the coefficients of its edge values (q0 = {gmr, gpr},
 // q1 = {gmi, gpi}, q2 = {h, q} of the slot image): with d = delta at the
 // left edge and n at the right one,
@@ -421,10 +420,10 @@ __device__ __forceinline__ void det_edge_slot(float2 y, float4 rho, float4 sig, 
     const float2 dldx = fma(gr, di, mul(neg(gi), rr));  // Im(conj(gbar) r); times 2 pi later
     adj_x = add(adj_x, dldx);
     adj_tau = __fmaf_rn(dldx.x, fe.x, __fmaf_rn(dldx.y, fe.y, adj_tau));
-    const float2 Er = add(splat<float2>(1.f), em_r);  // gbar_rho += gbar conj(E)
-    const float2 r2 = fma(gr, Er, mul(gi, em_i)), i2 = fma(gi, Er, mul(neg(gr), em_i));
-    adj_rr = __fadd_rn(adj_rr, __fadd_rn(r2.x, r2.y));
-    adj_ri = __fadd_rn(adj_ri, __fadd_rn(i2.x, i2.y));
+    // the prefactor: r = rho E, so conj(gbar_rho) rho = sum conj(gbar) r, whose
+    // imaginary part is the sum of dldx
+    adj_rr = __fmaf_rn(gr.x, rr.x, __fmaf_rn(gr.y, rr.y, __fmaf_rn(gi.x, di.x, __fmaf_rn(gi.y, di.y, adj_rr))));
+    adj_ri = __fadd_rn(adj_ri, __fadd_rn(dldx.x, dldx.y));
   }
 }
 }  // namespace pv
@@ -810,17 +809,24 @@ __global__ void __launch_bounds__(kThreads) k_rb_mixed(LaunchArgs a) {
         ar[d][0] = d < D ? slot->red[kNBasis + D + d] : 0.f;
         ar[d][1] = d < D ? slot->red[kNBasis + 2 * D + d] : 0.f;
       }
-      float rho[kMaxDet][2];
-      {
+      if constexpr (PHASE64) {
+        // this path sums gbar conj(E) = gbar_rho: G_d = conj(gbar_rho) rho
+        float rho[kMaxDet][2];
         const float4 r01 = lds4(wc + 6), rs = lds4(wc + 9);
         rho[0][0] = r01.x; rho[1][0] = r01.y; rho[0][1] = r01.z; rho[1][1] = r01.w;
         if (ds >= 0) { rho[dss][0] = rs.x; rho[dss][1] = rs.y; }
         if (D < kMaxDet) rho[kMaxDet - 1][0] = rho[kMaxDet - 1][1] = 0.f;
+#pragma unroll
+        for (int d = 0; d < kMaxDet; ++d) {
+          const float a_r = ar[d][0], a_i = ar[d][1];
+          ar[d][0] = a_r * rho[d][0] + a_i * rho[d][1];
+          ar[d][1] = a_r * rho[d][1] - a_i * rho[d][0];
+        }
       }
       double g = 0.0;
       if (lane < kNPar) {
         const WalkerTan<float>& tn = *reinterpret_cast<const WalkerTan<float>*>(slot->tan[buf]);  // prefetched
-        g = f2d_int(chain_rule_lanes<D>(lane, ac, at, ar, rho, tn));
+        g = f2d_int(chain_rule_lanes<D>(lane, ac, at, ar, tn));
       }
       if (MALA) mala_finish(a.mala, w, lane, logl, g);
       else if (lane < kNPar) a.grad[RB_IDX(w * kNPar + lane, a.W * kNPar, 106)] = g;
