@@ -209,7 +209,7 @@ def impl_flops_per_walker(D: int, B: int, grad: bool) -> int:
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the main kernel on this workload, from an ncu capture of this kernel version
 # (None once the kernel changes and until it is captured again).
-MAIN_KERNEL_TRAFFIC_BYTES = None
+MAIN_KERNEL_TRAFFIC_BYTES = 2391552
 
 
 # Algorithmic FP32 flops of the full-grid sum per (walker, grid point) with 3
