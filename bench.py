@@ -188,10 +188,8 @@ def algorithmic_work(D: int, B: int, grad: bool) -> dict:
     return {"fp64": fp64, "fp32": fp32, "sfu_sincos": sfu, "total": fp64 + fp32 + sfu}
 
 
-# This implementation's own FP32 flop count of the same kernel (the float-float
-# emulation of the FP64-class work included): 150 per edge for the phase dot
-# product, 70 per (edge, detector) for delay, reduction, sin/cos and ratio, 25
-# per (bin, detector) for the contraction; the gradient adds 16 D B + 17 D E + 20 E.
+# This implementation's own FP32 flop count of the same kernel (the float-pair
+# emulation of the FP64-class work included), reported beside the algorithmic one.
 def impl_flops_per_walker(D: int, B: int, grad: bool) -> int:
     # FP32 flops the mixed kernel spends per walker (FMA = 2): per edge the
     # float-pair phase sum (11 per basis term: high part rounded to the
